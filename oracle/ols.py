@@ -1,0 +1,86 @@
+"""Per-marker least squares: the linear association test the scan computes (Section 2.2).
+
+Test infrastructure (see the package docstring).
+
+The paper states its test as a correlation of standardised genotypes with the
+residualised, standardised panel (Eq. 2) turned into t (Eq. 3), "equivalent to a
+correlation-based linear association test". The test it stands for is the OLS fit
+of each phenotype on [1, C, g] per marker; `ols_direct` solves exactly that, and
+`ols_projected` computes the same numbers the way Eq. 1-3 do (project, correlate,
+convert), with the genotype projected on Q as well (Frisch-Waugh-Lovell).
+
+Reading: degrees of freedom df = N - q - 1 (q = rank [1, C]); with an intercept
+only, q = 1 and df = N - 2 as in Eq. 3.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# A marker is untestable when it has no observed call, is constant, or is (up to
+# this relative residual) inside the covariate span.
+MARKER_TOL = 1e-10
+
+
+def ols_direct(X: np.ndarray, g: np.ndarray, Y: np.ndarray):
+    """OLS of every column of Y on W = [X, g_j] for each marker j, by QR of W.
+
+    X: [N][q] full column rank; g: [M][N] imputed genotypes; Y: [N][P].
+    Returns (beta, se, t) each [M][P] (the coefficient of g_j, its standard error
+    sqrt(RSS/df * [(W^T W)^-1]_gg), and beta/se) and df. Untestable markers give NaN.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    g = np.atleast_2d(np.asarray(g, dtype=np.float64))
+    N, q = X.shape
+    M, P = g.shape[0], Y.shape[1]
+    df = N - q - 1
+    beta = np.full((M, P), np.nan)
+    se = np.full((M, P), np.nan)
+    for j in range(M):
+        if not np.all(np.isfinite(g[j])):
+            continue
+        W = np.column_stack([X, g[j]])
+        Qw, Rw = np.linalg.qr(W)
+        gc = g[j] - g[j].mean()
+        rgg = abs(Rw[-1, -1])
+        if not np.isfinite(rgg) or np.linalg.norm(gc) == 0.0 or rgg <= MARKER_TOL ** 0.5 * np.linalg.norm(gc):
+            continue
+        coef = np.linalg.solve(Rw, Qw.T @ Y)
+        resid = Y - W @ coef
+        rss = (resid * resid).sum(axis=0)
+        beta[j] = coef[-1]
+        se[j] = np.sqrt(rss / df) / rgg
+    with np.errstate(invalid="ignore", divide="ignore"):
+        t = beta / se
+    return beta, se, t, df
+
+
+def ols_projected(Q: np.ndarray, g: np.ndarray, Yres: np.ndarray):
+    """Eq. 2 and Eq. 3 with the genotype projected on Q too (FWL form of the same OLS).
+
+    Q: [N][q] orthonormal basis of [1, C]; g: [M][N] imputed genotypes; Yres: [N][P]
+    residualised panel (Eq. 1). r = g_res . y_res / (|g_res| |y_res|),
+    t = r sqrt(df / (1 - r^2)), beta = g_res . y_res / |g_res|^2, se = |beta / t|.
+    Returns (r, beta, se, t, df, gres2 [M] = |g_res|^2).
+    """
+    Q = np.asarray(Q, dtype=np.float64)
+    g = np.atleast_2d(np.asarray(g, dtype=np.float64))
+    Yres = np.asarray(Yres, dtype=np.float64)
+    N, q = Q.shape
+    df = N - q - 1
+    gc = g - g.mean(axis=1, keepdims=True)
+    gres = gc - (gc @ Q) @ Q.T
+    gres2 = (gres * gres).sum(axis=1)
+    gc2 = (gc * gc).sum(axis=1)
+    bad = ~(gres2 > MARKER_TOL * gc2)
+    ynorm = np.linalg.norm(Yres, axis=0)
+    num = gres @ Yres
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r = num / np.sqrt(gres2)[:, None] / ynorm[None, :]
+        r = np.clip(r, -1.0, 1.0)
+        t = r * np.sqrt(df / ((1.0 - r) * (1.0 + r)))
+        beta = num / gres2[:, None]
+        se = ynorm[None, :] * np.sqrt((1.0 - r) * (1.0 + r) / df) / np.sqrt(gres2)[:, None]
+    for a in (r, beta, se, t):
+        a[bad] = np.nan
+    return r, beta, se, t, df, np.where(bad, np.nan, gres2)
