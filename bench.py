@@ -1,0 +1,383 @@
+"""Benchmark of the genome scan: SNP-phenotype tests/s at N = 23,000 samples, P = 20,480 phenotypes.
+
+One step = the whole scan path (decode with mean imputation, projection on the covariate
+basis, marker norms, the contraction with the standardised panel and the fused statistics
+epilogue with hit collection and per-phenotype best) over one block of 65,536 8-bit-dosage
+markers, the streaming unit of the 8.9M-marker workload. Inputs are seeded synthetic data of
+the paper's shape (the paper's cohort is not available). The blocks (1.5 GB each) and the
+panel (1.9 GB of bf16 operands) are far larger than the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. --impl reference times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SNP-phenotype tests/s at N=23k,P=20,480: split-precision vs FP32, % roofline"
+UNIT = "SNP-phenotype tests/s"
+WORKLOAD = "n23000_m8900000_p20480_c20_u8"
+THR = 7.30103  # -log10(5e-8)
+RESIDENT = 4   # distinct genotype blocks kept in HBM and cycled
+
+
+def _args():
+    a = argparse.ArgumentParser()
+    a.add_argument("--gpus", type=int, default=1)
+    a.add_argument("--steps", type=int, default=20)
+    a.add_argument("--warmup", type=int, default=3)
+    a.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    a.add_argument("--fp32-steps", type=int, default=2)
+    a.add_argument("--e2e-steps", type=int, default=8)
+    a.add_argument("--cpu-seconds", type=float, default=15.0)
+    a.add_argument("--no-cpu-baseline", action="store_true")
+    return a.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def _max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------- CPU oracle timing
+
+def _oracle_sample(Yt, cov_t, G, seconds: float):
+    """Time the FP64 oracle (projected form, with p-values) on groups of 16 markers of the
+    benchmark block against the full phenotype panel until `seconds` have passed."""
+    import numpy as np
+
+    import oracle
+
+    ref_panel = oracle.prepare_panel(Yt.numpy().T.astype(np.float64), cov_t.numpy().T)
+    G = G.numpy()
+    done, t_total = 0, 0.0
+    while t_total < seconds and done + 16 <= G.shape[0]:
+        t0 = time.perf_counter()
+        oracle.scan(G[done:done + 16], "u8", ref_panel, mode="projected")
+        t_total += time.perf_counter() - t0
+        done += 16
+    return done, t_total, Yt.shape[0]
+
+
+def _reference(args, dist, rank, ws):
+    """--impl reference: the FP64 CPU oracle, rank 0 only."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synth
+
+    w = synth.WORKLOADS[WORKLOAD]
+    pan = synth.make_panel(w, device="cpu", planted_blocks=1)
+    ref_panel = oracle.prepare_panel(pan["Yt"].numpy().T.astype(np.float64), pan["cov_t"].numpy().T)
+    per_step = 8
+    f = synth.maf(w.seed, 0, per_step * (args.steps + args.warmup))
+    G = synth.dosage_bytes(w.seed, 0, f, w.N).numpy()
+    for s in range(args.warmup):
+        oracle.scan(G[s * per_step:(s + 1) * per_step], "u8", ref_panel, mode="projected")
+    t0 = time.perf_counter()
+    for s in range(args.warmup, args.warmup + args.steps):
+        oracle.scan(G[s * per_step:(s + 1) * per_step], "u8", ref_panel, mode="projected")
+    dt = time.perf_counter() - t0
+    tests = per_step * w.P * args.steps
+    value = tests / dt
+    cores = os.cpu_count()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} markers x {w.P} phenotypes per step, FP64 projected "
+                                   "OLS with p-values (NumPy; BLAS threads on all cores)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def _config(w):
+    return {"workload": f"{WORKLOAD}: N={w.N} samples, {w.block}-marker blocks of 8-bit dosages "
+                        f"(M={w.M} in the whole scan), P={w.P} phenotypes, C=20 covariate columns "
+                        "(intercept + 19), hits at -log10 p >= 7.30103",
+            "N": w.N, "P": w.P, "C": 20, "block_markers": w.block, "encoding": "u8 dosage",
+            "precision": "split-bf16 (A exact bf16, panel bf16 hi+lo, fp32 accumulate)",
+            "l2": f"inputs larger than L2: {RESIDENT} resident 1.5 GB blocks cycled, 1.9 GB panel"}
+
+
+# ------------------------------------------------------------------------- ours
+
+def _ours(args, dist, rank, ws):
+    import numpy as np
+    import torch
+
+    import paper_2604_21095_gb300 as tg
+    import synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tg.build()
+    w = synth.WORKLOADS[WORKLOAD]
+    ctx = tg.tg_create(local)
+    stream = torch.cuda.current_stream(dev)
+
+    # panel (prepared once, timed separately)
+    pan = synth.make_panel(w, device=dev, planted_blocks=RESIDENT)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    panel = tg.tg_prepare_panel(ctx, pan["Yt"], w.N, w.P, pan["cov_t"], stream=stream)
+    prepare_ms = 1000 * (time.perf_counter() - t0)
+    want_cpu = rank == 0 and ws == 1 and not args.no_cpu_baseline
+    cpu_inputs = (pan["Yt"].cpu(), pan["cov_t"].cpu()) if want_cpu else None
+    del pan
+
+    # resident blocks: rank r scans blocks r, r + ws, ... of the workload
+    blocks = [synth.make_block(w, rank + ws * i, device=dev)["G"] for i in range(RESIDENT)]
+    M = blocks[0].shape[0]
+    cap = 1 << 20
+    hits = torch.zeros(cap * 24, dtype=torch.uint8, device=dev)
+    n_hits = torch.zeros(1, dtype=torch.int64, device=dev)
+    best = torch.zeros(w.P, dtype=torch.int64, device=dev)
+    out = tg.make_outputs(hits=hits, n_hits=n_hits, best=best)
+
+    def step(i, prec):
+        opts = tg.tg_scan_opts(prec, 0, THR)
+        b = i % RESIDENT
+        tg.tg_scan_block(ctx, panel, blocks[b], w.N, M, tg.TG_ENC_U8_DOSAGE, opts, out,
+                         marker_offset=(rank + ws * b) * w.block, stream=stream)
+
+    # split-BF16, the headline
+    for i in range(args.warmup):
+        step(i, tg.TG_PREC_SPLIT_BF16)
+    torch.cuda.synchronize()
+    n_hits.zero_()
+    best.zero_()
+    tg.tg_stage_times(ctx, reset=True)
+    tg.tg_set_profiling(ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for i in range(args.steps):
+            step(i, tg.TG_PREC_SPLIT_BF16)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    _barrier(dist)
+    ms = ev0.elapsed_time(ev1)
+    tg.tg_set_profiling(ctx, False)
+    stages = tg.tg_stage_times(ctx, reset=True)
+    status = tg.tg_status_poll(ctx, stream)
+    if status != tg.TG_OK:
+        raise SystemExit(f"device status {status}: {tg.tg_last_error()}")
+    ms_max = _max_over_ranks(dist, ms)
+    tests_step = M * w.P
+    value = tests_step * args.steps * ws / (ms_max / 1000.0)
+    launches = sum(n for _, n in stages.values())
+    nh = int(n_hits.item())
+
+    # FP32 SIMT scan on the same GPU, same blocks
+    fp32 = None
+    if args.fp32_steps > 0:
+        step(0, tg.TG_PREC_FP32)
+        torch.cuda.synchronize()
+        tg.tg_set_profiling(ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.fp32_steps):
+            step(i, tg.TG_PREC_FP32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tg.tg_set_profiling(ctx, False)
+        st32 = tg.tg_stage_times(ctx, reset=True)
+        ms32 = _max_over_ranks(dist, e0.elapsed_time(e1))
+        fp32 = {"value": tests_step * args.fp32_steps * ws / (ms32 / 1000.0), "unit": UNIT,
+                "ms_per_step": ms32 / args.fp32_steps,
+                "scan_kernel_ms": st32["scan"][0] / max(1, st32["scan"][1])}
+
+    # end to end through the host-buffer entry point: pinned host blocks in, hits and best out
+    e2e = None
+    if args.e2e_steps > 0:
+        host = torch.empty((RESIDENT * M, blocks[0].shape[1]), dtype=torch.uint8, pin_memory=True)
+        for i, b in enumerate(blocks):
+            host[i * M:(i + 1) * M].copy_(b)
+        hits_h = torch.zeros(cap * 24, dtype=torch.uint8, pin_memory=True)
+        best_h = torch.zeros(w.P, dtype=torch.int64, pin_memory=True)
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, THR)
+        per_call = RESIDENT
+        calls = max(1, args.e2e_steps // per_call)
+        tg.tg_scan_host(ctx, panel, host, w.N, per_call * M, tg.TG_ENC_U8_DOSAGE, M, opts, hits_h,
+                        best_h, stream=stream)
+        torch.cuda.synchronize()
+        _barrier(dist)
+        t0 = time.perf_counter()
+        nh_e2e = 0
+        for _ in range(calls):
+            nh_e2e = tg.tg_scan_host(ctx, panel, host, w.N, per_call * M, tg.TG_ENC_U8_DOSAGE, M,
+                                     opts, hits_h, best_h, stream=stream)
+        dt = _max_over_ranks(dist, time.perf_counter() - t0)
+        steps_e2e = calls * per_call
+        e2e = {"value": tests_step * steps_e2e * ws / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(M * blocks[0].shape[1]),
+               "d2h_bytes_per_step": int((8 + 24 * min(nh_e2e, cap) + 8 * w.P) / per_call),
+               "ms_per_step": 1000 * dt / steps_e2e, "api": "tg_scan_host (C ABI, host buffers)"}
+
+    peaks, peak_src = _peaks()
+    gemm_ms = stages["scan"][0] / max(1, stages["scan"][1])
+    flops = 2.0 * w.N * M * w.P                      # Eq. 2, algorithmic
+    achieved = flops / (gemm_ms / 1000.0) / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": _traffic(),
+                "kernel": "k_tc_scan (tcgen05 split-BF16 + fused epilogue)",
+                "issued_tflops": 2 * achieved, "peak_source": f"{peak_src} bf16 sustained",
+                "kernel_ms": gemm_ms,
+                "stage_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in stages.items()}}
+
+    cpu = None
+    if want_cpu:
+        done, secs, P = _oracle_sample(cpu_inputs[0], cpu_inputs[1], blocks[0][:4096].cpu(),
+                                       args.cpu_seconds)
+        cpu = {"value": done * P / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{done} markers x {P} phenotypes of block 0, FP64 projected OLS with "
+                         f"p-values, {secs:.1f} s (panel preparation excluded, as on the GPU)"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": _config(w), "clocks": clk.summary(), "gpu_launches": launches,
+            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "fp32": fp32,
+            "split_vs_fp32": (value / fp32["value"]) if fp32 else None,
+            "prepare_panel_ms": prepare_ms, "hits_in_timed_steps": nh,
+        }))
+    tg.tg_panel_free(panel)
+    tg.tg_destroy(ctx)
+
+
+def _traffic():
+    """DRAM bytes per launch of the scan kernel from a committed ncu summary, if one exists
+    for the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "tc_scan_traffic.json")
+    src = os.path.join(ROOT, "paper_2604_21095_gb300", "csrc", "k_tc.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return rec["bytes_per_launch"] if rec.get("k_tc_sha256") == h else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def main():
+    args = _args()
+    dist, rank, ws = _dist()
+    if args.impl == "reference":
+        _reference(args, dist, rank, ws)
+    else:
+        _ours(args, dist, rank, ws)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

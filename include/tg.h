@@ -1,0 +1,207 @@
+/*
+ * tg.h - C ABI of the GB300 genome-scan library (libtg.so).
+ *
+ * Method: TorchGWAS (arXiv 2604.21095), Section 2.2. A phenotype panel Y (N samples x P
+ * traits) is mean-centred, residualised against an orthonormal covariate basis Q and
+ * standardised once (Eq. 1); each block of M markers is then decoded, standardised and
+ * correlated with the whole panel (Eq. 2), and every correlation is turned into a t
+ * statistic (Eq. 3), a -log10 p-value, an effect size and its standard error.
+ *
+ * Conventions for every call:
+ *   - Data pointers marked "device" are CUDA device memory owned by the caller; the
+ *     library never frees them. Pointers marked "host" are host memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *     asynchronous on it unless stated otherwise; argument errors are returned
+ *     synchronously, before any work is queued.
+ *   - Errors found by a kernel (hit-buffer overflow, a bounded wait that ran out) are
+ *     latched in a per-context device status word and returned by tg_status_poll().
+ *   - On failure a call returns a non-zero tg_status and sets a thread-local message
+ *     readable with tg_last_error().
+ *   - Matrices are dense with an explicit leading dimension (elements unless noted).
+ *   - Only sm_103a (GB300) is supported; every compute step runs in the library's own
+ *     CUDA kernels. There is no CPU path.
+ */
+#ifndef TG_H_
+#define TG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TG_ABI_VERSION 1
+
+typedef struct tg_ctx tg_ctx;
+typedef struct tg_panel tg_panel;
+
+typedef enum {
+  TG_OK = 0,
+  TG_ERR_INVALID_ARG = 1, /* bad pointer, size, stride, alignment or enum */
+  TG_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  TG_ERR_OOM = 3,         /* device allocation failed */
+  TG_ERR_NONFINITE = 4,   /* NaN or Inf in the phenotypes or covariates */
+  TG_ERR_RANK = 5,        /* too few samples for the covariate rank (N <= q + 1) */
+  TG_ERR_CAPACITY = 6,    /* more hits than the hit buffer holds (the count is still exact) */
+  TG_ERR_TIMEOUT = 7,     /* a bounded device-side wait ran out */
+  TG_ERR_UNSUPPORTED = 8  /* a size beyond the library's limits, or no sm_103a device */
+} tg_status;
+
+typedef enum {
+  TG_PREC_FP32 = 0,      /* FP32 operands, FP32 SIMT contraction */
+  TG_PREC_SPLIT_BF16 = 1 /* exact BF16 genotype codes, panel split into BF16 hi + lo,
+                            two tcgen05 tensor-core products accumulated in FP32 */
+} tg_precision;
+
+typedef enum {
+  TG_ENC_2BIT = 0,     /* PLINK 1 .bed SNP-major: sample i in bits 2(i%4)+{0,1} of byte i/4;
+                          field 00 -> 2 copies of allele 1, 10 -> 1, 11 -> 0, 01 -> missing */
+  TG_ENC_U8_DOSAGE = 1 /* one byte b per sample, allele-1 dosage 2b/255 */
+} tg_encoding;
+
+/* Per-call scan options. */
+typedef struct {
+  int32_t precision;   /* tg_precision */
+  int32_t full_output; /* nonzero: write beta, se, t, -log10 p of every (marker, phenotype) */
+  double hit_mlog10p;  /* collect pairs with -log10 p >= this; <= 0 or NaN: no hit list */
+} tg_scan_opts;
+
+/* One association above the hit threshold (24 bytes). */
+typedef struct {
+  uint32_t marker; /* marker_offset + row within the block */
+  uint32_t pheno;  /* phenotype column */
+  float beta;      /* OLS effect of one allele-1 copy */
+  float se;        /* its standard error */
+  float t;         /* Eq. 3 t statistic, df = N - q - 1 */
+  float mlog10p;   /* -log10 of the two-sided p-value */
+} tg_hit;
+
+/* Outputs of tg_scan_block. Every pointer is device memory and may be NULL when that
+ * output is not wanted (beta/se/t/mlog10p are ignored unless opts->full_output). */
+typedef struct {
+  float* beta;    /* [M][ldo] row-major: row = marker of the block, column = phenotype */
+  float* se;
+  float* t;
+  float* mlog10p;
+  int64_t ldo;            /* >= P */
+  tg_hit* hits;           /* hit records, unordered; [hit_capacity] */
+  int64_t hit_capacity;
+  unsigned long long* n_hits; /* running count; the caller zeroes it. Counts every hit, also
+                                 those past hit_capacity (then TG_ERR_CAPACITY is latched) */
+  unsigned long long* best;   /* [P] running per-phenotype best marker; the caller zeroes it.
+                                 key = (bits of float |r|) << 32 | (0xFFFFFFFF - marker):
+                                 larger |r| wins, ties go to the smaller marker */
+  double* marker_norm2;   /* [M] |g_res|^2 in allele units (NaN: marker untestable) */
+  int32_t* marker_nobs;   /* [M] observed calls */
+  double* marker_mean;    /* [M] observed mean in decode units (counts, or bytes for dosages) */
+} tg_outputs;
+
+/* Library version string and ABI number. */
+const char* tg_version(void);
+int tg_abi_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* tg_last_error(void);
+const char* tg_status_string(tg_status s);
+
+/* Create a context on CUDA device `device`: workspace, status word, side stream.
+ * Fails with TG_ERR_UNSUPPORTED unless the device is sm_103. */
+tg_status tg_create(tg_ctx** ctx, int device);
+tg_status tg_destroy(tg_ctx* ctx);
+
+/* Section 2.2, Eq. 1 and the standardisation after it.
+ * Builds X = [1, C], an orthonormal basis Q of span(X) by FP64 Householder QR (a column
+ * whose remaining norm is <= 1e-9 of its own norm is dropped; q = rank), the residualised
+ * panel Y_res = (I - Q Q^T)(Y - Ybar) in FP64, the column norms s_p = |y_res,p| and the
+ * unit-norm panel in the forms the scan consumes.
+ *   Y: device, float [P][ldy] storage = column-major N x P (phenotype p at Y + p*ldy), ldy >= N.
+ *   C: device, double column-major N x n_cov (covariate k at C + k*ldc), ldc >= N; NULL if n_cov = 0.
+ *      The intercept is added by the library and must not be passed.
+ * Synchronous: returns after the panel is ready. A phenotype whose residual norm is
+ * <= 1e-12 of its centred norm has no test (its outputs are NaN).
+ * Errors: TG_ERR_NONFINITE (NaN/Inf in Y or C), TG_ERR_RANK (N <= q + 1),
+ * TG_ERR_UNSUPPORTED (n_cov > 63), TG_ERR_INVALID_ARG. The panel is owned by the library. */
+tg_status tg_prepare_panel(tg_ctx* ctx, const float* Y, int64_t ldy, int64_t N, int64_t P,
+                           const double* C, int64_t ldc, int64_t n_cov, tg_panel** out,
+                           void* stream);
+
+/* Panel shape: samples, phenotypes, covariate rank q (intercept included), df = N - q - 1. */
+tg_status tg_panel_info(const tg_panel* panel, int64_t* N, int64_t* P, int64_t* q, int64_t* df);
+
+/* Borrowed device pointer to Q: double column-major N x q (column k at Q + k*ldq). */
+tg_status tg_panel_Q(const tg_panel* panel, const double** Q, int64_t* ldq, int64_t* q);
+
+/* Borrowed device pointers to Y_res (double column-major N x P, column p at Yres + p*ld)
+ * and to s (double [P], column norms of Y_res). */
+tg_status tg_panel_Yres(const tg_panel* panel, const double** Yres, int64_t* ld, const double** s);
+
+tg_status tg_panel_free(tg_panel* panel);
+
+/* Section 2.2, genotype batches: decode one block of M markers into the contraction
+ * operand and the exact per-marker statistics (the first step of tg_scan_block, exposed
+ * on its own for testing and for callers that keep the operand).
+ *   G: device, uint8 [M][ldg]; ldg >= ceil(N/4) (2-bit) or >= N (dosage), ldg % 16 == 0,
+ *      G 16-byte aligned.
+ *   missing: device, uint32 [M][ldm] bit mask (bit i%32 of word i/32 set = call i missing),
+ *      ldm >= ceil(N/32); dosage only (must be NULL for 2-bit, where it is in-band); may be NULL.
+ *   A_hi, A_lo: device operand rows of lda elements, lda >= N, lda % 64 == 0. For
+ *      TG_PREC_SPLIT_BF16 both are bf16: observed calls hold the exact code (or byte), a
+ *      missing call holds bf16(mean) in A_hi and bf16(mean - bf16(mean)) in A_lo, every
+ *      other A_lo entry and columns N..lda-1 are 0. For TG_PREC_FP32 A_hi is float
+ *      (missing = float(mean)) and A_lo must be NULL.
+ *   n_obs, S, S2 (int32/int64/int64 [M]): exact observed count, sum and sum of squares in
+ *      decode units; mean (double [M]): S / n_obs, one correctly rounded division (NaN if
+ *      n_obs = 0). Any of these four may be NULL. */
+tg_status tg_decode_block(tg_ctx* ctx, const uint8_t* G, int64_t ldg, int32_t encoding, int64_t N,
+                          int64_t M, const uint32_t* missing, int64_t ldm, int32_t precision,
+                          void* A_hi, void* A_lo, int64_t lda, int32_t* n_obs, int64_t* S,
+                          int64_t* S2, double* mean, void* stream);
+
+/* Section 2.2 Eq. 2 and Eq. 3 for one block: decode (mean imputation of missing calls),
+ * project each marker on Q (|g_res|^2 = |g_c|^2 - |Q^T g_c|^2), contract the block with the
+ * whole panel, and turn every correlation r into t = r sqrt(df / (1 - r^2)),
+ * beta = r s_p / |g_res|, se = |beta / t| and -log10 p, p = I_{1-r^2}(df/2, 1/2) (two-sided).
+ *   G, ldg, encoding, missing, ldm: as tg_decode_block; N must equal the panel's N.
+ *   marker_offset: global index of the block's first marker (used in hits and best).
+ *   opts: precision, full output and hit threshold. out: see tg_outputs.
+ * Workspace is grown on demand (cudaMalloc); a call with a larger M than any before may
+ * therefore synchronise the device. M = 0 is a no-op. */
+tg_status tg_scan_block(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G, int64_t ldg,
+                        int32_t encoding, int64_t N, int64_t M, int64_t marker_offset,
+                        const uint32_t* missing, int64_t ldm, const tg_scan_opts* opts,
+                        const tg_outputs* out, void* stream);
+
+/* The scan of a whole genotype matrix held in HOST memory (pinned for overlap): blocks of
+ * block_markers rows are copied to the device on the context's side stream, double
+ * buffered, while the previous block is scanned on `stream`; hits, their count and the
+ * per-phenotype best keys are copied back to host memory at the end. Synchronous.
+ *   G_host: host uint8 [M][ldg]; hits_host: host [hit_capacity]; n_hits: host, total hit
+ *   count (may exceed hit_capacity, then TG_ERR_CAPACITY); best_host: host [P] or NULL.
+ * Only hit collection is supported here (opts->full_output must be 0). */
+tg_status tg_scan_host(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G_host, int64_t ldg,
+                       int32_t encoding, int64_t N, int64_t M, int64_t block_markers,
+                       int64_t marker_offset, const tg_scan_opts* opts, tg_hit* hits_host,
+                       int64_t hit_capacity, int64_t* n_hits, unsigned long long* best_host,
+                       void* stream);
+
+/* Synchronise `stream`, then return and clear the latched device status
+ * (TG_ERR_CAPACITY, TG_ERR_TIMEOUT) of work queued so far. */
+tg_status tg_status_poll(tg_ctx* ctx, void* stream);
+
+/* Stage timing with CUDA events on the launching stream (off by default). */
+#define TG_N_STAGES 5 /* 0 decode, 1 projection, 2 marker norm, 3 contraction+epilogue, 4 H2D */
+tg_status tg_set_profiling(tg_ctx* ctx, int enable);
+/* Total milliseconds and kernel launches per stage since the last reset (synchronises
+ * the recorded events). Either array may be NULL. */
+tg_status tg_stage_times(tg_ctx* ctx, double* ms, int64_t* launches, int reset);
+
+/* Spin on a device word until it becomes nonzero or limit_ns elapses, with the same
+ * bounded wait the scan kernels use. Returns TG_ERR_TIMEOUT (and latches nothing) when
+ * the limit ran out; used to test failure detection without hanging a GPU. Synchronous. */
+tg_status tg_bounded_wait_test(tg_ctx* ctx, const uint32_t* flag, int64_t limit_ns, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TG_H_ */

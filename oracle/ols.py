@@ -17,8 +17,9 @@ from __future__ import annotations
 import numpy as np
 
 # A marker is untestable when it has no observed call, is constant, or is (up to
-# this relative residual) inside the covariate span.
-MARKER_TOL = 1e-10
+# this relative residual) inside the covariate span: |g_res|^2 <= 1e-5 |g_c|^2, i.e. the
+# covariates explain at least 99.999% of its variance (variance inflation >= 1e5).
+MARKER_TOL = 1e-5
 
 
 def ols_direct(X: np.ndarray, g: np.ndarray, Y: np.ndarray):

@@ -1,0 +1,655 @@
+// C ABI of the genome-scan library: argument checks, device memory of contexts and panels,
+// tensor maps, stage timing and the orchestration of the kernels of one block scan.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+#include "pvalue.cuh"
+
+using namespace tg;
+
+namespace {
+
+thread_local std::string g_err;
+
+const char* kVersion = "tg 0.1.0 (sm_103a)";
+
+// The spin limit of device-side waits: generous enough for a FULL-output tile epilogue.
+constexpr long long kSpinNs = 4000000000ll;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D bf16 tensor map: rows x K elements, row stride ld elements, box box_rows x 32, 64B swizzle.
+bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t ld,
+               uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {32u, box_rows};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+#define TG_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+#define TG_ARG(cond, msg)                                   \
+  do {                                                      \
+    if (!(cond)) return fail(TG_ERR_INVALID_ARG, msg);      \
+  } while (0)
+
+// ---------------------------------------------------------------- profiling
+struct StageScope {
+  tg_ctx* c;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  StageScope(tg_ctx* c_, int s_, cudaStream_t st_, int nlaunch) : c(c_), stage(s_), st(st_) {
+    c->launches[stage] += nlaunch;
+    if (!c->prof) return;
+    a = take();
+    b = take();
+    cudaEventRecord(a, st);
+  }
+  ~StageScope() {
+    if (!c->prof || !a) return;
+    cudaEventRecord(b, st);
+    c->pending.push_back({a, b, stage});
+  }
+  cudaEvent_t take() {
+    if (!c->event_pool.empty()) {
+      cudaEvent_t e = c->event_pool.back();
+      c->event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+
+cudaError_t ensure_markers(tg_ctx* c, int64_t M) {
+  if (M <= c->cap_m) return cudaSuccess;
+  const int64_t cap = round_up(M, MT);
+  dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
+  dfree(c->rinv); dfree(c->rinv64); dfree(c->tflags);
+  c->cap_m = 0;
+  cudaError_t e;
+  if ((e = dalloc(&c->nobs, cap)) || (e = dalloc(&c->mean, cap)) || (e = dalloc(&c->gc2, cap)) ||
+      (e = dalloc(&c->qg, cap * QCOLS)) || (e = dalloc(&c->gres2, cap)) ||
+      (e = dalloc(&c->rinv, cap)) || (e = dalloc(&c->rinv64, cap)) ||
+      (e = dalloc(&c->tflags, cap / MT)))
+    return e;
+  c->cap_m = cap;
+  return cudaSuccess;
+}
+
+// Operand rows: bf16 hi (+ lo) for the split form, float for FP32.
+cudaError_t ensure_operands(tg_ctx* c, int64_t M, int64_t Npad, int prec, bool need_lo) {
+  const int64_t rows = round_up(M, MT);
+  const bool fits = rows <= c->cap_rows && Npad <= c->cap_npad;
+  const bool have = prec == TG_PREC_FP32 ? c->A32 != nullptr
+                                         : (c->Ahi != nullptr && (!need_lo || c->Alo != nullptr));
+  if (fits && have) return cudaSuccess;
+  const int64_t R = fits ? c->cap_rows : std::max(rows, c->cap_rows);
+  const int64_t K = fits ? c->cap_npad : std::max(Npad, c->cap_npad);
+  if (!fits) {
+    dfree(c->Ahi); dfree(c->Alo); dfree(c->A32);
+  }
+  cudaError_t e = cudaSuccess;
+  if (prec == TG_PREC_FP32 && !c->A32) e = dalloc(&c->A32, (size_t)(R * K));
+  if (!e && prec == TG_PREC_SPLIT_BF16 && !c->Ahi) e = dalloc(&c->Ahi, (size_t)(R * K));
+  if (!e && prec == TG_PREC_SPLIT_BF16 && need_lo && !c->Alo) e = dalloc(&c->Alo, (size_t)(R * K));
+  if (e) return e;
+  c->cap_rows = R;
+  c->cap_npad = K;
+  return cudaSuccess;
+}
+
+struct ScanArgs {
+  const uint8_t* G;
+  int64_t ldg;
+  int encoding;
+  int64_t N, M, marker_offset;
+  const uint32_t* missing;
+  int64_t ldm;
+  tg_scan_opts opts;
+  tg_outputs out;
+};
+
+tg_status check_scan_args(const tg_ctx* c, const tg_panel* p, const ScanArgs& a) {
+  TG_ARG(c && p, "null context or panel");
+  TG_ARG(a.encoding == TG_ENC_2BIT || a.encoding == TG_ENC_U8_DOSAGE, "unknown encoding");
+  TG_ARG(a.opts.precision == TG_PREC_FP32 || a.opts.precision == TG_PREC_SPLIT_BF16,
+         "unknown precision");
+  TG_ARG(a.N == p->N, "N differs from the panel's sample count");
+  TG_ARG(a.M >= 0, "M < 0");
+  TG_ARG(a.marker_offset >= 0 && a.marker_offset + a.M <= 0xFFFFFFFFll,
+         "marker indices must fit in 32 bits");
+  if (a.M == 0) return TG_OK;
+  TG_ARG(a.G != nullptr && aligned(a.G, 16), "G must be a 16-byte aligned device pointer");
+  const int64_t need = a.encoding == TG_ENC_2BIT ? (a.N + 3) / 4 : a.N;
+  TG_ARG(a.ldg >= need && a.ldg % 16 == 0, "ldg must be >= the packed row length and a multiple of 16");
+  if (a.encoding == TG_ENC_2BIT)
+    TG_ARG(a.missing == nullptr, "2-bit calls carry missingness in-band: missing must be NULL");
+  if (a.missing) TG_ARG(a.ldm >= (a.N + 31) / 32 && aligned(a.missing, 4), "bad missing mask stride");
+  if (a.opts.full_output) {
+    TG_ARG(a.out.ldo >= p->P, "ldo < P");
+    TG_ARG(a.out.beta || a.out.se || a.out.t || a.out.mlog10p, "full_output without output arrays");
+  }
+  const bool hits = a.opts.hit_mlog10p > 0.0;
+  if (hits) TG_ARG(a.out.n_hits && a.out.hit_capacity >= 0 && (a.out.hits || a.out.hit_capacity == 0),
+                   "hit collection needs hits, hit_capacity and n_hits");
+  return TG_OK;
+}
+
+float r2_threshold(tg_panel* p, double mlog10p) {
+  if (!(mlog10p > 0.0)) return 2.0f;  // never reached
+  const double r2 = host_r2_threshold(mlog10p, (double)p->df, p->lnB);
+  return (float)r2;
+}
+
+tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream_t st) {
+  tg_panel* p = const_cast<tg_panel*>(pc);
+  if (a.M == 0) return TG_OK;
+  const int prec = a.opts.precision;
+  const bool has_lo = prec == TG_PREC_SPLIT_BF16 && (a.encoding == TG_ENC_2BIT || a.missing);
+  TG_CUDA(ensure_markers(c, a.M));
+  TG_CUDA(ensure_operands(c, a.M, p->Npad, prec, has_lo));
+  const float kappa = a.encoding == TG_ENC_U8_DOSAGE ? (float)(2.0 / 255.0) : 1.0f;
+  void* Ahi = prec == TG_PREC_FP32 ? (void*)c->A32 : (void*)c->Ahi;
+  {
+    StageScope s(c, STAGE_DECODE, st, 1);
+    if (has_lo) TG_CUDA(cudaMemsetAsync(c->tflags, 0, sizeof(int) * (size_t)((a.M + MT - 1) / MT), st));
+    TG_CUDA(launch_decode(a.G, a.ldg, a.encoding, a.N, a.M, a.missing, a.ldm, prec, Ahi,
+                          has_lo ? c->Alo : nullptr, p->Npad, c->nobs, nullptr, nullptr, c->mean,
+                          c->gc2, has_lo ? c->tflags : nullptr, st));
+  }
+  const int64_t nq = p->q - 1;
+  if (nq > 0) {
+    StageScope s(c, STAGE_PROJECT, st, 1);
+    TG_CUDA(launch_project(Ahi, has_lo ? c->Alo : nullptr, prec == TG_PREC_FP32, p->Npad, a.M,
+                           p->Npad, p->QB, nq, c->qg, st));
+  }
+  {
+    StageScope s(c, STAGE_NORM, st, 1);
+    TG_CUDA(launch_marker_norm(a.M, c->nobs, c->gc2, c->qg, nq, kappa, c->gres2,
+                               a.out.marker_norm2, c->rinv, c->rinv64, st));
+    if (a.out.marker_nobs)
+      TG_CUDA(cudaMemcpyAsync(a.out.marker_nobs, c->nobs, sizeof(int32_t) * a.M,
+                              cudaMemcpyDeviceToDevice, st));
+    if (a.out.marker_mean)
+      TG_CUDA(cudaMemcpyAsync(a.out.marker_mean, c->mean, sizeof(double) * a.M,
+                              cudaMemcpyDeviceToDevice, st));
+  }
+  EpiParams ep{};
+  ep.M = (int)a.M;
+  ep.P = (int)p->P;
+  ep.marker_offset = a.marker_offset;
+  ep.df = (double)p->df;
+  ep.df_f = (float)p->df;
+  ep.lnB = p->lnB;
+  ep.kappa = kappa;
+  ep.do_hits = a.opts.hit_mlog10p > 0.0 && a.out.n_hits != nullptr;
+  ep.r2_thr = ep.do_hits ? r2_threshold(p, a.opts.hit_mlog10p) : 2.0f;
+  ep.do_full = a.opts.full_output ? 1 : 0;
+  ep.do_best = a.out.best != nullptr;
+  ep.row_inv = c->rinv;
+  ep.row_inv64 = c->rinv64;
+  ep.col_s = p->col_s;
+  ep.col_s64 = p->s;
+  ep.col_rmul = p->col_rmul;
+  ep.beta = a.out.beta;
+  ep.se = a.out.se;
+  ep.t = a.out.t;
+  ep.mlp = a.out.mlog10p;
+  ep.ldo = a.out.ldo;
+  ep.hits = a.out.hits;
+  ep.hit_cap = a.out.hit_capacity;
+  ep.n_hits = a.out.n_hits;
+  ep.best = a.out.best;
+  ep.status = c->status;
+  {
+    StageScope s(c, STAGE_GEMM, st, 1);
+    if (prec == TG_PREC_FP32) {
+      TG_CUDA(launch_sgemm_scan(c->A32, p->Npad, p->B32, p->Npad, p->Npad, ep, st));
+    } else {
+      CUtensorMap tA, tAlo;
+      if (!make_tmap(&tA, c->Ahi, a.M, p->Npad, p->Npad, MT))
+        return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
+      if (has_lo && !make_tmap(&tAlo, c->Alo, a.M, p->Npad, p->Npad, MT))
+        return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the imputation operand");
+      TG_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi, &p->tmBlo, p->Npad, has_lo,
+                             c->tflags, ep, c->sm_count, kSpinNs, st));
+    }
+  }
+  return TG_OK;
+}
+
+}  // namespace
+
+namespace tg {
+
+tg_status fail(tg_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+tg_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? TG_ERR_OOM : TG_ERR_CUDA;
+}
+
+double host_lnbeta_half(double df) {
+  const double a = 0.5 * df;
+  return std::lgamma(a) + std::lgamma(0.5) - std::lgamma(a + 0.5);
+}
+
+// Smallest r^2 whose -log10 p reaches the threshold (bisection on |r|, monotone in |r|).
+double host_r2_threshold(double mlog10p, double df, double lnB) {
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (mlog10p_r(mid, df, lnB) >= mlog10p) hi = mid; else lo = mid;
+  }
+  return hi * hi;
+}
+
+}  // namespace tg
+
+extern "C" {
+
+const char* tg_version(void) { return kVersion; }
+int tg_abi_version(void) { return TG_ABI_VERSION; }
+const char* tg_last_error(void) { return g_err.c_str(); }
+
+const char* tg_status_string(tg_status s) {
+  switch (s) {
+    case TG_OK: return "ok";
+    case TG_ERR_INVALID_ARG: return "invalid argument";
+    case TG_ERR_CUDA: return "CUDA error";
+    case TG_ERR_OOM: return "out of device memory";
+    case TG_ERR_NONFINITE: return "non-finite input";
+    case TG_ERR_RANK: return "too few samples for the covariate rank";
+    case TG_ERR_CAPACITY: return "hit buffer overflow";
+    case TG_ERR_TIMEOUT: return "device wait timed out";
+    case TG_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+tg_status tg_create(tg_ctx** out, int device) {
+  TG_ARG(out != nullptr, "null output pointer");
+  *out = nullptr;
+  int ndev = 0;
+  TG_CUDA(cudaGetDeviceCount(&ndev));
+  TG_ARG(device >= 0 && device < ndev, "no such CUDA device");
+  TG_CUDA(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  TG_CUDA(cudaGetDeviceProperties(&prop, device));
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(TG_ERR_UNSUPPORTED, std::string("needs an sm_103 (GB300) device, found ") + prop.name);
+  if (!encode_fn()) return fail(TG_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+  tg_ctx* c = new tg_ctx();
+  c->device = device;
+  c->sm_count = prop.multiProcessorCount;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) ||
+      (e = dalloc(&c->status, 4)) || (e = dalloc(&c->scratch, 256)) ||
+      (e = cudaMemset(c->status, 0, 16)) ||
+      (e = cudaEventCreateWithFlags(&c->ev_copied[0], cudaEventDisableTiming)) ||
+      (e = cudaEventCreateWithFlags(&c->ev_copied[1], cudaEventDisableTiming)) ||
+      (e = cudaEventCreateWithFlags(&c->ev_free[0], cudaEventDisableTiming)) ||
+      (e = cudaEventCreateWithFlags(&c->ev_free[1], cudaEventDisableTiming))) {
+    tg_destroy(c);
+    return cuda_fail(e, "tg_create");
+  }
+  *out = c;
+  return TG_OK;
+}
+
+tg_status tg_destroy(tg_ctx* c) {
+  if (!c) return TG_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  dfree(c->status); dfree(c->scratch);
+  dfree(c->Ahi); dfree(c->Alo); dfree(c->A32);
+  dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
+  dfree(c->rinv); dfree(c->rinv64); dfree(c->tflags);
+  dfree(c->stage_buf[0]); dfree(c->stage_buf[1]);
+  dfree(c->dhits); dfree(c->dnhits); dfree(c->dbest);
+  for (auto& ev : c->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+  for (auto ev : c->event_pool) cudaEventDestroy(ev);
+  for (int i = 0; i < 2; ++i) {
+    if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+    if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
+  }
+  if (c->side) cudaStreamDestroy(c->side);
+  delete c;
+  return TG_OK;
+}
+
+tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, int64_t P,
+                           const double* C, int64_t ldc, int64_t n_cov, tg_panel** out,
+                           void* stream) {
+  TG_ARG(c && out, "null context or output");
+  *out = nullptr;
+  TG_ARG(N > 0 && P >= 0 && n_cov >= 0, "bad sizes");
+  TG_ARG(N <= (1ll << 30), "N too large");
+  TG_ARG(Y != nullptr || P == 0, "null Y");
+  TG_ARG(ldy >= N, "ldy < N");
+  if (n_cov > QMAX - 1) return fail(TG_ERR_UNSUPPORTED, "at most 63 covariates");
+  if (n_cov > 0) TG_ARG(C != nullptr && ldc >= N, "null C or ldc < N");
+  TG_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  tg_panel* p = new tg_panel();
+  p->device = c->device;
+  p->N = N;
+  p->P = P;
+  p->n_cov = n_cov;
+  p->Npad = round_up(N, KPAD);
+  p->Ppad = round_up(std::max<int64_t>(P, 1), PPAD);
+  const int64_t k = 1 + n_cov;
+  auto cleanup = [&](tg_status s) { tg_panel_free(p); return s; };
+  cudaError_t e;
+  int* dint = nullptr;  // [0] rank, [1..k] kept flags
+  if ((e = dalloc(&p->X, (size_t)(2 * k * N))) || (e = dalloc(&p->Q, (size_t)(k * N))) ||
+      (e = dalloc(&p->Yres, (size_t)(std::max<int64_t>(P, 1) * N))) ||
+      (e = dalloc(&p->s, (size_t)std::max<int64_t>(P, 1))) ||
+      (e = dalloc(&p->col_s, (size_t)std::max<int64_t>(P, 1))) ||
+      (e = dalloc(&p->col_rmul, (size_t)p->Ppad)) ||
+      (e = dalloc(&p->Bhi, (size_t)(p->Ppad * p->Npad))) ||
+      (e = dalloc(&p->Blo, (size_t)(p->Ppad * p->Npad))) ||
+      (e = dalloc(&p->B32, (size_t)(p->Ppad * p->Npad))) ||
+      (e = dalloc(&p->QB, (size_t)(QCOLS * p->Npad))) || (e = dalloc(&dint, (size_t)(1 + k))))
+    return cleanup(cuda_fail(e, "tg_prepare_panel allocation"));
+  auto run = [&]() -> cudaError_t {
+    cudaError_t r;
+    if ((r = cudaMemsetAsync(c->scratch, 0, 16, st))) return r;
+    if ((r = cudaMemsetAsync(p->Bhi, 0, sizeof(__nv_bfloat16) * p->Ppad * p->Npad, st))) return r;
+    if ((r = cudaMemsetAsync(p->Blo, 0, sizeof(__nv_bfloat16) * p->Ppad * p->Npad, st))) return r;
+    if ((r = cudaMemsetAsync(p->B32, 0, sizeof(float) * p->Ppad * p->Npad, st))) return r;
+    if ((r = cudaMemsetAsync(p->col_rmul, 0, sizeof(float) * p->Ppad, st))) return r;
+    if ((r = launch_build_design(p->X, C, ldc, N, n_cov, c->scratch, st))) return r;
+    if ((r = launch_householder(p->X, N, k, p->Q, dint, dint + 1, st))) return r;
+    return cudaSuccess;
+  };
+  if ((e = run())) { cudaFree(dint); return cleanup(cuda_fail(e, "tg_prepare_panel basis")); }
+  int rank = 0;
+  if ((e = cudaMemcpyAsync(&rank, dint, sizeof(int), cudaMemcpyDeviceToHost, st)) ||
+      (e = cudaStreamSynchronize(st))) {
+    cudaFree(dint);
+    return cleanup(cuda_fail(e, "tg_prepare_panel rank"));
+  }
+  cudaFree(dint);
+  p->q = rank;
+  p->df = N - rank - 1;
+  if (p->df <= 0) return cleanup(fail(TG_ERR_RANK, "N must exceed rank([1, C]) + 1"));
+  if ((e = launch_residualise(Y, ldy, p->Q, N, P, rank, p->Npad, p->Yres, p->s, p->col_s,
+                              p->col_rmul, p->Bhi, p->Blo, p->B32, c->scratch, st)) ||
+      (e = launch_qcols(p->Q, N, rank, p->Npad, p->QB, st)))
+    return cleanup(cuda_fail(e, "tg_prepare_panel residualise"));
+  uint32_t flags = 0;
+  if ((e = cudaMemcpyAsync(&flags, c->scratch, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) ||
+      (e = cudaStreamSynchronize(st)))
+    return cleanup(cuda_fail(e, "tg_prepare_panel"));
+  if (flags & 1u) return cleanup(fail(TG_ERR_NONFINITE, "non-finite covariate"));
+  if (flags & 2u) return cleanup(fail(TG_ERR_NONFINITE, "non-finite phenotype"));
+  p->lnB = host_lnbeta_half((double)p->df);
+  if (!make_tmap(&p->tmBhi, p->Bhi, p->Ppad, p->Npad, p->Npad, 256) ||
+      !make_tmap(&p->tmBlo, p->Blo, p->Ppad, p->Npad, p->Npad, 256))
+    return cleanup(fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panel"));
+  *out = p;
+  return TG_OK;
+}
+
+tg_status tg_panel_info(const tg_panel* p, int64_t* N, int64_t* P, int64_t* q, int64_t* df) {
+  TG_ARG(p, "null panel");
+  if (N) *N = p->N;
+  if (P) *P = p->P;
+  if (q) *q = p->q;
+  if (df) *df = p->df;
+  return TG_OK;
+}
+
+tg_status tg_panel_Q(const tg_panel* p, const double** Q, int64_t* ldq, int64_t* q) {
+  TG_ARG(p, "null panel");
+  if (Q) *Q = p->Q;
+  if (ldq) *ldq = p->N;
+  if (q) *q = p->q;
+  return TG_OK;
+}
+
+tg_status tg_panel_Yres(const tg_panel* p, const double** Yres, int64_t* ld, const double** s) {
+  TG_ARG(p, "null panel");
+  if (Yres) *Yres = p->Yres;
+  if (ld) *ld = p->N;
+  if (s) *s = p->s;
+  return TG_OK;
+}
+
+tg_status tg_panel_free(tg_panel* p) {
+  if (!p) return TG_OK;
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  dfree(p->X); dfree(p->Q); dfree(p->Yres); dfree(p->s); dfree(p->col_s); dfree(p->col_rmul);
+  dfree(p->Bhi); dfree(p->Blo); dfree(p->B32); dfree(p->QB);
+  delete p;
+  return TG_OK;
+}
+
+tg_status tg_decode_block(tg_ctx* c, const uint8_t* G, int64_t ldg, int32_t encoding, int64_t N,
+                          int64_t M, const uint32_t* missing, int64_t ldm, int32_t precision,
+                          void* A_hi, void* A_lo, int64_t lda, int32_t* n_obs, int64_t* S,
+                          int64_t* S2, double* mean, void* stream) {
+  TG_ARG(c, "null context");
+  TG_ARG(encoding == TG_ENC_2BIT || encoding == TG_ENC_U8_DOSAGE, "unknown encoding");
+  TG_ARG(precision == TG_PREC_FP32 || precision == TG_PREC_SPLIT_BF16, "unknown precision");
+  TG_ARG(N > 0 && M >= 0, "bad sizes");
+  if (M == 0) return TG_OK;
+  TG_ARG(G && aligned(G, 16), "G must be a 16-byte aligned device pointer");
+  const int64_t need = encoding == TG_ENC_2BIT ? (N + 3) / 4 : N;
+  TG_ARG(ldg >= need && ldg % 16 == 0, "ldg must be >= the packed row length and a multiple of 16");
+  if (encoding == TG_ENC_2BIT) TG_ARG(missing == nullptr, "missing must be NULL for 2-bit calls");
+  if (missing) TG_ARG(ldm >= (N + 31) / 32, "ldm too small");
+  TG_ARG(A_hi && aligned(A_hi, 16), "A_hi must be a 16-byte aligned device pointer");
+  TG_ARG(lda >= N && lda % KPAD == 0, "lda must be >= N and a multiple of 64");
+  if (precision == TG_PREC_FP32) TG_ARG(A_lo == nullptr, "A_lo must be NULL for FP32");
+  if (A_lo) TG_ARG(aligned(A_lo, 16), "A_lo must be 16-byte aligned");
+  TG_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  StageScope s(c, STAGE_DECODE, st, 1);
+  TG_CUDA(launch_decode(G, ldg, encoding, N, M, missing, ldm, precision, A_hi, A_lo, lda, n_obs,
+                        S, S2, mean, nullptr, nullptr, st));
+  return TG_OK;
+}
+
+tg_status tg_scan_block(tg_ctx* c, const tg_panel* p, const uint8_t* G, int64_t ldg,
+                        int32_t encoding, int64_t N, int64_t M, int64_t marker_offset,
+                        const uint32_t* missing, int64_t ldm, const tg_scan_opts* opts,
+                        const tg_outputs* out, void* stream) {
+  TG_ARG(opts && out, "null options or outputs");
+  ScanArgs a{G, ldg, encoding, N, M, marker_offset, missing, ldm, *opts, *out};
+  tg_status s = check_scan_args(c, p, a);
+  if (s != TG_OK) return s;
+  TG_CUDA(cudaSetDevice(c->device));
+  return scan_impl(c, p, a, (cudaStream_t)stream);
+}
+
+tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int64_t ldg,
+                       int32_t encoding, int64_t N, int64_t M, int64_t block_markers,
+                       int64_t marker_offset, const tg_scan_opts* opts, tg_hit* hits_host,
+                       int64_t hit_capacity, int64_t* n_hits, unsigned long long* best_host,
+                       void* stream) {
+  TG_ARG(c && p && opts && n_hits, "null argument");
+  TG_ARG(!opts->full_output, "tg_scan_host collects hits only");
+  TG_ARG(block_markers > 0 && M >= 0, "bad block size");
+  TG_ARG(hit_capacity >= 0 && (hits_host || hit_capacity == 0), "bad hit buffer");
+  TG_ARG(G_host || M == 0, "null G_host");
+  TG_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t blk_bytes = (size_t)(block_markers * ldg);
+  if (c->stage_bytes < blk_bytes) {
+    dfree(c->stage_buf[0]);
+    dfree(c->stage_buf[1]);
+    c->stage_bytes = 0;
+    TG_CUDA(dalloc(&c->stage_buf[0], blk_bytes));
+    TG_CUDA(dalloc(&c->stage_buf[1], blk_bytes));
+    c->stage_bytes = blk_bytes;
+  }
+  if (c->dhits_cap < std::max<int64_t>(hit_capacity, 1)) {
+    dfree(c->dhits);
+    c->dhits_cap = 0;
+    TG_CUDA(dalloc(&c->dhits, (size_t)std::max<int64_t>(hit_capacity, 1)));
+    c->dhits_cap = std::max<int64_t>(hit_capacity, 1);
+  }
+  if (!c->dnhits) TG_CUDA(dalloc(&c->dnhits, 1));
+  if (c->dbest_cap < p->P) {
+    dfree(c->dbest);
+    c->dbest_cap = 0;
+    TG_CUDA(dalloc(&c->dbest, (size_t)std::max<int64_t>(p->P, 1)));
+    c->dbest_cap = p->P;
+  }
+  TG_CUDA(cudaMemsetAsync(c->dnhits, 0, sizeof(unsigned long long), st));
+  TG_CUDA(cudaMemsetAsync(c->dbest, 0, sizeof(unsigned long long) * (size_t)std::max<int64_t>(p->P, 1), st));
+  tg_outputs o{};
+  o.hits = c->dhits;
+  o.hit_capacity = hit_capacity;
+  o.n_hits = c->dnhits;
+  o.best = best_host ? c->dbest : nullptr;
+  // the first waits on ev_free find no recorded work and pass
+  for (int64_t m0 = 0, b = 0; m0 < M; m0 += block_markers, ++b) {
+    const int buf = (int)(b & 1);
+    const int64_t rows = std::min<int64_t>(block_markers, M - m0);
+    TG_CUDA(cudaStreamWaitEvent(c->side, c->ev_free[buf], 0));
+    {
+      StageScope s(c, STAGE_H2D, c->side, 0);
+      TG_CUDA(cudaMemcpyAsync(c->stage_buf[buf], G_host + m0 * ldg, (size_t)(rows * ldg),
+                              cudaMemcpyHostToDevice, c->side));
+    }
+    TG_CUDA(cudaEventRecord(c->ev_copied[buf], c->side));
+    TG_CUDA(cudaStreamWaitEvent(st, c->ev_copied[buf], 0));
+    ScanArgs a{c->stage_buf[buf], ldg, encoding, N, rows, marker_offset + m0, nullptr, 0, *opts, o};
+    tg_status s = check_scan_args(c, p, a);
+    if (s != TG_OK) return s;
+    s = scan_impl(c, p, a, st);
+    if (s != TG_OK) return s;
+    TG_CUDA(cudaEventRecord(c->ev_free[buf], st));
+  }
+  unsigned long long nh = 0;
+  TG_CUDA(cudaMemcpyAsync(&nh, c->dnhits, sizeof(nh), cudaMemcpyDeviceToHost, st));
+  TG_CUDA(cudaStreamSynchronize(st));
+  *n_hits = (int64_t)nh;
+  const int64_t ncopy = std::min<int64_t>((int64_t)nh, hit_capacity);
+  if (ncopy > 0)
+    TG_CUDA(cudaMemcpyAsync(hits_host, c->dhits, sizeof(tg_hit) * (size_t)ncopy,
+                            cudaMemcpyDeviceToHost, st));
+  if (best_host)
+    TG_CUDA(cudaMemcpyAsync(best_host, c->dbest, sizeof(unsigned long long) * (size_t)p->P,
+                            cudaMemcpyDeviceToHost, st));
+  TG_CUDA(cudaStreamSynchronize(st));
+  if ((int64_t)nh > hit_capacity) return fail(TG_ERR_CAPACITY, "more hits than hit_capacity");
+  return TG_OK;
+}
+
+tg_status tg_status_poll(tg_ctx* c, void* stream) {
+  TG_ARG(c, "null context");
+  TG_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t word = 0;
+  TG_CUDA(cudaStreamSynchronize(st));
+  TG_CUDA(cudaMemcpy(&word, c->status, sizeof(word), cudaMemcpyDeviceToHost));
+  TG_CUDA(cudaMemset(c->status, 0, sizeof(word)));
+  if (word & ST_TIMEOUT) return fail(TG_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (word & ST_CAPACITY) return fail(TG_ERR_CAPACITY, "more hits than hit_capacity");
+  return TG_OK;
+}
+
+tg_status tg_set_profiling(tg_ctx* c, int enable) {
+  TG_ARG(c, "null context");
+  c->prof = enable != 0;
+  return TG_OK;
+}
+
+tg_status tg_stage_times(tg_ctx* c, double* ms, int64_t* launches, int reset) {
+  TG_ARG(c, "null context");
+  TG_CUDA(cudaSetDevice(c->device));
+  for (auto& ev : c->pending) {
+    TG_CUDA(cudaEventSynchronize(ev.b));
+    float t = 0.f;
+    TG_CUDA(cudaEventElapsedTime(&t, ev.a, ev.b));
+    c->stage_ms[ev.stage] += t;
+    c->event_pool.push_back(ev.a);
+    c->event_pool.push_back(ev.b);
+  }
+  c->pending.clear();
+  for (int i = 0; i < TG_N_STAGES; ++i) {
+    if (ms) ms[i] = c->stage_ms[i];
+    if (launches) launches[i] = c->launches[i];
+    if (reset) {
+      c->stage_ms[i] = 0;
+      c->launches[i] = 0;
+    }
+  }
+  return TG_OK;
+}
+
+tg_status tg_bounded_wait_test(tg_ctx* c, const uint32_t* flag, int64_t limit_ns, void* stream) {
+  TG_ARG(c && flag && limit_ns > 0, "bad argument");
+  TG_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t* res = c->scratch + 8;
+  TG_CUDA(cudaMemsetAsync(res, 0, sizeof(uint32_t), st));
+  TG_CUDA(launch_wait_test(flag, limit_ns, res, st));
+  uint32_t h = 0;
+  TG_CUDA(cudaMemcpyAsync(&h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
+  TG_CUDA(cudaStreamSynchronize(st));
+  if (h == 2u) return fail(TG_ERR_TIMEOUT, "the flag was not set within the limit");
+  if (h != 1u) return fail(TG_ERR_CUDA, "wait kernel did not report");
+  return TG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tg.h"
+
+namespace tg {
+
+// Latched device status bits (ctx->status).
+enum : uint32_t { ST_CAPACITY = 1u, ST_TIMEOUT = 2u };
+
+constexpr int KPAD = 64;     // sample dimension (GEMM K) padding of every operand row
+constexpr int PPAD = 256;    // phenotype rows padding of the panel operands (tensor-core N tile)
+constexpr int QMAX = 64;     // intercept + at most 63 covariates
+constexpr int QCOLS = 64;    // projection columns (Q columns 1..q-1), zero padded
+constexpr int MT = 128;      // marker rows per tensor-core tile
+
+enum Stage { STAGE_DECODE = 0, STAGE_PROJECT = 1, STAGE_NORM = 2, STAGE_GEMM = 3, STAGE_H2D = 4 };
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Per-element statistics inputs shared by both contraction kernels' epilogues.
+struct EpiParams {
+  int M, P;                    // block rows (markers) and panel phenotypes
+  long long marker_offset;
+  double df;                   // N - q - 1
+  float df_f;
+  double lnB;                  // ln Beta(df/2, 1/2)
+  float kappa;                 // allele units per decode unit (1 or 2/255)
+  float r2_thr;                // hit threshold on r^2 (> 1 disables)
+  int do_full, do_hits, do_best;
+  const float* row_inv;        // [M] 1/|a_res| (decode units), NaN = untestable
+  const double* row_inv64;     // [M]
+  const float* col_s;          // [P] s_p, NaN = untestable phenotype
+  const double* col_s64;       // [P]
+  const float* col_rmul;       // [P] 1 or NaN
+  float *beta, *se, *t, *mlp;  // FULL outputs, [M][ldo]
+  long long ldo;
+  tg_hit* hits;
+  long long hit_cap;
+  unsigned long long* n_hits;
+  unsigned long long* best;
+  uint32_t* status;
+};
+
+struct Events {
+  cudaEvent_t a, b;
+  int stage;
+};
+
+}  // namespace tg
+
+struct tg_panel {
+  int device = 0;
+  int64_t N = 0, P = 0, n_cov = 0, q = 0, df = 0, Npad = 0, Ppad = 0;
+  double* X = nullptr;        // [(1+n_cov)][N] design, reduced in place by the QR
+  double* Q = nullptr;        // [q][N] (column-major N x q)
+  double* Yres = nullptr;     // [P][N]
+  double* s = nullptr;        // [P]
+  float* col_s = nullptr;     // [P]
+  float* col_rmul = nullptr;  // [Ppad]
+  __nv_bfloat16* Bhi = nullptr;  // [Ppad][Npad] unit-norm panel, high part
+  __nv_bfloat16* Blo = nullptr;  // [Ppad][Npad] low part
+  float* B32 = nullptr;          // [Ppad][Npad] unit-norm panel in FP32
+  float* QB = nullptr;           // [QCOLS][Npad] Q columns 1..q-1 in FP32 (rest zero)
+  double lnB = 0;
+  CUtensorMap tmBhi, tmBlo;
+};
+
+struct tg_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t side = nullptr;
+  uint32_t* status = nullptr;   // device word (ST_* bits)
+  uint32_t* scratch = nullptr;  // small device scratch (rank, flags)
+  // decode / projection workspace
+  int64_t cap_rows = 0, cap_npad = 0;          // A buffers: rows x npad
+  __nv_bfloat16* Ahi = nullptr;
+  __nv_bfloat16* Alo = nullptr;
+  float* A32 = nullptr;
+  int64_t cap_m = 0;                            // per-marker arrays
+  int32_t* nobs = nullptr;
+  double* mean = nullptr;
+  double* gc2 = nullptr;
+  float* qg = nullptr;                          // [cap_m][QCOLS]
+  double* gres2 = nullptr;
+  float* rinv = nullptr;
+  double* rinv64 = nullptr;
+  int* tflags = nullptr;                        // per 128-row tile: block row has a missing call
+  // host-streamed scan
+  uint8_t* stage_buf[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  tg_hit* dhits = nullptr;
+  int64_t dhits_cap = 0;
+  unsigned long long* dnhits = nullptr;
+  unsigned long long* dbest = nullptr;
+  int64_t dbest_cap = 0;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  // profiling
+  bool prof = false;
+  std::vector<tg::Events> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double stage_ms[TG_N_STAGES] = {0, 0, 0, 0, 0};
+  int64_t launches[TG_N_STAGES] = {0, 0, 0, 0, 0};
+};
+
+namespace tg {
+
+// error reporting (api.cu)
+tg_status fail(tg_status s, const std::string& msg);
+tg_status cuda_fail(cudaError_t e, const char* what);
+
+// panel kernels (k_panel.cu)
+cudaError_t launch_build_design(double* X, const double* C, int64_t ldc, int64_t N, int64_t n_cov,
+                                uint32_t* flags, cudaStream_t st);
+cudaError_t launch_householder(double* X, int64_t N, int64_t k, double* Q, int* rank_out,
+                               int* kept_out, cudaStream_t st);
+cudaError_t launch_residualise(const float* Y, int64_t ldy, const double* Q, int64_t N, int64_t P,
+                               int64_t q, int64_t Npad, double* Yres, double* s, float* col_s,
+                               float* col_rmul, __nv_bfloat16* Bhi, __nv_bfloat16* Blo, float* B32,
+                               uint32_t* flags, cudaStream_t st);
+cudaError_t launch_qcols(const double* Q, int64_t N, int64_t q, int64_t Npad, float* QB,
+                         cudaStream_t st);
+
+// decode (k_decode.cu)
+cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,
+                          const uint32_t* missing, int64_t ldm, int precision, void* Ahi, void* Alo,
+                          int64_t lda, int32_t* nobs, int64_t* S, int64_t* S2, double* mean,
+                          double* gc2, int* tflags, cudaStream_t st);
+
+// SIMT kernels (k_simt.cu)
+cudaError_t launch_project(const void* Ahi, const __nv_bfloat16* Alo, int a_is_f32, int64_t lda,
+                           int64_t M, int64_t K, const float* QB, int64_t nq, float* qg,
+                           cudaStream_t st);
+cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
+                               int64_t nq, float kappa, double* gres2_units_out,
+                               double* norm2_allele_out, float* rinv, double* rinv64,
+                               cudaStream_t st);
+cudaError_t launch_sgemm_scan(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t K,
+                              const EpiParams& ep, cudaStream_t st);
+
+// tensor-core kernel (k_tc.cu)
+cudaError_t launch_tc_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
+                           const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
+                           bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
+                           long long spin_ns, cudaStream_t st);
+
+// bounded wait test (k_tc.cu)
+cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,
+                             cudaStream_t st);
+
+// p-value helpers on the host (pvalue.cuh)
+double host_lnbeta_half(double df);
+double host_r2_threshold(double mlog10p, double df, double lnB);
+
+}  // namespace tg

@@ -1,0 +1,215 @@
+// Genotype decode with mean imputation (Section 2.2: genotypes processed in batches of markers).
+//
+// One warp per marker row. Pass 1 reads the packed row with 16-byte loads and counts,
+// exactly in integers, the observed calls n, their sum S and sum of squares S2 (decode
+// units: allele-1 counts for 2-bit calls, bytes for dosages); mean = S / n is one IEEE
+// division and |g_c|^2 = (n S2 - S^2) / n one more. Pass 2 re-reads the row (cache-hot)
+// and writes the contraction operand with 16-byte stores: the exact code of an observed
+// call, the imputed mean of a missing one, zero past N.
+//
+// 2-bit fields follow the PLINK 1 .bed table: 00 -> 2, 10 -> 1, 11 -> 0, 01 -> missing.
+// With lo = w & 0x55.. and hi = (w >> 1) & 0x55.. per 32-bit word: count 2 = ~lo & ~hi,
+// count 1 = hi & ~lo, count 0 = lo & hi, missing = lo & ~hi.
+#include <cuda_bf16.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace tg {
+namespace {
+
+constexpr int kWarps = 8;
+
+template <int ENC>
+__device__ __forceinline__ void row_stats(const uint8_t* __restrict__ row, int N,
+                                          const uint32_t* __restrict__ mrow, int lane,
+                                          unsigned long long& n, unsigned long long& S,
+                                          unsigned long long& S2) {
+  n = S = S2 = 0;
+  if (ENC == TG_ENC_2BIT) {
+    const int nb = (N + 3) >> 2;
+    const int nchunk = (nb + 15) >> 4;
+    for (int c = lane; c < nchunk; c += 32) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + c);
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int base = c * 64 + q * 16;  // first sample of this word
+        const int left = N - base;
+        if (left <= 0) break;
+        const uint32_t valid =
+            (left >= 16) ? 0x55555555u : (0x55555555u & ((1u << (2 * left)) - 1u));
+        const uint32_t w = w4[q];
+        const uint32_t lo = w & 0x55555555u;
+        const uint32_t hi = (w >> 1) & 0x55555555u;
+        const uint32_t two = ~lo & ~hi & valid;
+        const uint32_t one = hi & ~lo & valid;
+        const uint32_t zero = lo & hi & valid;
+        const int c2 = __popc(two), c1 = __popc(one);
+        n += (unsigned)(c2 + c1 + __popc(zero));
+        S += (unsigned)(2 * c2 + c1);
+        S2 += (unsigned)(4 * c2 + c1);
+      }
+    }
+  } else {
+    const int nchunk = (N + 15) >> 4;
+    for (int c = lane; c < nchunk; c += 32) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + c);
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+      uint32_t mbits = 0;
+      if (mrow) mbits = (mrow[(c * 16) >> 5] >> ((c * 16) & 31)) & 0xFFFFu;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = c * 16 + q * 4 + b;
+          const uint32_t u = (w4[q] >> (8 * b)) & 0xFFu;
+          if (i < N && !((mbits >> (q * 4 + b)) & 1u)) {
+            n += 1;
+            S += u;
+            S2 += u * u;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+    S += __shfl_xor_sync(0xffffffffu, S, o);
+    S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+  }
+}
+
+// 8 decoded samples starting at i0 (a multiple of 8): values and missing bits.
+template <int ENC>
+__device__ __forceinline__ void load8(const uint8_t* __restrict__ row, const uint32_t* __restrict__ mrow,
+                                      int i0, int N, float v[8], uint32_t& miss) {
+  miss = 0;
+  if (ENC == TG_ENC_2BIT) {
+    const uint32_t w = *reinterpret_cast<const uint16_t*>(row + (i0 >> 2));
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const uint32_t f = (w >> (2 * s)) & 3u;
+      v[s] = (f == 0u) ? 2.0f : (f == 2u) ? 1.0f : 0.0f;
+      if (f == 1u && i0 + s < N) miss |= 1u << s;
+    }
+  } else {
+    const uint2 w = *reinterpret_cast<const uint2*>(row + i0);
+    if (mrow) miss = (mrow[i0 >> 5] >> (i0 & 31)) & 0xFFu;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) v[s] = (float)(((s < 4 ? w.x : w.y) >> (8 * (s & 3))) & 0xFFu);
+  }
+#pragma unroll
+  for (int s = 0; s < 8; ++s)
+    if (i0 + s >= N) v[s] = 0.0f;
+  if (i0 + 8 > N) miss &= (N > i0) ? ((1u << (N - i0)) - 1u) : 0u;
+}
+
+template <int ENC, int PREC>
+__global__ void __launch_bounds__(kWarps * 32) k_decode(
+    const uint8_t* __restrict__ G, long long ldg, int N, long long M,
+    const uint32_t* __restrict__ miss, long long ldm, void* __restrict__ Ahi,
+    __nv_bfloat16* __restrict__ Alo, long long lda, int32_t* __restrict__ nobs_out,
+    long long* __restrict__ S_out, long long* __restrict__ S2_out, double* __restrict__ mean_out,
+    double* __restrict__ gc2_out, int* __restrict__ tflags) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long j = (long long)blockIdx.x * kWarps + warp;
+  if (j >= M) return;
+  const uint8_t* row = G + j * ldg;
+  const uint32_t* mrow = miss ? miss + j * ldm : nullptr;
+  unsigned long long n, S, S2;
+  row_stats<ENC>(row, N, mrow, lane, n, S, S2);
+  const double dn = (double)n;
+  const double mean = n ? (double)S / dn : __longlong_as_double(0x7ff8000000000000ll);
+  if (lane == 0) {
+    if (nobs_out) nobs_out[j] = (int32_t)n;
+    if (S_out) S_out[j] = (long long)S;
+    if (S2_out) S2_out[j] = (long long)S2;
+    if (mean_out) mean_out[j] = mean;
+    if (gc2_out) {
+      const long long num = (long long)S2 * (long long)n - (long long)S * (long long)S;
+      gc2_out[j] = n ? (double)num / dn : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    if (tflags && n < (unsigned long long)N) atomicOr(tflags + (j / MT), 1);
+  }
+  // pass 2: operand row
+  const double m_imp = n ? mean : 0.0;
+  const long long steps = lda >> 3;
+  if (PREC == TG_PREC_SPLIT_BF16) {
+    const __nv_bfloat16 mh = __double2bfloat16(m_imp);
+    const __nv_bfloat16 ml = __double2bfloat16(m_imp - (double)__bfloat162float(mh));
+    __nv_bfloat16* ah = reinterpret_cast<__nv_bfloat16*>(Ahi) + j * lda;
+    __nv_bfloat16* al = Alo ? Alo + j * lda : nullptr;
+    for (long long t = lane; t < steps; t += 32) {
+      const int i0 = (int)(t << 3);
+      float v[8];
+      uint32_t ms = 0;
+      if (i0 < N) {
+        load8<ENC>(row, mrow, i0, N, v, ms);
+      } else {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[s] = 0.0f;
+      }
+      __align__(16) __nv_bfloat16 hv[8];
+      __align__(16) __nv_bfloat16 lv[8];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const bool m = (ms >> s) & 1u;
+        hv[s] = m ? mh : __float2bfloat16_rn(v[s]);
+        lv[s] = m ? ml : __float2bfloat16_rn(0.0f);
+      }
+      *reinterpret_cast<uint4*>(ah + i0) = *reinterpret_cast<const uint4*>(hv);
+      if (al) *reinterpret_cast<uint4*>(al + i0) = *reinterpret_cast<const uint4*>(lv);
+    }
+  } else {
+    const float mf = (float)m_imp;
+    float* af = reinterpret_cast<float*>(Ahi) + j * lda;
+    for (long long t = lane; t < steps; t += 32) {
+      const int i0 = (int)(t << 3);
+      float v[8];
+      uint32_t ms = 0;
+      if (i0 < N) {
+        load8<ENC>(row, mrow, i0, N, v, ms);
+      } else {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[s] = 0.0f;
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s)
+        if ((ms >> s) & 1u) v[s] = mf;
+      reinterpret_cast<float4*>(af + i0)[0] = make_float4(v[0], v[1], v[2], v[3]);
+      reinterpret_cast<float4*>(af + i0)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+  }
+}
+
+template <int ENC, int PREC>
+cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32_t* missing,
+               int64_t ldm, void* Ahi, void* Alo, int64_t lda, int32_t* nobs, int64_t* S,
+               int64_t* S2, double* mean, double* gc2, int* tflags, cudaStream_t st) {
+  const unsigned grid = (unsigned)((M + kWarps - 1) / kWarps);
+  k_decode<ENC, PREC><<<grid, kWarps * 32, 0, st>>>(
+      G, ldg, (int)N, M, missing, ldm, Ahi, reinterpret_cast<__nv_bfloat16*>(Alo), lda, nobs,
+      reinterpret_cast<long long*>(S), reinterpret_cast<long long*>(S2), mean, gc2, tflags);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,
+                          const uint32_t* missing, int64_t ldm, int precision, void* Ahi, void* Alo,
+                          int64_t lda, int32_t* nobs, int64_t* S, int64_t* S2, double* mean,
+                          double* gc2, int* tflags, cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  if (encoding == TG_ENC_2BIT) {
+    return precision == TG_PREC_SPLIT_BF16
+               ? go<TG_ENC_2BIT, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, Alo, lda, nobs, S, S2, mean, gc2, tflags, st)
+               : go<TG_ENC_2BIT, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, Alo, lda, nobs, S, S2, mean, gc2, tflags, st);
+  }
+  return precision == TG_PREC_SPLIT_BF16
+             ? go<TG_ENC_U8_DOSAGE, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, Alo, lda, nobs, S, S2, mean, gc2, tflags, st)
+             : go<TG_ENC_U8_DOSAGE, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, Alo, lda, nobs, S, S2, mean, gc2, tflags, st);
+}
+
+}  // namespace tg

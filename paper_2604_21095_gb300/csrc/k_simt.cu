@@ -1,0 +1,289 @@
+// SIMT kernels: marker projection on Q, marker norms, and the plain FP32 scan.
+//
+// Projection (a reading of Section 2.2, where the paper only standardises each marker):
+// every marker is projected on the covariate basis too, so that the correlation with the
+// residualised panel is the exact OLS test. Because every column of the residualised
+// panel is orthogonal to Q (intercept included), g_res . y_res = g_imputed . y_res, so the
+// contraction can use the imputed codes directly and only the norm needs the projection:
+// |g_res|^2 = |g_c|^2 - sum_{k>=1} (q_k . g)^2 (q_0 = the intercept direction drops out).
+//
+// The FP32 scan is the plain-precision form of Eq. 2: FP32 operands, FP32 FFMA, 128 x 128
+// tiles of 8 x 8 per thread, followed by the same fused epilogue as the tensor-core path.
+#include <cuda_bf16.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace tg {
+namespace {
+
+// ---------------------------------------------------------------- projection
+// qg[m][k] = sum_i A[m][i] QB[k][i]; tile 64 markers x 32 columns, 32 samples per step.
+template <bool F32>
+__global__ void __launch_bounds__(256) k_project(const void* __restrict__ Ahi_,
+                                                 const __nv_bfloat16* __restrict__ Alo,
+                                                 long long lda, long long M, int K,
+                                                 const float* __restrict__ QB, int nq,
+                                                 float* __restrict__ qg) {
+  __shared__ __align__(16) float As[32][64 + 4];
+  __shared__ __align__(16) float Qs[32][32 + 4];
+  const int tid = threadIdx.x;
+  const long long m0 = (long long)blockIdx.x * 64;
+  const int k0 = blockIdx.y * 32;
+  const int tx = tid & 15, ty = tid >> 4;  // 2 columns (k) x 4 markers per thread
+  // FP32 partial sums over 256 samples, flushed into FP64 totals
+  float acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  double tot[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  for (int i0 = 0; i0 < K; i0 += 32) {
+    // A tile: 64 rows x 32 samples
+    if (F32) {
+      const float* A = reinterpret_cast<const float*>(Ahi_);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = tid + u * 256;       // 512 float4
+        const int r = e >> 3, c4 = (e & 7) * 4;
+        const long long gm = m0 + r;
+        float4 v = make_float4(0, 0, 0, 0);
+        if (gm < M) v = *reinterpret_cast<const float4*>(A + gm * lda + i0 + c4);
+        As[c4 + 0][r] = v.x;
+        As[c4 + 1][r] = v.y;
+        As[c4 + 2][r] = v.z;
+        As[c4 + 3][r] = v.w;
+      }
+    } else {
+      const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(Ahi_);
+      const int r = tid >> 2, c8 = (tid & 3) * 8;  // 256 x 8 bf16
+      const long long gm = m0 + r;
+      float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (gm < M) {
+        const uint4 h = *reinterpret_cast<const uint4*>(A + gm * lda + i0 + c8);
+        const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&h);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) v[s] = __bfloat162float(hb[s]);
+        if (Alo) {
+          const uint4 l = *reinterpret_cast<const uint4*>(Alo + gm * lda + i0 + c8);
+          const __nv_bfloat16* lb = reinterpret_cast<const __nv_bfloat16*>(&l);
+#pragma unroll
+          for (int s = 0; s < 8; ++s) v[s] += __bfloat162float(lb[s]);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) As[c8 + s][r] = v[s];
+    }
+    {  // Q tile: 32 columns x 32 samples
+      const int r = tid >> 3, c4 = (tid & 7) * 4;
+      const float4 v = *reinterpret_cast<const float4*>(QB + (long long)(k0 + r) * K + i0 + c4);
+      Qs[c4 + 0][r] = v.x;
+      Qs[c4 + 1][r] = v.y;
+      Qs[c4 + 2][r] = v.z;
+      Qs[c4 + 3][r] = v.w;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[i][ty * 4]);
+      const float2 q = *reinterpret_cast<const float2*>(&Qs[i][tx * 2]);
+      acc[0][0] += a.x * q.x; acc[0][1] += a.x * q.y;
+      acc[1][0] += a.y * q.x; acc[1][1] += a.y * q.y;
+      acc[2][0] += a.z * q.x; acc[2][1] += a.z * q.y;
+      acc[3][0] += a.w * q.x; acc[3][1] += a.w * q.y;
+    }
+    __syncthreads();
+    if (((i0 >> 5) & 7) == 7 || i0 + 32 >= K) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          tot[a][b] += (double)acc[a][b];
+          acc[a][b] = 0.0f;
+        }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const long long gm = m0 + ty * 4 + a;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int k = k0 + tx * 2 + b;
+      if (k < nq) qg[gm * QCOLS + k] = (float)tot[a][b];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- marker norms
+__global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
+                              const double* __restrict__ gc2, const float* __restrict__ qg, int nq,
+                              float kappa, double* __restrict__ gres2u,
+                              double* __restrict__ norm2_allele, float* __restrict__ rinv,
+                              double* __restrict__ rinv64) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const double c2 = gc2[j];
+  double s = 0.0;
+  for (int k = 0; k < nq; ++k) {
+    const double v = (double)qg[j * QCOLS + k];
+    s += v * v;
+  }
+  const double r2 = c2 - s;
+  const bool ok = nobs[j] > 0 && c2 > 0.0 && r2 > 1e-5 * c2;  // untestable: R^2 on covariates >= 0.99999
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const double inv = ok ? 1.0 / sqrt(r2) : nan;
+  gres2u[j] = ok ? r2 : nan;
+  if (norm2_allele) norm2_allele[j] = ok ? r2 * (double)kappa * (double)kappa : nan;
+  rinv[j] = (float)inv;
+  rinv64[j] = inv;
+}
+
+// ---------------------------------------------------------------- FP32 scan
+constexpr int BM = 128, BN = 128, BK = 16;
+
+__global__ void __launch_bounds__(256, 1) k_sgemm_scan(const float* __restrict__ A, long long lda,
+                                                    const float* __restrict__ B, long long ldb,
+                                                    int K, EpiParams ep) {
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  __shared__ unsigned long long colbest[BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const long long m0 = (long long)blockIdx.y * BM;
+  const int n0 = blockIdx.x * BN;
+  // global -> smem mapping: each thread moves 2 float4 of A and 2 of B per K step
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  const float* Ag0 = A + (m0 + lr) * lda + lk;
+  const float* Ag1 = A + (m0 + lr + 64) * lda + lk;
+  const float* Bg0 = B + (long long)(n0 + lr) * ldb + lk;
+  const float* Bg1 = B + (long long)(n0 + lr + 64) * ldb + lk;
+  if (tid < BN) colbest[tid] = 0ull;
+
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+
+  float4 ra0 = *reinterpret_cast<const float4*>(Ag0);
+  float4 ra1 = *reinterpret_cast<const float4*>(Ag1);
+  float4 rb0 = *reinterpret_cast<const float4*>(Bg0);
+  float4 rb1 = *reinterpret_cast<const float4*>(Bg1);
+  int buf = 0;
+  auto stash = [&](int bf) {
+    As[bf][lk + 0][lr] = ra0.x; As[bf][lk + 1][lr] = ra0.y; As[bf][lk + 2][lr] = ra0.z; As[bf][lk + 3][lr] = ra0.w;
+    As[bf][lk + 0][lr + 64] = ra1.x; As[bf][lk + 1][lr + 64] = ra1.y; As[bf][lk + 2][lr + 64] = ra1.z; As[bf][lk + 3][lr + 64] = ra1.w;
+    Bs[bf][lk + 0][lr] = rb0.x; Bs[bf][lk + 1][lr] = rb0.y; Bs[bf][lk + 2][lr] = rb0.z; Bs[bf][lk + 3][lr] = rb0.w;
+    Bs[bf][lk + 0][lr + 64] = rb1.x; Bs[bf][lk + 1][lr + 64] = rb1.y; Bs[bf][lk + 2][lr + 64] = rb1.z; Bs[bf][lk + 3][lr + 64] = rb1.w;
+  };
+  stash(0);
+  __syncthreads();
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    const bool more = k0 + BK < K;
+    if (more) {
+      ra0 = *reinterpret_cast<const float4*>(Ag0 + k0 + BK);
+      ra1 = *reinterpret_cast<const float4*>(Ag1 + k0 + BK);
+      rb0 = *reinterpret_cast<const float4*>(Bg0 + k0 + BK);
+      rb1 = *reinterpret_cast<const float4*>(Bg1 + k0 + BK);
+    }
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+    if (more) {
+      stash(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+
+  // epilogue: rows m0 + {ty*4 + a, 64 + ty*4 + a}, columns n0 + {tx*4 + b, 64 + tx*4 + b}
+  unsigned long long cb[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) cb[b] = 0ull;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const long long row = m0 + (a < 4 ? ty * 4 + a : 64 + ty * 4 + (a - 4));
+    if (row >= ep.M) continue;
+    const float rinv = ep.row_inv[row];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int col = n0 + (b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4));
+      if (col >= ep.P) continue;
+      const float D = acc[a][b];
+      const float r = corr_nan(D, rinv, ep.col_rmul[col]);
+      if (ep.do_best) {
+        const unsigned long long key = best_key(r, ep.marker_offset + row);
+        cb[b] = key > cb[b] ? key : cb[b];
+      }
+      if (ep.do_hits && r * r >= ep.r2_thr) emit_hit(ep, D, (int)row, col);
+      if (ep.do_full) {
+        float be, se, t, mlp;
+        elem_full(ep, r, ep.col_s[col], rinv, be, se, t, mlp);
+        const long long o = row * ep.ldo + col;
+        if (ep.beta) ep.beta[o] = be;
+        if (ep.se) ep.se[o] = se;
+        if (ep.t) ep.t[o] = t;
+        if (ep.mlp) ep.mlp[o] = mlp;
+      }
+    }
+  }
+  if (ep.do_best) {
+    // the two ty of a warp share columns: combine, then one shared atomic per column and warp
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, cb[b], 16);
+      cb[b] = o > cb[b] ? o : cb[b];
+    }
+    if ((tid & 16) == 0) {
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int c = b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4);
+        if (cb[b]) atomicMax(&colbest[c], cb[b]);
+      }
+    }
+    __syncthreads();
+    if (tid < BN && n0 + tid < ep.P && colbest[tid]) atomicMax(ep.best + n0 + tid, colbest[tid]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_project(const void* Ahi, const __nv_bfloat16* Alo, int a_is_f32, int64_t lda,
+                           int64_t M, int64_t K, const float* QB, int64_t nq, float* qg,
+                           cudaStream_t st) {
+  if (M == 0 || nq == 0) return cudaSuccess;
+  dim3 grid((unsigned)((M + 63) / 64), (unsigned)((nq + 31) / 32));
+  if (a_is_f32)
+    k_project<true><<<grid, 256, 0, st>>>(Ahi, nullptr, lda, M, (int)K, QB, (int)nq, qg);
+  else
+    k_project<false><<<grid, 256, 0, st>>>(Ahi, Alo, lda, M, (int)K, QB, (int)nq, qg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
+                               int64_t nq, float kappa, double* gres2_units_out,
+                               double* norm2_allele_out, float* rinv, double* rinv64,
+                               cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  k_marker_norm<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, nobs, gc2, qg, (int)nq, kappa,
+                                                             gres2_units_out, norm2_allele_out,
+                                                             rinv, rinv64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sgemm_scan(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t K,
+                              const EpiParams& ep, cudaStream_t st) {
+  if (ep.M == 0 || ep.P == 0) return cudaSuccess;
+  dim3 grid((unsigned)((ep.P + BN - 1) / BN), (unsigned)((ep.M + BM - 1) / BM));
+  k_sgemm_scan<<<grid, 256, 0, st>>>(A, lda, B, ldb, (int)K, ep);
+  return cudaGetLastError();
+}
+
+}  // namespace tg

@@ -1,0 +1,424 @@
+// Tensor-core scan: Eq. 2 of Section 2.2 on tcgen05, fused with Eq. 3 and the p-value.
+//
+// D = A (B_hi + B_lo)^T [+ A_lo B_hi^T] for a block of markers against the whole panel:
+//   A     [M][K] bf16  exact genotype codes (or dosage bytes); a missing call holds bf16(mean)
+//   A_lo  [M][K] bf16  mean - bf16(mean) at missing calls, 0 elsewhere (2-bit / masked blocks)
+//   B_hi, B_lo [P][K]  bf16 split of the unit-norm residualised panel, y ~= hi + lo
+// K = samples (zero padded), FP32 accumulation in tensor memory.
+//
+// Persistent kernel, one CTA per SM, 192 threads, warp-specialised:
+//   warp 0 lane 0  TMA producer: 128x32 A tiles and 256x32 B tiles (64-byte swizzle) into a
+//                  ring of shared-memory stages, completion tracked by mbarrier transaction bytes
+//   warp 1 lane 0  MMA issuer: per 32-wide K step, 2 x (2 or 3) tcgen05.mma 128x256x16 into an
+//                  FP32 accumulator in TMEM; two accumulators (512 columns) so the epilogue of
+//                  one tile overlaps the products of the next
+//   warps 2..5     epilogue: tcgen05.ld of the 128 x 256 accumulator (thread = marker row),
+//                  r = D / |g_res|, hits above the r^2 threshold, per-phenotype best marker,
+//                  optionally every statistic.
+// Every mbarrier wait is bounded: past the limit the kernel latches ST_TIMEOUT, raises a
+// shared abort flag, lets in-flight copies and products finish (again bounded), frees its
+// TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace tg {
+namespace {
+
+constexpr int TBM = 128, TBN = 256, TBK = 32;  // TBK bf16 = 64 bytes = one swizzle row
+constexpr int A_BYTES = TBM * TBK * 2;         // 8 KB
+constexpr int B_BYTES = TBN * TBK * 2;         // 16 KB
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 512;                 // two 128 x 256 FP32 accumulators
+constexpr int kGroupM = 8;                     // raster: 8 m-tiles per group
+
+template <bool HAS_LO>
+struct Cfg {
+  static constexpr int kStageBytes = A_BYTES * (HAS_LO ? 2 : 1) + 2 * B_BYTES;
+  static constexpr int kStages = HAS_LO ? 4 : 5;
+  static constexpr int kBarBytes = 256;
+  static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;  // + alignment slack
+};
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
+// both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
+                            ((uint32_t)(TBM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of 64 bytes,
+// 8-row core groups 512 bytes apart (SBO), version 1, start address >> 4.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)4 << 61;            // layout: 64-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// Bounded wait for the completion of phase `parity`; false on timeout or abort.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                       long long limit_ns, uint32_t* status) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if ((long long)(globaltimer_ns() - t0) > limit_ns) {
+      *abort_flag = 1;
+      atomicOr(status, ST_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint32_t dst, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tile_coord(int tile, int n_mt, int n_nt, int& mt, int& nt) {
+  const int group = kGroupM * n_nt;
+  const int g = tile / group;
+  const int first = g * kGroupM;
+  const int gm = min(kGroupM, n_mt - first);
+  const int idx = tile - g * group;
+  mt = first + idx % gm;
+  nt = idx / gm;
+}
+
+// Epilogue of 32 accumulator columns held by one thread (its marker row).
+__device__ __forceinline__ void epilogue_chunk(const EpiParams& ep, const float v[32], long long row,
+                                               bool row_ok, float rinv, int col0, int lane) {
+  unsigned long long key[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int col = col0 + i;
+    float r = __int_as_float(0x7fc00000);
+    if (row_ok && col < ep.P) r = corr_nan(v[i], rinv, ep.col_rmul[col]);
+    key[i] = ep.do_best ? best_key(r, ep.marker_offset + row) : 0ull;
+    if (ep.do_hits && r * r >= ep.r2_thr) emit_hit(ep, v[i], (int)row, col);
+    if (ep.do_full && row_ok && col < ep.P) {
+      float be, se, t, mlp;
+      elem_full(ep, r, ep.col_s[col], rinv, be, se, t, mlp);
+      const long long o = row * ep.ldo + col;
+      if (ep.beta) ep.beta[o] = be;
+      if (ep.se) ep.se[o] = se;
+      if (ep.t) ep.t[o] = t;
+      if (ep.mlp) ep.mlp[o] = mlp;
+    }
+  }
+  if (!ep.do_best) return;
+  // reduce-scatter over the warp: afterwards lane l holds the max key of column col0 + l
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const unsigned long long send = upper ? key[i] : key[i + s];
+      const unsigned long long keep = upper ? key[i + s] : key[i];
+      const unsigned long long got = __shfl_xor_sync(0xffffffffu, send, s);
+      key[i] = keep > got ? keep : got;
+    }
+  }
+  const int col = col0 + lane;
+  if (col < ep.P && key[0] != 0ull) atomicMax(ep.best + col, key[0]);
+}
+
+template <bool HAS_LO>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+              const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+              int num_kb, int n_mt, int n_nt, const int* __restrict__ tflags, long long spin_ns,
+              EpiParams ep) {
+  using C = Cfg<HAS_LO>;
+  constexpr int S = C::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t bars = base + S * C::kStageBytes;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (S + s); };
+  auto tfull_bar = [&](int a) { return bars + 8u * (2 * S + a); };
+  auto tempty_bar = [&](int a) { return bars + 8u * (2 * S + 2 + a); };
+  const uint32_t drain_bar = bars + 8u * (2 * S + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * C::kStageBytes + 8 * (2 * S + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  auto sA = [&](int s) { return base + s * C::kStageBytes; };
+  auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
+  auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + B_BYTES; };
+  auto sAlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * B_BYTES; };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 4);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+  const int num_tiles = n_mt * n_nt;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA producer
+    int stage = 0;
+    uint32_t phase = 0;
+    int armed[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) armed[s] = -1;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      int mt, nt;
+      tile_coord(tile, n_mt, n_nt, mt, nt);
+      const bool lo = HAS_LO && tflags[mt] != 0;
+      const uint32_t bytes = A_BYTES + 2 * B_BYTES + (lo ? A_BYTES : 0);
+      for (int kb = 0; kb < num_kb; ++kb) {
+        if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, spin_ns, ep.status)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(full_bar(stage), bytes);
+        armed[stage] = (int)phase;
+        tma_load_2d(&tmAhi, sA(stage), full_bar(stage), kb * TBK, mt * TBM);
+        tma_load_2d(&tmBhi, sBhi(stage), full_bar(stage), kb * TBK, nt * TBN);
+        tma_load_2d(&tmBlo, sBlo(stage), full_bar(stage), kb * TBK, nt * TBN);
+        if (lo) tma_load_2d(&tmAlo, sAlo(stage), full_bar(stage), kb * TBK, mt * TBM);
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+    // copies still in flight land before the CTA leaves (bounded)
+    for (int s = 0; s < S; ++s)
+      if (armed[s] >= 0) mbar_wait(full_bar(s), (uint32_t)armed[s], abort_flag, spin_ns, ep.status);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    int stage = 0;
+    uint32_t phase = 0;
+    int local = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++local) {
+      int mt, nt;
+      tile_coord(tile, n_mt, n_nt, mt, nt);
+      const bool lo = HAS_LO && tflags[mt] != 0;
+      const int acc = local & 1;
+      const uint32_t acc_phase = (uint32_t)(local >> 1) & 1u;
+      if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, spin_ns, ep.status)) break;
+      tc_fence_after();
+      const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
+      for (int kb = 0; kb < num_kb; ++kb) {
+        if (!mbar_wait(full_bar(stage), phase, abort_flag, spin_ns, ep.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int k = 0; k < TBK / 16; ++k) {
+          const uint64_t a = sdesc_sw64(sA(stage) + 32u * k);
+          const uint64_t bh = sdesc_sw64(sBhi(stage) + 32u * k);
+          const uint64_t bl = sdesc_sw64(sBlo(stage) + 32u * k);
+          tc_mma(d, a, bh, (kb | k) != 0 ? 1u : 0u);
+          tc_mma(d, a, bl, 1u);
+          if (lo) tc_mma(d, sdesc_sw64(sAlo(stage) + 32u * k), bh, 1u);
+        }
+        tc_commit(empty_bar(stage));
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (ok) tc_commit(tfull_bar(acc));
+    }
+    // every product issued so far completes before TMEM is released (bounded)
+    tc_commit(drain_bar);
+    mbar_wait(drain_bar, 0u, abort_flag, spin_ns, ep.status);
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int quarter = warp & 3;  // TMEM lanes this warp may read
+    int local = 0;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++local) {
+      int mt, nt;
+      tile_coord(tile, n_mt, n_nt, mt, nt);
+      const int acc = local & 1;
+      const uint32_t acc_phase = (uint32_t)(local >> 1) & 1u;
+      if (!mbar_wait(tfull_bar(acc), acc_phase, abort_flag, spin_ns, ep.status)) break;
+      tc_fence_after();
+      const long long row = (long long)mt * TBM + quarter * 32 + lane;
+      const bool row_ok = row < ep.M;
+      const float rinv = row_ok ? ep.row_inv[row] : __int_as_float(0x7fc00000);
+      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TBN);
+#pragma unroll 1
+      for (int c = 0; c < TBN / 32; ++c) {
+        float v[32];
+        __syncwarp();  // tcgen05.ld is .sync.aligned: the warp reconverges after hit branches
+        tc_ld32(tbase + (uint32_t)(c * 32), v);
+        epilogue_chunk(ep, v, row, row_ok, rinv, nt * TBN + c * 32, lane);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(acc));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+__global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, uint32_t* result) {
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+    if (*flag) {
+      *result = 1u;
+      return;
+    }
+    if ((long long)(globaltimer_ns() - t0) > limit_ns) {
+      *result = 2u;
+      return;
+    }
+    __nanosleep(1000);
+  }
+}
+
+template <bool HAS_LO>
+cudaError_t go(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* bh,
+               const CUtensorMap* bl, int64_t K, const int* tflags, const EpiParams& ep,
+               int sm_count, long long spin_ns, cudaStream_t st) {
+  using C = Cfg<HAS_LO>;
+  static bool attr_set = false;  // per process; the attribute is per function
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_scan<HAS_LO>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int n_mt = (ep.M + TBM - 1) / TBM;
+  const int n_nt = (ep.P + TBN - 1) / TBN;
+  const int tiles = n_mt * n_nt;
+  const int grid = tiles < sm_count ? tiles : sm_count;
+  k_tc_scan<HAS_LO><<<grid, kThreads, C::kSmem, st>>>(*a, *alo, *bh, *bl, (int)(K / TBK), n_mt,
+                                                       n_nt, tflags, spin_ns, ep);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
+                           const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
+                           bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
+                           long long spin_ns, cudaStream_t st) {
+  if (ep.M == 0 || ep.P == 0) return cudaSuccess;
+  if (K % TBK) return cudaErrorInvalidValue;
+  return has_lo ? go<true>(tmAhi, tmAlo, tmBhi, tmBlo, K, tflags, ep, sm_count, spin_ns, st)
+                : go<false>(tmAhi, tmAhi, tmBhi, tmBlo, K, tflags, ep, sm_count, spin_ns, st);
+}
+
+cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,
+                             cudaStream_t st) {
+  k_wait_test<<<1, 1, 0, st>>>(flag, limit_ns, result);
+  return cudaGetLastError();
+}
+
+}  // namespace tg

@@ -1,0 +1,121 @@
+"""Parity at the full benchmark size, N = 23,000 samples, P = 20,480 phenotypes, 20 covariate
+columns, 8-bit dosages, 65,536-marker blocks, split-BF16 tensor-core scan with hit collection
+(the configuration the benchmark times). The oracle recomputes sampled outputs one by one:
+every hit, every planted pair, the best marker of sampled phenotypes and sampled marker norms.
+A second case writes every statistic for a 256-marker block at the same N and P and compares
+a sample of elements."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2604_21095_gb300 as tg
+import synth
+from scan_util import run_scan
+
+pytestmark = pytest.mark.gpu
+
+W = synth.WORKLOADS["n23000_m8900000_p20480_c20_u8"]
+THR = 7.30103  # -log10(5e-8)
+
+
+@pytest.fixture(scope="module")
+def full(tgctx):
+    torch.cuda.synchronize()
+    pan = synth.make_panel(W, device="cuda", planted_blocks=1)
+    panel = tg.tg_prepare_panel(tgctx, pan["Yt"], W.N, W.P, pan["cov_t"])
+    blk = synth.make_block(W, 0, device="cuda")
+    yield pan, panel, blk
+    tg.tg_panel_free(panel)
+
+
+def _sub_oracle(pan, blk, markers, phenos):
+    """Oracle statistics for the sub-block of `markers` against the sub-panel of `phenos`."""
+    Y = pan["Yt"][phenos].cpu().numpy().T.astype(np.float64)
+    C = pan["cov_t"].cpu().numpy().T
+    ref_panel = oracle.prepare_panel(Y, C)
+    G = blk["G"][markers].cpu().numpy()
+    return oracle.scan(G, "u8", ref_panel, mode="projected")
+
+
+def test_fullsize_hits_planted_best_norms(tgctx, full):
+    pan, panel, blk = full
+    res = run_scan(tgctx, panel, blk["G"], W.N, W.P, "u8", "split", full=False, hit_mlog10p=THR,
+                   hit_capacity=1 << 20)
+    assert res["status"] == tg.TG_OK
+    hits = res["hits"]
+    assert 0 < len(hits) == res["n_hits"]
+    # every planted pair is a hit
+    got = {(int(h["marker"]), int(h["pheno"])) for h in hits}
+    for m, p in pan["pairs"]:
+        assert (m, p) in got, (m, p)
+    # every hit agrees with the oracle, recomputed pair by pair
+    markers = sorted({int(h["marker"]) for h in hits})
+    phenos = sorted({int(h["pheno"]) for h in hits})
+    ref = _sub_oracle(pan, blk, markers, phenos)
+    mi = {m: i for i, m in enumerate(markers)}
+    pi = {p: i for i, p in enumerate(phenos)}
+    worst = {"mlog10p": 0.0, "beta_rel": 0.0}
+    for h in hits:
+        j, p = mi[int(h["marker"])], pi[int(h["pheno"])]
+        mo = ref["mlog10p"][j, p]
+        d = abs(h["mlog10p"] - mo)
+        assert d <= max(1e-3, 1e-5 * mo), (h, mo)
+        assert mo >= THR - max(1e-3, 1e-5 * mo)
+        b, se = ref["beta"][j, p], ref["se"][j, p]
+        db = abs(h["beta"] - b) / max(abs(b), se)
+        assert db <= 1e-4, (h, b)
+        assert abs(h["se"] - se) <= 1e-4 * se
+        worst["mlog10p"] = max(worst["mlog10p"], d)
+        worst["beta_rel"] = max(worst["beta_rel"], db)
+    print(f"\nfull size: {len(hits)} hits, max errors vs oracle {worst}")
+    # best marker of planted phenotypes is the planted marker
+    for m, p in pan["pairs"][:8]:
+        assert res["best_marker"][p] == m
+    # marker norms for a sample of markers
+    rng = np.random.default_rng(0)
+    sm = np.sort(rng.choice(blk["M"], 128, replace=False))
+    refm = _sub_oracle(pan, blk, sm.tolist(), [0])
+    assert np.allclose(res["norm2"][sm], refm["gres2"], rtol=1e-6)
+    assert np.array_equal(res["nobs"][sm], refm["decode"]["n_obs"])
+
+
+def test_fullsize_best_of_a_null_phenotype(tgctx, full):
+    pan, panel, blk = full
+    planted = {p for _, p in pan["pairs"]}
+    p0 = next(p for p in range(W.P) if p not in planted)
+    res = run_scan(tgctx, panel, blk["G"], W.N, W.P, "u8", "split", full=False, hit_mlog10p=THR,
+                   hit_capacity=1 << 20)
+    best = -1.0
+    arg = -1
+    for m0 in range(0, blk["M"], 8192):
+        idx = list(range(m0, min(blk["M"], m0 + 8192)))
+        r = np.abs(_sub_oracle(pan, blk, idx, [p0])["r"][:, 0])
+        j = int(np.nanargmax(r))
+        if r[j] > best:
+            best, arg = float(r[j]), m0 + j
+    jg = int(res["best_marker"][p0])
+    rg = abs(_sub_oracle(pan, blk, [jg], [p0])["r"][0, 0])
+    assert rg >= best - 1e-6, (jg, rg, arg, best)
+    assert abs(res["best_absr"][p0] - rg) <= 1e-6
+
+
+def test_fullsize_every_statistic_sampled(tgctx, full):
+    pan, panel, blk = full
+    G = blk["G"][:256].contiguous()
+    res = run_scan(tgctx, panel, G, W.N, W.P, "u8", "split", full=True)
+    rng = np.random.default_rng(1)
+    markers = np.sort(rng.choice(256, 48, replace=False)).tolist()
+    phenos = np.sort(rng.choice(W.P, 300, replace=False)).tolist()
+    ref = _sub_oracle(pan, {"G": G}, markers, phenos)
+    for k in ("mlog10p", "beta", "se", "t"):
+        sub = res[k][np.ix_(markers, phenos)]
+        assert np.isfinite(sub).all()
+    sub = lambda k: res[k][np.ix_(markers, phenos)]
+    dm = np.abs(sub("mlog10p") - ref["mlog10p"])
+    assert np.all(dm <= np.maximum(1e-3, 1e-5 * ref["mlog10p"]))
+    db = np.abs(sub("beta") - ref["beta"])
+    assert np.all(db <= 1e-4 * np.maximum(np.abs(ref["beta"]), ref["se"]))
+    assert np.all(np.abs(sub("se") - ref["se"]) <= 1e-4 * ref["se"])
+    print(f"\nfull size FULL output, sampled max errors: -log10p {dm.max():.2e}, "
+          f"beta/max(|beta|,se) {(db / np.maximum(np.abs(ref['beta']), ref['se'])).max():.2e}")

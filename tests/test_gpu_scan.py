@@ -1,0 +1,181 @@
+"""GPU parity of the whole block scan (decode, projection, contraction, epilogue) against
+the FP64 oracle, for both precision forms and both genotype encodings, at sizes that span
+several tiles in both directions with ragged edges, plus the degenerate cases."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2604_21095_gb300 as tg
+import synth
+from scan_util import compare_best, compare_full, compare_hits, oracle_panel, run_scan
+
+pytestmark = pytest.mark.gpu
+
+THR = 5.0  # hit threshold (-log10 p) for the small cases: planted effects pass it
+
+
+def _case(encoding, N=2000, M=1000, P=300, n_cov=4, missing=0.01, seed=11, masked=False):
+    w = synth.Workload(f"test_{encoding}_{N}_{M}_{P}", N=N, M=M, P=P, n_cov=n_cov,
+                       encoding=encoding, missing=missing if not masked else 0.0, seed=seed,
+                       block=M, causal_per_pheno=2)
+    pan = synth.make_panel(w)
+    blk = synth.make_block(w, 0)
+    miss = None
+    if masked:
+        miss = synth.missing_words(seed, 0, M, N, missing)
+    return w, pan, blk, miss
+
+
+@pytest.fixture(scope="module")
+def panels(tgctx):
+    made = {}
+    yield made
+    for p in made.values():
+        tg.tg_panel_free(p)
+
+
+def _panel(tgctx, panels, key, pan, N, P):
+    if key not in panels:
+        cov = pan["cov_t"]
+        panels[key] = tg.tg_prepare_panel(tgctx, pan["Yt"].cuda(), N, P,
+                                          cov.cuda() if cov.shape[0] else None)
+    return panels[key]
+
+
+@pytest.mark.parametrize("encoding,masked", [("2bit", False), ("u8", False), ("u8", True)])
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_scan_matches_oracle(tgctx, panels, encoding, masked, precision):
+    w, pan, blk, miss = _case(encoding, masked=masked)
+    panel = _panel(tgctx, panels, ("main", encoding, masked), pan, w.N, w.P)
+    G = blk["G"].cuda()
+    res = run_scan(tgctx, panel, G, w.N, w.P, encoding, precision, full=True, hit_mlog10p=THR,
+                   missing=None if miss is None else miss.cuda(), marker_offset=7)
+    assert res["status"] == tg.TG_OK
+    ref_panel = oracle_panel(pan["Yt"], pan["cov_t"])
+    ref = oracle.scan(blk["G"].numpy(), encoding, ref_panel,
+                      None if miss is None else miss.numpy(), mode="projected")
+    err = compare_full(res, ref, label=f"{encoding}/{precision}")
+    want, got = compare_hits(res, ref, THR, marker_offset=7)
+    assert want >= 2 * w.P * 0.5 and got > 0
+    compare_best(res, ref)
+    dec = ref["decode"]
+    assert np.array_equal(res["nobs"], dec["n_obs"])
+    assert np.array_equal(res["mean"], dec["mean_units"])
+    ok = np.isfinite(ref["gres2"])
+    assert np.array_equal(np.isfinite(res["norm2"]), ok)
+    assert np.allclose(res["norm2"][ok], ref["gres2"][ok], rtol=1e-6)
+    print(f"\nmax |error| vs FP64 oracle, {encoding}{'+mask' if masked else ''}/{precision}: {err}")
+
+
+def test_scan_direct_oracle_agrees(tgctx, panels):
+    """The direct-OLS oracle (the definition) on a slice of the same case."""
+    w, pan, blk, _ = _case("2bit")
+    panel = _panel(tgctx, panels, ("main", "2bit", False), pan, w.N, w.P)
+    G = blk["G"][:64].cuda()
+    res = run_scan(tgctx, panel, G, w.N, w.P, "2bit", "split", full=True)
+    ref_panel = oracle_panel(pan["Yt"], pan["cov_t"])
+    ref = oracle.scan(blk["G"][:64].numpy(), "2bit", ref_panel, mode="direct")
+    ok = np.isfinite(ref["t"])
+    assert np.all(np.abs(res["mlog10p"][ok] - ref["mlog10p"][ok]) <= np.maximum(1e-3, 1e-5 * ref["mlog10p"][ok]))
+    assert np.all(np.abs(res["beta"][ok] - ref["beta"][ok]) <= 1e-4 * np.maximum(np.abs(ref["beta"][ok]), ref["se"][ok]))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_intercept_only_is_pearson(tgctx, precision):
+    """No covariates: q = 1, df = N - 2 and r is the Pearson correlation (Eq. 2, Eq. 3 as printed)."""
+    N, M, P = 1999, 130, 3
+    cov = synth.covariates(21, N, 0)
+    Yt = synth.phenotypes(21, cov, P)
+    counts, miss = synth.hard_calls(21, 0, synth.maf(21, 0, M), N, 0.0)
+    G = synth.pack_2bit(counts, miss)
+    panel = tg.tg_prepare_panel(tgctx, Yt.cuda(), N, P, None)
+    try:
+        assert tg.tg_panel_info(panel)[2:] == (1, N - 2)
+        res = run_scan(tgctx, panel, G.cuda(), N, P, "2bit", precision, full=True)
+    finally:
+        tg.tg_panel_free(panel)
+    g = counts.numpy().astype(np.float64)
+    y = Yt.numpy().T.astype(np.float64)
+    for j in range(0, M, 13):
+        for p in range(P):
+            r = np.corrcoef(g[j], y[:, p])[0, 1]
+            t = r * math.sqrt((N - 2) / (1 - r * r))
+            assert abs(res["t"][j, p] - t) <= 2e-5 * max(1.0, abs(t))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_degenerate_markers_and_phenotypes(tgctx, precision):
+    N, M, P = 301, 9, 5
+    cov = synth.covariates(31, N, 3)
+    counts, miss = synth.hard_calls(31, 0, synth.maf(31, 0, M, lo=0.2), N, 0.05)
+    miss[0] = True                               # every call missing
+    counts[1] = 1
+    miss[1] = False                              # monomorphic
+    cov[2] = counts[2].double()                  # marker 2 lies in the covariate span
+    miss[2] = False
+    Yt = synth.phenotypes(31, cov, P)
+    Yt[3] = 1.25                                 # constant phenotype
+    G = synth.pack_2bit(counts, miss)
+    panel = tg.tg_prepare_panel(tgctx, Yt.cuda(), N, P, cov.cuda())
+    try:
+        res = run_scan(tgctx, panel, G.cuda(), N, P, "2bit", precision, full=True, hit_mlog10p=0.01)
+    finally:
+        tg.tg_panel_free(panel)
+    for k in ("beta", "se", "t", "mlog10p"):
+        assert np.isnan(res[k][:3]).all() and np.isnan(res[k][:, 3]).all()
+        assert np.isfinite(res[k][3:, [0, 1, 2, 4]]).all()
+    assert np.isnan(res["norm2"][:3]).all()
+    assert res["nobs"][0] == 0 and np.isnan(res["mean"][0])
+    for h in res["hits"]:
+        assert h["marker"] >= 3 and h["pheno"] != 3
+    assert res["best_marker"][3] == -1
+    ref = oracle.scan(G.numpy(), "2bit", oracle_panel(Yt, cov), mode="projected")
+    ok = np.isfinite(ref["r"])
+    assert np.array_equal(ok, np.isfinite(res["t"]))
+
+
+@pytest.mark.parametrize("M,P", [(1, 1), (129, 257), (256, 256), (5, 1000)])
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_tile_edges(tgctx, M, P, precision):
+    N = 515
+    w = synth.Workload("edge", N=N, M=M, P=P, n_cov=2, encoding="u8", missing=0.0, seed=M + P, block=M)
+    pan = synth.make_panel(w)
+    blk = synth.make_block(w, 0)
+    panel = tg.tg_prepare_panel(tgctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+    try:
+        res = run_scan(tgctx, panel, blk["G"].cuda(), N, P, "u8", precision, full=True)
+    finally:
+        tg.tg_panel_free(panel)
+    ref = oracle.scan(blk["G"].numpy(), "u8", oracle_panel(pan["Yt"], pan["cov_t"]))
+    compare_full(res, ref, label=f"edge {M}x{P}/{precision}")
+    compare_best(res, ref)
+
+
+def test_empty_block_is_a_noop(tgctx):
+    N, P = 64, 2
+    cov = synth.covariates(41, N, 1)
+    panel = tg.tg_prepare_panel(tgctx, synth.phenotypes(41, cov, P).cuda(), N, P, cov.cuda())
+    try:
+        G = torch.zeros(0, 16, dtype=torch.uint8, device="cuda")
+        res = run_scan(tgctx, panel, G, N, P, "2bit", "split", full=False, hit_mlog10p=1.0)
+        assert res["n_hits"] == 0 and res["status"] == tg.TG_OK
+    finally:
+        tg.tg_panel_free(panel)
+
+
+def test_blocks_accumulate_hits_and_best(tgctx, panels):
+    """Two half blocks with marker offsets give the same hits and best as one block."""
+    w, pan, blk, _ = _case("2bit")
+    panel = _panel(tgctx, panels, ("main", "2bit", False), pan, w.N, w.P)
+    G = blk["G"].cuda()
+    whole = run_scan(tgctx, panel, G, w.N, w.P, "2bit", "split", full=False, hit_mlog10p=THR)
+    a = run_scan(tgctx, panel, G[:500], w.N, w.P, "2bit", "split", full=False, hit_mlog10p=THR)
+    b = run_scan(tgctx, panel, G[500:], w.N, w.P, "2bit", "split", full=False, hit_mlog10p=THR,
+                 marker_offset=500)
+    key = lambda hs: sorted((int(h["marker"]), int(h["pheno"])) for h in hs)
+    assert key(whole["hits"]) == sorted(key(a["hits"]) + key(b["hits"]))
+    best = np.maximum(a["best_key"], b["best_key"])
+    assert np.array_equal(best, whole["best_key"])
