@@ -44,7 +44,21 @@ def _args():
     a.add_argument("--e2e-steps", type=int, default=8)
     a.add_argument("--cpu-seconds", type=float, default=15.0)
     a.add_argument("--no-cpu-baseline", action="store_true")
+    # smaller cases of the same kernels (profiling captures); the default is the full size
+    a.add_argument("--phenotypes", type=int, default=None)
+    a.add_argument("--block-markers", type=int, default=None)
     return a.parse_args()
+
+
+def _workload(args):
+    import dataclasses
+
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    if args.phenotypes or args.block_markers:
+        w = dataclasses.replace(w, P=args.phenotypes or w.P, block=args.block_markers or w.block,
+                                name=w.name + "_reduced")
+    return w
 
 
 def _peaks():
@@ -131,6 +145,11 @@ def _max_over_ranks(dist, x: float) -> float:
     return float(t.item())
 
 
+def rank_blocks(rank: int, ws: int, count: int):
+    """Blocks of the marker stream scanned by `rank` of `ws` replicas: rank, rank + ws, ..."""
+    return [rank + ws * i for i in range(count)]
+
+
 def _barrier(dist):
     if dist is not None:
         dist.barrier()
@@ -193,10 +212,10 @@ def _reference(args, dist, rank, ws):
 
 
 def _config(w):
-    return {"workload": f"{WORKLOAD}: N={w.N} samples, {w.block}-marker blocks of 8-bit dosages "
-                        f"(M={w.M} in the whole scan), P={w.P} phenotypes, C=20 covariate columns "
-                        "(intercept + 19), hits at -log10 p >= 7.30103",
-            "N": w.N, "P": w.P, "C": 20, "block_markers": w.block, "encoding": "u8 dosage",
+    return {"workload": f"{w.name}: N={w.N} samples, {w.block}-marker blocks of 8-bit dosages "
+                        f"(M={w.M} in the whole scan), P={w.P} phenotypes, C={w.n_cov + 1} covariate columns "
+                        f"(intercept + {w.n_cov}), hits at -log10 p >= 7.30103",
+            "N": w.N, "P": w.P, "C": w.n_cov + 1, "block_markers": w.block, "encoding": "u8 dosage",
             "precision": "split-bf16 (A exact bf16, panel bf16 hi+lo, fp32 accumulate)",
             "l2": f"inputs larger than L2: {RESIDENT} resident 1.5 GB blocks cycled, 1.9 GB panel"}
 
@@ -214,7 +233,7 @@ def _ours(args, dist, rank, ws):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     tg.build()
-    w = synth.WORKLOADS[WORKLOAD]
+    w = _workload(args)
     ctx = tg.tg_create(local)
     stream = torch.cuda.current_stream(dev)
 
@@ -229,7 +248,8 @@ def _ours(args, dist, rank, ws):
     del pan
 
     # resident blocks: rank r scans blocks r, r + ws, ... of the workload
-    blocks = [synth.make_block(w, rank + ws * i, device=dev)["G"] for i in range(RESIDENT)]
+    mine = rank_blocks(rank, ws, RESIDENT)
+    blocks = [synth.make_block(w, b, device=dev)["G"] for b in mine]
     M = blocks[0].shape[0]
     cap = 1 << 20
     hits = torch.zeros(cap * 24, dtype=torch.uint8, device=dev)
@@ -241,7 +261,7 @@ def _ours(args, dist, rank, ws):
         opts = tg.tg_scan_opts(prec, 0, THR)
         b = i % RESIDENT
         tg.tg_scan_block(ctx, panel, blocks[b], w.N, M, tg.TG_ENC_U8_DOSAGE, opts, out,
-                         marker_offset=(rank + ws * b) * w.block, stream=stream)
+                         marker_offset=mine[b] * w.block, stream=stream)
 
     # split-BF16, the headline
     for i in range(args.warmup):
@@ -278,6 +298,7 @@ def _ours(args, dist, rank, ws):
     if args.fp32_steps > 0:
         step(0, tg.TG_PREC_FP32)
         torch.cuda.synchronize()
+        tg.tg_stage_times(ctx, reset=True)
         tg.tg_set_profiling(ctx, True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -290,7 +311,8 @@ def _ours(args, dist, rank, ws):
         ms32 = _max_over_ranks(dist, e0.elapsed_time(e1))
         fp32 = {"value": tests_step * args.fp32_steps * ws / (ms32 / 1000.0), "unit": UNIT,
                 "ms_per_step": ms32 / args.fp32_steps,
-                "scan_kernel_ms": st32["scan"][0] / max(1, st32["scan"][1])}
+                "scan_kernel_ms": st32["scan"][0] / max(1, st32["scan"][1]),
+                "stage_ms_per_step": {k: v[0] / args.fp32_steps for k, v in st32.items()}}
 
     # end to end through the host-buffer entry point: pinned host blocks in, hits and best out
     e2e = None
@@ -306,6 +328,8 @@ def _ours(args, dist, rank, ws):
         tg.tg_scan_host(ctx, panel, host, w.N, per_call * M, tg.TG_ENC_U8_DOSAGE, M, opts, hits_h,
                         best_h, stream=stream)
         torch.cuda.synchronize()
+        tg.tg_stage_times(ctx, reset=True)
+        tg.tg_set_profiling(ctx, True)
         _barrier(dist)
         t0 = time.perf_counter()
         nh_e2e = 0
@@ -313,11 +337,14 @@ def _ours(args, dist, rank, ws):
             nh_e2e = tg.tg_scan_host(ctx, panel, host, w.N, per_call * M, tg.TG_ENC_U8_DOSAGE, M,
                                      opts, hits_h, best_h, stream=stream)
         dt = _max_over_ranks(dist, time.perf_counter() - t0)
+        tg.tg_set_profiling(ctx, False)
+        ste = tg.tg_stage_times(ctx, reset=True)
         steps_e2e = calls * per_call
         e2e = {"value": tests_step * steps_e2e * ws / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(M * blocks[0].shape[1]),
                "d2h_bytes_per_step": int((8 + 24 * min(nh_e2e, cap) + 8 * w.P) / per_call),
-               "ms_per_step": 1000 * dt / steps_e2e, "api": "tg_scan_host (C ABI, host buffers)"}
+               "ms_per_step": 1000 * dt / steps_e2e, "api": "tg_scan_host (C ABI, host buffers)",
+               "stage_ms_per_step": {k: v[0] / steps_e2e for k, v in ste.items()}}
 
     peaks, peak_src = _peaks()
     gemm_ms = stages["scan"][0] / max(1, stages["scan"][1])

@@ -190,7 +190,8 @@ tg_status tg_scan_host(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G_host
 tg_status tg_status_poll(tg_ctx* ctx, void* stream);
 
 /* Stage timing with CUDA events on the launching stream (off by default). */
-#define TG_N_STAGES 5 /* 0 decode, 1 projection, 2 marker norm, 3 contraction+epilogue, 4 H2D */
+#define TG_N_STAGES 6 /* 0 decode, 1 projection, 2 marker norm, 3 contraction + epilogue,
+                         4 H2D copies, 5 statistics of hits / full output */
 tg_status tg_set_profiling(tg_ctx* ctx, int enable);
 /* Total milliseconds and kernel launches per stage since the last reset (synchronises
  * the recorded events). Either array may be NULL. */

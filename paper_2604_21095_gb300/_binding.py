@@ -17,8 +17,8 @@ TG_OK, TG_ERR_INVALID_ARG, TG_ERR_CUDA, TG_ERR_OOM, TG_ERR_NONFINITE, TG_ERR_RAN
     TG_ERR_CAPACITY, TG_ERR_TIMEOUT, TG_ERR_UNSUPPORTED = range(9)
 TG_PREC_FP32, TG_PREC_SPLIT_BF16 = 0, 1
 TG_ENC_2BIT, TG_ENC_U8_DOSAGE = 0, 1
-TG_N_STAGES = 5
-STAGES = ("decode", "project", "norm", "scan", "h2d")
+TG_N_STAGES = 6
+STAGES = ("decode", "project", "norm", "scan", "h2d", "stats")
 
 
 class TgError(RuntimeError):

@@ -244,12 +244,17 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   ep.se = a.out.se;
   ep.t = a.out.t;
   ep.mlp = a.out.mlog10p;
+  ep.rstore = a.out.t ? a.out.t : a.out.mlog10p ? a.out.mlog10p : a.out.beta ? a.out.beta : a.out.se;
   ep.ldo = a.out.ldo;
   ep.hits = a.out.hits;
   ep.hit_cap = a.out.hit_capacity;
   ep.n_hits = a.out.n_hits;
   ep.best = a.out.best;
   ep.status = c->status;
+  unsigned long long* hit_start = reinterpret_cast<unsigned long long*>(c->scratch + 16);
+  if (ep.do_hits)
+    TG_CUDA(cudaMemcpyAsync(hit_start, ep.n_hits, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, st));
   {
     StageScope s(c, STAGE_GEMM, st, 1);
     if (prec == TG_PREC_FP32) {
@@ -263,6 +268,11 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       TG_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi, &p->tmBlo, p->Npad, has_lo,
                              c->tflags, ep, c->sm_count, kSpinNs, st));
     }
+  }
+  if (ep.do_hits || ep.do_full) {
+    StageScope s(c, STAGE_STATS, st, (ep.do_hits ? 1 : 0) + (ep.do_full ? 1 : 0));
+    if (ep.do_hits) TG_CUDA(launch_hit_stats(ep, hit_start, st));
+    if (ep.do_full) TG_CUDA(launch_full_stats(ep, st));
   }
   return TG_OK;
 }

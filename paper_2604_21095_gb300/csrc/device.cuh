@@ -46,24 +46,9 @@ __device__ __forceinline__ float corr_nan(float D, float rinv, float rmul) {
   return fminf(1.0f, fmaxf(-1.0f, r));
 }
 
-// Full statistics of one element (FP32, p-value in FP64).
-__device__ __forceinline__ void elem_full(const EpiParams& ep, float r, float s_p, float rinv,
-                                          float& beta, float& se, float& t, float& mlp) {
-  const float omr2 = (1.0f - r) * (1.0f + r);
-  const float scale = s_p * rinv / ep.kappa;  // s_p / |g_res| in allele units
-  beta = r * scale;
-  se = scale * sqrtf(omr2 / ep.df_f);
-  t = r * sqrtf(ep.df_f / omr2);
-  mlp = (float)mlog10p_r((double)r, ep.df, ep.lnB);
-}
-
-// Append one hit (FP64 statistics from the FP32 product D).
-__device__ __forceinline__ void emit_hit(const EpiParams& ep, float D, int row, int col) {
-  const double rinv = ep.row_inv64[row];
-  double r = (double)D * rinv;
-  r = fmin(1.0, fmax(-1.0, r));
-  const double omr2 = (1.0 - r) * (1.0 + r);
-  const double scale = ep.col_s64[col] * rinv / (double)ep.kappa;
+// Append a raw hit record: marker, phenotype and the product D (in the beta slot). The
+// statistics kernel that runs after the contraction turns it into beta, se, t, -log10 p.
+__device__ __forceinline__ void emit_hit_raw(const EpiParams& ep, float D, long long row, int col) {
   const unsigned long long slot = atomicAdd(ep.n_hits, 1ull);
   if ((long long)slot >= ep.hit_cap) {
     atomicOr(ep.status, ST_CAPACITY);
@@ -72,10 +57,10 @@ __device__ __forceinline__ void emit_hit(const EpiParams& ep, float D, int row, 
   tg_hit h;
   h.marker = (uint32_t)(ep.marker_offset + row);
   h.pheno = (uint32_t)col;
-  h.beta = (float)(r * scale);
-  h.se = (float)(scale * sqrt(omr2 / ep.df));
-  h.t = (float)(r * sqrt(ep.df / omr2));
-  h.mlog10p = (float)mlog10p_r(r, ep.df, ep.lnB);
+  h.beta = D;
+  h.se = 0.0f;
+  h.t = 0.0f;
+  h.mlog10p = 0.0f;
   ep.hits[slot] = h;
 }
 

@@ -22,7 +22,8 @@ constexpr int QMAX = 64;     // intercept + at most 63 covariates
 constexpr int QCOLS = 64;    // projection columns (Q columns 1..q-1), zero padded
 constexpr int MT = 128;      // marker rows per tensor-core tile
 
-enum Stage { STAGE_DECODE = 0, STAGE_PROJECT = 1, STAGE_NORM = 2, STAGE_GEMM = 3, STAGE_H2D = 4 };
+enum Stage { STAGE_DECODE = 0, STAGE_PROJECT = 1, STAGE_NORM = 2, STAGE_GEMM = 3, STAGE_H2D = 4,
+             STAGE_STATS = 5 };
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -42,6 +43,7 @@ struct EpiParams {
   const double* col_s64;       // [P]
   const float* col_rmul;       // [P] 1 or NaN
   float *beta, *se, *t, *mlp;  // FULL outputs, [M][ldo]
+  float* rstore;               // FULL mode: where the contraction leaves r (one of the above)
   long long ldo;
   tg_hit* hits;
   long long hit_cap;
@@ -108,8 +110,8 @@ struct tg_ctx {
   bool prof = false;
   std::vector<tg::Events> pending;
   std::vector<cudaEvent_t> event_pool;
-  double stage_ms[TG_N_STAGES] = {0, 0, 0, 0, 0};
-  int64_t launches[TG_N_STAGES] = {0, 0, 0, 0, 0};
+  double stage_ms[TG_N_STAGES] = {0, 0, 0, 0, 0, 0};
+  int64_t launches[TG_N_STAGES] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace tg {
@@ -146,6 +148,10 @@ cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2
                                cudaStream_t st);
 cudaError_t launch_sgemm_scan(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t K,
                               const EpiParams& ep, cudaStream_t st);
+
+// statistics after the contraction (k_stats.cu)
+cudaError_t launch_full_stats(const EpiParams& ep, cudaStream_t st);
+cudaError_t launch_hit_stats(const EpiParams& ep, const unsigned long long* start, cudaStream_t st);
 
 // tensor-core kernel (k_tc.cu)
 cudaError_t launch_tc_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,

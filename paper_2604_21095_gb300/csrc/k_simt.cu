@@ -222,16 +222,8 @@ __global__ void __launch_bounds__(256, 1) k_sgemm_scan(const float* __restrict__
         const unsigned long long key = best_key(r, ep.marker_offset + row);
         cb[b] = key > cb[b] ? key : cb[b];
       }
-      if (ep.do_hits && r * r >= ep.r2_thr) emit_hit(ep, D, (int)row, col);
-      if (ep.do_full) {
-        float be, se, t, mlp;
-        elem_full(ep, r, ep.col_s[col], rinv, be, se, t, mlp);
-        const long long o = row * ep.ldo + col;
-        if (ep.beta) ep.beta[o] = be;
-        if (ep.se) ep.se[o] = se;
-        if (ep.t) ep.t[o] = t;
-        if (ep.mlp) ep.mlp[o] = mlp;
-      }
+      if (ep.do_hits && r * r >= ep.r2_thr) emit_hit_raw(ep, D, row, col);
+      if (ep.do_full) ep.rstore[row * ep.ldo + col] = r;
     }
   }
   if (ep.do_best) {

@@ -6,15 +6,20 @@
 //   B_hi, B_lo [P][K]  bf16 split of the unit-norm residualised panel, y ~= hi + lo
 // K = samples (zero padded), FP32 accumulation in tensor memory.
 //
-// Persistent kernel, one CTA per SM, 192 threads, warp-specialised:
+// Persistent kernel, one CTA per SM, 384 threads (3 warpgroups), warp-specialised:
 //   warp 0 lane 0  TMA producer: 128x32 A tiles and 256x32 B tiles (64-byte swizzle) into a
 //                  ring of shared-memory stages, completion tracked by mbarrier transaction bytes
 //   warp 1 lane 0  MMA issuer: per 32-wide K step, 2 x (2 or 3) tcgen05.mma 128x256x16 into an
-//                  FP32 accumulator in TMEM; two accumulators (512 columns) so the epilogue of
-//                  one tile overlaps the products of the next
-//   warps 2..5     epilogue: tcgen05.ld of the 128 x 256 accumulator (thread = marker row),
-//                  r = D / |g_res|, hits above the r^2 threshold, per-phenotype best marker,
-//                  optionally every statistic.
+//                  FP32 accumulator in TMEM
+//   warps 4..11    epilogue: tcgen05.ld of the accumulator (thread = marker row, each warp one
+//                  TMEM lane quarter and one half of the 256 columns), r = D / |g_res|, hits
+//                  above the r^2 threshold, per-phenotype best marker, optionally every statistic.
+// Accumulation is chunked: the tensor core sums at most 512 samples (16 K blocks) into a
+// fresh TMEM accumulator, and the epilogue warps add the chunk results into FP32 totals held
+// in registers with round-to-nearest adds. The tensor core's FP32 accumulation drops low bits
+// toward zero at each chained addition, which over 23,000 samples biases |r| low by about
+// 5e-5 relative; chunks of 512 keep that bias near 1e-6. Two chunk accumulators (512 TMEM
+// columns) alternate, so draining one overlaps the products of the next.
 // Every mbarrier wait is bounded: past the limit the kernel latches ST_TIMEOUT, raises a
 // shared abort flag, lets in-flight copies and products finish (again bounded), frees its
 // TMEM and returns.
@@ -30,8 +35,17 @@ namespace {
 constexpr int TBM = 128, TBN = 256, TBK = 32;  // TBK bf16 = 64 bytes = one swizzle row
 constexpr int A_BYTES = TBM * TBK * 2;         // 8 KB
 constexpr int B_BYTES = TBN * TBK * 2;         // 16 KB
-constexpr int kThreads = 192;
-constexpr int kTmemCols = 512;                 // two 128 x 256 FP32 accumulators
+constexpr int kEpiWarps = 8;
+// Three warpgroups: warpgroup 0 = producer warp, MMA warp and two idle warps; warpgroups 1-2 =
+// the 8 epilogue warps. At launch every thread gets 168 registers (384 x 168 = 64,512); then
+// warpgroup 0 gives registers back (56 each) and the epilogue warpgroups take them
+// (224 each): 128 x 56 + 256 x 224 = 64,512, the launch total, so the increase cannot stall.
+constexpr int kThreads = 384;
+constexpr int kRegsLow = 56;
+constexpr int kRegsHigh = 224;
+static_assert(128 * kRegsLow + 256 * kRegsHigh <= kThreads * 168, "register split exceeds launch");
+constexpr int kTmemCols = 512;                 // two 128 x 256 FP32 chunk accumulators
+constexpr int kChunkKB = 16;                   // K blocks per accumulation chunk (512 samples)
 constexpr int kGroupM = 8;                     // raster: 8 m-tiles per group
 
 template <bool HAS_LO>
@@ -86,7 +100,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait for the completion of phase `parity`; false on timeout or abort.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                        long long limit_ns, uint32_t* status) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
@@ -163,42 +177,55 @@ __device__ __forceinline__ void tile_coord(int tile, int n_mt, int n_nt, int& mt
   nt = idx / gm;
 }
 
-// Epilogue of 32 accumulator columns held by one thread (its marker row).
-__device__ __forceinline__ void epilogue_chunk(const EpiParams& ep, const float v[32], long long row,
-                                               bool row_ok, float rinv, int col0, int lane) {
-  unsigned long long key[32];
+// Statistics of the 128 totals one thread holds: its marker row against 128 consecutive
+// phenotype columns starting at col0, in groups of 16 columns.
+__device__ __forceinline__ void epilogue_tile(const EpiParams& ep, const float (&tot)[128],
+                                              long long row, long long row_base, bool row_ok,
+                                              float rinv, int col0, int lane) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    const int col = col0 + i;
-    float r = __int_as_float(0x7fc00000);
-    if (row_ok && col < ep.P) r = corr_nan(v[i], rinv, ep.col_rmul[col]);
-    key[i] = ep.do_best ? best_key(r, ep.marker_offset + row) : 0ull;
-    if (ep.do_hits && r * r >= ep.r2_thr) emit_hit(ep, v[i], (int)row, col);
-    if (ep.do_full && row_ok && col < ep.P) {
-      float be, se, t, mlp;
-      elem_full(ep, r, ep.col_s[col], rinv, be, se, t, mlp);
-      const long long o = row * ep.ldo + col;
-      if (ep.beta) ep.beta[o] = be;
-      if (ep.se) ep.se[o] = se;
-      if (ep.t) ep.t[o] = t;
-      if (ep.mlp) ep.mlp[o] = mlp;
+  for (int grp = 0; grp < 8; ++grp) {
+    float m[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int col = col0 + grp * 16 + e;
+      const float D = tot[grp * 16 + e];
+      float r = __int_as_float(0x7fc00000);
+      if (row_ok && col < ep.P) r = corr_nan(D, rinv, ep.col_rmul[col]);
+      m[e] = (r == r) ? fabsf(r) : -1.0f;
+      if (ep.do_hits && r * r >= ep.r2_thr) emit_hit_raw(ep, D, row, col);
+      if (ep.do_full && row_ok && col < ep.P) ep.rstore[row * ep.ldo + col] = r;
+    }
+    if (!ep.do_best) continue;
+    // max over the warp's 32 rows: lanes l and l^16 first, then a reduce-scatter over 16
+    // lanes after which lane l holds the column max for column grp*16 + (l & 15)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) m[i] = fmaxf(m[i], __shfl_xor_sync(0xffffffffu, m[i], 16));
+#pragma unroll
+    for (int s = 8; s >= 1; s >>= 1) {
+      const bool upper = (lane & s) != 0;
+#pragma unroll
+      for (int i = 0; i < s; ++i) {
+        const float send = upper ? m[i] : m[i + s];
+        const float keep = upper ? m[i + s] : m[i];
+        m[i] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, send, s));
+      }
+    }
+    const float cmax = m[0];
+    // the lowest lane (smallest marker) reaching the column max owns the candidate
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const float ce = __shfl_sync(0xffffffffu, cmax, e);
+      const int col = col0 + grp * 16 + e;
+      float r = __int_as_float(0x7fc00000);
+      if (row_ok && col < ep.P) r = corr_nan(tot[grp * 16 + e], rinv, ep.col_rmul[col]);
+      const float a = (r == r) ? fabsf(r) : -1.0f;
+      const unsigned b = __ballot_sync(0xffffffffu, ce >= 0.0f && a == ce);
+      if (lane == e && b != 0u) {
+        const long long marker = ep.marker_offset + row_base + (__ffs(b) - 1);
+        atomicMax(ep.best + col, best_key(ce, marker));
+      }
     }
   }
-  if (!ep.do_best) return;
-  // reduce-scatter over the warp: afterwards lane l holds the max key of column col0 + l
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const bool upper = (lane & s) != 0;
-#pragma unroll
-    for (int i = 0; i < s; ++i) {
-      const unsigned long long send = upper ? key[i] : key[i + s];
-      const unsigned long long keep = upper ? key[i + s] : key[i];
-      const unsigned long long got = __shfl_xor_sync(0xffffffffu, send, s);
-      key[i] = keep > got ? keep : got;
-    }
-  }
-  const int col = col0 + lane;
-  if (col < ep.P && key[0] != 0ull) atomicMax(ep.best + col, key[0]);
 }
 
 template <bool HAS_LO>
@@ -216,8 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t bars = base + S * C::kStageBytes;
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 8u * (S + s); };
-  auto tfull_bar = [&](int a) { return bars + 8u * (2 * S + a); };
-  auto tempty_bar = [&](int a) { return bars + 8u * (2 * S + 2 + a); };
+  auto cfull_bar = [&](int a) { return bars + 8u * (2 * S + a); };
+  auto cempty_bar = [&](int a) { return bars + 8u * (2 * S + 2 + a); };
   const uint32_t drain_bar = bars + 8u * (2 * S + 4);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * C::kStageBytes + 8 * (2 * S + 5));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -234,8 +261,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(empty_bar(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
-      mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), 4);
+      mbar_init(cfull_bar(a), 1);
+      mbar_init(cempty_bar(a), kEpiWarps);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -254,8 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
   const int num_tiles = n_mt * n_nt;
-
-  if (warp == 0 && lane == 0) {
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
+    if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ TMA producer
     int stage = 0;
     uint32_t phase = 0;
@@ -288,72 +316,99 @@ __global__ void __launch_bounds__(kThreads, 1)
     // copies still in flight land before the CTA leaves (bounded)
     for (int s = 0; s < S; ++s)
       if (armed[s] >= 0) mbar_wait(full_bar(s), (uint32_t)armed[s], abort_flag, spin_ns, ep.status);
-  } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
+    // Each chunk of kChunkKB K blocks starts a fresh accumulator (no chained accumulation
+    // across chunks); the two chunk accumulators alternate.
     int stage = 0;
     uint32_t phase = 0;
-    int local = 0;
+    uint32_t g = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++local) {
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
       tile_coord(tile, n_mt, n_nt, mt, nt);
       const bool lo = HAS_LO && tflags[mt] != 0;
-      const int acc = local & 1;
-      const uint32_t acc_phase = (uint32_t)(local >> 1) & 1u;
-      if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, spin_ns, ep.status)) break;
-      tc_fence_after();
-      const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
-      for (int kb = 0; kb < num_kb; ++kb) {
-        if (!mbar_wait(full_bar(stage), phase, abort_flag, spin_ns, ep.status)) {
+      for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kChunkKB, ++g) {
+        const int acc = (int)(g & 1u);
+        const uint32_t ph = (g >> 1) & 1u;
+        if (!mbar_wait(cempty_bar(acc), ph ^ 1u, abort_flag, spin_ns, ep.status)) {
           ok = false;
           break;
         }
         tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
+        const int kb1 = min(num_kb, kb0 + kChunkKB);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          if (!mbar_wait(full_bar(stage), phase, abort_flag, spin_ns, ep.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
 #pragma unroll
-        for (int k = 0; k < TBK / 16; ++k) {
-          const uint64_t a = sdesc_sw64(sA(stage) + 32u * k);
-          const uint64_t bh = sdesc_sw64(sBhi(stage) + 32u * k);
-          const uint64_t bl = sdesc_sw64(sBlo(stage) + 32u * k);
-          tc_mma(d, a, bh, (kb | k) != 0 ? 1u : 0u);
-          tc_mma(d, a, bl, 1u);
-          if (lo) tc_mma(d, sdesc_sw64(sAlo(stage) + 32u * k), bh, 1u);
+          for (int k = 0; k < TBK / 16; ++k) {
+            const uint64_t a = sdesc_sw64(sA(stage) + 32u * k);
+            const uint64_t bh = sdesc_sw64(sBhi(stage) + 32u * k);
+            const uint64_t bl = sdesc_sw64(sBlo(stage) + 32u * k);
+            tc_mma(d, a, bh, (kb > kb0 || k > 0) ? 1u : 0u);
+            tc_mma(d, a, bl, 1u);
+            if (lo) tc_mma(d, sdesc_sw64(sAlo(stage) + 32u * k), bh, 1u);
+          }
+          tc_commit(empty_bar(stage));
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
         }
-        tc_commit(empty_bar(stage));
-        if (++stage == S) {
-          stage = 0;
-          phase ^= 1u;
-        }
+        if (ok) tc_commit(cfull_bar(acc));
       }
-      if (ok) tc_commit(tfull_bar(acc));
     }
     // every product issued so far completes before TMEM is released (bounded)
     tc_commit(drain_bar);
     mbar_wait(drain_bar, 0u, abort_flag, spin_ns, ep.status);
-  } else if (warp >= 2) {
+    }
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
     // ------------------------------------------------------------ epilogue
-    const int quarter = warp & 3;  // TMEM lanes this warp may read
-    int local = 0;
-    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++local) {
+    // 8 warps: (TMEM lane quarter, column half) pairs; FP32 running totals in registers.
+    const int quarter = warp & 3;
+    const int half = (warp - 4) >> 2;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
       tile_coord(tile, n_mt, n_nt, mt, nt);
-      const int acc = local & 1;
-      const uint32_t acc_phase = (uint32_t)(local >> 1) & 1u;
-      if (!mbar_wait(tfull_bar(acc), acc_phase, abort_flag, spin_ns, ep.status)) break;
-      tc_fence_after();
-      const long long row = (long long)mt * TBM + quarter * 32 + lane;
+      float tot[128];
+#pragma unroll
+      for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
+      for (int kb0 = 0; kb0 < num_kb; kb0 += kChunkKB, ++g) {
+        const int acc = (int)(g & 1u);
+        const uint32_t ph = (g >> 1) & 1u;
+        if (!mbar_wait(cfull_bar(acc), ph, abort_flag, spin_ns, ep.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                               (uint32_t)(acc * TBN + half * 128);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float v[32];
+          __syncwarp();  // tcgen05.ld is .sync.aligned
+          tc_ld32(taddr + (uint32_t)(i * 32), v);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) tot[i * 32 + e] += v[e];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(cempty_bar(acc));
+      }
+      if (!ok) break;
+      const long long row_base = (long long)mt * TBM + quarter * 32;
+      const long long row = row_base + lane;
       const bool row_ok = row < ep.M;
       const float rinv = row_ok ? ep.row_inv[row] : __int_as_float(0x7fc00000);
-      const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TBN);
-#pragma unroll 1
-      for (int c = 0; c < TBN / 32; ++c) {
-        float v[32];
-        __syncwarp();  // tcgen05.ld is .sync.aligned: the warp reconverges after hit branches
-        tc_ld32(tbase + (uint32_t)(c * 32), v);
-        epilogue_chunk(ep, v, row, row_ok, rinv, nt * TBN + c * 32, lane);
-      }
-      tc_fence_before();
+      epilogue_tile(ep, tot, row, row_base, row_ok, rinv, nt * TBN + half * 128, lane);
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(acc));
     }
   }
   tc_fence_before();

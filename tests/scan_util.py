@@ -125,7 +125,7 @@ def compare_hits(res, ref, thr, marker_offset=0, tol_band=None):
     return len(want), len(got)
 
 
-def compare_best(res, ref, r_tol=R_TOL):
+def compare_best(res, ref, r_tol=R_TOL, marker_offset=0):
     """Per phenotype the GPU's best marker is a valid argmax of |r| within the r tolerance."""
     absr = np.abs(np.nan_to_num(ref["r"], nan=-1.0))
     for p in range(absr.shape[1]):
@@ -133,7 +133,7 @@ def compare_best(res, ref, r_tol=R_TOL):
         if col.max() < 0:
             assert res["best_marker"][p] == -1
             continue
-        j = res["best_marker"][p]
+        j = res["best_marker"][p] - marker_offset
         assert 0 <= j < col.size
         assert col[j] >= col.max() - 2 * r_tol, (p, j, col[j], col.max())
         assert abs(res["best_absr"][p] - col[j]) <= r_tol * 2 + 1e-7

@@ -60,7 +60,7 @@ def test_scan_matches_oracle(tgctx, panels, encoding, masked, precision):
     err = compare_full(res, ref, label=f"{encoding}/{precision}")
     want, got = compare_hits(res, ref, THR, marker_offset=7)
     assert want >= 2 * w.P * 0.5 and got > 0
-    compare_best(res, ref)
+    compare_best(res, ref, marker_offset=7)
     dec = ref["decode"]
     assert np.array_equal(res["nobs"], dec["n_obs"])
     assert np.array_equal(res["mean"], dec["mean_units"])
