@@ -207,10 +207,28 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
                           c->gc2, has_lo ? c->tflags : nullptr, st));
   }
   const int64_t nq = p->q - 1;
+  CUtensorMap tA, tAlo;
+  if (prec == TG_PREC_SPLIT_BF16) {
+    if (!make_tmap(&tA, c->Ahi, a.M, p->Npad, p->Npad, MT))
+      return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
+    if (has_lo && !make_tmap(&tAlo, c->Alo, a.M, p->Npad, p->Npad, MT))
+      return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the imputation operand");
+  }
   if (nq > 0) {
     StageScope s(c, STAGE_PROJECT, st, 1);
-    TG_CUDA(launch_project(Ahi, has_lo ? c->Alo : nullptr, prec == TG_PREC_FP32, p->Npad, a.M,
-                           p->Npad, p->QB, nq, c->qg, st));
+    if (prec == TG_PREC_FP32) {
+      TG_CUDA(launch_project(Ahi, nullptr, 1, p->Npad, a.M, p->Npad, p->QB, nq, c->qg, st));
+    } else {
+      EpiParams pp{};
+      pp.M = (int)a.M;
+      pp.P = (int)nq;
+      pp.status = c->status;
+      pp.raw_out = c->qg;
+      pp.raw_cols = (int)nq;
+      pp.raw_ld = QCOLS;
+      TG_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmQhi, &p->tmQlo, p->Npad, has_lo,
+                             c->tflags, pp, c->sm_count, kSpinNs, st));
+    }
   }
   {
     StageScope s(c, STAGE_NORM, st, 1);
@@ -260,11 +278,6 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     if (prec == TG_PREC_FP32) {
       TG_CUDA(launch_sgemm_scan(c->A32, p->Npad, p->B32, p->Npad, p->Npad, ep, st));
     } else {
-      CUtensorMap tA, tAlo;
-      if (!make_tmap(&tA, c->Ahi, a.M, p->Npad, p->Npad, MT))
-        return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
-      if (has_lo && !make_tmap(&tAlo, c->Alo, a.M, p->Npad, p->Npad, MT))
-        return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the imputation operand");
       TG_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi, &p->tmBlo, p->Npad, has_lo,
                              c->tflags, ep, c->sm_count, kSpinNs, st));
     }
@@ -414,7 +427,9 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
       (e = dalloc(&p->Bhi, (size_t)(p->Ppad * p->Npad))) ||
       (e = dalloc(&p->Blo, (size_t)(p->Ppad * p->Npad))) ||
       (e = dalloc(&p->B32, (size_t)(p->Ppad * p->Npad))) ||
-      (e = dalloc(&p->QB, (size_t)(QCOLS * p->Npad))) || (e = dalloc(&dint, (size_t)(1 + k))))
+      (e = dalloc(&p->QB, (size_t)(QCOLS * p->Npad))) ||
+      (e = dalloc(&p->QBhi, (size_t)(QCOLS * p->Npad))) ||
+      (e = dalloc(&p->QBlo, (size_t)(QCOLS * p->Npad))) || (e = dalloc(&dint, (size_t)(1 + k))))
     return cleanup(cuda_fail(e, "tg_prepare_panel allocation"));
   auto run = [&]() -> cudaError_t {
     cudaError_t r;
@@ -440,7 +455,7 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
   if (p->df <= 0) return cleanup(fail(TG_ERR_RANK, "N must exceed rank([1, C]) + 1"));
   if ((e = launch_residualise(Y, ldy, p->Q, N, P, rank, p->Npad, p->Yres, p->s, p->col_s,
                               p->col_rmul, p->Bhi, p->Blo, p->B32, c->scratch, st)) ||
-      (e = launch_qcols(p->Q, N, rank, p->Npad, p->QB, st)))
+      (e = launch_qcols(p->Q, N, rank, p->Npad, p->QB, p->QBhi, p->QBlo, st)))
     return cleanup(cuda_fail(e, "tg_prepare_panel residualise"));
   uint32_t flags = 0;
   if ((e = cudaMemcpyAsync(&flags, c->scratch, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) ||
@@ -450,7 +465,9 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
   if (flags & 2u) return cleanup(fail(TG_ERR_NONFINITE, "non-finite phenotype"));
   p->lnB = host_lnbeta_half((double)p->df);
   if (!make_tmap(&p->tmBhi, p->Bhi, p->Ppad, p->Npad, p->Npad, 256) ||
-      !make_tmap(&p->tmBlo, p->Blo, p->Ppad, p->Npad, p->Npad, 256))
+      !make_tmap(&p->tmBlo, p->Blo, p->Ppad, p->Npad, p->Npad, 256) ||
+      !make_tmap(&p->tmQhi, p->QBhi, QCOLS, p->Npad, p->Npad, 64) ||
+      !make_tmap(&p->tmQlo, p->QBlo, QCOLS, p->Npad, p->Npad, 64))
     return cleanup(fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panel"));
   *out = p;
   return TG_OK;
@@ -486,7 +503,7 @@ tg_status tg_panel_free(tg_panel* p) {
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   dfree(p->X); dfree(p->Q); dfree(p->Yres); dfree(p->s); dfree(p->col_s); dfree(p->col_rmul);
-  dfree(p->Bhi); dfree(p->Blo); dfree(p->B32); dfree(p->QB);
+  dfree(p->Bhi); dfree(p->Blo); dfree(p->B32); dfree(p->QB); dfree(p->QBhi); dfree(p->QBlo);
   delete p;
   return TG_OK;
 }

@@ -50,6 +50,8 @@ struct EpiParams {
   unsigned long long* n_hits;
   unsigned long long* best;
   uint32_t* status;
+  float* raw_out;              // projection mode: D of the first raw_cols columns, [M][raw_ld]
+  int raw_cols, raw_ld;
 };
 
 struct Events {
@@ -72,8 +74,11 @@ struct tg_panel {
   __nv_bfloat16* Blo = nullptr;  // [Ppad][Npad] low part
   float* B32 = nullptr;          // [Ppad][Npad] unit-norm panel in FP32
   float* QB = nullptr;           // [QCOLS][Npad] Q columns 1..q-1 in FP32 (rest zero)
+  __nv_bfloat16* QBhi = nullptr; // [QCOLS][Npad] the same split into bf16 hi + lo
+  __nv_bfloat16* QBlo = nullptr;
   double lnB = 0;
-  CUtensorMap tmBhi, tmBlo;
+  CUtensorMap tmBhi, tmBlo;      // phenotype panel, 256-row boxes
+  CUtensorMap tmQhi, tmQlo;      // covariate projection columns, 64-row boxes
 };
 
 struct tg_ctx {
@@ -130,7 +135,7 @@ cudaError_t launch_residualise(const float* Y, int64_t ldy, const double* Q, int
                                float* col_rmul, __nv_bfloat16* Bhi, __nv_bfloat16* Blo, float* B32,
                                uint32_t* flags, cudaStream_t st);
 cudaError_t launch_qcols(const double* Q, int64_t N, int64_t q, int64_t Npad, float* QB,
-                         cudaStream_t st);
+                         __nv_bfloat16* QBhi, __nv_bfloat16* QBlo, cudaStream_t st);
 
 // decode (k_decode.cu)
 cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,

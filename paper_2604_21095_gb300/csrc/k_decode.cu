@@ -29,6 +29,7 @@ __device__ __forceinline__ void row_stats(const uint8_t* __restrict__ row, int N
   if (ENC == TG_ENC_2BIT) {
     const int nb = (N + 3) >> 2;
     const int nchunk = (nb + 15) >> 4;
+#pragma unroll 4
     for (int c = lane; c < nchunk; c += 32) {
       const uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + c);
       const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
@@ -53,6 +54,7 @@ __device__ __forceinline__ void row_stats(const uint8_t* __restrict__ row, int N
     }
   } else {
     const int nchunk = (N + 15) >> 4;
+#pragma unroll 4
     for (int c = lane; c < nchunk; c += 32) {
       const uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + c);
       const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
@@ -141,6 +143,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_decode(
     const __nv_bfloat16 ml = __double2bfloat16(m_imp - (double)__bfloat162float(mh));
     __nv_bfloat16* ah = reinterpret_cast<__nv_bfloat16*>(Ahi) + j * lda;
     __nv_bfloat16* al = Alo ? Alo + j * lda : nullptr;
+#pragma unroll 4
     for (long long t = lane; t < steps; t += 32) {
       const int i0 = (int)(t << 3);
       float v[8];
@@ -165,6 +168,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_decode(
   } else {
     const float mf = (float)m_imp;
     float* af = reinterpret_cast<float*>(Ahi) + j * lda;
+#pragma unroll 4
     for (long long t = lane; t < steps; t += 32) {
       const int i0 = (int)(t << 3);
       float v[8];

@@ -178,11 +178,17 @@ __global__ void __launch_bounds__(256) k_residualise(
 }
 
 __global__ void k_qcols(const double* __restrict__ Q, long long N, int q, long long Npad,
-                        float* __restrict__ QB) {
+                        float* __restrict__ QB, __nv_bfloat16* __restrict__ QBhi,
+                        __nv_bfloat16* __restrict__ QBlo) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int r = blockIdx.y;  // QB row r = Q column r + 1
   if (i >= Npad) return;
-  QB[(long long)r * Npad + i] = (r + 1 < q && i < N) ? (float)Q[(long long)(r + 1) * N + i] : 0.0f;
+  const double v = (r + 1 < q && i < N) ? Q[(long long)(r + 1) * N + i] : 0.0;
+  const long long o = (long long)r * Npad + i;
+  QB[o] = (float)v;
+  const __nv_bfloat16 h = __double2bfloat16(v);
+  QBhi[o] = h;
+  QBlo[o] = __double2bfloat16(v - (double)__bfloat162float(h));
 }
 
 }  // namespace
@@ -212,9 +218,9 @@ cudaError_t launch_residualise(const float* Y, int64_t ldy, const double* Q, int
 }
 
 cudaError_t launch_qcols(const double* Q, int64_t N, int64_t q, int64_t Npad, float* QB,
-                         cudaStream_t st) {
+                         __nv_bfloat16* QBhi, __nv_bfloat16* QBlo, cudaStream_t st) {
   dim3 grid((unsigned)((Npad + 255) / 256), QCOLS);
-  k_qcols<<<grid, 256, 0, st>>>(Q, N, (int)q, Npad, QB);
+  k_qcols<<<grid, 256, 0, st>>>(Q, N, (int)q, Npad, QB, QBhi, QBlo);
   return cudaGetLastError();
 }
 

@@ -58,8 +58,10 @@ struct Cfg {
 
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
 // both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
-                            ((uint32_t)(TBM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(TBM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -134,12 +136,12 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                       uint32_t accumulate) {
+                                       uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -232,8 +234,9 @@ template <bool HAS_LO>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
               const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-              int num_kb, int n_mt, int n_nt, const int* __restrict__ tflags, long long spin_ns,
-              EpiParams ep) {
+              int num_kb, int n_mt, int n_nt, int bn, const int* __restrict__ tflags,
+              long long spin_ns, EpiParams ep) {
+  // bn = B rows per tile: 256 for the phenotype panel, 64 for the covariate projection
   using C = Cfg<HAS_LO>;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int mt, nt;
       tile_coord(tile, n_mt, n_nt, mt, nt);
       const bool lo = HAS_LO && tflags[mt] != 0;
-      const uint32_t bytes = A_BYTES + 2 * B_BYTES + (lo ? A_BYTES : 0);
+      const uint32_t bytes = A_BYTES + 2u * (uint32_t)bn * (TBK * 2) + (lo ? A_BYTES : 0);
       for (int kb = 0; kb < num_kb; ++kb) {
         if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, spin_ns, ep.status)) {
           ok = false;
@@ -304,8 +307,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_expect_tx(full_bar(stage), bytes);
         armed[stage] = (int)phase;
         tma_load_2d(&tmAhi, sA(stage), full_bar(stage), kb * TBK, mt * TBM);
-        tma_load_2d(&tmBhi, sBhi(stage), full_bar(stage), kb * TBK, nt * TBN);
-        tma_load_2d(&tmBlo, sBlo(stage), full_bar(stage), kb * TBK, nt * TBN);
+        tma_load_2d(&tmBhi, sBhi(stage), full_bar(stage), kb * TBK, nt * bn);
+        tma_load_2d(&tmBlo, sBlo(stage), full_bar(stage), kb * TBK, nt * bn);
         if (lo) tma_load_2d(&tmAlo, sAlo(stage), full_bar(stage), kb * TBK, mt * TBM);
         if (++stage == S) {
           stage = 0;
@@ -324,6 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;
     uint32_t g = 0;
     bool ok = true;
+    const uint32_t idesc = idesc_bf16(bn);
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
       tile_coord(tile, n_mt, n_nt, mt, nt);
@@ -349,9 +353,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t a = sdesc_sw64(sA(stage) + 32u * k);
             const uint64_t bh = sdesc_sw64(sBhi(stage) + 32u * k);
             const uint64_t bl = sdesc_sw64(sBlo(stage) + 32u * k);
-            tc_mma(d, a, bh, (kb > kb0 || k > 0) ? 1u : 0u);
-            tc_mma(d, a, bl, 1u);
-            if (lo) tc_mma(d, sdesc_sw64(sAlo(stage) + 32u * k), bh, 1u);
+            tc_mma(d, a, bh, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+            tc_mma(d, a, bl, idesc, 1u);
+            if (lo) tc_mma(d, sdesc_sw64(sAlo(stage) + 32u * k), bh, idesc, 1u);
           }
           tc_commit(empty_bar(stage));
           if (++stage == S) {
@@ -406,8 +410,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const long long row_base = (long long)mt * TBM + quarter * 32;
       const long long row = row_base + lane;
       const bool row_ok = row < ep.M;
-      const float rinv = row_ok ? ep.row_inv[row] : __int_as_float(0x7fc00000);
-      epilogue_tile(ep, tot, row, row_base, row_ok, rinv, nt * TBN + half * 128, lane);
+      const float rinv = (row_ok && ep.row_inv) ? ep.row_inv[row] : __int_as_float(0x7fc00000);
+      if (ep.raw_out) {
+        // covariate projection: the first raw_cols columns of the tile, unnormalised
+        if (row_ok && half == 0) {
+#pragma unroll
+          for (int e = 0; e < 64; ++e)
+            if (e < ep.raw_cols) ep.raw_out[row * ep.raw_ld + e] = tot[e];
+        }
+      } else {
+        epilogue_tile(ep, tot, row, row_base, row_ok, rinv, nt * TBN + half * 128, lane);
+      }
       __syncwarp();
     }
   }
@@ -450,11 +463,12 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* 
     attr_set = true;
   }
   const int n_mt = (ep.M + TBM - 1) / TBM;
-  const int n_nt = (ep.P + TBN - 1) / TBN;
+  const int bn = ep.raw_out ? 64 : TBN;
+  const int n_nt = (ep.P + bn - 1) / bn;
   const int tiles = n_mt * n_nt;
   const int grid = tiles < sm_count ? tiles : sm_count;
   k_tc_scan<HAS_LO><<<grid, kThreads, C::kSmem, st>>>(*a, *alo, *bh, *bl, (int)(K / TBK), n_mt,
-                                                       n_nt, tflags, spin_ns, ep);
+                                                       n_nt, bn, tflags, spin_ns, ep);
   return cudaGetLastError();
 }
 

@@ -11,7 +11,7 @@ import torch
 import oracle
 import paper_2604_21095_gb300 as tg
 import synth
-from scan_util import run_scan
+from scan_util import r_tol, run_scan
 
 pytestmark = pytest.mark.gpu
 
@@ -96,8 +96,9 @@ def test_fullsize_best_of_a_null_phenotype(tgctx, full):
             best, arg = float(r[j]), m0 + j
     jg = int(res["best_marker"][p0])
     rg = abs(_sub_oracle(pan, blk, [jg], [p0])["r"][0, 0])
-    assert rg >= best - 1e-6, (jg, rg, arg, best)
-    assert abs(res["best_absr"][p0] - rg) <= 1e-6
+    tol = 2 * r_tol(W.N - W.n_cov - 2)
+    assert rg >= best - tol, (jg, rg, arg, best)
+    assert abs(res["best_absr"][p0] - rg) <= tol
 
 
 def test_fullsize_every_statistic_sampled(tgctx, full):
