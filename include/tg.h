@@ -172,6 +172,33 @@ tg_status tg_scan_block(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G, in
                         const uint32_t* missing, int64_t ldm, const tg_scan_opts* opts,
                         const tg_outputs* out, void* stream);
 
+/* The same block scan for callers that cannot allocate device memory. The paper has no
+ * counterpart: this is a deployment variant. Some callers must not call cudaMalloc or cudaFree
+ * while they scan, e.g. a host application whose device memory belongs to another allocator
+ * (a framework's caching pool, a fixed budget), or a latency-critical loop that cannot take
+ * the device-wide synchronisation cudaMalloc/cudaFree may cause. This call needs no context
+ * and allocates nothing: its scratch (decoded genotype operand, per-marker statistics, status
+ * word) is one static device array of 64 MiB that every GPU loading the library keeps until
+ * the process exits.
+ *   Arguments and outputs: as tg_scan_block (the panel comes from tg_prepare_panel, made
+ *   beforehand). The current device must be the panel's device.
+ *   Limit: the block must fit the 64 MiB scratch, about (2 or 4 bytes + 2 more with missing
+ *   calls) x round_up(N, 64) per marker, e.g. about 1,400 dosage markers at N = 23,000 or
+ *   15,000 at N = 2,000 in the split form; larger blocks return TG_ERR_UNSUPPORTED with the
+ *   maximum in the message, before anything is launched.
+ *   The first call on a device does a one-time set-up (it looks up the array's device address
+ *   with cudaGetSymbolAddress while that device is current); make that first call before any
+ *   stream capture.
+ *   Every call shares the one array, which keeps the last call's contents (the call clears
+ *   what must start at zero): calls that overlap on the GPU, from several threads or streams,
+ *   race on it and must be serialised by the caller.
+ *   Synchronous: returns after the scan finished on `stream`, with TG_ERR_CAPACITY or
+ *   TG_ERR_TIMEOUT if the kernels reported one. */
+tg_status tg_scan_block_static(const tg_panel* panel, const uint8_t* G, int64_t ldg,
+                               int32_t encoding, int64_t N, int64_t M, int64_t marker_offset,
+                               const uint32_t* missing, int64_t ldm, const tg_scan_opts* opts,
+                               const tg_outputs* out, void* stream);
+
 /* The scan of a whole genotype matrix held in HOST memory (pinned for overlap): blocks of
  * block_markers rows are copied to the device on the context's side stream, double
  * buffered, while the previous block is scanned on `stream`; hits, their count and the

@@ -61,6 +61,8 @@ _SIGS = {
                                   _I64, _VP, _VP, _VP, _VP, _VP]),
     "tg_scan_block": (C.c_int, [_VP, _VP, _VP, _I64, _I32, _I64, _I64, _I64, _VP, _I64,
                                 C.POINTER(tg_scan_opts), C.POINTER(tg_outputs), _VP]),
+    "tg_scan_block_static": (C.c_int, [_VP, _VP, _I64, _I32, _I64, _I64, _I64, _VP, _I64,
+                                       C.POINTER(tg_scan_opts), C.POINTER(tg_outputs), _VP]),
     "tg_scan_host": (C.c_int, [_VP, _VP, _VP, _I64, _I32, _I64, _I64, _I64, _I64,
                                C.POINTER(tg_scan_opts), _VP, _I64, C.POINTER(_I64), _VP, _VP]),
     "tg_status_poll": (C.c_int, [_VP, _VP]),
@@ -221,6 +223,16 @@ def tg_scan_block(ctx, panel, G, N, M, encoding, opts: tg_scan_opts, out: tg_out
     ldm = _ld(missing) if missing is not None else 0
     _check(load().tg_scan_block(ctx, panel, _ptr(G), _ld(G), encoding, N, M, marker_offset,
                                 _ptr(missing), ldm, C.byref(opts), C.byref(out), _stream(stream)))
+
+
+def tg_scan_block_static(panel, G, N, M, encoding, opts: tg_scan_opts, out: tg_outputs,
+                         marker_offset=0, missing=None, stream=None):
+    """tg_scan_block without a context and without any device allocation (static scratch).
+    Synchronous; raises TgError on failure (including TG_ERR_CAPACITY / TG_ERR_TIMEOUT)."""
+    ldm = _ld(missing) if missing is not None else 0
+    _check(load().tg_scan_block_static(panel, _ptr(G), _ld(G), encoding, N, M, marker_offset,
+                                       _ptr(missing), ldm, C.byref(opts), C.byref(out),
+                                       _stream(stream)))
 
 
 def tg_scan_host(ctx, panel, G_host, N, M, encoding, block_markers, opts: tg_scan_opts,
