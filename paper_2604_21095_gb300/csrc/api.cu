@@ -278,8 +278,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     if (prec == TG_PREC_FP32) {
       TG_CUDA(launch_sgemm_scan(c->A32, p->Npad, p->B32, p->Npad, p->Npad, ep, st));
     } else {
-      TG_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi, &p->tmBlo, p->Npad, has_lo,
-                             c->tflags, ep, c->sm_count, kSpinNs, st));
+      TG_CUDA(launch_tc2_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi2, &p->tmBlo2, p->Npad, has_lo,
+                              c->tflags, ep, c->sm_count, kSpinNs, st));
     }
   }
   if (ep.do_hits || ep.do_full) {
@@ -466,6 +466,8 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
   p->lnB = host_lnbeta_half((double)p->df);
   if (!make_tmap(&p->tmBhi, p->Bhi, p->Ppad, p->Npad, p->Npad, 256) ||
       !make_tmap(&p->tmBlo, p->Blo, p->Ppad, p->Npad, p->Npad, 256) ||
+      !make_tmap(&p->tmBhi2, p->Bhi, p->Ppad, p->Npad, p->Npad, 128) ||
+      !make_tmap(&p->tmBlo2, p->Blo, p->Ppad, p->Npad, p->Npad, 128) ||
       !make_tmap(&p->tmQhi, p->QBhi, QCOLS, p->Npad, p->Npad, 64) ||
       !make_tmap(&p->tmQlo, p->QBlo, QCOLS, p->Npad, p->Npad, 64))
     return cleanup(fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panel"));

@@ -78,6 +78,7 @@ struct tg_panel {
   __nv_bfloat16* QBlo = nullptr;
   double lnB = 0;
   CUtensorMap tmBhi, tmBlo;      // phenotype panel, 256-row boxes
+  CUtensorMap tmBhi2, tmBlo2;    // phenotype panel, 128-row boxes (one CTA's half of a pair tile)
   CUtensorMap tmQhi, tmQlo;      // covariate projection columns, 64-row boxes
 };
 
@@ -163,6 +164,12 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
                            const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
                            bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
                            long long spin_ns, cudaStream_t st);
+
+// tensor-core kernel on CTA pairs, 256 x 256 tiles (k_tc2.cu)
+cudaError_t launch_tc2_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
+                            const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
+                            bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
+                            long long spin_ns, cudaStream_t st);
 
 // bounded wait test (k_tc.cu)
 cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,

@@ -28,25 +28,12 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace tg {
 namespace {
 
-constexpr int TBM = 128, TBN = 256, TBK = 32;  // TBK bf16 = 64 bytes = one swizzle row
-constexpr int A_BYTES = TBM * TBK * 2;         // 8 KB
-constexpr int B_BYTES = TBN * TBK * 2;         // 16 KB
-constexpr int kEpiWarps = 8;
-// Three warpgroups: warpgroup 0 = producer warp, MMA warp and two idle warps; warpgroups 1-2 =
-// the 8 epilogue warps. At launch every thread gets 168 registers (384 x 168 = 64,512); then
-// warpgroup 0 gives registers back (56 each) and the epilogue warpgroups take them
-// (224 each): 128 x 56 + 256 x 224 = 64,512, the launch total, so the increase cannot stall.
-constexpr int kThreads = 384;
-constexpr int kRegsLow = 56;
-constexpr int kRegsHigh = 224;
-static_assert(128 * kRegsLow + 256 * kRegsHigh <= kThreads * 168, "register split exceeds launch");
-constexpr int kTmemCols = 512;                 // two 128 x 256 FP32 chunk accumulators
-constexpr int kChunkKB = 16;                   // K blocks per accumulation chunk (512 samples)
-constexpr int kGroupM = 8;                     // raster: 8 m-tiles per group
+using namespace tcx;
 
 template <bool HAS_LO>
 struct Cfg {
@@ -55,180 +42,6 @@ struct Cfg {
   static constexpr int kBarBytes = 256;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;  // + alignment slack
 };
-
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
-// both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(TBM >> 4) << 24);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of 64 bytes,
-// 8-row core groups 512 bytes apart (SBO), version 1, start address >> 4.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset
-  d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)4 << 61;            // layout: 64-byte swizzle
-  return d;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0u;
-}
-
-// Bounded wait for the completion of phase `parity`; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                       long long limit_ns, uint32_t* status) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  for (;;) {
-#pragma unroll 1
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if ((long long)(globaltimer_ns() - t0) > limit_ns) {
-      *abort_flag = 1;
-      atomicOr(status, ST_TIMEOUT);
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint32_t dst, uint32_t bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-      "%3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                       uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tile_coord(int tile, int n_mt, int n_nt, int& mt, int& nt) {
-  const int group = kGroupM * n_nt;
-  const int g = tile / group;
-  const int first = g * kGroupM;
-  const int gm = min(kGroupM, n_mt - first);
-  const int idx = tile - g * group;
-  mt = first + idx % gm;
-  nt = idx / gm;
-}
-
-// Statistics of the 128 totals one thread holds: its marker row against 128 consecutive
-// phenotype columns starting at col0, in groups of 16 columns.
-__device__ __forceinline__ void epilogue_tile(const EpiParams& ep, const float (&tot)[128],
-                                              long long row, long long row_base, bool row_ok,
-                                              float rinv, int col0, int lane) {
-#pragma unroll
-  for (int grp = 0; grp < 8; ++grp) {
-    float m[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const int col = col0 + grp * 16 + e;
-      const float D = tot[grp * 16 + e];
-      float r = __int_as_float(0x7fc00000);
-      if (row_ok && col < ep.P) r = corr_nan(D, rinv, ep.col_rmul[col]);
-      m[e] = (r == r) ? fabsf(r) : -1.0f;
-      if (ep.do_hits && r * r >= ep.r2_thr) emit_hit_raw(ep, D, row, col);
-      if (ep.do_full && row_ok && col < ep.P) ep.rstore[row * ep.ldo + col] = r;
-    }
-    if (!ep.do_best) continue;
-    // max over the warp's 32 rows: lanes l and l^16 first, then a reduce-scatter over 16
-    // lanes after which lane l holds the column max for column grp*16 + (l & 15)
-#pragma unroll
-    for (int i = 0; i < 16; ++i) m[i] = fmaxf(m[i], __shfl_xor_sync(0xffffffffu, m[i], 16));
-#pragma unroll
-    for (int s = 8; s >= 1; s >>= 1) {
-      const bool upper = (lane & s) != 0;
-#pragma unroll
-      for (int i = 0; i < s; ++i) {
-        const float send = upper ? m[i] : m[i + s];
-        const float keep = upper ? m[i + s] : m[i];
-        m[i] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, send, s));
-      }
-    }
-    const float cmax = m[0];
-    // the lowest lane (smallest marker) reaching the column max owns the candidate
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const float ce = __shfl_sync(0xffffffffu, cmax, e);
-      const int col = col0 + grp * 16 + e;
-      float r = __int_as_float(0x7fc00000);
-      if (row_ok && col < ep.P) r = corr_nan(tot[grp * 16 + e], rinv, ep.col_rmul[col]);
-      const float a = (r == r) ? fabsf(r) : -1.0f;
-      const unsigned b = __ballot_sync(0xffffffffu, ce >= 0.0f && a == ce);
-      if (lane == e && b != 0u) {
-        const long long marker = ep.marker_offset + row_base + (__ffs(b) - 1);
-        atomicMax(ep.best + col, best_key(ce, marker));
-      }
-    }
-  }
-}
 
 template <bool HAS_LO>
 __global__ void __launch_bounds__(kThreads, 1)

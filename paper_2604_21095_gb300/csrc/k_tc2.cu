@@ -1,0 +1,372 @@
+// Tensor-core scan on CTA pairs: Eq. 2 of Section 2.2 with tcgen05.mma.cta_group::2.
+//
+// The same product as k_tc.cu, D = A (B_hi + B_lo)^T [+ A_lo B_hi^T], on 256 x 256 tiles
+// computed by a cluster of two CTAs on two SMs. Each CTA loads its own 128 marker rows of A
+// and its own half (128 phenotype rows) of B_hi / B_lo; the pair's leader (cluster rank 0)
+// issues one 256 x 256 x 16 MMA that reads A from both CTAs and B from both CTAs and writes
+// rows 0-127 of D into the leader's tensor memory and rows 128-255 into the peer's. Per SM,
+// each MMA of the same size reads 8 KB of shared memory instead of 12 KB, and each K block
+// brings 24 KB over L2 instead of 40 KB, which is what limits the one-CTA kernel.
+//
+// Roles (384 threads, three warpgroups, as in k_tc.cu):
+//   warp 0 lane 0 (both CTAs)   TMA producer into the local stage ring; every copy signals
+//                               the leader's full barrier (cta_group::2 completion)
+//   warp 1 lane 0 (leader only) MMA issuer; commits are multicast to both CTAs' barriers
+//   warps 4..11 (both CTAs)     epilogue on the local 128 rows; the drained signal goes to
+//                               the leader's chunk-empty barrier (16 arrivals: 8 per CTA)
+// Accumulation is chunked exactly as in k_tc.cu (fresh accumulator every 512 samples, FP32
+// totals in registers). Every wait is bounded; a timeout raises the abort flag in both CTAs.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "device.cuh"
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace tg {
+namespace {
+
+using namespace tcx;
+
+constexpr int HB_BYTES = 128 * TBK * 2;  // one CTA's half of a B tile: 8 KB
+
+template <bool HAS_LO>
+struct Cfg2 {
+  static constexpr int kStageBytes = A_BYTES * (HAS_LO ? 2 : 1) + 2 * HB_BYTES;  // 24 or 32 KB
+  static constexpr int kStages = HAS_LO ? 6 : 8;
+  static constexpr int kBarBytes = 256;
+  static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;
+};
+
+constexpr uint32_t kIdesc2 = idesc_bf16_m(256, 256);
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t num_clusters() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+// TMA into local shared memory, completion counted on a barrier that may be the peer's.
+__device__ __forceinline__ void tma_load_2d_pair(const CUtensorMap* map, uint32_t dst,
+                                                 uint32_t bar_cluster, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster)
+      : "memory");
+}
+__device__ __forceinline__ void tc2_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc2), "r"(accumulate)
+      : "memory");
+}
+// Arrive on the barrier at this offset in both CTAs once every prior MMA has completed.
+__device__ __forceinline__ void tc2_commit_both(uint32_t bar) {
+  const uint16_t mask = 0x3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+      "[%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void tc2_commit_local(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// Tile (pair of m-tiles, n-tile) of cluster-level tile index `tile`.
+__device__ __forceinline__ void tile_coord2(int tile, int n_mp, int n_nt, int& mp, int& nt) {
+  constexpr int kGroupP = kGroupM / 2;
+  const int group = kGroupP * n_nt;
+  const int g = tile / group;
+  const int first = g * kGroupP;
+  const int gm = min(kGroupP, n_mp - first);
+  const int idx = tile - g * group;
+  mp = first + idx % gm;
+  nt = idx / gm;
+}
+
+template <bool HAS_LO>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    k_tc2_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+               const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+               int num_kb, int n_mt, int n_nt, const int* __restrict__ tflags, long long spin_ns,
+               EpiParams ep) {
+  using C = Cfg2<HAS_LO>;
+  constexpr int S = C::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t bars = base + S * C::kStageBytes;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (S + s); };
+  auto cfull_bar = [&](int a) { return bars + 8u * (2 * S + a); };
+  auto cempty_bar = [&](int a) { return bars + 8u * (2 * S + 2 + a); };
+  const uint32_t drain_bar = bars + 8u * (2 * S + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * C::kStageBytes + 8 * (2 * S + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  auto sA = [&](int s) { return base + s * C::kStageBytes; };
+  auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
+  auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + HB_BYTES; };
+  auto sAlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * HB_BYTES; };
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const uint32_t peer_abort = map_to_rank(smem_u32((const void*)abort_flag), rank ^ 1u);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(cfull_bar(a), 1);
+      mbar_init(cempty_bar(a), 2 * kEpiWarps);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncwarp();
+  cluster_sync_all();  // both CTAs' barriers initialised, both TMEM allocations done
+  tc_fence_after();
+  const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+  const int n_mp = (n_mt + 1) / 2;
+  const int num_tiles = n_mp * n_nt;
+  const int cid = (int)cluster_id(), ncl = (int)num_clusters();
+  // a timeout in either CTA stops both
+  auto wait = [&](uint32_t bar, uint32_t parity) {
+    const bool ok = mbar_wait(bar, parity, abort_flag, spin_ns, ep.status);
+    if (!ok) st_cluster_u32(peer_abort, 1u);
+    return ok;
+  };
+
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
+    if (warp == 0 && lane == 0) {
+      // ---------------------------------------------------------- TMA producer (both CTAs)
+      int stage = 0;
+      uint32_t phase = 0;
+      int armed[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) armed[s] = -1;
+      bool ok = true;
+      for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
+        int mp, nt;
+        tile_coord2(tile, n_mp, n_nt, mp, nt);
+        const int mt0 = 2 * mp;
+        const bool lo = HAS_LO && (tflags[mt0] != 0 || (mt0 + 1 < n_mt && tflags[mt0 + 1] != 0));
+        const uint32_t pair_bytes = 2u * (A_BYTES + 2 * HB_BYTES + (lo ? A_BYTES : 0));
+        const int arow = (mt0 + (int)rank) * TBM;
+        const int brow = nt * TBN + (int)rank * 128;
+        for (int kb = 0; kb < num_kb; ++kb) {
+          if (!wait(empty_bar(stage), phase ^ 1u)) {
+            ok = false;
+            break;
+          }
+          if (*abort_flag) {
+            ok = false;
+            break;
+          }
+          if (leader) {
+            mbar_expect_tx(full_bar(stage), pair_bytes);
+            armed[stage] = (int)phase;
+          }
+          const uint32_t fb = map_to_rank(full_bar(stage), 0u);
+          tma_load_2d_pair(&tmAhi, sA(stage), fb, kb * TBK, arow);
+          tma_load_2d_pair(&tmBhi, sBhi(stage), fb, kb * TBK, brow);
+          tma_load_2d_pair(&tmBlo, sBlo(stage), fb, kb * TBK, brow);
+          if (lo) tma_load_2d_pair(&tmAlo, sAlo(stage), fb, kb * TBK, arow);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      // the leader's armed stages complete only when both CTAs' copies have landed (bounded)
+      if (leader)
+        for (int s = 0; s < S; ++s)
+          if (armed[s] >= 0) mbar_wait(full_bar(s), (uint32_t)armed[s], abort_flag, spin_ns, ep.status);
+    } else if (warp == 1 && lane == 0 && leader) {
+      // ---------------------------------------------------------- MMA issuer (leader)
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t g = 0;
+      bool ok = true;
+      for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
+        int mp, nt;
+        tile_coord2(tile, n_mp, n_nt, mp, nt);
+        const int mt0 = 2 * mp;
+        const bool lo = HAS_LO && (tflags[mt0] != 0 || (mt0 + 1 < n_mt && tflags[mt0 + 1] != 0));
+        for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kChunkKB, ++g) {
+          const int acc = (int)(g & 1u);
+          const uint32_t ph = (g >> 1) & 1u;
+          if (!wait(cempty_bar(acc), ph ^ 1u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
+          const int kb1 = min(num_kb, kb0 + kChunkKB);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!wait(full_bar(stage), phase)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int k = 0; k < TBK / 16; ++k) {
+              const uint64_t a = sdesc_sw64(sA(stage) + 32u * k);
+              const uint64_t bh = sdesc_sw64(sBhi(stage) + 32u * k);
+              const uint64_t bl = sdesc_sw64(sBlo(stage) + 32u * k);
+              tc2_mma(d, a, bh, (kb > kb0 || k > 0) ? 1u : 0u);
+              tc2_mma(d, a, bl, 1u);
+              if (lo) tc2_mma(d, sdesc_sw64(sAlo(stage) + 32u * k), bh, 1u);
+            }
+            tc2_commit_both(empty_bar(stage));
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (ok) tc2_commit_both(cfull_bar(acc));
+        }
+      }
+      tc2_commit_local(drain_bar);
+      mbar_wait(drain_bar, 0u, abort_flag, spin_ns, ep.status);
+    }
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
+    // ------------------------------------------------------------ epilogue (both CTAs)
+    const int quarter = warp & 3;
+    const int half = (warp - 4) >> 2;
+    const uint32_t leader_cempty0 = map_to_rank(cempty_bar(0), 0u);
+    const uint32_t leader_cempty1 = map_to_rank(cempty_bar(1), 0u);
+    uint32_t g = 0;
+    bool ok = true;
+    for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
+      int mp, nt;
+      tile_coord2(tile, n_mp, n_nt, mp, nt);
+      float tot[128];
+#pragma unroll
+      for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
+      for (int kb0 = 0; kb0 < num_kb; kb0 += kChunkKB, ++g) {
+        const int acc = (int)(g & 1u);
+        const uint32_t ph = (g >> 1) & 1u;
+        if (!wait(cfull_bar(acc), ph)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                               (uint32_t)(acc * TBN + half * 128);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          float v[32];
+          __syncwarp();  // tcgen05.ld is .sync.aligned
+          tc_ld32(taddr + (uint32_t)(i * 32), v);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) tot[i * 32 + e] += v[e];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(acc ? leader_cempty1 : leader_cempty0);
+      }
+      if (!ok) break;
+      const long long row_base = (long long)(2 * mp + (int)rank) * TBM + quarter * 32;
+      const long long row = row_base + lane;
+      const bool row_ok = row < ep.M;
+      const float rinv = row_ok ? ep.row_inv[row] : __int_as_float(0x7fc00000);
+      epilogue_tile(ep, tot, row, row_base, row_ok, rinv, nt * TBN + half * 128, lane);
+      __syncwarp();
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  __syncwarp();
+  cluster_sync_all();  // neither CTA leaves while the other may still signal its barriers
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+template <bool HAS_LO>
+cudaError_t go2(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* bh,
+                const CUtensorMap* bl, int64_t K, const int* tflags, const EpiParams& ep,
+                int sm_count, long long spin_ns, cudaStream_t st) {
+  using C = Cfg2<HAS_LO>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc2_scan<HAS_LO>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int n_mt = (ep.M + TBM - 1) / TBM;
+  const int n_nt = (ep.P + TBN - 1) / TBN;
+  const int tiles = ((n_mt + 1) / 2) * n_nt;
+  const int pairs = tiles < sm_count / 2 ? tiles : sm_count / 2;
+  k_tc2_scan<HAS_LO><<<2 * pairs, kThreads, C::kSmem, st>>>(*a, *alo, *bh, *bl, (int)(K / TBK),
+                                                            n_mt, n_nt, tflags, spin_ns, ep);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc2_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
+                            const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
+                            bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
+                            long long spin_ns, cudaStream_t st) {
+  if (ep.M == 0 || ep.P == 0) return cudaSuccess;
+  if (K % TBK) return cudaErrorInvalidValue;
+  return has_lo ? go2<true>(tmAhi, tmAlo, tmBhi, tmBlo, K, tflags, ep, sm_count, spin_ns, st)
+                : go2<false>(tmAhi, tmAhi, tmBhi, tmBlo, K, tflags, ep, sm_count, spin_ns, st);
+}
+
+}  // namespace tg
