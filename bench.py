@@ -45,6 +45,9 @@ def _args():
     a.add_argument("--cpu-seconds", type=float, default=15.0)
     a.add_argument("--no-cpu-baseline", action="store_true")
     # smaller cases of the same kernels (profiling captures); the default is the full size
+    a.add_argument("--workload", default=WORKLOAD,
+                   help="n23000_m8900000_p20480_c20_u8 (default, 8-bit dosages, P=20,480) or "
+                        "n23000_m1000000_p2048_c10_2bit (PLINK 2-bit calls, 0.5%% missing, P=2,048)")
     a.add_argument("--phenotypes", type=int, default=None)
     a.add_argument("--block-markers", type=int, default=None)
     return a.parse_args()
@@ -54,7 +57,7 @@ def _workload(args):
     import dataclasses
 
     import synth
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[args.workload]
     if args.phenotypes or args.block_markers:
         w = dataclasses.replace(w, P=args.phenotypes or w.P, block=args.block_markers or w.block,
                                 name=w.name + "_reduced")
@@ -157,7 +160,7 @@ def _barrier(dist):
 
 # ------------------------------------------------------------------------- CPU oracle timing
 
-def _oracle_sample(Yt, cov_t, G, seconds: float):
+def _oracle_sample(Yt, cov_t, G, seconds: float, encoding: str = "u8"):
     """Time the FP64 oracle (projected form, with p-values) on groups of 16 markers of the
     benchmark block against the full phenotype panel until `seconds` have passed."""
     import numpy as np
@@ -169,7 +172,7 @@ def _oracle_sample(Yt, cov_t, G, seconds: float):
     done, t_total = 0, 0.0
     while t_total < seconds and done + 16 <= G.shape[0]:
         t0 = time.perf_counter()
-        oracle.scan(G[done:done + 16], "u8", ref_panel, mode="projected")
+        oracle.scan(G[done:done + 16], encoding, ref_panel, mode="projected")
         t_total += time.perf_counter() - t0
         done += 16
     return done, t_total, Yt.shape[0]
@@ -184,17 +187,21 @@ def _reference(args, dist, rank, ws):
     import oracle
     import synth
 
-    w = synth.WORKLOADS[WORKLOAD]
+    w = _workload(args)
     pan = synth.make_panel(w, device="cpu", planted_blocks=1)
     ref_panel = oracle.prepare_panel(pan["Yt"].numpy().T.astype(np.float64), pan["cov_t"].numpy().T)
     per_step = 8
     f = synth.maf(w.seed, 0, per_step * (args.steps + args.warmup))
-    G = synth.dosage_bytes(w.seed, 0, f, w.N).numpy()
+    if w.encoding == "u8":
+        G = synth.dosage_bytes(w.seed, 0, f, w.N).numpy()
+    else:
+        counts, miss = synth.hard_calls(w.seed, 0, f, w.N, w.missing)
+        G = synth.pack_2bit(counts, miss).numpy()
     for s in range(args.warmup):
-        oracle.scan(G[s * per_step:(s + 1) * per_step], "u8", ref_panel, mode="projected")
+        oracle.scan(G[s * per_step:(s + 1) * per_step], w.encoding, ref_panel, mode="projected")
     t0 = time.perf_counter()
     for s in range(args.warmup, args.warmup + args.steps):
-        oracle.scan(G[s * per_step:(s + 1) * per_step], "u8", ref_panel, mode="projected")
+        oracle.scan(G[s * per_step:(s + 1) * per_step], w.encoding, ref_panel, mode="projected")
     dt = time.perf_counter() - t0
     tests = per_step * w.P * args.steps
     value = tests / dt
@@ -212,12 +219,17 @@ def _reference(args, dist, rank, ws):
 
 
 def _config(w):
-    return {"workload": f"{w.name}: N={w.N} samples, {w.block}-marker blocks of 8-bit dosages "
+    enc = "8-bit dosages" if w.encoding == "u8" else f"PLINK 2-bit calls ({100 * w.missing:g}% missing)"
+    return {"workload": f"{w.name}: N={w.N} samples, {w.block}-marker blocks of {enc} "
                         f"(M={w.M} in the whole scan), P={w.P} phenotypes, C={w.n_cov + 1} covariate columns "
                         f"(intercept + {w.n_cov}), hits at -log10 p >= 7.30103",
-            "N": w.N, "P": w.P, "C": w.n_cov + 1, "block_markers": w.block, "encoding": "u8 dosage",
+            "N": w.N, "P": w.P, "C": w.n_cov + 1, "block_markers": w.block,
+            "encoding": "u8 dosage" if w.encoding == "u8" else "2-bit PLINK",
             "precision": "split-bf16 (A exact bf16, panel bf16 hi+lo, fp32 accumulate)",
-            "l2": f"inputs larger than L2: {RESIDENT} resident 1.5 GB blocks cycled, 1.9 GB panel"}
+            "l2": f"inputs larger than L2: {RESIDENT} resident genotype blocks of "
+                  f"{w.block * (w.N if w.encoding == 'u8' else (w.N + 3) // 4) / 1e9:.2f} GB cycled, "
+                  f"{2 * 2 * w.P * w.N / 1e9:.2f} GB bf16 panel; the decoded operand alone is "
+                  f"{2 * w.block * w.N / 1e9:.2f} GB per block"}
 
 
 # ------------------------------------------------------------------------- ours
@@ -234,6 +246,7 @@ def _ours(args, dist, rank, ws):
     dev = torch.device("cuda", local)
     tg.build()
     w = _workload(args)
+    enc = tg.TG_ENC_U8_DOSAGE if w.encoding == "u8" else tg.TG_ENC_2BIT
     ctx = tg.tg_create(local)
     stream = torch.cuda.current_stream(dev)
 
@@ -260,7 +273,7 @@ def _ours(args, dist, rank, ws):
     def step(i, prec):
         opts = tg.tg_scan_opts(prec, 0, THR)
         b = i % RESIDENT
-        tg.tg_scan_block(ctx, panel, blocks[b], w.N, M, tg.TG_ENC_U8_DOSAGE, opts, out,
+        tg.tg_scan_block(ctx, panel, blocks[b], w.N, M, enc, opts, out,
                          marker_offset=mine[b] * w.block, stream=stream)
 
     # split-BF16, the headline
@@ -325,7 +338,7 @@ def _ours(args, dist, rank, ws):
         opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, THR)
         per_call = RESIDENT
         calls = max(1, args.e2e_steps // per_call)
-        tg.tg_scan_host(ctx, panel, host, w.N, per_call * M, tg.TG_ENC_U8_DOSAGE, M, opts, hits_h,
+        tg.tg_scan_host(ctx, panel, host, w.N, per_call * M, enc, M, opts, hits_h,
                         best_h, stream=stream)
         torch.cuda.synchronize()
         tg.tg_stage_times(ctx, reset=True)
@@ -334,7 +347,7 @@ def _ours(args, dist, rank, ws):
         t0 = time.perf_counter()
         nh_e2e = 0
         for _ in range(calls):
-            nh_e2e = tg.tg_scan_host(ctx, panel, host, w.N, per_call * M, tg.TG_ENC_U8_DOSAGE, M,
+            nh_e2e = tg.tg_scan_host(ctx, panel, host, w.N, per_call * M, enc, M,
                                      opts, hits_h, best_h, stream=stream)
         dt = _max_over_ranks(dist, time.perf_counter() - t0)
         tg.tg_set_profiling(ctx, False)
@@ -361,7 +374,7 @@ def _ours(args, dist, rank, ws):
     cpu = None
     if want_cpu:
         done, secs, P = _oracle_sample(cpu_inputs[0], cpu_inputs[1], blocks[0][:4096].cpu(),
-                                       args.cpu_seconds)
+                                       args.cpu_seconds, w.encoding)
         cpu = {"value": done * P / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{done} markers x {P} phenotypes of block 0, FP64 projected OLS with "
                          f"p-values, {secs:.1f} s (panel preparation excluded, as on the GPU)"}

@@ -14,11 +14,11 @@
 //   warps 4..11    epilogue: tcgen05.ld of the accumulator (thread = marker row, each warp one
 //                  TMEM lane quarter and one half of the 256 columns), r = D / |g_res|, hits
 //                  above the r^2 threshold, per-phenotype best marker, optionally every statistic.
-// Accumulation is chunked: the tensor core sums at most 512 samples (16 K blocks) into a
+// Accumulation is chunked: the tensor core sums at most 1024 samples (32 K blocks) into a
 // fresh TMEM accumulator, and the epilogue warps add the chunk results into FP32 totals held
 // in registers with round-to-nearest adds. The tensor core's FP32 accumulation drops low bits
 // toward zero at each chained addition, which over 23,000 samples biases |r| low by about
-// 5e-5 relative; chunks of 512 keep that bias near 1e-6. Two chunk accumulators (512 TMEM
+// 5e-5 relative; chunks of 1024 keep that bias near 2e-6. Two chunk accumulators (512 TMEM
 // columns) alternate, so draining one overlaps the products of the next.
 // Every mbarrier wait is bounded: past the limit the kernel latches ST_TIMEOUT, raises a
 // shared abort flag, lets in-flight copies and products finish (again bounded), frees its

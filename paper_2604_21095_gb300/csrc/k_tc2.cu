@@ -14,7 +14,7 @@
 //   warp 1 lane 0 (leader only) MMA issuer; commits are multicast to both CTAs' barriers
 //   warps 4..11 (both CTAs)     epilogue on the local 128 rows; the drained signal goes to
 //                               the leader's chunk-empty barrier (16 arrivals: 8 per CTA)
-// Accumulation is chunked exactly as in k_tc.cu (fresh accumulator every 512 samples, FP32
+// Accumulation is chunked exactly as in k_tc.cu (fresh accumulator every 1024 samples, FP32
 // totals in registers). Every wait is bounded; a timeout raises the abort flag in both CTAs.
 #include <cuda.h>
 #include <cuda_bf16.h>

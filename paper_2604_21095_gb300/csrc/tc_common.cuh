@@ -25,8 +25,8 @@ constexpr int kRegsLow = 56;
 constexpr int kRegsHigh = 224;
 static_assert(128 * kRegsLow + 256 * kRegsHigh <= kThreads * 168, "register split exceeds launch");
 constexpr int kTmemCols = 512;                 // two 128 x 256 FP32 chunk accumulators
-constexpr int kChunkKB = 16;                   // K blocks per accumulation chunk (512 samples)
-constexpr int kGroupM = 8;                     // raster: 8 m-tiles per group
+constexpr int kChunkKB = 32;                   // K blocks per accumulation chunk (1024 samples)
+constexpr int kGroupM = 16;                    // raster: 16 m-tiles per group
 
 
 

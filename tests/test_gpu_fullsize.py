@@ -120,3 +120,55 @@ def test_fullsize_every_statistic_sampled(tgctx, full):
     assert np.all(np.abs(sub("se") - ref["se"]) <= 1e-4 * ref["se"])
     print(f"\nfull size FULL output, sampled max errors: -log10p {dm.max():.2e}, "
           f"beta/max(|beta|,se) {(db / np.maximum(np.abs(ref['beta']), ref['se'])).max():.2e}")
+
+
+W2 = synth.WORKLOADS["n23000_m1000000_p2048_c10_2bit"]
+
+
+def test_2bit_panel2048_block_hits_and_sampled_statistics(tgctx):
+    """2-bit calls with 0.5% missing (imputation products active), N = 23,000, P = 2,048,
+    intercept + 9 covariates, one 65,536-marker block: every hit and a sample of every
+    statistic against the oracle."""
+    torch.cuda.synchronize()
+    pan = synth.make_panel(W2, device="cuda", planted_blocks=1)
+    panel = tg.tg_prepare_panel(tgctx, pan["Yt"], W2.N, W2.P, pan["cov_t"])
+    try:
+        blk = synth.make_block(W2, 0, device="cuda")
+        res = run_scan(tgctx, panel, blk["G"], W2.N, W2.P, "2bit", "split", full=False,
+                       hit_mlog10p=THR, hit_capacity=1 << 20)
+        assert res["status"] == tg.TG_OK and res["n_hits"] == len(res["hits"]) > 0
+        got = {(int(h["marker"]), int(h["pheno"])) for h in res["hits"]}
+        for m, p in pan["pairs"]:
+            assert (m, p) in got, (m, p)
+        markers = sorted({int(h["marker"]) for h in res["hits"]})
+        phenos = sorted({int(h["pheno"]) for h in res["hits"]})
+        Y = pan["Yt"][phenos].cpu().numpy().T.astype(np.float64)
+        ref = oracle.scan(blk["G"][markers].cpu().numpy(), "2bit",
+                          oracle.prepare_panel(Y, pan["cov_t"].cpu().numpy().T))
+        mi = {m: i for i, m in enumerate(markers)}
+        pi = {p: i for i, p in enumerate(phenos)}
+        worst = 0.0
+        for h in res["hits"]:
+            j, p = mi[int(h["marker"])], pi[int(h["pheno"])]
+            mo = ref["mlog10p"][j, p]
+            assert abs(h["mlog10p"] - mo) <= max(1e-3, 1e-5 * mo), (h, mo)
+            assert abs(h["beta"] - ref["beta"][j, p]) <= 1e-4 * max(abs(ref["beta"][j, p]), ref["se"][j, p])
+            worst = max(worst, abs(h["mlog10p"] - mo))
+        # every statistic for 256 markers, sampled against the oracle
+        G = blk["G"][:256].contiguous()
+        full = run_scan(tgctx, panel, G, W2.N, W2.P, "2bit", "split", full=True)
+        rng = np.random.default_rng(2)
+        sm = np.sort(rng.choice(256, 40, replace=False)).tolist()
+        sp = np.sort(rng.choice(W2.P, 200, replace=False)).tolist()
+        Y = pan["Yt"][sp].cpu().numpy().T.astype(np.float64)
+        ref2 = oracle.scan(G[sm].cpu().numpy(), "2bit",
+                           oracle.prepare_panel(Y, pan["cov_t"].cpu().numpy().T))
+        sub = lambda k: full[k][np.ix_(sm, sp)]
+        dm = np.abs(sub("mlog10p") - ref2["mlog10p"])
+        assert np.all(dm <= np.maximum(1e-3, 1e-5 * ref2["mlog10p"]))
+        db = np.abs(sub("beta") - ref2["beta"])
+        assert np.all(db <= 1e-4 * np.maximum(np.abs(ref2["beta"]), ref2["se"]))
+        print(f"\n2-bit P=2048: {len(res['hits'])} hits, max hit |d -log10 p| {worst:.2e}; "
+              f"sampled max |d -log10 p| {dm.max():.2e}")
+    finally:
+        tg.tg_panel_free(panel)
