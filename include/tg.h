@@ -212,6 +212,49 @@ tg_status tg_scan_host(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G_host
                        int64_t hit_capacity, int64_t* n_hits, unsigned long long* best_host,
                        void* stream);
 
+/* ---- Batched form: many panels, ragged blocks, one captured graph, tuned tiles ----------- */
+
+/* One panel made of n panels that were prepared from the same N samples and the same
+ * covariates (their covariate bases must be bit-identical; otherwise TG_ERR_INVALID_ARG):
+ * the phenotype columns are concatenated in order, so panel i's columns start at the sum of
+ * the earlier panels' P. Scanning it runs one persistent kernel over all panels' columns
+ * (Section 2.1: the panel is prepared once and reused; here several panels share one scan).
+ * The inputs stay valid and owned by the caller; the result is a new library-owned panel.
+ * Synchronous. */
+tg_status tg_panel_concat(tg_ctx* ctx, const tg_panel* const* panels, int n, tg_panel** out,
+                          void* stream);
+
+typedef struct tg_graph tg_graph;
+
+/* Capture the scans of n_blocks genotype blocks (each as tg_scan_block: device pointer G[b],
+ * M[b] markers, global marker offset marker_offset[b], optional mask missing[b]; the arrays
+ * themselves are host memory) into one CUDA graph. Hits, their count and the per-phenotype
+ * best keys accumulate in `out` over all blocks; full output and per-marker outputs are not
+ * supported here. The context's workspace is sized for the largest block before the capture
+ * and is then held by the graph: while the graph exists, tg_scan_block on the same context
+ * only accepts blocks that fit it. */
+tg_status tg_scan_graph_create(tg_ctx* ctx, const tg_panel* panel, int n_blocks,
+                               const uint8_t* const* G, const int64_t* M,
+                               const int64_t* marker_offset, const uint32_t* const* missing,
+                               int64_t ldg, int64_t ldm, int32_t encoding, int64_t N,
+                               const tg_scan_opts* opts, const tg_outputs* out, tg_graph** graph);
+/* Replay the captured scans on `stream` (asynchronous). */
+tg_status tg_scan_graph_launch(tg_graph* graph, void* stream);
+tg_status tg_scan_graph_free(tg_graph* graph);
+
+/* Time the tensor-core scan of an M-marker block of this panel with each candidate kernel
+ * (CTA pairs on 256 x 256 tiles, or one CTA per 128 x 256 tile) and raster group, on a
+ * pseudo-random block, and keep the fastest for blocks of this size (same power of two) in the
+ * context. Synchronous; allocates a temporary block. */
+tg_status tg_autotune(tg_ctx* ctx, const tg_panel* panel, int32_t encoding, int64_t M,
+                      void* stream);
+/* The tuned choice for M-marker blocks: kernel 2 = CTA pairs, 1 = one CTA per tile; group =
+ * m-tiles per raster group. */
+tg_status tg_tuning(const tg_ctx* ctx, int64_t M, int32_t* kernel, int32_t* group);
+/* Set the choice for M-marker blocks by hand (e.g. from a saved tuning): kernel 1 or 2, group
+ * in [1, 1024]. */
+tg_status tg_set_tuning(tg_ctx* ctx, int64_t M, int32_t kernel, int32_t group);
+
 /* Synchronise `stream`, then return and clear the latched device status
  * (TG_ERR_CAPACITY, TG_ERR_TIMEOUT) of work queued so far. */
 tg_status tg_status_poll(tg_ctx* ctx, void* stream);

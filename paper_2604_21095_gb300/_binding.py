@@ -65,6 +65,16 @@ _SIGS = {
                                        C.POINTER(tg_scan_opts), C.POINTER(tg_outputs), _VP]),
     "tg_scan_host": (C.c_int, [_VP, _VP, _VP, _I64, _I32, _I64, _I64, _I64, _I64,
                                C.POINTER(tg_scan_opts), _VP, _I64, C.POINTER(_I64), _VP, _VP]),
+    "tg_panel_concat": (C.c_int, [_VP, C.POINTER(_VP), C.c_int, C.POINTER(_VP), _VP]),
+    "tg_scan_graph_create": (C.c_int, [_VP, _VP, C.c_int, C.POINTER(_VP), C.POINTER(_I64),
+                                       C.POINTER(_I64), C.POINTER(_VP), _I64, _I64, _I32, _I64,
+                                       C.POINTER(tg_scan_opts), C.POINTER(tg_outputs),
+                                       C.POINTER(_VP)]),
+    "tg_scan_graph_launch": (C.c_int, [_VP, _VP]),
+    "tg_scan_graph_free": (C.c_int, [_VP]),
+    "tg_autotune": (C.c_int, [_VP, _VP, _I32, _I64, _VP]),
+    "tg_tuning": (C.c_int, [_VP, _I64, C.POINTER(_I32), C.POINTER(_I32)]),
+    "tg_set_tuning": (C.c_int, [_VP, _I64, _I32, _I32]),
     "tg_status_poll": (C.c_int, [_VP, _VP]),
     "tg_set_profiling": (C.c_int, [_VP, C.c_int]),
     "tg_stage_times": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_I64), C.c_int]),
@@ -248,6 +258,54 @@ def tg_scan_host(ctx, panel, G_host, N, M, encoding, block_markers, opts: tg_sca
         return n.value
     _check(st)
     return n.value
+
+
+def tg_panel_concat(ctx, panels, stream=None):
+    """One panel whose columns are the given panels' columns, in order."""
+    arr = (_VP * len(panels))(*[p.value if isinstance(p, _VP) else p for p in panels])
+    out = _VP()
+    _check(load().tg_panel_concat(ctx, arr, len(panels), C.byref(out), _stream(stream)))
+    return out
+
+
+def tg_scan_graph_create(ctx, panel, blocks, N, encoding, opts: tg_scan_opts, out: tg_outputs,
+                         marker_offsets, missing=None):
+    """blocks: list of uint8 device tensors [M_b][ldg] (same ldg); returns a graph handle."""
+    n = len(blocks)
+    G = (_VP * n)(*[b.data_ptr() for b in blocks])
+    M = (_I64 * n)(*[b.shape[0] for b in blocks])
+    off = (_I64 * n)(*marker_offsets)
+    miss = None
+    ldm = 0
+    if missing is not None:
+        miss = (_VP * n)(*[_ptr(m) for m in missing])
+        ldm = next(_ld(m) for m in missing if m is not None)
+    g = _VP()
+    _check(load().tg_scan_graph_create(ctx, panel, n, G, M, off, miss, _ld(blocks[0]), ldm,
+                                       encoding, N, C.byref(opts), C.byref(out), C.byref(g)))
+    return g
+
+
+def tg_scan_graph_launch(graph, stream=None):
+    _check(load().tg_scan_graph_launch(graph, _stream(stream)))
+
+
+def tg_scan_graph_free(graph):
+    _check(load().tg_scan_graph_free(graph))
+
+
+def tg_autotune(ctx, panel, encoding, M, stream=None):
+    _check(load().tg_autotune(ctx, panel, encoding, M, _stream(stream)))
+
+
+def tg_tuning(ctx, M):
+    k, g = _I32(), _I32()
+    _check(load().tg_tuning(ctx, M, C.byref(k), C.byref(g)))
+    return {"kernel": "pair" if k.value == 2 else "single", "group_m": g.value}
+
+
+def tg_set_tuning(ctx, M, kernel: str, group_m: int):
+    _check(load().tg_set_tuning(ctx, M, 2 if kernel == "pair" else 1, group_m))
 
 
 def tg_status_poll(ctx, stream=None) -> int:

@@ -38,6 +38,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+}  // namespace
+
+namespace tg {
 // 2-D bf16 tensor map: rows x K elements, row stride ld elements, box box_rows x 32, 64B swizzle.
 bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t ld,
                uint32_t box_rows) {
@@ -52,6 +55,9 @@ bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
+}  // namespace tg
+
+namespace {
 
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
@@ -147,16 +153,9 @@ cudaError_t ensure_operands(tg_ctx* c, int64_t M, int64_t Npad, int prec, bool n
   return cudaSuccess;
 }
 
-struct ScanArgs {
-  const uint8_t* G;
-  int64_t ldg;
-  int encoding;
-  int64_t N, M, marker_offset;
-  const uint32_t* missing;
-  int64_t ldm;
-  tg_scan_opts opts;
-  tg_outputs out;
-};
+}  // namespace
+
+namespace tg {
 
 tg_status check_scan_args(const tg_ctx* c, const tg_panel* p, const ScanArgs& a) {
   TG_ARG(c && p, "null context or panel");
@@ -184,17 +183,33 @@ tg_status check_scan_args(const tg_ctx* c, const tg_panel* p, const ScanArgs& a)
   return TG_OK;
 }
 
+}  // namespace tg
+
+namespace {
+
 float r2_threshold(tg_panel* p, double mlog10p) {
   if (!(mlog10p > 0.0)) return 2.0f;  // never reached
   const double r2 = host_r2_threshold(mlog10p, (double)p->df, p->lnB);
   return (float)r2;
 }
 
+}  // namespace
+
+namespace tg {
+
 tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream_t st) {
   tg_panel* p = const_cast<tg_panel*>(pc);
   if (a.M == 0) return TG_OK;
   const int prec = a.opts.precision;
   const bool has_lo = prec == TG_PREC_SPLIT_BF16 && (a.encoding == TG_ENC_2BIT || a.missing);
+  if (c->graphs_alive > 0) {
+    const bool grow = a.M > c->cap_m || round_up(a.M, MT) > c->cap_rows || p->Npad > c->cap_npad ||
+                      (prec == TG_PREC_FP32 ? !c->A32 : (!c->Ahi || (has_lo && !c->Alo)));
+    if (grow)
+      return fail(TG_ERR_INVALID_ARG,
+                  "the context's workspace is held by a captured scan graph: scan blocks no "
+                  "larger than the graph's, or use another context");
+  }
   TG_CUDA(ensure_markers(c, a.M));
   TG_CUDA(ensure_operands(c, a.M, p->Npad, prec, has_lo));
   const float kappa = a.encoding == TG_ENC_U8_DOSAGE ? (float)(2.0 / 255.0) : 1.0f;
@@ -278,8 +293,14 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     if (prec == TG_PREC_FP32) {
       TG_CUDA(launch_sgemm_scan(c->A32, p->Npad, p->B32, p->Npad, p->Npad, ep, st));
     } else {
-      TG_CUDA(launch_tc2_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi2, &p->tmBlo2, p->Npad, has_lo,
-                              c->tflags, ep, c->sm_count, kSpinNs, st));
+      const int b = tune_bucket(a.M);
+      const int group = c->tune_group[b] > 0 ? c->tune_group[b] : 16;
+      if (c->tune_kernel[b] == TUNE_SINGLE)
+        TG_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi, &p->tmBlo, p->Npad, has_lo,
+                               c->tflags, ep, c->sm_count, kSpinNs, st, group));
+      else
+        TG_CUDA(launch_tc2_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi2, &p->tmBlo2, p->Npad, has_lo,
+                                c->tflags, ep, c->sm_count, kSpinNs, st, group));
     }
   }
   if (ep.do_hits || ep.do_full) {
@@ -290,7 +311,7 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   return TG_OK;
 }
 
-}  // namespace
+}  // namespace tg
 
 namespace tg {
 
@@ -322,6 +343,13 @@ double host_r2_threshold(double mlog10p, double df, double lnB) {
 }
 
 }  // namespace tg
+
+struct tg_graph {
+  tg_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches[TG_N_STAGES] = {0, 0, 0, 0, 0, 0};
+};
 
 extern "C" {
 
@@ -678,6 +706,279 @@ tg_status tg_bounded_wait_test(tg_ctx* c, const uint32_t* flag, int64_t limit_ns
   TG_CUDA(cudaStreamSynchronize(st));
   if (h == 2u) return fail(TG_ERR_TIMEOUT, "the flag was not set within the limit");
   if (h != 1u) return fail(TG_ERR_CUDA, "wait kernel did not report");
+  return TG_OK;
+}
+
+
+// ------------------------------------------------------------------ batched form
+
+tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_panel** out,
+                          void* stream) {
+  TG_ARG(c && panels && out && n >= 1, "bad arguments");
+  *out = nullptr;
+  const tg_panel* p0 = panels[0];
+  TG_ARG(p0 != nullptr, "null panel");
+  int64_t P = 0;
+  for (int i = 0; i < n; ++i) {
+    TG_ARG(panels[i] != nullptr, "null panel");
+    const tg_panel* pi = panels[i];
+    TG_ARG(pi->N == p0->N && pi->q == p0->q && pi->n_cov == p0->n_cov && pi->device == p0->device,
+           "panels differ in samples or covariate rank");
+    P += pi->P;
+  }
+  TG_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t N = p0->N, q = p0->q;
+  // the covariate bases must be identical (same covariates, same deterministic QR)
+  {
+    std::vector<double> a((size_t)(q * N)), b((size_t)(q * N));
+    TG_CUDA(cudaMemcpy(a.data(), p0->Q, sizeof(double) * a.size(), cudaMemcpyDeviceToHost));
+    for (int i = 1; i < n; ++i) {
+      TG_CUDA(cudaMemcpy(b.data(), panels[i]->Q, sizeof(double) * b.size(), cudaMemcpyDeviceToHost));
+      if (std::memcmp(a.data(), b.data(), sizeof(double) * a.size()) != 0)
+        return fail(TG_ERR_INVALID_ARG, "panels were prepared with different covariates");
+    }
+  }
+  tg_panel* r = new tg_panel();
+  r->device = p0->device;
+  r->N = N;
+  r->P = P;
+  r->n_cov = p0->n_cov;
+  r->q = q;
+  r->df = p0->df;
+  r->Npad = p0->Npad;
+  r->Ppad = round_up(std::max<int64_t>(P, 1), PPAD);
+  r->lnB = p0->lnB;
+  const int64_t Np = r->Npad, Pp = r->Ppad;
+  cudaError_t e;
+  if ((e = dalloc(&r->Q, (size_t)(q * N))) || (e = dalloc(&r->Yres, (size_t)(std::max<int64_t>(P, 1) * N))) ||
+      (e = dalloc(&r->s, (size_t)std::max<int64_t>(P, 1))) ||
+      (e = dalloc(&r->col_s, (size_t)std::max<int64_t>(P, 1))) || (e = dalloc(&r->col_rmul, (size_t)Pp)) ||
+      (e = dalloc(&r->Bhi, (size_t)(Pp * Np))) || (e = dalloc(&r->Blo, (size_t)(Pp * Np))) ||
+      (e = dalloc(&r->B32, (size_t)(Pp * Np))) || (e = dalloc(&r->QB, (size_t)(QCOLS * Np))) ||
+      (e = dalloc(&r->QBhi, (size_t)(QCOLS * Np))) || (e = dalloc(&r->QBlo, (size_t)(QCOLS * Np)))) {
+    tg_panel_free(r);
+    return cuda_fail(e, "tg_panel_concat allocation");
+  }
+  auto run = [&]() -> cudaError_t {
+    cudaError_t x;
+    if ((x = cudaMemsetAsync(r->Bhi, 0, sizeof(__nv_bfloat16) * Pp * Np, st)) ||
+        (x = cudaMemsetAsync(r->Blo, 0, sizeof(__nv_bfloat16) * Pp * Np, st)) ||
+        (x = cudaMemsetAsync(r->B32, 0, sizeof(float) * Pp * Np, st)) ||
+        (x = cudaMemsetAsync(r->col_rmul, 0, sizeof(float) * Pp, st)) ||
+        (x = cudaMemcpyAsync(r->Q, p0->Q, sizeof(double) * q * N, cudaMemcpyDeviceToDevice, st)) ||
+        (x = cudaMemcpyAsync(r->QB, p0->QB, sizeof(float) * QCOLS * Np, cudaMemcpyDeviceToDevice, st)) ||
+        (x = cudaMemcpyAsync(r->QBhi, p0->QBhi, 2 * QCOLS * Np, cudaMemcpyDeviceToDevice, st)) ||
+        (x = cudaMemcpyAsync(r->QBlo, p0->QBlo, 2 * QCOLS * Np, cudaMemcpyDeviceToDevice, st)))
+      return x;
+    int64_t off = 0;
+    for (int i = 0; i < n; ++i) {
+      const tg_panel* pi = panels[i];
+      const int64_t k = pi->P;
+      if (k == 0) continue;
+      if ((x = cudaMemcpyAsync(r->Yres + off * N, pi->Yres, sizeof(double) * k * N, cudaMemcpyDeviceToDevice, st)) ||
+          (x = cudaMemcpyAsync(r->s + off, pi->s, sizeof(double) * k, cudaMemcpyDeviceToDevice, st)) ||
+          (x = cudaMemcpyAsync(r->col_s + off, pi->col_s, sizeof(float) * k, cudaMemcpyDeviceToDevice, st)) ||
+          (x = cudaMemcpyAsync(r->col_rmul + off, pi->col_rmul, sizeof(float) * k, cudaMemcpyDeviceToDevice, st)) ||
+          (x = cudaMemcpyAsync(r->Bhi + off * Np, pi->Bhi, 2 * k * Np, cudaMemcpyDeviceToDevice, st)) ||
+          (x = cudaMemcpyAsync(r->Blo + off * Np, pi->Blo, 2 * k * Np, cudaMemcpyDeviceToDevice, st)) ||
+          (x = cudaMemcpyAsync(r->B32 + off * Np, pi->B32, sizeof(float) * k * Np, cudaMemcpyDeviceToDevice, st)))
+        return x;
+      off += k;
+    }
+    return cudaStreamSynchronize(st);
+  };
+  if ((e = run())) {
+    tg_panel_free(r);
+    return cuda_fail(e, "tg_panel_concat copy");
+  }
+  if (!make_tmap(&r->tmBhi, r->Bhi, Pp, Np, Np, 256) || !make_tmap(&r->tmBlo, r->Blo, Pp, Np, Np, 256) ||
+      !make_tmap(&r->tmBhi2, r->Bhi, Pp, Np, Np, 128) || !make_tmap(&r->tmBlo2, r->Blo, Pp, Np, Np, 128) ||
+      !make_tmap(&r->tmQhi, r->QBhi, QCOLS, Np, Np, 64) || !make_tmap(&r->tmQlo, r->QBlo, QCOLS, Np, Np, 64)) {
+    tg_panel_free(r);
+    return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the concatenated panel");
+  }
+  *out = r;
+  return TG_OK;
+}
+
+tg_status tg_scan_graph_create(tg_ctx* c, const tg_panel* p, int n_blocks,
+                               const uint8_t* const* G, const int64_t* M,
+                               const int64_t* marker_offset, const uint32_t* const* missing,
+                               int64_t ldg, int64_t ldm, int32_t encoding, int64_t N,
+                               const tg_scan_opts* opts, const tg_outputs* out, tg_graph** graph) {
+  TG_ARG(c && p && G && M && marker_offset && opts && out && graph && n_blocks >= 1, "bad arguments");
+  *graph = nullptr;
+  TG_ARG(!opts->full_output, "captured scan graphs collect hits and best markers only");
+  TG_ARG(!out->marker_norm2 && !out->marker_nobs && !out->marker_mean,
+         "per-marker outputs are not supported in captured scan graphs");
+  TG_CUDA(cudaSetDevice(c->device));
+  int64_t maxM = 0;
+  bool any_lo = false;
+  for (int b = 0; b < n_blocks; ++b) {
+    ScanArgs a{G[b], ldg, encoding, N, M[b], marker_offset[b], missing ? missing[b] : nullptr, ldm,
+               *opts, *out};
+    tg_status s = check_scan_args(c, p, a);
+    if (s != TG_OK) return s;
+    maxM = std::max(maxM, M[b]);
+    any_lo |= encoding == TG_ENC_2BIT || (missing && missing[b]);
+  }
+  const bool lo = opts->precision == TG_PREC_SPLIT_BF16 && any_lo;
+  // size the workspace now: nothing may allocate inside the capture
+  TG_CUDA(ensure_markers(c, maxM));
+  TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision, lo));
+  cudaStream_t cap = nullptr;
+  TG_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  tg_graph* g = new tg_graph();
+  g->ctx = c;
+  int64_t before[TG_N_STAGES];
+  std::memcpy(before, c->launches, sizeof(before));
+  const bool prof = c->prof;
+  c->prof = false;
+  tg_status s = TG_OK;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int b = 0; b < n_blocks && s == TG_OK; ++b) {
+      ScanArgs a{G[b], ldg, encoding, N, M[b], marker_offset[b], missing ? missing[b] : nullptr,
+                 ldm, *opts, *out};
+      s = scan_impl(c, p, a, cap);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g->graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  c->prof = prof;
+  for (int i = 0; i < TG_N_STAGES; ++i) {
+    g->launches[i] = c->launches[i] - before[i];
+    c->launches[i] = before[i];
+  }
+  cudaStreamDestroy(cap);
+  if (s == TG_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (s != TG_OK || e != cudaSuccess) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return s != TG_OK ? s : cuda_fail(e, "tg_scan_graph_create capture");
+  }
+  c->graphs_alive += 1;
+  *graph = g;
+  return TG_OK;
+}
+
+tg_status tg_scan_graph_launch(tg_graph* g, void* stream) {
+  TG_ARG(g && g->exec, "null graph");
+  TG_CUDA(cudaSetDevice(g->ctx->device));
+  TG_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+  for (int i = 0; i < TG_N_STAGES; ++i) g->ctx->launches[i] += g->launches[i];
+  return TG_OK;
+}
+
+tg_status tg_scan_graph_free(tg_graph* g) {
+  if (!g) return TG_OK;
+  cudaSetDevice(g->ctx->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  g->ctx->graphs_alive -= 1;
+  delete g;
+  return TG_OK;
+}
+
+tg_status tg_autotune(tg_ctx* c, const tg_panel* p, int32_t encoding, int64_t M, void* stream) {
+  TG_ARG(c && p && M > 0, "bad arguments");
+  TG_ARG(encoding == TG_ENC_2BIT || encoding == TG_ENC_U8_DOSAGE, "unknown encoding");
+  TG_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ldg = round_up(encoding == TG_ENC_2BIT ? (p->N + 3) / 4 : p->N, 16);
+  uint8_t* G = nullptr;
+  tg_hit* hits = nullptr;
+  unsigned long long* cnt = nullptr;
+  unsigned long long* best = nullptr;
+  cudaError_t e;
+  auto cleanup = [&]() { dfree(G); dfree(hits); dfree(cnt); dfree(best); };
+  if ((e = dalloc(&G, (size_t)(M * ldg))) || (e = dalloc(&hits, 1024)) || (e = dalloc(&cnt, 1)) ||
+      (e = dalloc(&best, (size_t)std::max<int64_t>(p->P, 1)))) {
+    cleanup();
+    return cuda_fail(e, "tg_autotune allocation");
+  }
+  if ((e = launch_fill_random(G, (size_t)(M * ldg), 0x5eed5eedull, st))) {
+    cleanup();
+    return cuda_fail(e, "tg_autotune fill");
+  }
+  tg_outputs o{};
+  o.hits = hits;
+  o.hit_capacity = 1024;
+  o.n_hits = cnt;
+  o.best = best;
+  const tg_scan_opts opts{TG_PREC_SPLIT_BF16, 0, 7.30103};
+  ScanArgs a{G, ldg, encoding, p->N, M, 0, nullptr, 0, opts, o};
+  const int b = tune_bucket(M);
+  const int kinds[] = {TUNE_PAIR, TUNE_PAIR, TUNE_PAIR, TUNE_PAIR, TUNE_SINGLE, TUNE_SINGLE, TUNE_SINGLE};
+  const int groups[] = {4, 8, 16, 32, 8, 16, 32};
+  const int save_k = c->tune_kernel[b], save_g = c->tune_group[b];
+  const bool prof = c->prof;
+  // the trial launches do not count in the caller's stage statistics
+  tg_stage_times(c, nullptr, nullptr, 0);
+  double save_ms[TG_N_STAGES];
+  int64_t save_n[TG_N_STAGES];
+  std::memcpy(save_ms, c->stage_ms, sizeof(save_ms));
+  std::memcpy(save_n, c->launches, sizeof(save_n));
+  double best_ms = 1e30;
+  int best_i = -1;
+  tg_status s = TG_OK;
+  for (int i = 0; i < 7 && s == TG_OK; ++i) {
+    c->tune_kernel[b] = kinds[i];
+    c->tune_group[b] = groups[i];
+    c->prof = false;
+    s = scan_impl(c, p, a, st);  // warm-up (and first-use set-up)
+    if (s != TG_OK) break;
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st))) { s = cuda_fail(e, "autotune"); break; }
+    double ms_before[TG_N_STAGES];
+    int64_t n_before[TG_N_STAGES];
+    tg_stage_times(c, ms_before, n_before, 0);
+    c->prof = true;
+    for (int r = 0; r < 2 && s == TG_OK; ++r) s = scan_impl(c, p, a, st);
+    c->prof = false;
+    double ms_after[TG_N_STAGES];
+    int64_t n_after[TG_N_STAGES];
+    tg_stage_times(c, ms_after, n_after, 0);
+    const double t = (ms_after[STAGE_GEMM] - ms_before[STAGE_GEMM]) / 2.0;
+    if (t < best_ms) {
+      best_ms = t;
+      best_i = i;
+    }
+  }
+  c->prof = prof;
+  if (s == TG_OK) {
+    if ((e = cudaStreamSynchronize(st))) s = cuda_fail(e, "tg_autotune");
+  }
+  tg_stage_times(c, nullptr, nullptr, 0);
+  std::memcpy(c->stage_ms, save_ms, sizeof(save_ms));
+  std::memcpy(c->launches, save_n, sizeof(save_n));
+  if (s != TG_OK || best_i < 0) {
+    c->tune_kernel[b] = save_k;
+    c->tune_group[b] = save_g;
+  } else {
+    c->tune_kernel[b] = kinds[best_i];
+    c->tune_group[b] = groups[best_i];
+  }
+  cleanup();
+  return s;
+}
+
+tg_status tg_set_tuning(tg_ctx* c, int64_t M, int32_t kernel, int32_t group) {
+  TG_ARG(c && M > 0, "bad arguments");
+  TG_ARG(kernel == 1 || kernel == 2, "kernel must be 1 (one CTA per tile) or 2 (CTA pairs)");
+  TG_ARG(group >= 1 && group <= 1024, "group must be in [1, 1024]");
+  const int b = tune_bucket(M);
+  c->tune_kernel[b] = kernel == 1 ? TUNE_SINGLE : TUNE_PAIR;
+  c->tune_group[b] = group;
+  return TG_OK;
+}
+
+tg_status tg_tuning(const tg_ctx* c, int64_t M, int32_t* kernel, int32_t* group) {
+  TG_ARG(c && M > 0, "bad arguments");
+  const int b = tune_bucket(M);
+  if (kernel) *kernel = c->tune_kernel[b] == TUNE_SINGLE ? 1 : 2;
+  if (group) *group = c->tune_group[b] > 0 ? c->tune_group[b] : 16;
   return TG_OK;
 }
 

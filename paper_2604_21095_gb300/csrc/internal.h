@@ -59,6 +59,27 @@ struct Events {
   int stage;
 };
 
+// Arguments of one block scan (the tg_scan_block call).
+struct ScanArgs {
+  const uint8_t* G;
+  int64_t ldg;
+  int encoding;
+  int64_t N, M, marker_offset;
+  const uint32_t* missing;
+  int64_t ldm;
+  tg_scan_opts opts;
+  tg_outputs out;
+};
+
+// Kernel choice per block-size bucket (floor(log2 M)), set by tg_autotune.
+enum { TUNE_DEFAULT = 0, TUNE_PAIR = 1, TUNE_SINGLE = 2 };
+constexpr int kTuneBuckets = 40;
+inline int tune_bucket(int64_t M) {
+  int b = 0;
+  while ((M >> (b + 1)) > 0 && b + 1 < kTuneBuckets) ++b;
+  return b;
+}
+
 }  // namespace tg
 
 struct tg_panel {
@@ -118,13 +139,22 @@ struct tg_ctx {
   std::vector<cudaEvent_t> event_pool;
   double stage_ms[TG_N_STAGES] = {0, 0, 0, 0, 0, 0};
   int64_t launches[TG_N_STAGES] = {0, 0, 0, 0, 0, 0};
+  // captured scan graphs that hold pointers into this workspace
+  int graphs_alive = 0;
+  // autotuned kernel per block-size bucket
+  int tune_kernel[tg::kTuneBuckets] = {};
+  int tune_group[tg::kTuneBuckets] = {};
 };
 
 namespace tg {
 
-// error reporting (api.cu)
+// error reporting and orchestration (api.cu)
 tg_status fail(tg_status s, const std::string& msg);
 tg_status cuda_fail(cudaError_t e, const char* what);
+tg_status check_scan_args(const tg_ctx* c, const tg_panel* p, const ScanArgs& a);
+tg_status scan_impl(tg_ctx* c, const tg_panel* p, const ScanArgs& a, cudaStream_t st);
+bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t ld,
+               uint32_t box_rows);
 
 // panel kernels (k_panel.cu)
 cudaError_t launch_build_design(double* X, const double* C, int64_t ldc, int64_t N, int64_t n_cov,
@@ -158,18 +188,19 @@ cudaError_t launch_sgemm_scan(const float* A, int64_t lda, const float* B, int64
 // statistics after the contraction (k_stats.cu)
 cudaError_t launch_full_stats(const EpiParams& ep, cudaStream_t st);
 cudaError_t launch_hit_stats(const EpiParams& ep, const unsigned long long* start, cudaStream_t st);
+cudaError_t launch_fill_random(uint8_t* p, size_t n, unsigned long long seed, cudaStream_t st);
 
 // tensor-core kernel (k_tc.cu)
 cudaError_t launch_tc_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
                            const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
                            bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
-                           long long spin_ns, cudaStream_t st);
+                           long long spin_ns, cudaStream_t st, int group_m = 16);
 
 // tensor-core kernel on CTA pairs, 256 x 256 tiles (k_tc2.cu)
 cudaError_t launch_tc2_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
                             const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
                             bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
-                            long long spin_ns, cudaStream_t st);
+                            long long spin_ns, cudaStream_t st, int group_m = 16);
 
 // bounded wait test (k_tc.cu)
 cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,

@@ -53,7 +53,24 @@ __global__ void __launch_bounds__(128) k_hit_stats(EpiParams ep,
   }
 }
 
+// Deterministic pseudo-random bytes (SplitMix64 of the index); used for timing trial blocks.
+__global__ void k_fill_random(uint8_t* __restrict__ p, size_t n, unsigned long long seed) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    p[i] = (uint8_t)((z ^ (z >> 31)) >> 24);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fill_random(uint8_t* p, size_t n, unsigned long long seed, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_fill_random<<<152 * 8, 256, 0, st>>>(p, n, seed);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_full_stats(const EpiParams& ep, cudaStream_t st) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;

@@ -47,7 +47,7 @@ template <bool HAS_LO>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
               const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-              int num_kb, int n_mt, int n_nt, int bn, const int* __restrict__ tflags,
+              int num_kb, int n_mt, int n_nt, int bn, int group_m, const int* __restrict__ tflags,
               long long spin_ns, EpiParams ep) {
   // bn = B rows per tile: 256 for the phenotype panel, 64 for the covariate projection
   using C = Cfg<HAS_LO>;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
-      tile_coord(tile, n_mt, n_nt, mt, nt);
+      tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
       const bool lo = HAS_LO && tflags[mt] != 0;
       const uint32_t bytes = A_BYTES + 2u * (uint32_t)bn * (TBK * 2) + (lo ? A_BYTES : 0);
       for (int kb = 0; kb < num_kb; ++kb) {
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t idesc = idesc_bf16(bn);
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
-      tile_coord(tile, n_mt, n_nt, mt, nt);
+      tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
       const bool lo = HAS_LO && tflags[mt] != 0;
       for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kChunkKB, ++g) {
         const int acc = (int)(g & 1u);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
-      tile_coord(tile, n_mt, n_nt, mt, nt);
+      tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
       float tot[128];
 #pragma unroll
       for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
@@ -266,7 +266,7 @@ __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, u
 template <bool HAS_LO>
 cudaError_t go(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* bh,
                const CUtensorMap* bl, int64_t K, const int* tflags, const EpiParams& ep,
-               int sm_count, long long spin_ns, cudaStream_t st) {
+               int sm_count, int group_m, long long spin_ns, cudaStream_t st) {
   using C = Cfg<HAS_LO>;
   static bool attr_set = false;  // per process; the attribute is per function
   if (!attr_set) {
@@ -281,7 +281,7 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* 
   const int tiles = n_mt * n_nt;
   const int grid = tiles < sm_count ? tiles : sm_count;
   k_tc_scan<HAS_LO><<<grid, kThreads, C::kSmem, st>>>(*a, *alo, *bh, *bl, (int)(K / TBK), n_mt,
-                                                       n_nt, bn, tflags, spin_ns, ep);
+                                                       n_nt, bn, group_m, tflags, spin_ns, ep);
   return cudaGetLastError();
 }
 
@@ -290,11 +290,11 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* 
 cudaError_t launch_tc_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
                            const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
                            bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
-                           long long spin_ns, cudaStream_t st) {
+                           long long spin_ns, cudaStream_t st, int group_m) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
-  if (K % TBK) return cudaErrorInvalidValue;
-  return has_lo ? go<true>(tmAhi, tmAlo, tmBhi, tmBlo, K, tflags, ep, sm_count, spin_ns, st)
-                : go<false>(tmAhi, tmAhi, tmBhi, tmBlo, K, tflags, ep, sm_count, spin_ns, st);
+  if (K % TBK || group_m < 1) return cudaErrorInvalidValue;
+  return has_lo ? go<true>(tmAhi, tmAlo, tmBhi, tmBlo, K, tflags, ep, sm_count, group_m, spin_ns, st)
+                : go<false>(tmAhi, tmAhi, tmBhi, tmBlo, K, tflags, ep, sm_count, group_m, spin_ns, st);
 }
 
 cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,

@@ -105,13 +105,14 @@ __device__ __forceinline__ void tc2_commit_local(uint32_t bar) {
       : "memory");
 }
 
-// Tile (pair of m-tiles, n-tile) of cluster-level tile index `tile`.
-__device__ __forceinline__ void tile_coord2(int tile, int n_mp, int n_nt, int& mp, int& nt) {
-  constexpr int kGroupP = kGroupM / 2;
-  const int group = kGroupP * n_nt;
+// Tile (pair of m-tiles, n-tile) of cluster-level tile index `tile`; group_p m-tile pairs
+// per raster group.
+__device__ __forceinline__ void tile_coord2(int tile, int n_mp, int n_nt, int group_p, int& mp,
+                                            int& nt) {
+  const int group = group_p * n_nt;
   const int g = tile / group;
-  const int first = g * kGroupP;
-  const int gm = min(kGroupP, n_mp - first);
+  const int first = g * group_p;
+  const int gm = min(group_p, n_mp - first);
   const int idx = tile - g * group;
   mp = first + idx % gm;
   nt = idx / gm;
@@ -121,8 +122,8 @@ template <bool HAS_LO>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_tc2_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
                const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-               int num_kb, int n_mt, int n_nt, const int* __restrict__ tflags, long long spin_ns,
-               EpiParams ep) {
+               int num_kb, int n_mt, int n_nt, int group_p, const int* __restrict__ tflags,
+               long long spin_ns, EpiParams ep) {
   using C = Cfg2<HAS_LO>;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -195,7 +196,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
         int mp, nt;
-        tile_coord2(tile, n_mp, n_nt, mp, nt);
+        tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
         const int mt0 = 2 * mp;
         const bool lo = HAS_LO && (tflags[mt0] != 0 || (mt0 + 1 < n_mt && tflags[mt0 + 1] != 0));
         const uint32_t pair_bytes = 2u * (A_BYTES + 2 * HB_BYTES + (lo ? A_BYTES : 0));
@@ -237,7 +238,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
         int mp, nt;
-        tile_coord2(tile, n_mp, n_nt, mp, nt);
+        tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
         const int mt0 = 2 * mp;
         const bool lo = HAS_LO && (tflags[mt0] != 0 || (mt0 + 1 < n_mt && tflags[mt0 + 1] != 0));
         for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kChunkKB, ++g) {
@@ -288,7 +289,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
       int mp, nt;
-      tile_coord2(tile, n_mp, n_nt, mp, nt);
+      tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
       float tot[128];
 #pragma unroll
       for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
@@ -339,7 +340,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 template <bool HAS_LO>
 cudaError_t go2(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* bh,
                 const CUtensorMap* bl, int64_t K, const int* tflags, const EpiParams& ep,
-                int sm_count, long long spin_ns, cudaStream_t st) {
+                int sm_count, int group_m, long long spin_ns, cudaStream_t st) {
   using C = Cfg2<HAS_LO>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -352,8 +353,10 @@ cudaError_t go2(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap*
   const int n_nt = (ep.P + TBN - 1) / TBN;
   const int tiles = ((n_mt + 1) / 2) * n_nt;
   const int pairs = tiles < sm_count / 2 ? tiles : sm_count / 2;
+  const int group_p = group_m / 2 > 0 ? group_m / 2 : 1;
   k_tc2_scan<HAS_LO><<<2 * pairs, kThreads, C::kSmem, st>>>(*a, *alo, *bh, *bl, (int)(K / TBK),
-                                                            n_mt, n_nt, tflags, spin_ns, ep);
+                                                            n_mt, n_nt, group_p, tflags, spin_ns,
+                                                            ep);
   return cudaGetLastError();
 }
 
@@ -362,11 +365,11 @@ cudaError_t go2(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap*
 cudaError_t launch_tc2_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
                             const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
                             bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
-                            long long spin_ns, cudaStream_t st) {
+                            long long spin_ns, cudaStream_t st, int group_m) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
-  if (K % TBK) return cudaErrorInvalidValue;
-  return has_lo ? go2<true>(tmAhi, tmAlo, tmBhi, tmBlo, K, tflags, ep, sm_count, spin_ns, st)
-                : go2<false>(tmAhi, tmAhi, tmBhi, tmBlo, K, tflags, ep, sm_count, spin_ns, st);
+  if (K % TBK || group_m < 1) return cudaErrorInvalidValue;
+  return has_lo ? go2<true>(tmAhi, tmAlo, tmBhi, tmBlo, K, tflags, ep, sm_count, group_m, spin_ns, st)
+                : go2<false>(tmAhi, tmAhi, tmBhi, tmBlo, K, tflags, ep, sm_count, group_m, spin_ns, st);
 }
 
 }  // namespace tg

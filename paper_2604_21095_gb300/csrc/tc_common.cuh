@@ -26,7 +26,7 @@ constexpr int kRegsHigh = 224;
 static_assert(128 * kRegsLow + 256 * kRegsHigh <= kThreads * 168, "register split exceeds launch");
 constexpr int kTmemCols = 512;                 // two 128 x 256 FP32 chunk accumulators
 constexpr int kChunkKB = 32;                   // K blocks per accumulation chunk (1024 samples)
-constexpr int kGroupM = 16;                    // raster: 16 m-tiles per group
+constexpr int kGroupM = 16;                    // default raster: 16 m-tiles per group
 
 
 
@@ -144,11 +144,14 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tile_coord(int tile, int n_mt, int n_nt, int& mt, int& nt) {
-  const int group = kGroupM * n_nt;
+// Raster: tiles go down group_m m-tiles (markers) first, then across the n-tiles (phenotypes),
+// so the tiles in flight at once share a few A stripes and a band of B stripes in L2.
+__device__ __forceinline__ void tile_coord(int tile, int n_mt, int n_nt, int group_m, int& mt,
+                                           int& nt) {
+  const int group = group_m * n_nt;
   const int g = tile / group;
-  const int first = g * kGroupM;
-  const int gm = min(kGroupM, n_mt - first);
+  const int first = g * group_m;
+  const int gm = min(group_m, n_mt - first);
   const int idx = tile - g * group;
   mt = first + idx % gm;
   nt = idx / gm;

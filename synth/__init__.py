@@ -17,4 +17,12 @@ from .gwas import (  # noqa: F401
     phenotypes,
     round_up,
 )
-from .workloads import WORKLOADS, Workload, make_block, make_panel  # noqa: F401
+from .workloads import (  # noqa: F401
+    BATCHED_PANELS,
+    WORKLOADS,
+    Workload,
+    make_block,
+    make_panel,
+    make_ragged_block,
+    ragged_blocks,
+)

@@ -48,8 +48,30 @@ WORKLOADS = {
                  encoding="2bit", missing=0.005, seed=2, block=65_536, planted=50),
         Workload("n23000_m8900000_p20480_c20_u8", N=23_000, M=8_900_000, P=20_480, n_cov=19,
                  encoding="u8", missing=0.0, seed=5, block=65_536, planted=50),
+        Workload("n23000_m500000_12panels_p8192_2bit", N=23_000, M=500_000, P=8192, n_cov=9,
+                 encoding="2bit", missing=0.005, seed=4, block=65_536, planted=50),
     )
 }
+
+# The batched workload: 12 phenotype panels of uneven size over the same samples and covariates.
+BATCHED_PANELS = (17, 256, 1000, 3500, 1, 64, 128, 300, 500, 626, 800, 1000)
+assert sum(BATCHED_PANELS) == 8192
+
+
+def ragged_blocks(seed: int, M: int, lo: int = 1000, hi: int = 65_536):
+    """Block sizes ~ U[lo, hi] drawn until they cover M markers; a short remainder is merged into
+    the last block while that stays <= hi (else it is its own block)."""
+    g = gwas.generator("cpu", seed, 99, 0)
+    sizes, total = [], 0
+    while total < M:
+        b = int(torch.randint(lo, hi + 1, (1,), generator=g))
+        b = min(b, M - total)
+        if b < lo and sizes and sizes[-1] + b <= hi:
+            sizes[-1] += b
+        else:
+            sizes.append(b)
+        total += b
+    return sizes
 
 
 def make_block(w: Workload, b: int, device="cpu", with_truth: bool = False) -> dict:
@@ -73,6 +95,15 @@ def make_block(w: Workload, b: int, device="cpu", with_truth: bool = False) -> d
         if with_truth:
             out["truth"] = out["G"][:, : w.N].to(torch.float64) * (2.0 / 255.0)
     return out
+
+
+def make_ragged_block(w: Workload, index: int, M: int, device="cpu") -> torch.Tensor:
+    """Packed genotypes of the index-th ragged block (M markers), drawn with its own keys."""
+    f = gwas.maf(w.seed, 1000 + index, M, device=device)
+    if w.encoding == "2bit":
+        counts, miss = gwas.hard_calls(w.seed, 1000 + index, f, w.N, w.missing, device=device)
+        return gwas.pack_2bit(counts, miss)
+    return gwas.dosage_bytes(w.seed, 1000 + index, f, w.N, device=device)
 
 
 def _planted_pairs(w: Workload, n_blocks: int):

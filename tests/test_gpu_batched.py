@@ -1,0 +1,163 @@
+"""The batched form: panels concatenated into one scan, ragged blocks replayed from one captured
+CUDA graph, and autotuned kernel choice; each checked against the plain per-panel, per-block
+scan (and that against the oracle elsewhere)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2604_21095_gb300 as tg
+import synth
+from scan_util import HIT_DTYPE, compare_best, compare_full, oracle_panel, run_scan
+
+pytestmark = pytest.mark.gpu
+
+N = 2000
+
+
+def _panels(tgctx, sizes, seed=81, n_cov=3):
+    cov = synth.covariates(seed, N, n_cov)
+    Yt = synth.phenotypes(seed, cov, sum(sizes))
+    parts, o = [], 0
+    for k in sizes:
+        parts.append(tg.tg_prepare_panel(tgctx, Yt[o:o + k].contiguous().cuda(), N, k, cov.cuda()))
+        o += k
+    return cov, Yt, parts
+
+
+def test_concat_equals_each_panel_scanned_alone(tgctx):
+    sizes = (17, 5, 300, 1)
+    cov, Yt, parts = _panels(tgctx, sizes)
+    cat = tg.tg_panel_concat(tgctx, parts)
+    try:
+        assert tg.tg_panel_info(cat) == (N, sum(sizes), 4, N - 5)
+        counts, miss = synth.hard_calls(81, 0, synth.maf(81, 0, 700), N, 0.01)
+        G = synth.pack_2bit(counts, miss).cuda()
+        whole = run_scan(tgctx, cat, G, N, sum(sizes), "2bit", "split", full=True, hit_mlog10p=3.0)
+        o = 0
+        for part, k in zip(parts, sizes):
+            alone = run_scan(tgctx, part, G, N, k, "2bit", "split", full=True, hit_mlog10p=3.0)
+            for key in ("beta", "se", "t", "mlog10p"):
+                assert np.array_equal(whole[key][:, o:o + k], alone[key], equal_nan=True), key
+            assert np.array_equal(whole["best_key"][o:o + k], alone["best_key"])
+            got = {(int(h["marker"]), int(h["pheno"]) - o) for h in whole["hits"] if o <= h["pheno"] < o + k}
+            assert got == {(int(h["marker"]), int(h["pheno"])) for h in alone["hits"]}
+            o += k
+        ref = oracle.scan(G.cpu().numpy(), "2bit", oracle_panel(Yt, cov))
+        compare_full(whole, ref, label="concatenated panel")
+    finally:
+        tg.tg_panel_free(cat)
+        for p in parts:
+            tg.tg_panel_free(p)
+
+
+def test_concat_refuses_different_covariates(tgctx):
+    cov_a, cov_b = synth.covariates(82, N, 2), synth.covariates(83, N, 2)
+    a = tg.tg_prepare_panel(tgctx, synth.phenotypes(82, cov_a, 3).cuda(), N, 3, cov_a.cuda())
+    b = tg.tg_prepare_panel(tgctx, synth.phenotypes(83, cov_b, 3).cuda(), N, 3, cov_b.cuda())
+    try:
+        with pytest.raises(tg.TgError) as e:
+            tg.tg_panel_concat(tgctx, [a, b])
+        assert e.value.status == tg.TG_ERR_INVALID_ARG
+    finally:
+        tg.tg_panel_free(a)
+        tg.tg_panel_free(b)
+
+
+def _accum_outputs(P, cap=1 << 14):
+    hits = torch.zeros(cap * HIT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    best = torch.zeros(P, dtype=torch.int64, device="cuda")
+    return hits, n, best, tg.make_outputs(hits=hits, n_hits=n, best=best)
+
+
+def _hitset(hits, n):
+    h = np.frombuffer(hits.cpu().numpy().tobytes(), dtype=HIT_DTYPE)[: int(n.item())]
+    return {(int(x["marker"]), int(x["pheno"])): float(x["mlog10p"]) for x in h}
+
+
+def test_graph_replay_equals_eager_scans_of_ragged_blocks(tgctx):
+    P = 300
+    cov = synth.covariates(84, N, 3)
+    panel = tg.tg_prepare_panel(tgctx, synth.phenotypes(84, cov, P).cuda(), N, P, cov.cuda())
+    ctx2 = tg.tg_create(0)  # the graph holds its context's workspace
+    try:
+        w = synth.Workload("ragged", N=N, M=3000, P=P, n_cov=3, encoding="2bit", missing=0.01,
+                           seed=84, block=1024)
+        sizes = [700, 1500, 333, 129]
+        blocks = [synth.make_ragged_block(w, i, m, device="cuda") for i, m in enumerate(sizes)]
+        offs = list(np.cumsum([0] + sizes[:-1]))
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, 3.0)
+        hits, n, best, out = _accum_outputs(P)
+        for b, o in zip(blocks, offs):
+            tg.tg_scan_block(tgctx, panel, b, N, b.shape[0], tg.TG_ENC_2BIT, opts, out, marker_offset=int(o))
+        assert tg.tg_status_poll(tgctx) == tg.TG_OK
+        eager = (_hitset(hits, n), best.cpu().numpy().copy())
+        hits2, n2, best2, out2 = _accum_outputs(P)
+        g = tg.tg_scan_graph_create(ctx2, panel, blocks, N, tg.TG_ENC_2BIT, opts, out2, [int(o) for o in offs])
+        try:
+            for _ in range(2):      # two replays from zeroed outputs give the same result
+                n2.zero_()
+                best2.zero_()
+                tg.tg_scan_graph_launch(g)
+                assert tg.tg_status_poll(ctx2) == tg.TG_OK
+                got = _hitset(hits2, n2)
+                assert set(got) == set(eager[0]) and len(got) > 0
+                for k, v in got.items():
+                    assert abs(v - eager[0][k]) <= max(1e-3, 1e-5 * v)
+                assert np.array_equal(best2.cpu().numpy(), eager[1])
+            # the graph holds ctx2's workspace: a larger block is refused, a smaller one scans
+            big = synth.make_ragged_block(w, 9, 1600, device="cuda")
+            with pytest.raises(tg.TgError) as e:
+                tg.tg_scan_block(ctx2, panel, big, N, 1600, tg.TG_ENC_2BIT, opts, out2)
+            assert e.value.status == tg.TG_ERR_INVALID_ARG
+            tg.tg_scan_block(ctx2, panel, blocks[2], N, 333, tg.TG_ENC_2BIT, opts, out2)
+            assert tg.tg_status_poll(ctx2) == tg.TG_OK
+        finally:
+            tg.tg_scan_graph_free(g)
+    finally:
+        tg.tg_destroy(ctx2)
+        tg.tg_panel_free(panel)
+
+
+def test_autotune_picks_a_kernel_and_results_stay_exact(tgctx):
+    P = 600
+    cov = synth.covariates(85, N, 3)
+    Yt = synth.phenotypes(85, cov, P)
+    panel = tg.tg_prepare_panel(tgctx, Yt.cuda(), N, P, cov.cuda())
+    ctx2 = tg.tg_create(0)
+    try:
+        M = 1000
+        tg.tg_autotune(ctx2, panel, tg.TG_ENC_U8_DOSAGE, M)
+        choice = tg.tg_tuning(ctx2, M)
+        assert choice["kernel"] in ("pair", "single") and choice["group_m"] in (4, 8, 16, 32)
+        G = synth.dosage_bytes(85, 0, synth.maf(85, 0, M), N).cuda()
+        res = run_scan(ctx2, panel, G, N, P, "u8", "split", full=True)
+        ref = oracle.scan(G.cpu().numpy(), "u8", oracle_panel(Yt, cov))
+        compare_full(res, ref, label=f"autotuned {choice}")
+        compare_best(res, ref)
+        print(f"\nautotuned choice for {M} markers x {P} phenotypes: {choice}")
+    finally:
+        tg.tg_destroy(ctx2)
+        tg.tg_panel_free(panel)
+
+
+@pytest.mark.parametrize("kernel,group", [("single", 8), ("single", 32), ("pair", 4), ("pair", 32)])
+def test_each_tuning_choice_matches_the_oracle(tgctx, kernel, group):
+    P = 257
+    cov = synth.covariates(86, N, 2)
+    Yt = synth.phenotypes(86, cov, P)
+    panel = tg.tg_prepare_panel(tgctx, Yt.cuda(), N, P, cov.cuda())
+    ctx2 = tg.tg_create(0)
+    try:
+        counts, miss = synth.hard_calls(86, 0, synth.maf(86, 0, 385), N, 0.01)
+        G = synth.pack_2bit(counts, miss).cuda()
+        tg.tg_set_tuning(ctx2, 385, kernel, group)
+        assert tg.tg_tuning(ctx2, 385) == {"kernel": kernel, "group_m": group}
+        ref = oracle.scan(G.cpu().numpy(), "2bit", oracle_panel(Yt, cov))
+        res = run_scan(ctx2, panel, G, N, P, "2bit", "split", full=True, hit_mlog10p=3.0)
+        compare_full(res, ref, label=f"{kernel}/{group}")
+        compare_best(res, ref)
+    finally:
+        tg.tg_destroy(ctx2)
+        tg.tg_panel_free(panel)
