@@ -5,8 +5,8 @@
 // product D). These kernels turn them into
 //   t = r sqrt(df / ((1 - r)(1 + r))),  beta = r s_p / (kappa |a_res|),
 //   se = s_p / (kappa |a_res|) sqrt((1 - r)(1 + r) / df),  -log10 p with p = I_{1-r^2}(df/2, 1/2).
-// Hit records are recomputed from D in FP64; FULL elements from the FP32 r with the p-value
-// in FP64.
+// Hit records are recomputed from D with FP64 r, beta and se; the p-values (of hits and of
+// FULL elements) are evaluated in FP32 log space (see pvalue.cuh).
 #include "device.cuh"
 #include "internal.h"
 
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) k_full_stats(EpiParams ep) {
     if (ep.beta) ep.beta[o] = r * scale;
     if (ep.se) ep.se[o] = scale * sqrtf(omr2 / ep.df_f);
     if (ep.t) ep.t[o] = r * sqrtf(ep.df_f / omr2);
-    if (ep.mlp) ep.mlp[o] = (float)mlog10p_r((double)r, ep.df, ep.lnB);
+    if (ep.mlp) ep.mlp[o] = mlog10p_r_f(r, ep.df_f, (float)ep.lnB);
   }
 }
 
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(128) k_hit_stats(EpiParams ep,
     h.beta = (float)(r * scale);
     h.se = (float)(scale * sqrt(omr2 / ep.df));
     h.t = (float)(r * sqrt(ep.df / omr2));
-    h.mlog10p = (float)mlog10p_r(r, ep.df, ep.lnB);
+    h.mlog10p = mlog10p_r_f((float)r, ep.df_f, (float)ep.lnB);
     ep.hits[i] = h;
   }
 }

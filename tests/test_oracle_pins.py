@@ -409,3 +409,24 @@ def test_planted_loci_rank_top_small_workload():
         found += m in top
     assert found >= 0.9 * len(pan_in["pairs"])
     assert res["df"] == w.N - (w.n_cov + 1) - 1
+
+
+def test_large_df_normal_deviate_used_on_gpu_is_within_tolerance():
+    """The GPU evaluates -log10 p for df >= 1500 from Hill's (1970) normal deviate for Student's
+    t instead of the continued fraction (which cancels badly in FP32 at large df). This pins the
+    approximation itself, evaluated here in float64, against the oracle over t in [0.01, 400]."""
+    sp = pytest.importorskip("scipy.special")
+
+    def hill_mlog10p(t, n):
+        a = n - 0.5
+        B = 48 * a * a
+        Y = a * math.log1p(t * t / n)
+        z = (((((-0.4 * Y - 3.3) * Y - 24) * Y - 85.5) / (0.8 * Y * Y + 100 + B) + Y + 3) / B + 1) * math.sqrt(Y)
+        x = z / math.sqrt(2)
+        return (x * x - math.log(sp.erfcx(x))) / math.log(10)
+
+    for n in (1500.0, 1994.0, 5000.0, 22979.0, 1e5, 1e6):
+        ts = np.concatenate([np.linspace(0.01, 10, 200), np.linspace(10, 400, 60)])
+        ref = oracle.mlog10p_from_t(ts, n)
+        got = np.array([hill_mlog10p(t, n) for t in ts])
+        assert np.all(np.abs(got - ref) <= 0.1 * np.maximum(1e-3, 1e-5 * ref)), n
