@@ -145,17 +145,22 @@ tg_status tg_panel_free(tg_panel* panel);
  *      G 16-byte aligned.
  *   missing: device, uint32 [M][ldm] bit mask (bit i%32 of word i/32 set = call i missing),
  *      ldm >= ceil(N/32); dosage only (must be NULL for 2-bit, where it is in-band); may be NULL.
- *   A_hi, A_lo: device operand rows of lda elements, lda >= N, lda % 64 == 0. For
- *      TG_PREC_SPLIT_BF16 both are bf16: observed calls hold the exact code (or byte), a
- *      missing call holds bf16(mean) in A_hi and bf16(mean - bf16(mean)) in A_lo, every
- *      other A_lo entry and columns N..lda-1 are 0. For TG_PREC_FP32 A_hi is float
- *      (missing = float(mean)) and A_lo must be NULL.
+ *   A: device operand rows of lda elements, lda >= N, lda % 64 == 0, 16-byte aligned;
+ *      columns N..lda-1 are written 0.
+ *      TG_PREC_FP32: float; an observed call holds its code (or byte), a missing call
+ *      float(mean).
+ *      TG_PREC_SPLIT_BF16: bf16, the row centred on a shift c: c = round(128 mean) / 128 for
+ *      2-bit calls, round(mean) for dosage bytes (round half to even; c = 0 if n_obs = 0), so
+ *      that an observed call holds code - c exactly and a missing call bf16(mean - c)
+ *      (|mean - c| <= 1/256 or 1/2). The scan adds c sum_i y_i back per phenotype.
+ *   shift: device float [M], receives c (exact in float); split form only (NULL for FP32,
+ *      where it must be NULL); may be NULL.
  *   n_obs, S, S2 (int32/int64/int64 [M]): exact observed count, sum and sum of squares in
  *      decode units; mean (double [M]): S / n_obs, one correctly rounded division (NaN if
  *      n_obs = 0). Any of these four may be NULL. */
 tg_status tg_decode_block(tg_ctx* ctx, const uint8_t* G, int64_t ldg, int32_t encoding, int64_t N,
                           int64_t M, const uint32_t* missing, int64_t ldm, int32_t precision,
-                          void* A_hi, void* A_lo, int64_t lda, int32_t* n_obs, int64_t* S,
+                          void* A, float* shift, int64_t lda, int32_t* n_obs, int64_t* S,
                           int64_t* S2, double* mean, void* stream);
 
 /* Section 2.2 Eq. 2 and Eq. 3 for one block: decode (mean imputation of missing calls),
@@ -182,10 +187,10 @@ tg_status tg_scan_block(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G, in
  * the process exits.
  *   Arguments and outputs: as tg_scan_block (the panel comes from tg_prepare_panel, made
  *   beforehand). The current device must be the panel's device.
- *   Limit: the block must fit the 64 MiB scratch, about (2 or 4 bytes + 2 more with missing
- *   calls) x round_up(N, 64) per marker, e.g. about 1,400 dosage markers at N = 23,000 or
- *   15,000 at N = 2,000 in the split form; larger blocks return TG_ERR_UNSUPPORTED with the
- *   maximum in the message, before anything is launched.
+ *   Limit: the block must fit the 64 MiB scratch, about (2 bytes split, 4 bytes FP32) x
+ *   round_up(N, 64) per marker, e.g. about 1,400 markers at N = 23,000 or 15,000 at N = 2,000
+ *   in the split form; larger blocks return TG_ERR_UNSUPPORTED with the maximum in the
+ *   message, before anything is launched.
  *   The first call on a device does a one-time set-up (it looks up the array's device address
  *   with cudaGetSymbolAddress while that device is current); make that first call before any
  *   stream capture.

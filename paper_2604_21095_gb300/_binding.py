@@ -211,11 +211,11 @@ def tg_panel_free(panel):
     _check(load().tg_panel_free(panel))
 
 
-def tg_decode_block(ctx, G, N, M, encoding, precision, A_hi, A_lo=None, missing=None,
+def tg_decode_block(ctx, G, N, M, encoding, precision, A, shift=None, missing=None,
                     n_obs=None, S=None, S2=None, mean=None, stream=None):
     ldm = _ld(missing) if missing is not None else 0
     _check(load().tg_decode_block(ctx, _ptr(G), _ld(G), encoding, N, M, _ptr(missing), ldm,
-                                  precision, _ptr(A_hi), _ptr(A_lo), _ld(A_hi), _ptr(n_obs),
+                                  precision, _ptr(A), _ptr(shift), _ld(A), _ptr(n_obs),
                                   _ptr(S), _ptr(S2), _ptr(mean), _stream(stream)))
 
 

@@ -118,35 +118,32 @@ struct StageScope {
 cudaError_t ensure_markers(tg_ctx* c, int64_t M) {
   if (M <= c->cap_m) return cudaSuccess;
   const int64_t cap = round_up(M, MT);
-  dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
-  dfree(c->rinv); dfree(c->rinv64); dfree(c->tflags);
+  dfree(c->nobs); dfree(c->mean); dfree(c->shift); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
+  dfree(c->rinv); dfree(c->rinv64);
   c->cap_m = 0;
   cudaError_t e;
-  if ((e = dalloc(&c->nobs, cap)) || (e = dalloc(&c->mean, cap)) || (e = dalloc(&c->gc2, cap)) ||
-      (e = dalloc(&c->qg, cap * QCOLS)) || (e = dalloc(&c->gres2, cap)) ||
-      (e = dalloc(&c->rinv, cap)) || (e = dalloc(&c->rinv64, cap)) ||
-      (e = dalloc(&c->tflags, cap / MT)))
+  if ((e = dalloc(&c->nobs, cap)) || (e = dalloc(&c->mean, cap)) || (e = dalloc(&c->shift, cap)) ||
+      (e = dalloc(&c->gc2, cap)) || (e = dalloc(&c->qg, cap * QCOLS)) ||
+      (e = dalloc(&c->gres2, cap)) || (e = dalloc(&c->rinv, cap)) || (e = dalloc(&c->rinv64, cap)))
     return e;
   c->cap_m = cap;
   return cudaSuccess;
 }
 
-// Operand rows: bf16 hi (+ lo) for the split form, float for FP32.
-cudaError_t ensure_operands(tg_ctx* c, int64_t M, int64_t Npad, int prec, bool need_lo) {
+// Operand rows: centred bf16 for the split form, float for FP32.
+cudaError_t ensure_operands(tg_ctx* c, int64_t M, int64_t Npad, int prec) {
   const int64_t rows = round_up(M, MT);
   const bool fits = rows <= c->cap_rows && Npad <= c->cap_npad;
-  const bool have = prec == TG_PREC_FP32 ? c->A32 != nullptr
-                                         : (c->Ahi != nullptr && (!need_lo || c->Alo != nullptr));
+  const bool have = prec == TG_PREC_FP32 ? c->A32 != nullptr : c->Ahi != nullptr;
   if (fits && have) return cudaSuccess;
   const int64_t R = fits ? c->cap_rows : std::max(rows, c->cap_rows);
   const int64_t K = fits ? c->cap_npad : std::max(Npad, c->cap_npad);
   if (!fits) {
-    dfree(c->Ahi); dfree(c->Alo); dfree(c->A32);
+    dfree(c->Ahi); dfree(c->A32);
   }
   cudaError_t e = cudaSuccess;
   if (prec == TG_PREC_FP32 && !c->A32) e = dalloc(&c->A32, (size_t)(R * K));
   if (!e && prec == TG_PREC_SPLIT_BF16 && !c->Ahi) e = dalloc(&c->Ahi, (size_t)(R * K));
-  if (!e && prec == TG_PREC_SPLIT_BF16 && need_lo && !c->Alo) e = dalloc(&c->Alo, (size_t)(R * K));
   if (e) return e;
   c->cap_rows = R;
   c->cap_npad = K;
@@ -201,48 +198,44 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   tg_panel* p = const_cast<tg_panel*>(pc);
   if (a.M == 0) return TG_OK;
   const int prec = a.opts.precision;
-  const bool has_lo = prec == TG_PREC_SPLIT_BF16 && (a.encoding == TG_ENC_2BIT || a.missing);
+  const bool split = prec == TG_PREC_SPLIT_BF16;
   if (c->graphs_alive > 0) {
     const bool grow = a.M > c->cap_m || round_up(a.M, MT) > c->cap_rows || p->Npad > c->cap_npad ||
-                      (prec == TG_PREC_FP32 ? !c->A32 : (!c->Ahi || (has_lo && !c->Alo)));
+                      (prec == TG_PREC_FP32 ? !c->A32 : !c->Ahi);
     if (grow)
       return fail(TG_ERR_INVALID_ARG,
                   "the context's workspace is held by a captured scan graph: scan blocks no "
                   "larger than the graph's, or use another context");
   }
   TG_CUDA(ensure_markers(c, a.M));
-  TG_CUDA(ensure_operands(c, a.M, p->Npad, prec, has_lo));
+  TG_CUDA(ensure_operands(c, a.M, p->Npad, prec));
   const float kappa = a.encoding == TG_ENC_U8_DOSAGE ? (float)(2.0 / 255.0) : 1.0f;
   void* Ahi = prec == TG_PREC_FP32 ? (void*)c->A32 : (void*)c->Ahi;
   {
     StageScope s(c, STAGE_DECODE, st, 1);
-    if (has_lo) TG_CUDA(cudaMemsetAsync(c->tflags, 0, sizeof(int) * (size_t)((a.M + MT - 1) / MT), st));
     TG_CUDA(launch_decode(a.G, a.ldg, a.encoding, a.N, a.M, a.missing, a.ldm, prec, Ahi,
-                          has_lo ? c->Alo : nullptr, p->Npad, c->nobs, nullptr, nullptr, c->mean,
-                          c->gc2, has_lo ? c->tflags : nullptr, st));
+                          split ? c->shift : nullptr, p->Npad, c->nobs, nullptr, nullptr, c->mean,
+                          c->gc2, st));
   }
   const int64_t nq = p->q - 1;
-  CUtensorMap tA, tAlo;
-  if (prec == TG_PREC_SPLIT_BF16) {
-    if (!make_tmap(&tA, c->Ahi, a.M, p->Npad, p->Npad, MT))
-      return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
-    if (has_lo && !make_tmap(&tAlo, c->Alo, a.M, p->Npad, p->Npad, MT))
-      return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the imputation operand");
-  }
+  CUtensorMap tA;
+  if (split && !make_tmap(&tA, c->Ahi, a.M, p->Npad, p->Npad, MT))
+    return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
   if (nq > 0) {
     StageScope s(c, STAGE_PROJECT, st, 1);
-    if (prec == TG_PREC_FP32) {
-      TG_CUDA(launch_project(Ahi, nullptr, 1, p->Npad, a.M, p->Npad, p->QB, nq, c->qg, st));
+    if (!split) {
+      TG_CUDA(launch_project(c->A32, p->Npad, a.M, p->Npad, p->QB, nq, c->qg, st));
     } else {
       EpiParams pp{};
       pp.M = (int)a.M;
       pp.P = (int)nq;
       pp.status = c->status;
+      pp.row_shift = c->shift;
+      pp.col_cs = p->qcs;
       pp.raw_out = c->qg;
       pp.raw_cols = (int)nq;
       pp.raw_ld = QCOLS;
-      TG_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmQhi, &p->tmQlo, p->Npad, has_lo,
-                             c->tflags, pp, c->sm_count, kSpinNs, st));
+      TG_CUDA(launch_tc_scan(&tA, &p->tmQhi, &p->tmQlo, p->Npad, pp, c->sm_count, kSpinNs, st));
     }
   }
   {
@@ -273,6 +266,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   ep.col_s = p->col_s;
   ep.col_s64 = p->s;
   ep.col_rmul = p->col_rmul;
+  ep.row_shift = split ? c->shift : nullptr;
+  ep.col_cs = p->col_cs;
   ep.beta = a.out.beta;
   ep.se = a.out.se;
   ep.t = a.out.t;
@@ -296,11 +291,11 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       const int b = tune_bucket(a.M);
       const int group = c->tune_group[b] > 0 ? c->tune_group[b] : 16;
       if (c->tune_kernel[b] == TUNE_SINGLE)
-        TG_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi, &p->tmBlo, p->Npad, has_lo,
-                               c->tflags, ep, c->sm_count, kSpinNs, st, group));
+        TG_CUDA(launch_tc_scan(&tA, &p->tmBhi, &p->tmBlo, p->Npad, ep, c->sm_count, kSpinNs, st,
+                               group));
       else
-        TG_CUDA(launch_tc2_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi2, &p->tmBlo2, p->Npad, has_lo,
-                                c->tflags, ep, c->sm_count, kSpinNs, st, group));
+        TG_CUDA(launch_tc2_scan(&tA, &p->tmBhi2, &p->tmBlo2, p->Npad, ep, c->sm_count, kSpinNs, st,
+                                group));
     }
   }
   if (ep.do_hits || ep.do_full) {
@@ -407,9 +402,9 @@ tg_status tg_destroy(tg_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   dfree(c->status); dfree(c->scratch);
-  dfree(c->Ahi); dfree(c->Alo); dfree(c->A32);
+  dfree(c->Ahi); dfree(c->A32); dfree(c->shift);
   dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
-  dfree(c->rinv); dfree(c->rinv64); dfree(c->tflags);
+  dfree(c->rinv); dfree(c->rinv64);
   dfree(c->stage_buf[0]); dfree(c->stage_buf[1]);
   dfree(c->dhits); dfree(c->dnhits); dfree(c->dbest);
   for (auto& ev : c->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
@@ -451,7 +446,8 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
       (e = dalloc(&p->Yres, (size_t)(std::max<int64_t>(P, 1) * N))) ||
       (e = dalloc(&p->s, (size_t)std::max<int64_t>(P, 1))) ||
       (e = dalloc(&p->col_s, (size_t)std::max<int64_t>(P, 1))) ||
-      (e = dalloc(&p->col_rmul, (size_t)p->Ppad)) ||
+      (e = dalloc(&p->col_rmul, (size_t)p->Ppad)) || (e = dalloc(&p->col_cs, (size_t)p->Ppad)) ||
+      (e = dalloc(&p->qcs, (size_t)QCOLS)) ||
       (e = dalloc(&p->Bhi, (size_t)(p->Ppad * p->Npad))) ||
       (e = dalloc(&p->Blo, (size_t)(p->Ppad * p->Npad))) ||
       (e = dalloc(&p->B32, (size_t)(p->Ppad * p->Npad))) ||
@@ -466,6 +462,7 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
     if ((r = cudaMemsetAsync(p->Blo, 0, sizeof(__nv_bfloat16) * p->Ppad * p->Npad, st))) return r;
     if ((r = cudaMemsetAsync(p->B32, 0, sizeof(float) * p->Ppad * p->Npad, st))) return r;
     if ((r = cudaMemsetAsync(p->col_rmul, 0, sizeof(float) * p->Ppad, st))) return r;
+    if ((r = cudaMemsetAsync(p->col_cs, 0, sizeof(float) * p->Ppad, st))) return r;
     if ((r = launch_build_design(p->X, C, ldc, N, n_cov, c->scratch, st))) return r;
     if ((r = launch_householder(p->X, N, k, p->Q, dint, dint + 1, st))) return r;
     return cudaSuccess;
@@ -482,8 +479,8 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
   p->df = N - rank - 1;
   if (p->df <= 0) return cleanup(fail(TG_ERR_RANK, "N must exceed rank([1, C]) + 1"));
   if ((e = launch_residualise(Y, ldy, p->Q, N, P, rank, p->Npad, p->Yres, p->s, p->col_s,
-                              p->col_rmul, p->Bhi, p->Blo, p->B32, c->scratch, st)) ||
-      (e = launch_qcols(p->Q, N, rank, p->Npad, p->QB, p->QBhi, p->QBlo, st)))
+                              p->col_rmul, p->Bhi, p->Blo, p->B32, p->col_cs, c->scratch, st)) ||
+      (e = launch_qcols(p->Q, N, rank, p->Npad, p->QB, p->QBhi, p->QBlo, p->qcs, st)))
     return cleanup(cuda_fail(e, "tg_prepare_panel residualise"));
   uint32_t flags = 0;
   if ((e = cudaMemcpyAsync(&flags, c->scratch, sizeof(uint32_t), cudaMemcpyDeviceToHost, st)) ||
@@ -533,6 +530,7 @@ tg_status tg_panel_free(tg_panel* p) {
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   dfree(p->X); dfree(p->Q); dfree(p->Yres); dfree(p->s); dfree(p->col_s); dfree(p->col_rmul);
+  dfree(p->col_cs); dfree(p->qcs);
   dfree(p->Bhi); dfree(p->Blo); dfree(p->B32); dfree(p->QB); dfree(p->QBhi); dfree(p->QBlo);
   delete p;
   return TG_OK;
@@ -540,7 +538,7 @@ tg_status tg_panel_free(tg_panel* p) {
 
 tg_status tg_decode_block(tg_ctx* c, const uint8_t* G, int64_t ldg, int32_t encoding, int64_t N,
                           int64_t M, const uint32_t* missing, int64_t ldm, int32_t precision,
-                          void* A_hi, void* A_lo, int64_t lda, int32_t* n_obs, int64_t* S,
+                          void* A, float* shift, int64_t lda, int32_t* n_obs, int64_t* S,
                           int64_t* S2, double* mean, void* stream) {
   TG_ARG(c, "null context");
   TG_ARG(encoding == TG_ENC_2BIT || encoding == TG_ENC_U8_DOSAGE, "unknown encoding");
@@ -552,15 +550,14 @@ tg_status tg_decode_block(tg_ctx* c, const uint8_t* G, int64_t ldg, int32_t enco
   TG_ARG(ldg >= need && ldg % 16 == 0, "ldg must be >= the packed row length and a multiple of 16");
   if (encoding == TG_ENC_2BIT) TG_ARG(missing == nullptr, "missing must be NULL for 2-bit calls");
   if (missing) TG_ARG(ldm >= (N + 31) / 32, "ldm too small");
-  TG_ARG(A_hi && aligned(A_hi, 16), "A_hi must be a 16-byte aligned device pointer");
+  TG_ARG(A && aligned(A, 16), "A must be a 16-byte aligned device pointer");
   TG_ARG(lda >= N && lda % KPAD == 0, "lda must be >= N and a multiple of 64");
-  if (precision == TG_PREC_FP32) TG_ARG(A_lo == nullptr, "A_lo must be NULL for FP32");
-  if (A_lo) TG_ARG(aligned(A_lo, 16), "A_lo must be 16-byte aligned");
+  if (precision == TG_PREC_FP32) TG_ARG(shift == nullptr, "shift must be NULL for FP32");
   TG_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
   StageScope s(c, STAGE_DECODE, st, 1);
-  TG_CUDA(launch_decode(G, ldg, encoding, N, M, missing, ldm, precision, A_hi, A_lo, lda, n_obs,
-                        S, S2, mean, nullptr, nullptr, st));
+  TG_CUDA(launch_decode(G, ldg, encoding, N, M, missing, ldm, precision, A, shift, lda, n_obs,
+                        S, S2, mean, nullptr, st));
   return TG_OK;
 }
 
@@ -754,6 +751,7 @@ tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_pa
   if ((e = dalloc(&r->Q, (size_t)(q * N))) || (e = dalloc(&r->Yres, (size_t)(std::max<int64_t>(P, 1) * N))) ||
       (e = dalloc(&r->s, (size_t)std::max<int64_t>(P, 1))) ||
       (e = dalloc(&r->col_s, (size_t)std::max<int64_t>(P, 1))) || (e = dalloc(&r->col_rmul, (size_t)Pp)) ||
+      (e = dalloc(&r->col_cs, (size_t)Pp)) || (e = dalloc(&r->qcs, (size_t)QCOLS)) ||
       (e = dalloc(&r->Bhi, (size_t)(Pp * Np))) || (e = dalloc(&r->Blo, (size_t)(Pp * Np))) ||
       (e = dalloc(&r->B32, (size_t)(Pp * Np))) || (e = dalloc(&r->QB, (size_t)(QCOLS * Np))) ||
       (e = dalloc(&r->QBhi, (size_t)(QCOLS * Np))) || (e = dalloc(&r->QBlo, (size_t)(QCOLS * Np)))) {
@@ -766,6 +764,8 @@ tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_pa
         (x = cudaMemsetAsync(r->Blo, 0, sizeof(__nv_bfloat16) * Pp * Np, st)) ||
         (x = cudaMemsetAsync(r->B32, 0, sizeof(float) * Pp * Np, st)) ||
         (x = cudaMemsetAsync(r->col_rmul, 0, sizeof(float) * Pp, st)) ||
+        (x = cudaMemsetAsync(r->col_cs, 0, sizeof(float) * Pp, st)) ||
+        (x = cudaMemcpyAsync(r->qcs, p0->qcs, sizeof(float) * QCOLS, cudaMemcpyDeviceToDevice, st)) ||
         (x = cudaMemcpyAsync(r->Q, p0->Q, sizeof(double) * q * N, cudaMemcpyDeviceToDevice, st)) ||
         (x = cudaMemcpyAsync(r->QB, p0->QB, sizeof(float) * QCOLS * Np, cudaMemcpyDeviceToDevice, st)) ||
         (x = cudaMemcpyAsync(r->QBhi, p0->QBhi, 2 * QCOLS * Np, cudaMemcpyDeviceToDevice, st)) ||
@@ -780,6 +780,7 @@ tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_pa
           (x = cudaMemcpyAsync(r->s + off, pi->s, sizeof(double) * k, cudaMemcpyDeviceToDevice, st)) ||
           (x = cudaMemcpyAsync(r->col_s + off, pi->col_s, sizeof(float) * k, cudaMemcpyDeviceToDevice, st)) ||
           (x = cudaMemcpyAsync(r->col_rmul + off, pi->col_rmul, sizeof(float) * k, cudaMemcpyDeviceToDevice, st)) ||
+          (x = cudaMemcpyAsync(r->col_cs + off, pi->col_cs, sizeof(float) * k, cudaMemcpyDeviceToDevice, st)) ||
           (x = cudaMemcpyAsync(r->Bhi + off * Np, pi->Bhi, 2 * k * Np, cudaMemcpyDeviceToDevice, st)) ||
           (x = cudaMemcpyAsync(r->Blo + off * Np, pi->Blo, 2 * k * Np, cudaMemcpyDeviceToDevice, st)) ||
           (x = cudaMemcpyAsync(r->B32 + off * Np, pi->B32, sizeof(float) * k * Np, cudaMemcpyDeviceToDevice, st)))
@@ -814,19 +815,16 @@ tg_status tg_scan_graph_create(tg_ctx* c, const tg_panel* p, int n_blocks,
          "per-marker outputs are not supported in captured scan graphs");
   TG_CUDA(cudaSetDevice(c->device));
   int64_t maxM = 0;
-  bool any_lo = false;
   for (int b = 0; b < n_blocks; ++b) {
     ScanArgs a{G[b], ldg, encoding, N, M[b], marker_offset[b], missing ? missing[b] : nullptr, ldm,
                *opts, *out};
     tg_status s = check_scan_args(c, p, a);
     if (s != TG_OK) return s;
     maxM = std::max(maxM, M[b]);
-    any_lo |= encoding == TG_ENC_2BIT || (missing && missing[b]);
   }
-  const bool lo = opts->precision == TG_PREC_SPLIT_BF16 && any_lo;
   // size the workspace now: nothing may allocate inside the capture
   TG_CUDA(ensure_markers(c, maxM));
-  TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision, lo));
+  TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision));
   cudaStream_t cap = nullptr;
   TG_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   tg_graph* g = new tg_graph();

@@ -131,13 +131,13 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
     return fail(TG_ERR_INVALID_ARG, "hit collection needs hits, hit_capacity and n_hits");
 
   // size check before anything is touched
-  const bool has_lo = prec == TG_PREC_SPLIT_BF16 && (encoding == TG_ENC_2BIT || missing);
+  const bool split = prec == TG_PREC_SPLIT_BF16;
   const int64_t rows = round_up(M, MT);
   const size_t elem = prec == TG_PREC_FP32 ? 4 : 2;
   Carver probe{nullptr};
   probe.take<uint32_t>(4);
   probe.take<unsigned long long>(1);
-  probe.take<int>((size_t)(rows / MT));
+  probe.take<float>((size_t)rows);
   probe.take<int32_t>((size_t)rows);
   probe.take<double>((size_t)rows);
   probe.take<double>((size_t)rows);
@@ -146,9 +146,8 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   probe.take<float>((size_t)rows);
   probe.take<double>((size_t)rows);
   probe.take<unsigned char>((size_t)rows * p->Npad * elem);
-  if (has_lo) probe.take<unsigned char>((size_t)rows * p->Npad * 2);
   if (probe.used > kStaticScratchBytes) {
-    const size_t per = (size_t)p->Npad * (elem + (has_lo ? 2 : 0)) + 4 * QCOLS + 64;
+    const size_t per = (size_t)p->Npad * elem + 4 * QCOLS + 64;
     return fail(TG_ERR_UNSUPPORTED,
                 "block too large for the 64 MiB static scratch: at most about " +
                     std::to_string(kStaticScratchBytes / per) + " markers at N = " +
@@ -166,7 +165,7 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   Carver cv{ds->base};
   uint32_t* status = cv.take<uint32_t>(4);
   unsigned long long* hit_start = cv.take<unsigned long long>(1);
-  int* tflags = cv.take<int>((size_t)(rows / MT));
+  float* shift = cv.take<float>((size_t)rows);
   int32_t* nobs = cv.take<int32_t>((size_t)rows);
   double* mean = cv.take<double>((size_t)rows);
   double* gc2 = cv.take<double>((size_t)rows);
@@ -175,7 +174,6 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   float* rinv = cv.take<float>((size_t)rows);
   double* rinv64 = cv.take<double>((size_t)rows);
   void* Ahi = cv.take<unsigned char>((size_t)rows * p->Npad * elem);
-  __nv_bfloat16* Alo = has_lo ? cv.take<__nv_bfloat16>((size_t)rows * p->Npad) : nullptr;
 
   cudaStream_t st = (cudaStream_t)stream;
   const float kappa = encoding == TG_ENC_U8_DOSAGE ? (float)(2.0 / 255.0) : 1.0f;
@@ -186,29 +184,28 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   } while (0)
   // every call shares the scratch and it keeps the last call's contents: clear what must start at 0
   TGS_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), st));
-  if (has_lo) TGS_CUDA(cudaMemsetAsync(tflags, 0, sizeof(int) * (size_t)(rows / MT), st));
-  TGS_CUDA(launch_decode(G, ldg, encoding, N, M, missing, ldm, prec, Ahi, Alo, p->Npad, nobs,
-                         nullptr, nullptr, mean, gc2, has_lo ? tflags : nullptr, st));
-  CUtensorMap tA, tAlo;
-  if (prec == TG_PREC_SPLIT_BF16) {
-    if (!tmap_static(&tA, Ahi, M, p->Npad, p->Npad, MT) ||
-        (has_lo && !tmap_static(&tAlo, Alo, M, p->Npad, p->Npad, MT)))
-      return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
-  }
+  TGS_CUDA(launch_decode(G, ldg, encoding, N, M, missing, ldm, prec, Ahi,
+                         split ? shift : nullptr, p->Npad, nobs, nullptr, nullptr, mean, gc2, st));
+  CUtensorMap tA;
+  if (split && !tmap_static(&tA, Ahi, M, p->Npad, p->Npad, MT))
+    return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
   const int64_t nq = p->q - 1;
   if (nq > 0) {
-    if (prec == TG_PREC_FP32) {
-      TGS_CUDA(launch_project(Ahi, nullptr, 1, p->Npad, M, p->Npad, p->QB, nq, qg, st));
+    if (!split) {
+      TGS_CUDA(launch_project(reinterpret_cast<const float*>(Ahi), p->Npad, M, p->Npad, p->QB, nq,
+                              qg, st));
     } else {
       EpiParams pp{};
       pp.M = (int)M;
       pp.P = (int)nq;
       pp.status = status;
+      pp.row_shift = shift;
+      pp.col_cs = p->qcs;
       pp.raw_out = qg;
       pp.raw_cols = (int)nq;
       pp.raw_ld = QCOLS;
-      TGS_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmQhi, &p->tmQlo, p->Npad, has_lo,
-                              tflags, pp, ds->sm_count, kStaticSpinNs, st));
+      TGS_CUDA(launch_tc_scan(&tA, &p->tmQhi, &p->tmQlo, p->Npad, pp, ds->sm_count, kStaticSpinNs,
+                              st));
     }
   }
   TGS_CUDA(launch_marker_norm(M, nobs, gc2, qg, nq, kappa, gres2, out->marker_norm2, rinv, rinv64, st));
@@ -233,6 +230,8 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   ep.col_s = p->col_s;
   ep.col_s64 = p->s;
   ep.col_rmul = p->col_rmul;
+  ep.row_shift = split ? shift : nullptr;
+  ep.col_cs = p->col_cs;
   ep.beta = out->beta;
   ep.se = out->se;
   ep.t = out->t;
@@ -247,12 +246,12 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   if (ep.do_hits)
     TGS_CUDA(cudaMemcpyAsync(hit_start, ep.n_hits, sizeof(unsigned long long),
                              cudaMemcpyDeviceToDevice, st));
-  if (prec == TG_PREC_FP32) {
+  if (!split) {
     TGS_CUDA(launch_sgemm_scan(reinterpret_cast<const float*>(Ahi), p->Npad, p->B32, p->Npad,
                                p->Npad, ep, st));
   } else {
-    TGS_CUDA(launch_tc_scan(&tA, has_lo ? &tAlo : &tA, &p->tmBhi, &p->tmBlo, p->Npad, has_lo,
-                            tflags, ep, ds->sm_count, kStaticSpinNs, st));
+    TGS_CUDA(launch_tc_scan(&tA, &p->tmBhi, &p->tmBlo, p->Npad, ep, ds->sm_count, kStaticSpinNs,
+                            st));
   }
   if (ep.do_hits) TGS_CUDA(launch_hit_stats(ep, hit_start, st));
   if (ep.do_full) TGS_CUDA(launch_full_stats(ep, st));

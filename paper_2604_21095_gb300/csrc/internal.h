@@ -42,6 +42,8 @@ struct EpiParams {
   const float* col_s;          // [P] s_p, NaN = untestable phenotype
   const double* col_s64;       // [P]
   const float* col_rmul;       // [P] 1 or NaN
+  const float* row_shift;      // [M] c the operand row was shifted by (NULL = none)
+  const float* col_cs;         // [P] sum_i of the B operand column (the shift's add-back)
   float *beta, *se, *t, *mlp;  // FULL outputs, [M][ldo]
   float* rstore;               // FULL mode: where the contraction leaves r (one of the above)
   long long ldo;
@@ -91,12 +93,14 @@ struct tg_panel {
   double* s = nullptr;        // [P]
   float* col_s = nullptr;     // [P]
   float* col_rmul = nullptr;  // [Ppad]
+  float* col_cs = nullptr;    // [Ppad] sum_i (Bhi + Blo)[p][i], in FP32
   __nv_bfloat16* Bhi = nullptr;  // [Ppad][Npad] unit-norm panel, high part
   __nv_bfloat16* Blo = nullptr;  // [Ppad][Npad] low part
   float* B32 = nullptr;          // [Ppad][Npad] unit-norm panel in FP32
   float* QB = nullptr;           // [QCOLS][Npad] Q columns 1..q-1 in FP32 (rest zero)
   __nv_bfloat16* QBhi = nullptr; // [QCOLS][Npad] the same split into bf16 hi + lo
   __nv_bfloat16* QBlo = nullptr;
+  float* qcs = nullptr;          // [QCOLS] sum_i (QBhi + QBlo)[k][i]
   double lnB = 0;
   CUtensorMap tmBhi, tmBlo;      // phenotype panel, 256-row boxes
   CUtensorMap tmBhi2, tmBlo2;    // phenotype panel, 128-row boxes (one CTA's half of a pair tile)
@@ -111,18 +115,17 @@ struct tg_ctx {
   uint32_t* scratch = nullptr;  // small device scratch (rank, flags)
   // decode / projection workspace
   int64_t cap_rows = 0, cap_npad = 0;          // A buffers: rows x npad
-  __nv_bfloat16* Ahi = nullptr;
-  __nv_bfloat16* Alo = nullptr;
+  __nv_bfloat16* Ahi = nullptr;                 // centred split operand
   float* A32 = nullptr;
   int64_t cap_m = 0;                            // per-marker arrays
   int32_t* nobs = nullptr;
   double* mean = nullptr;
+  float* shift = nullptr;                       // [cap_m] per-row shift of the split operand
   double* gc2 = nullptr;
   float* qg = nullptr;                          // [cap_m][QCOLS]
   double* gres2 = nullptr;
   float* rinv = nullptr;
   double* rinv64 = nullptr;
-  int* tflags = nullptr;                        // per 128-row tile: block row has a missing call
   // host-streamed scan
   uint8_t* stage_buf[2] = {nullptr, nullptr};
   size_t stage_bytes = 0;
@@ -164,20 +167,19 @@ cudaError_t launch_householder(double* X, int64_t N, int64_t k, double* Q, int* 
 cudaError_t launch_residualise(const float* Y, int64_t ldy, const double* Q, int64_t N, int64_t P,
                                int64_t q, int64_t Npad, double* Yres, double* s, float* col_s,
                                float* col_rmul, __nv_bfloat16* Bhi, __nv_bfloat16* Blo, float* B32,
-                               uint32_t* flags, cudaStream_t st);
+                               float* col_cs, uint32_t* flags, cudaStream_t st);
 cudaError_t launch_qcols(const double* Q, int64_t N, int64_t q, int64_t Npad, float* QB,
-                         __nv_bfloat16* QBhi, __nv_bfloat16* QBlo, cudaStream_t st);
+                         __nv_bfloat16* QBhi, __nv_bfloat16* QBlo, float* qcs, cudaStream_t st);
 
 // decode (k_decode.cu)
 cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,
-                          const uint32_t* missing, int64_t ldm, int precision, void* Ahi, void* Alo,
-                          int64_t lda, int32_t* nobs, int64_t* S, int64_t* S2, double* mean,
-                          double* gc2, int* tflags, cudaStream_t st);
+                          const uint32_t* missing, int64_t ldm, int precision, void* Ahi,
+                          float* shift, int64_t lda, int32_t* nobs, int64_t* S, int64_t* S2,
+                          double* mean, double* gc2, cudaStream_t st);
 
 // SIMT kernels (k_simt.cu)
-cudaError_t launch_project(const void* Ahi, const __nv_bfloat16* Alo, int a_is_f32, int64_t lda,
-                           int64_t M, int64_t K, const float* QB, int64_t nq, float* qg,
-                           cudaStream_t st);
+cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, const float* QB,
+                           int64_t nq, float* qg, cudaStream_t st);
 cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
                                int64_t nq, float kappa, double* gres2_units_out,
                                double* norm2_allele_out, float* rinv, double* rinv64,
@@ -191,15 +193,13 @@ cudaError_t launch_hit_stats(const EpiParams& ep, const unsigned long long* star
 cudaError_t launch_fill_random(uint8_t* p, size_t n, unsigned long long seed, cudaStream_t st);
 
 // tensor-core kernel (k_tc.cu)
-cudaError_t launch_tc_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
-                           const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
-                           bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
+cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
+                           const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
                            long long spin_ns, cudaStream_t st, int group_m = 16);
 
 // tensor-core kernel on CTA pairs, 256 x 256 tiles (k_tc2.cu)
-cudaError_t launch_tc2_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
-                            const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
-                            bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
+cudaError_t launch_tc2_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
+                            const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
                             long long spin_ns, cudaStream_t st, int group_m = 16);
 
 // bounded wait test (k_tc.cu)

@@ -4,8 +4,13 @@
 // exactly in integers, the observed calls n, their sum S and sum of squares S2 (decode
 // units: allele-1 counts for 2-bit calls, bytes for dosages); mean = S / n is one IEEE
 // division and |g_c|^2 = (n S2 - S^2) / n one more. Pass 2 re-reads the row (cache-hot)
-// and writes the contraction operand with 16-byte stores: the exact code of an observed
-// call, the imputed mean of a missing one, zero past N.
+// and writes the contraction operand with 16-byte stores, zero past N:
+//   FP32 form: the code of an observed call, the mean at a missing one.
+//   split form (bf16): the row shifted by c = the mean rounded to a grid on which every
+//   observed value minus c is exact in bf16 (2-bit: multiples of 2^-7, |code - c| <= 2;
+//   dosage: integers, |byte - c| <= 255), and bf16(mean - c) at a missing call
+//   (|mean - c| <= 2^-8 or 1/2, so its rounding error is <= 2^-17 or 2^-10). The scan adds
+//   c * sum_i y_i back per phenotype column, so imputation needs no extra product.
 //
 // 2-bit fields follow the PLINK 1 .bed table: 00 -> 2, 10 -> 1, 11 -> 0, 01 -> missing.
 // With lo = w & 0x55.. and hi = (w >> 1) & 0x55.. per 32-bit word: count 2 = ~lo & ~hi,
@@ -108,13 +113,20 @@ __device__ __forceinline__ void load8(const uint8_t* __restrict__ row, const uin
   if (i0 + 8 > N) miss &= (N > i0) ? ((1u << (N - i0)) - 1u) : 0u;
 }
 
+// Shift of a marker row for the split form (see above); 0 when no call is observed.
+template <int ENC>
+__device__ __forceinline__ double row_shift(unsigned long long n, double mean) {
+  if (!n) return 0.0;
+  return ENC == TG_ENC_2BIT ? rint(mean * 128.0) * (1.0 / 128.0) : rint(mean);
+}
+
 template <int ENC, int PREC>
 __global__ void __launch_bounds__(kWarps * 32) k_decode(
     const uint8_t* __restrict__ G, long long ldg, int N, long long M,
     const uint32_t* __restrict__ miss, long long ldm, void* __restrict__ Ahi,
-    __nv_bfloat16* __restrict__ Alo, long long lda, int32_t* __restrict__ nobs_out,
+    float* __restrict__ shift_out, long long lda, int32_t* __restrict__ nobs_out,
     long long* __restrict__ S_out, long long* __restrict__ S2_out, double* __restrict__ mean_out,
-    double* __restrict__ gc2_out, int* __restrict__ tflags) {
+    double* __restrict__ gc2_out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long j = (long long)blockIdx.x * kWarps + warp;
   if (j >= M) return;
@@ -133,37 +145,35 @@ __global__ void __launch_bounds__(kWarps * 32) k_decode(
       const long long num = (long long)S2 * (long long)n - (long long)S * (long long)S;
       gc2_out[j] = n ? (double)num / dn : __longlong_as_double(0x7ff8000000000000ll);
     }
-    if (tflags && n < (unsigned long long)N) atomicOr(tflags + (j / MT), 1);
   }
   // pass 2: operand row
   const double m_imp = n ? mean : 0.0;
   const long long steps = lda >> 3;
   if (PREC == TG_PREC_SPLIT_BF16) {
-    const __nv_bfloat16 mh = __double2bfloat16(m_imp);
-    const __nv_bfloat16 ml = __double2bfloat16(m_imp - (double)__bfloat162float(mh));
+    const double c = row_shift<ENC>(n, mean);
+    if (lane == 0 && shift_out) shift_out[j] = (float)c;
+    const float cf = (float)c;  // exact: a multiple of 2^-7 in [0, 2] or an integer in [0, 255]
+    const __nv_bfloat16 mh = __double2bfloat16(m_imp - c);
     __nv_bfloat16* ah = reinterpret_cast<__nv_bfloat16*>(Ahi) + j * lda;
-    __nv_bfloat16* al = Alo ? Alo + j * lda : nullptr;
 #pragma unroll 4
     for (long long t = lane; t < steps; t += 32) {
       const int i0 = (int)(t << 3);
       float v[8];
       uint32_t ms = 0;
+      __align__(16) __nv_bfloat16 hv[8];
       if (i0 < N) {
         load8<ENC>(row, mrow, i0, N, v, ms);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const bool m = (ms >> s) & 1u;
+          // v - c is exact in FP32 and in bf16; samples past N stay 0
+          hv[s] = m ? mh : __float2bfloat16_rn(i0 + s < N ? v[s] - cf : 0.0f);
+        }
       } else {
 #pragma unroll
-        for (int s = 0; s < 8; ++s) v[s] = 0.0f;
-      }
-      __align__(16) __nv_bfloat16 hv[8];
-      __align__(16) __nv_bfloat16 lv[8];
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        const bool m = (ms >> s) & 1u;
-        hv[s] = m ? mh : __float2bfloat16_rn(v[s]);
-        lv[s] = m ? ml : __float2bfloat16_rn(0.0f);
+        for (int s = 0; s < 8; ++s) hv[s] = __float2bfloat16_rn(0.0f);
       }
       *reinterpret_cast<uint4*>(ah + i0) = *reinterpret_cast<const uint4*>(hv);
-      if (al) *reinterpret_cast<uint4*>(al + i0) = *reinterpret_cast<const uint4*>(lv);
     }
   } else {
     const float mf = (float)m_imp;
@@ -190,30 +200,30 @@ __global__ void __launch_bounds__(kWarps * 32) k_decode(
 
 template <int ENC, int PREC>
 cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32_t* missing,
-               int64_t ldm, void* Ahi, void* Alo, int64_t lda, int32_t* nobs, int64_t* S,
-               int64_t* S2, double* mean, double* gc2, int* tflags, cudaStream_t st) {
+               int64_t ldm, void* Ahi, float* shift, int64_t lda, int32_t* nobs, int64_t* S,
+               int64_t* S2, double* mean, double* gc2, cudaStream_t st) {
   const unsigned grid = (unsigned)((M + kWarps - 1) / kWarps);
   k_decode<ENC, PREC><<<grid, kWarps * 32, 0, st>>>(
-      G, ldg, (int)N, M, missing, ldm, Ahi, reinterpret_cast<__nv_bfloat16*>(Alo), lda, nobs,
-      reinterpret_cast<long long*>(S), reinterpret_cast<long long*>(S2), mean, gc2, tflags);
+      G, ldg, (int)N, M, missing, ldm, Ahi, shift, lda, nobs, reinterpret_cast<long long*>(S),
+      reinterpret_cast<long long*>(S2), mean, gc2);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,
-                          const uint32_t* missing, int64_t ldm, int precision, void* Ahi, void* Alo,
-                          int64_t lda, int32_t* nobs, int64_t* S, int64_t* S2, double* mean,
-                          double* gc2, int* tflags, cudaStream_t st) {
+                          const uint32_t* missing, int64_t ldm, int precision, void* Ahi,
+                          float* shift, int64_t lda, int32_t* nobs, int64_t* S, int64_t* S2,
+                          double* mean, double* gc2, cudaStream_t st) {
   if (M == 0) return cudaSuccess;
   if (encoding == TG_ENC_2BIT) {
     return precision == TG_PREC_SPLIT_BF16
-               ? go<TG_ENC_2BIT, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, Alo, lda, nobs, S, S2, mean, gc2, tflags, st)
-               : go<TG_ENC_2BIT, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, Alo, lda, nobs, S, S2, mean, gc2, tflags, st);
+               ? go<TG_ENC_2BIT, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, shift, lda, nobs, S, S2, mean, gc2, st)
+               : go<TG_ENC_2BIT, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, shift, lda, nobs, S, S2, mean, gc2, st);
   }
   return precision == TG_PREC_SPLIT_BF16
-             ? go<TG_ENC_U8_DOSAGE, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, Alo, lda, nobs, S, S2, mean, gc2, tflags, st)
-             : go<TG_ENC_U8_DOSAGE, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, Alo, lda, nobs, S, S2, mean, gc2, tflags, st);
+             ? go<TG_ENC_U8_DOSAGE, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, shift, lda, nobs, S, S2, mean, gc2, st)
+             : go<TG_ENC_U8_DOSAGE, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, shift, lda, nobs, S, S2, mean, gc2, st);
 }
 
 }  // namespace tg

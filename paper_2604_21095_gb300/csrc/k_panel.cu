@@ -5,7 +5,10 @@
 //      1e-9 of its own norm is dropped (rank detection); Q = H_0 ... H_{q-1} [I_q; 0].
 //   3. Per phenotype: Y_res = (I - Q Q^T)(Y - Ybar), s_p = |y_res|, and the unit-norm column
 //      y_res / s_p written as FP32 and as a BF16 pair hi = bf16(y), lo = bf16(y - hi).
-//   4. Q columns 1..q-1 (the non-intercept directions) in FP32 for the marker projection.
+//   4. Q columns 1..q-1 (the non-intercept directions) in FP32 and as a BF16 pair for the
+//      marker projection.
+//   5. Per column of the BF16 pairs, sum_i (hi + lo) in FP64: the scan adds c * sum back for a
+//      marker row shifted by c (the split operand is centred; see k_decode.cu).
 #include <cuda_bf16.h>
 
 #include "device.cuh"
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(256) k_residualise(
     const float* __restrict__ Y, long long ldy, const double* __restrict__ Q, long long N, int q,
     long long Npad, double* __restrict__ Yres, double* __restrict__ s_out, float* __restrict__ col_s,
     float* __restrict__ col_rmul, __nv_bfloat16* __restrict__ Bhi, __nv_bfloat16* __restrict__ Blo,
-    float* __restrict__ B32, uint32_t* flags) {
+    float* __restrict__ B32, float* __restrict__ col_cs, uint32_t* flags) {
   __shared__ double red[33];
   __shared__ double coef[QMAX];
   const long long p = blockIdx.x;
@@ -168,13 +171,31 @@ __global__ void __launch_bounds__(256) k_residualise(
   __nv_bfloat16* bh = Bhi + p * Npad;
   __nv_bfloat16* bl = Blo + p * Npad;
   float* bf = B32 + p * Npad;
+  double bsum = 0.0;
   for (long long i = tid; i < Npad; i += nt) {
     const double u = (i < N) ? yr[i] * inv : 0.0;
     const __nv_bfloat16 h = __double2bfloat16(u);
+    const __nv_bfloat16 l = __double2bfloat16(u - (double)__bfloat162float(h));
     bh[i] = h;
-    bl[i] = __double2bfloat16(u - (double)__bfloat162float(h));
+    bl[i] = l;
     bf[i] = (float)u;
+    bsum += (double)__bfloat162float(h) + (double)__bfloat162float(l);
   }
+  bsum = block_sum(bsum, red);
+  if (tid == 0) col_cs[p] = (float)bsum;
+}
+
+// Row sums of the bf16 pair of the projection columns.
+__global__ void __launch_bounds__(256) k_qcolsum(const __nv_bfloat16* __restrict__ QBhi,
+                                                 const __nv_bfloat16* __restrict__ QBlo,
+                                                 long long Npad, float* __restrict__ qcs) {
+  __shared__ double red[33];
+  const long long r = blockIdx.x;
+  double cs = 0.0;
+  for (long long i = threadIdx.x; i < Npad; i += blockDim.x)
+    cs += (double)__bfloat162float(QBhi[r * Npad + i]) + (double)__bfloat162float(QBlo[r * Npad + i]);
+  cs = block_sum(cs, red);
+  if (threadIdx.x == 0) qcs[r] = (float)cs;
 }
 
 __global__ void k_qcols(const double* __restrict__ Q, long long N, int q, long long Npad,
@@ -210,17 +231,20 @@ cudaError_t launch_householder(double* X, int64_t N, int64_t k, double* Q, int* 
 cudaError_t launch_residualise(const float* Y, int64_t ldy, const double* Q, int64_t N, int64_t P,
                                int64_t q, int64_t Npad, double* Yres, double* s, float* col_s,
                                float* col_rmul, __nv_bfloat16* Bhi, __nv_bfloat16* Blo, float* B32,
-                               uint32_t* flags, cudaStream_t st) {
+                               float* col_cs, uint32_t* flags, cudaStream_t st) {
   if (P == 0) return cudaSuccess;
   k_residualise<<<(unsigned)P, 256, 0, st>>>(Y, ldy, Q, N, (int)q, Npad, Yres, s, col_s, col_rmul,
-                                             Bhi, Blo, B32, flags);
+                                             Bhi, Blo, B32, col_cs, flags);
   return cudaGetLastError();
 }
 
 cudaError_t launch_qcols(const double* Q, int64_t N, int64_t q, int64_t Npad, float* QB,
-                         __nv_bfloat16* QBhi, __nv_bfloat16* QBlo, cudaStream_t st) {
+                         __nv_bfloat16* QBhi, __nv_bfloat16* QBlo, float* qcs, cudaStream_t st) {
   dim3 grid((unsigned)((Npad + 255) / 256), QCOLS);
   k_qcols<<<grid, 256, 0, st>>>(Q, N, (int)q, Npad, QB, QBhi, QBlo);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_qcolsum<<<QCOLS, 256, 0, st>>>(QBhi, QBlo, Npad, qcs);
   return cudaGetLastError();
 }
 

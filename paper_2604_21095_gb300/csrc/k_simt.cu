@@ -19,10 +19,8 @@ namespace {
 
 // ---------------------------------------------------------------- projection
 // qg[m][k] = sum_i A[m][i] QB[k][i]; tile 64 markers x 32 columns, 32 samples per step.
-template <bool F32>
-__global__ void __launch_bounds__(256) k_project(const void* __restrict__ Ahi_,
-                                                 const __nv_bfloat16* __restrict__ Alo,
-                                                 long long lda, long long M, int K,
+__global__ void __launch_bounds__(256) k_project(const float* __restrict__ A, long long lda,
+                                                 long long M, int K,
                                                  const float* __restrict__ QB, int nq,
                                                  float* __restrict__ qg) {
   __shared__ __align__(16) float As[32][64 + 4];
@@ -35,40 +33,17 @@ __global__ void __launch_bounds__(256) k_project(const void* __restrict__ Ahi_,
   float acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   double tot[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   for (int i0 = 0; i0 < K; i0 += 32) {
-    // A tile: 64 rows x 32 samples
-    if (F32) {
-      const float* A = reinterpret_cast<const float*>(Ahi_);
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int e = tid + u * 256;       // 512 float4
-        const int r = e >> 3, c4 = (e & 7) * 4;
-        const long long gm = m0 + r;
-        float4 v = make_float4(0, 0, 0, 0);
-        if (gm < M) v = *reinterpret_cast<const float4*>(A + gm * lda + i0 + c4);
-        As[c4 + 0][r] = v.x;
-        As[c4 + 1][r] = v.y;
-        As[c4 + 2][r] = v.z;
-        As[c4 + 3][r] = v.w;
-      }
-    } else {
-      const __nv_bfloat16* A = reinterpret_cast<const __nv_bfloat16*>(Ahi_);
-      const int r = tid >> 2, c8 = (tid & 3) * 8;  // 256 x 8 bf16
+    for (int u = 0; u < 2; ++u) {  // A tile: 64 rows x 32 samples as 512 float4
+      const int e = tid + u * 256;
+      const int r = e >> 3, c4 = (e & 7) * 4;
       const long long gm = m0 + r;
-      float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (gm < M) {
-        const uint4 h = *reinterpret_cast<const uint4*>(A + gm * lda + i0 + c8);
-        const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&h);
-#pragma unroll
-        for (int s = 0; s < 8; ++s) v[s] = __bfloat162float(hb[s]);
-        if (Alo) {
-          const uint4 l = *reinterpret_cast<const uint4*>(Alo + gm * lda + i0 + c8);
-          const __nv_bfloat16* lb = reinterpret_cast<const __nv_bfloat16*>(&l);
-#pragma unroll
-          for (int s = 0; s < 8; ++s) v[s] += __bfloat162float(lb[s]);
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < 8; ++s) As[c8 + s][r] = v[s];
+      float4 v = make_float4(0, 0, 0, 0);
+      if (gm < M) v = *reinterpret_cast<const float4*>(A + gm * lda + i0 + c4);
+      As[c4 + 0][r] = v.x;
+      As[c4 + 1][r] = v.y;
+      As[c4 + 2][r] = v.z;
+      As[c4 + 3][r] = v.w;
     }
     {  // Q tile: 32 columns x 32 samples
       const int r = tid >> 3, c4 = (tid & 7) * 4;
@@ -247,15 +222,11 @@ __global__ void __launch_bounds__(256, 1) k_sgemm_scan(const float* __restrict__
 
 }  // namespace
 
-cudaError_t launch_project(const void* Ahi, const __nv_bfloat16* Alo, int a_is_f32, int64_t lda,
-                           int64_t M, int64_t K, const float* QB, int64_t nq, float* qg,
-                           cudaStream_t st) {
+cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, const float* QB,
+                           int64_t nq, float* qg, cudaStream_t st) {
   if (M == 0 || nq == 0) return cudaSuccess;
   dim3 grid((unsigned)((M + 63) / 64), (unsigned)((nq + 31) / 32));
-  if (a_is_f32)
-    k_project<true><<<grid, 256, 0, st>>>(Ahi, nullptr, lda, M, (int)K, QB, (int)nq, qg);
-  else
-    k_project<false><<<grid, 256, 0, st>>>(Ahi, Alo, lda, M, (int)K, QB, (int)nq, qg);
+  k_project<<<grid, 256, 0, st>>>(A, lda, M, (int)K, QB, (int)nq, qg);
   return cudaGetLastError();
 }
 

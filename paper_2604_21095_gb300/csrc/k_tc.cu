@@ -1,15 +1,15 @@
 // Tensor-core scan: Eq. 2 of Section 2.2 on tcgen05, fused with Eq. 3 and the p-value.
 //
-// D = A (B_hi + B_lo)^T [+ A_lo B_hi^T] for a block of markers against the whole panel:
-//   A     [M][K] bf16  exact genotype codes (or dosage bytes); a missing call holds bf16(mean)
-//   A_lo  [M][K] bf16  mean - bf16(mean) at missing calls, 0 elsewhere (2-bit / masked blocks)
+// D = A (B_hi + B_lo)^T + c (sum_i B) for a block of markers against the whole panel:
+//   A     [M][K] bf16  each marker row shifted by its c (exact), bf16(mean - c) at a missing call
 //   B_hi, B_lo [P][K]  bf16 split of the unit-norm residualised panel, y ~= hi + lo
+//   c (per row), sum_i B (per column) added back in the epilogue
 // K = samples (zero padded), FP32 accumulation in tensor memory.
 //
 // Persistent kernel, one CTA per SM, 384 threads (3 warpgroups), warp-specialised:
 //   warp 0 lane 0  TMA producer: 128x32 A tiles and 256x32 B tiles (64-byte swizzle) into a
 //                  ring of shared-memory stages, completion tracked by mbarrier transaction bytes
-//   warp 1 lane 0  MMA issuer: per 32-wide K step, 2 x (2 or 3) tcgen05.mma 128x256x16 into an
+//   warp 1 lane 0  MMA issuer: per 32-wide K step, 2 x 2 tcgen05.mma 128x256x16 into an
 //                  FP32 accumulator in TMEM
 //   warps 4..11    epilogue: tcgen05.ld of the accumulator (thread = marker row, each warp one
 //                  TMEM lane quarter and one half of the 256 columns), r = D / |g_res|, hits
@@ -35,22 +35,19 @@ namespace {
 
 using namespace tcx;
 
-template <bool HAS_LO>
 struct Cfg {
-  static constexpr int kStageBytes = A_BYTES * (HAS_LO ? 2 : 1) + 2 * B_BYTES;
-  static constexpr int kStages = HAS_LO ? 4 : 5;
+  static constexpr int kStageBytes = A_BYTES + 2 * B_BYTES;  // 40 KB
+  static constexpr int kStages = 5;
   static constexpr int kBarBytes = 256;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;  // + alignment slack
 };
 
-template <bool HAS_LO>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
-              const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-              int num_kb, int n_mt, int n_nt, int bn, int group_m, const int* __restrict__ tflags,
-              long long spin_ns, EpiParams ep) {
+    k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmBhi,
+              const __grid_constant__ CUtensorMap tmBlo, int num_kb, int n_mt, int n_nt, int bn,
+              int group_m, long long spin_ns, EpiParams ep) {
   // bn = B rows per tile: 256 for the phenotype panel, 64 for the covariate projection
-  using C = Cfg<HAS_LO>;
+  using C = Cfg;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -68,7 +65,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto sA = [&](int s) { return base + s * C::kStageBytes; };
   auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
   auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + B_BYTES; };
-  auto sAlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * B_BYTES; };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -110,8 +106,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
       tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
-      const bool lo = HAS_LO && tflags[mt] != 0;
-      const uint32_t bytes = A_BYTES + 2u * (uint32_t)bn * (TBK * 2) + (lo ? A_BYTES : 0);
+      const uint32_t bytes = A_BYTES + 2u * (uint32_t)bn * (TBK * 2);
       for (int kb = 0; kb < num_kb; ++kb) {
         if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, spin_ns, ep.status)) {
           ok = false;
@@ -122,7 +117,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_load_2d(&tmAhi, sA(stage), full_bar(stage), kb * TBK, mt * TBM);
         tma_load_2d(&tmBhi, sBhi(stage), full_bar(stage), kb * TBK, nt * bn);
         tma_load_2d(&tmBlo, sBlo(stage), full_bar(stage), kb * TBK, nt * bn);
-        if (lo) tma_load_2d(&tmAlo, sAlo(stage), full_bar(stage), kb * TBK, mt * TBM);
         if (++stage == S) {
           stage = 0;
           phase ^= 1u;
@@ -144,7 +138,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
       tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
-      const bool lo = HAS_LO && tflags[mt] != 0;
       for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kChunkKB, ++g) {
         const int acc = (int)(g & 1u);
         const uint32_t ph = (g >> 1) & 1u;
@@ -168,7 +161,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t bl = sdesc_sw64(sBlo(stage) + 32u * k);
             tc_mma(d, a, bh, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
             tc_mma(d, a, bl, idesc, 1u);
-            if (lo) tc_mma(d, sdesc_sw64(sAlo(stage) + 32u * k), bh, idesc, 1u);
           }
           tc_commit(empty_bar(stage));
           if (++stage == S) {
@@ -224,15 +216,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const long long row = row_base + lane;
       const bool row_ok = row < ep.M;
       const float rinv = (row_ok && ep.row_inv) ? ep.row_inv[row] : __int_as_float(0x7fc00000);
+      const float shift = (row_ok && ep.row_shift) ? ep.row_shift[row] : 0.0f;
       if (ep.raw_out) {
         // covariate projection: the first raw_cols columns of the tile, unnormalised
         if (row_ok && half == 0) {
 #pragma unroll
           for (int e = 0; e < 64; ++e)
-            if (e < ep.raw_cols) ep.raw_out[row * ep.raw_ld + e] = tot[e];
+            if (e < ep.raw_cols)
+              ep.raw_out[row * ep.raw_ld + e] = fmaf(shift, ep.col_cs[e], tot[e]);
         }
       } else {
-        epilogue_tile(ep, tot, row, row_base, row_ok, rinv, nt * TBN + half * 128, lane);
+        epilogue_tile(ep, tot, row, row_base, row_ok, rinv, shift, nt * TBN + half * 128, lane);
       }
       __syncwarp();
     }
@@ -263,15 +257,12 @@ __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, u
   }
 }
 
-template <bool HAS_LO>
-cudaError_t go(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* bh,
-               const CUtensorMap* bl, int64_t K, const int* tflags, const EpiParams& ep,
-               int sm_count, int group_m, long long spin_ns, cudaStream_t st) {
-  using C = Cfg<HAS_LO>;
+cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* bl, int64_t K,
+               const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st) {
   static bool attr_set = false;  // per process; the attribute is per function
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_scan<HAS_LO>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg::kSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -280,21 +271,19 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* 
   const int n_nt = (ep.P + bn - 1) / bn;
   const int tiles = n_mt * n_nt;
   const int grid = tiles < sm_count ? tiles : sm_count;
-  k_tc_scan<HAS_LO><<<grid, kThreads, C::kSmem, st>>>(*a, *alo, *bh, *bl, (int)(K / TBK), n_mt,
-                                                       n_nt, bn, group_m, tflags, spin_ns, ep);
+  k_tc_scan<<<grid, kThreads, Cfg::kSmem, st>>>(*a, *bh, *bl, (int)(K / TBK), n_mt, n_nt, bn,
+                                                group_m, spin_ns, ep);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_tc_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
-                           const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
-                           bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
+cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
+                           const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
                            long long spin_ns, cudaStream_t st, int group_m) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   if (K % TBK || group_m < 1) return cudaErrorInvalidValue;
-  return has_lo ? go<true>(tmAhi, tmAlo, tmBhi, tmBlo, K, tflags, ep, sm_count, group_m, spin_ns, st)
-                : go<false>(tmAhi, tmAhi, tmBhi, tmBlo, K, tflags, ep, sm_count, group_m, spin_ns, st);
+  return go(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st);
 }
 
 cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,

@@ -1,6 +1,6 @@
 // Tensor-core scan on CTA pairs: Eq. 2 of Section 2.2 with tcgen05.mma.cta_group::2.
 //
-// The same product as k_tc.cu, D = A (B_hi + B_lo)^T [+ A_lo B_hi^T], on 256 x 256 tiles
+// The same product as k_tc.cu, D = A (B_hi + B_lo)^T + c (sum_i B), on 256 x 256 tiles
 // computed by a cluster of two CTAs on two SMs. Each CTA loads its own 128 marker rows of A
 // and its own half (128 phenotype rows) of B_hi / B_lo; the pair's leader (cluster rank 0)
 // issues one 256 x 256 x 16 MMA that reads A from both CTAs and B from both CTAs and writes
@@ -30,10 +30,9 @@ using namespace tcx;
 
 constexpr int HB_BYTES = 128 * TBK * 2;  // one CTA's half of a B tile: 8 KB
 
-template <bool HAS_LO>
 struct Cfg2 {
-  static constexpr int kStageBytes = A_BYTES * (HAS_LO ? 2 : 1) + 2 * HB_BYTES;  // 24 or 32 KB
-  static constexpr int kStages = HAS_LO ? 6 : 8;
+  static constexpr int kStageBytes = A_BYTES + 2 * HB_BYTES;  // 24 KB
+  static constexpr int kStages = 8;
   static constexpr int kBarBytes = 256;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;
 };
@@ -118,13 +117,11 @@ __device__ __forceinline__ void tile_coord2(int tile, int n_mp, int n_nt, int gr
   nt = idx / gm;
 }
 
-template <bool HAS_LO>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
-    k_tc2_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
-               const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
-               int num_kb, int n_mt, int n_nt, int group_p, const int* __restrict__ tflags,
-               long long spin_ns, EpiParams ep) {
-  using C = Cfg2<HAS_LO>;
+    k_tc2_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmBhi,
+               const __grid_constant__ CUtensorMap tmBlo, int num_kb, int n_mt, int n_nt,
+               int group_p, long long spin_ns, EpiParams ep) {
+  using C = Cfg2;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -142,7 +139,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   auto sA = [&](int s) { return base + s * C::kStageBytes; };
   auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
   auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + HB_BYTES; };
-  auto sAlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * HB_BYTES; };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
@@ -198,8 +194,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         int mp, nt;
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
         const int mt0 = 2 * mp;
-        const bool lo = HAS_LO && (tflags[mt0] != 0 || (mt0 + 1 < n_mt && tflags[mt0 + 1] != 0));
-        const uint32_t pair_bytes = 2u * (A_BYTES + 2 * HB_BYTES + (lo ? A_BYTES : 0));
+        const uint32_t pair_bytes = 2u * (A_BYTES + 2 * HB_BYTES);
         const int arow = (mt0 + (int)rank) * TBM;
         const int brow = nt * TBN + (int)rank * 128;
         for (int kb = 0; kb < num_kb; ++kb) {
@@ -219,7 +214,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           tma_load_2d_pair(&tmAhi, sA(stage), fb, kb * TBK, arow);
           tma_load_2d_pair(&tmBhi, sBhi(stage), fb, kb * TBK, brow);
           tma_load_2d_pair(&tmBlo, sBlo(stage), fb, kb * TBK, brow);
-          if (lo) tma_load_2d_pair(&tmAlo, sAlo(stage), fb, kb * TBK, arow);
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -239,8 +233,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
         int mp, nt;
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
-        const int mt0 = 2 * mp;
-        const bool lo = HAS_LO && (tflags[mt0] != 0 || (mt0 + 1 < n_mt && tflags[mt0 + 1] != 0));
         for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kChunkKB, ++g) {
           const int acc = (int)(g & 1u);
           const uint32_t ph = (g >> 1) & 1u;
@@ -264,7 +256,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
               const uint64_t bl = sdesc_sw64(sBlo(stage) + 32u * k);
               tc2_mma(d, a, bh, (kb > kb0 || k > 0) ? 1u : 0u);
               tc2_mma(d, a, bl, 1u);
-              if (lo) tc2_mma(d, sdesc_sw64(sAlo(stage) + 32u * k), bh, 1u);
             }
             tc2_commit_both(empty_bar(stage));
             if (++stage == S) {
@@ -320,7 +311,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       const long long row = row_base + lane;
       const bool row_ok = row < ep.M;
       const float rinv = row_ok ? ep.row_inv[row] : __int_as_float(0x7fc00000);
-      epilogue_tile(ep, tot, row, row_base, row_ok, rinv, nt * TBN + half * 128, lane);
+      const float shift = (row_ok && ep.row_shift) ? ep.row_shift[row] : 0.0f;
+      epilogue_tile(ep, tot, row, row_base, row_ok, rinv, shift, nt * TBN + half * 128, lane);
       __syncwarp();
     }
   }
@@ -337,15 +329,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   }
 }
 
-template <bool HAS_LO>
-cudaError_t go2(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap* bh,
-                const CUtensorMap* bl, int64_t K, const int* tflags, const EpiParams& ep,
-                int sm_count, int group_m, long long spin_ns, cudaStream_t st) {
-  using C = Cfg2<HAS_LO>;
+cudaError_t go2(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* bl, int64_t K,
+                const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc2_scan<HAS_LO>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_tc2_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg2::kSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -354,22 +343,19 @@ cudaError_t go2(const CUtensorMap* a, const CUtensorMap* alo, const CUtensorMap*
   const int tiles = ((n_mt + 1) / 2) * n_nt;
   const int pairs = tiles < sm_count / 2 ? tiles : sm_count / 2;
   const int group_p = group_m / 2 > 0 ? group_m / 2 : 1;
-  k_tc2_scan<HAS_LO><<<2 * pairs, kThreads, C::kSmem, st>>>(*a, *alo, *bh, *bl, (int)(K / TBK),
-                                                            n_mt, n_nt, group_p, tflags, spin_ns,
-                                                            ep);
+  k_tc2_scan<<<2 * pairs, kThreads, Cfg2::kSmem, st>>>(*a, *bh, *bl, (int)(K / TBK), n_mt, n_nt,
+                                                      group_p, spin_ns, ep);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_tc2_scan(const CUtensorMap* tmAhi, const CUtensorMap* tmAlo,
-                            const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
-                            bool has_lo, const int* tflags, const EpiParams& ep, int sm_count,
+cudaError_t launch_tc2_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
+                            const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
                             long long spin_ns, cudaStream_t st, int group_m) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   if (K % TBK || group_m < 1) return cudaErrorInvalidValue;
-  return has_lo ? go2<true>(tmAhi, tmAlo, tmBhi, tmBlo, K, tflags, ep, sm_count, group_m, spin_ns, st)
-                : go2<false>(tmAhi, tmAhi, tmBhi, tmBlo, K, tflags, ep, sm_count, group_m, spin_ns, st);
+  return go2(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st);
 }
 
 }  // namespace tg

@@ -159,16 +159,17 @@ __device__ __forceinline__ void tile_coord(int tile, int n_mt, int n_nt, int gro
 
 // Statistics of the 128 totals one thread holds: its marker row against 128 consecutive
 // phenotype columns starting at col0, in groups of 16 columns.
+// D of a column is tot + shift * col_cs[col] (the marker row was shifted by `shift`).
 __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, const float (&tot)[128],
                                               long long row, long long row_base, bool row_ok,
-                                              float rinv, int col0, int lane) {
+                                              float rinv, float shift, int col0, int lane) {
 #pragma unroll
   for (int grp = 0; grp < 8; ++grp) {
     float m[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int col = col0 + grp * 16 + e;
-      const float D = tot[grp * 16 + e];
+      const float D = (col < ep.P) ? fmaf(shift, ep.col_cs[col], tot[grp * 16 + e]) : 0.0f;
       float r = __int_as_float(0x7fc00000);
       if (row_ok && col < ep.P) r = corr_nan(D, rinv, ep.col_rmul[col]);
       m[e] = (r == r) ? fabsf(r) : -1.0f;
@@ -197,7 +198,8 @@ __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, const float (
       const float ce = __shfl_sync(0xffffffffu, cmax, e);
       const int col = col0 + grp * 16 + e;
       float r = __int_as_float(0x7fc00000);
-      if (row_ok && col < ep.P) r = corr_nan(tot[grp * 16 + e], rinv, ep.col_rmul[col]);
+      if (row_ok && col < ep.P)
+        r = corr_nan(fmaf(shift, ep.col_cs[col], tot[grp * 16 + e]), rinv, ep.col_rmul[col]);
       const float a = (r == r) ? fabsf(r) : -1.0f;
       const unsigned b = __ballot_sync(0xffffffffu, ce >= 0.0f && a == ce);
       if (lane == e && b != 0u) {

@@ -26,40 +26,44 @@ def _decode(tgctx, G, N, enc, prec, missing=None):
     lda = synth.round_up(N, 64)
     dev = G.device
     if prec == tg.TG_PREC_SPLIT_BF16:
-        A_hi = torch.full((M, lda), 7.0, dtype=torch.bfloat16, device=dev)
-        A_lo = torch.full((M, lda), 7.0, dtype=torch.bfloat16, device=dev)
+        A = torch.full((M, lda), 7.0, dtype=torch.bfloat16, device=dev)
+        shift = torch.full((M,), 7.0, dtype=torch.float32, device=dev)
     else:
-        A_hi = torch.full((M, lda), 7.0, dtype=torch.float32, device=dev)
-        A_lo = None
+        A = torch.full((M, lda), 7.0, dtype=torch.float32, device=dev)
+        shift = None
     n_obs = torch.zeros(M, dtype=torch.int32, device=dev)
     S = torch.zeros(M, dtype=torch.int64, device=dev)
     S2 = torch.zeros(M, dtype=torch.int64, device=dev)
     mean = torch.zeros(M, dtype=torch.float64, device=dev)
-    tg.tg_decode_block(tgctx, G, N, M, enc, prec, A_hi, A_lo, missing=missing, n_obs=n_obs, S=S,
+    tg.tg_decode_block(tgctx, G, N, M, enc, prec, A, shift, missing=missing, n_obs=n_obs, S=S,
                        S2=S2, mean=mean)
     torch.cuda.synchronize()
-    hi = A_hi.double().cpu().numpy()
-    lo = None if A_lo is None else A_lo.double().cpu().numpy()
-    return hi, lo, n_obs.cpu().numpy(), S.cpu().numpy(), S2.cpu().numpy(), mean.cpu().numpy()
+    a = A.double().cpu().numpy()
+    c = None if shift is None else shift.double().cpu().numpy()
+    return a, c, n_obs.cpu().numpy(), S.cpu().numpy(), S2.cpu().numpy(), mean.cpu().numpy()
 
 
-def _check_operand(hi, lo, units, miss, mean, prec, N):
-    lda = hi.shape[1]
-    assert np.all(hi[:, N:] == 0) and (lo is None or np.all(lo[:, N:] == 0))
+def _check_operand(a, shift, units, miss, mean, prec, N, enc):
+    """FP32: codes, float(mean) at missing calls. Split: the row centred on its shift c (the
+    mean rounded to multiples of 1/128 for 2-bit calls, to integers for dosage bytes, ties to
+    even, 0 without observed calls), exact at observed calls, bf16(mean - c) at missing ones."""
+    assert np.all(a[:, N:] == 0)
     obs = ~miss
-    exp_obs = np.where(obs, units, 0).astype(np.float64)
-    assert np.array_equal(np.where(obs, hi[:, :N], 0), exp_obs)
     m_imp = np.where(np.isnan(mean), 0.0, mean)
     if prec == tg.TG_PREC_SPLIT_BF16:
-        h = bf16_rn(m_imp)
-        l = bf16_rn(m_imp - h)
-        assert np.array_equal(np.where(miss, hi[:, :N], 0), np.where(miss, h[:, None], 0))
-        assert np.array_equal(np.where(miss, lo[:, :N], 0), np.where(miss, l[:, None], 0))
-        assert np.all(np.where(obs, lo[:, :N], 0) == 0)
+        grid = 128.0 if enc == tg.TG_ENC_2BIT else 1.0
+        c = np.where(np.isnan(mean), 0.0, np.rint(m_imp * grid) / grid)
+        assert np.array_equal(shift, c)
+        assert np.all(np.abs(m_imp - c) <= 0.5 / grid)
+        exp_obs = np.where(obs, units - c[:, None], 0)
+        assert np.array_equal(np.where(obs, a[:, :N], 0), exp_obs)
+        h = bf16_rn(m_imp - c)
+        assert np.array_equal(np.where(miss, a[:, :N], 0), np.where(miss, h[:, None], 0))
     else:
+        assert shift is None
+        assert np.array_equal(np.where(obs, a[:, :N], 0), np.where(obs, units, 0).astype(np.float64))
         f = m_imp.astype(np.float32).astype(np.float64)
-        assert np.array_equal(np.where(miss, hi[:, :N], 0), np.where(miss, f[:, None], 0))
-    del lda
+        assert np.array_equal(np.where(miss, a[:, :N], 0), np.where(miss, f[:, None], 0))
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 63, 64, 65, 130, 1999, 23001])
@@ -73,13 +77,13 @@ def test_decode_2bit_bit_exact(tgctx, N, prec):
     counts[1] = 2
     miss[1] = False                     # monomorphic
     G = synth.pack_2bit(counts, miss).cuda()
-    hi, lo, n, S, S2, mean = _decode(tgctx, G, N, tg.TG_ENC_2BIT, prec)
+    a, c, n, S, S2, mean = _decode(tgctx, G, N, tg.TG_ENC_2BIT, prec)
     units, m = oracle.decode_2bit(G.cpu().numpy(), N)
     n0, S0, S20, mean0 = oracle.marker_stats(units, m)
     assert np.array_equal(n, n0) and np.array_equal(S, S0) and np.array_equal(S2, S20)
     assert np.array_equal(np.isnan(mean), np.isnan(mean0))
     assert np.array_equal(mean[~np.isnan(mean)], mean0[~np.isnan(mean0)])   # bit-exact FP64
-    _check_operand(hi, lo, units, m, mean, prec, N)
+    _check_operand(a, c, units, m, mean, prec, N, tg.TG_ENC_2BIT)
 
 
 def test_decode_2bit_every_byte_value(tgctx):
@@ -90,12 +94,12 @@ def test_decode_2bit_every_byte_value(tgctx):
     G[1, :256] = row[::-1]
     G[2, :256] = np.roll(row, 77)
     Gt = torch.from_numpy(G).cuda()
-    hi, lo, n, S, S2, mean = _decode(tgctx, Gt, N, tg.TG_ENC_2BIT, tg.TG_PREC_SPLIT_BF16)
+    a, c, n, S, S2, mean = _decode(tgctx, Gt, N, tg.TG_ENC_2BIT, tg.TG_PREC_SPLIT_BF16)
     units, m = oracle.decode_2bit(G, N)
     n0, S0, S20, mean0 = oracle.marker_stats(units, m)
     assert np.array_equal(n, n0) and np.array_equal(S, S0) and np.array_equal(S2, S20)
     assert np.array_equal(mean, mean0)
-    _check_operand(hi, lo, units, m, mean, tg.TG_PREC_SPLIT_BF16, N)
+    _check_operand(a, c, units, m, mean, tg.TG_PREC_SPLIT_BF16, N, tg.TG_ENC_2BIT)
 
 
 @pytest.mark.parametrize("N", [1, 15, 16, 17, 33, 2000, 23000])
@@ -109,13 +113,13 @@ def test_decode_u8_bit_exact(tgctx, N, masked, prec):
     missing = synth.missing_words(5, N, M, N, 0.2).cuda() if masked else None
     if masked:
         missing[0] = -1                 # every call missing
-    hi, lo, n, S, S2, mean = _decode(tgctx, G, N, tg.TG_ENC_U8_DOSAGE, prec, missing)
+    a, c, n, S, S2, mean = _decode(tgctx, G, N, tg.TG_ENC_U8_DOSAGE, prec, missing)
     units, m = oracle.decode_u8(G.cpu().numpy(), N, None if missing is None else missing.cpu().numpy())
     n0, S0, S20, mean0 = oracle.marker_stats(units, m)
     assert np.array_equal(n, n0) and np.array_equal(S, S0) and np.array_equal(S2, S20)
     ok = ~np.isnan(mean0)
     assert np.array_equal(np.isnan(mean), ~ok) and np.array_equal(mean[ok], mean0[ok])
-    _check_operand(hi, lo, units, m, mean, prec, N)
+    _check_operand(a, c, units, m, mean, prec, N, tg.TG_ENC_U8_DOSAGE)
     del g
 
 
