@@ -15,6 +15,13 @@
 // 2-bit fields follow the PLINK 1 .bed table: 00 -> 2, 10 -> 1, 11 -> 0, 01 -> missing.
 // With lo = w & 0x55.. and hi = (w >> 1) & 0x55.. per 32-bit word: count 2 = ~lo & ~hi,
 // count 1 = hi & ~lo, count 0 = lo & hi, missing = lo & ~hi.
+//
+// The split writer takes 16 samples per lane and step (one packed word of 2-bit fields, or
+// 16 dosage bytes) and stores 32 bytes:
+//   2-bit: the row's four possible bf16 values, indexed by the raw field, sit in two words;
+//     one byte permute per pair of fields picks both values.
+//   dosage: a byte permute builds the float 2^23 + b, and subtracting 2^23 + c leaves b - c
+//     exactly; pairs are rounded to bf16x2 in one conversion.
 #include <cuda_bf16.h>
 
 #include "device.cuh"
@@ -63,18 +70,31 @@ __device__ __forceinline__ void row_stats(const uint8_t* __restrict__ row, int N
     for (int c = lane; c < nchunk; c += 32) {
       const uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + c);
       const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-      uint32_t mbits = 0;
-      if (mrow) mbits = (mrow[(c * 16) >> 5] >> ((c * 16) & 31)) & 0xFFFFu;
+      uint32_t skip = 0;  // bit k: byte k of the chunk is missing or past N
+      if (mrow) skip = (mrow[(c * 16) >> 5] >> ((c * 16) & 31)) & 0xFFFFu;
+      const int left = N - c * 16;
+      if (left < 16) skip |= 0xFFFFu << left;
+      if (skip == 0) {  // 16 observed bytes: sums of bytes and of their squares by dp4a
+        uint32_t s1 = 0, s2 = 0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 4; ++q) {
+          s1 = __dp4a(w4[q], 0x01010101u, s1);
+          s2 = __dp4a(w4[q], w4[q], s2);
+        }
+        n += 16;
+        S += s1;
+        S2 += s2;
+      } else {
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int i = c * 16 + q * 4 + b;
-          const uint32_t u = (w4[q] >> (8 * b)) & 0xFFu;
-          if (i < N && !((mbits >> (q * 4 + b)) & 1u)) {
-            n += 1;
-            S += u;
-            S2 += u * u;
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const uint32_t u = (w4[q] >> (8 * b)) & 0xFFu;
+            if (!((skip >> (q * 4 + b)) & 1u)) {
+              n += 1;
+              S += u;
+              S2 += u * u;
+            }
           }
         }
       }
@@ -111,6 +131,47 @@ __device__ __forceinline__ void load8(const uint8_t* __restrict__ row, const uin
   for (int s = 0; s < 8; ++s)
     if (i0 + s >= N) v[s] = 0.0f;
   if (i0 + 8 > N) miss &= (N > i0) ? ((1u << (N - i0)) - 1u) : 0u;
+}
+
+// 16 split-form values of 2-bit fields w (sample 16t + k in bits 2k..2k+1): eight bf16x2
+// words. lut0 = {field 00, field 01} and lut1 = {field 10, field 11} as bf16 pairs; the
+// permute selector for fields (f, g) is 0x1010 + 0x22 f + 0x2200 g (bytes 2f, 2f+1, 2g, 2g+1).
+__device__ __forceinline__ void split16_2bit(uint32_t w, uint32_t lut0, uint32_t lut1,
+                                             uint32_t (&o)[8]) {
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const uint32_t f = (w >> (4 * p)) & 3u, g = (w >> (4 * p + 2)) & 3u;
+    o[p] = __byte_perm(lut0, lut1, 0x1010u + 0x22u * f + 0x2200u * g);
+  }
+}
+
+// 16 split-form values of dosage bytes v: b - c exactly, bf16x2 words; bits of `miss` take
+// the missing value mh (a bf16 in the low half of mh2 and in the high half).
+__device__ __forceinline__ void split16_u8(uint4 v, float c_plus, uint32_t miss, uint32_t mh2,
+                                           uint32_t (&o)[8]) {
+  const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const uint32_t w = w4[p >> 1];
+    const uint32_t k = (uint32_t)(p & 1) * 2u;
+    const float a = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + k)) - c_plus;
+    const float b = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7441u + k)) - c_plus;
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    uint32_t r = *reinterpret_cast<uint32_t*>(&h);
+    const uint32_t m = (miss >> (2 * p)) & 3u;
+    if (m) r = __byte_perm(r, mh2, (m & 1u ? 0x0054u : 0x0010u) | (m & 2u ? 0x7600u : 0x3200u));
+    o[p] = r;
+  }
+}
+
+// Zero the values of samples >= N in a 16-sample group starting at i0 (i0 < N < i0 + 16).
+__device__ __forceinline__ void zero_tail16(uint32_t (&o)[8], int i0, int N) {
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const int i = i0 + 2 * p;
+    if (i >= N) o[p] = 0u;
+    else if (i + 1 >= N) o[p] &= 0xFFFFu;
+  }
 }
 
 // Shift of a marker row for the split form (see above); 0 when no call is observed.
@@ -154,26 +215,41 @@ __global__ void __launch_bounds__(kWarps * 32) k_decode(
     if (lane == 0 && shift_out) shift_out[j] = (float)c;
     const float cf = (float)c;  // exact: a multiple of 2^-7 in [0, 2] or an integer in [0, 255]
     const __nv_bfloat16 mh = __double2bfloat16(m_imp - c);
-    __nv_bfloat16* ah = reinterpret_cast<__nv_bfloat16*>(Ahi) + j * lda;
-#pragma unroll 4
-    for (long long t = lane; t < steps; t += 32) {
-      const int i0 = (int)(t << 3);
-      float v[8];
-      uint32_t ms = 0;
-      __align__(16) __nv_bfloat16 hv[8];
-      if (i0 < N) {
-        load8<ENC>(row, mrow, i0, N, v, ms);
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const bool m = (ms >> s) & 1u;
-          // v - c is exact in FP32 and in bf16; samples past N stay 0
-          hv[s] = m ? mh : __float2bfloat16_rn(i0 + s < N ? v[s] - cf : 0.0f);
+    const uint32_t mhu = (uint32_t)__bfloat16_as_ushort(mh);
+    uint4* ah = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(Ahi) + j * lda);
+    const long long groups = lda >> 4;  // 16 samples each
+    if (ENC == TG_ENC_2BIT) {
+      auto bits = [](float x) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)); };
+      const uint32_t lut0 = bits(2.0f - cf) | (mhu << 16);
+      const uint32_t lut1 = bits(1.0f - cf) | (bits(-cf) << 16);
+      const uint32_t* wrow = reinterpret_cast<const uint32_t*>(row);
+#pragma unroll 2
+      for (long long t = lane; t < groups; t += 32) {
+        const int i0 = (int)(t << 4);
+        uint32_t o[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (i0 < N) {
+          split16_2bit(__ldg(wrow + t), lut0, lut1, o);
+          if (i0 + 16 > N) zero_tail16(o, i0, N);
         }
-      } else {
-#pragma unroll
-        for (int s = 0; s < 8; ++s) hv[s] = __float2bfloat16_rn(0.0f);
+        ah[2 * t] = make_uint4(o[0], o[1], o[2], o[3]);
+        ah[2 * t + 1] = make_uint4(o[4], o[5], o[6], o[7]);
       }
-      *reinterpret_cast<uint4*>(ah + i0) = *reinterpret_cast<const uint4*>(hv);
+    } else {
+      const float c_plus = 8388608.0f + cf;  // 2^23 + c, exact
+      const uint32_t mh2 = mhu | (mhu << 16);
+      const uint4* vrow = reinterpret_cast<const uint4*>(row);
+#pragma unroll 2
+      for (long long t = lane; t < groups; t += 32) {
+        const int i0 = (int)(t << 4);
+        uint32_t o[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (i0 < N) {
+          const uint32_t ms = mrow ? (mrow[i0 >> 5] >> (i0 & 31)) & 0xFFFFu : 0u;
+          split16_u8(__ldg(vrow + t), c_plus, ms, mh2, o);
+          if (i0 + 16 > N) zero_tail16(o, i0, N);
+        }
+        ah[2 * t] = make_uint4(o[0], o[1], o[2], o[3]);
+        ah[2 * t + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+      }
     }
   } else {
     const float mf = (float)m_imp;
@@ -198,10 +274,169 @@ __global__ void __launch_bounds__(kWarps * 32) k_decode(
   }
 }
 
+// Split form for rows of up to kRowThreads * GPT * 16 samples: one block per marker row, the
+// packed row held in registers between the two passes (one read of the row from HBM, every
+// load of a thread in flight at once). Used for dosage rows, where the warp-per-row kernel's
+// second read of a 23 KB row misses L2 under load.
+constexpr int kRowThreads = 256;
+
+template <int ENC, int GPT>
+__global__ void __launch_bounds__(kRowThreads, GPT <= 6 ? 4 : 2) k_decode_rows(
+    const uint8_t* __restrict__ G, long long ldg, int N, const uint32_t* __restrict__ miss,
+    long long ldm, __nv_bfloat16* __restrict__ A, float* __restrict__ shift_out, long long lda,
+    int32_t* __restrict__ nobs_out, long long* __restrict__ S_out, long long* __restrict__ S2_out,
+    double* __restrict__ mean_out, double* __restrict__ gc2_out) {
+  __shared__ unsigned long long red[3][kRowThreads / 32];
+  __shared__ float s_c;
+  __shared__ uint32_t s_mh;
+  const long long j = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint8_t* row = G + j * ldg;
+  const uint32_t* mrow = miss ? miss + j * ldm : nullptr;
+  const int nvalid = (N + 15) >> 4;  // 16-sample groups holding a sample < N
+  // pass 1: load this thread's groups, count n, S, S2
+  uint32_t w[GPT];  // 2-bit: one word of 16 fields per group
+  uint4 v[GPT];     // dosage: 16 bytes per group
+  uint32_t ms[GPT]; // dosage: missing bits of the group
+  uint32_t n = 0, S = 0, S2 = 0;
+#pragma unroll
+  for (int g = 0; g < GPT; ++g) {
+    const int t = tid + g * kRowThreads;
+    if (ENC == TG_ENC_2BIT) {
+      w[g] = t < nvalid ? __ldg(reinterpret_cast<const uint32_t*>(row) + t) : 0u;
+    } else {
+      v[g] = t < nvalid ? __ldg(reinterpret_cast<const uint4*>(row) + t) : make_uint4(0, 0, 0, 0);
+      ms[g] = (t < nvalid && mrow) ? (mrow[t >> 1] >> ((t & 1) * 16)) & 0xFFFFu : 0u;
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < GPT; ++g) {
+    const int t = tid + g * kRowThreads;
+    if (t >= nvalid) continue;
+    const int left = N - t * 16;  // >= 1
+    if (ENC == TG_ENC_2BIT) {
+      const uint32_t valid = left >= 16 ? 0x55555555u : (0x55555555u & ((1u << (2 * left)) - 1u));
+      const uint32_t lo = w[g] & 0x55555555u, hi = (w[g] >> 1) & 0x55555555u;
+      const uint32_t two = ~lo & ~hi & valid, one = hi & ~lo & valid, zero = lo & hi & valid;
+      const uint32_t c2 = __popc(two), c1 = __popc(one);
+      n += c2 + c1 + __popc(zero);
+      S += 2 * c2 + c1;
+      S2 += 4 * c2 + c1;
+    } else {
+      uint32_t skip = ms[g];
+      if (left < 16) skip |= 0xFFFFu << left;
+      const uint32_t w4[4] = {v[g].x, v[g].y, v[g].z, v[g].w};
+      if (skip == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          S = __dp4a(w4[q], 0x01010101u, S);
+          S2 = __dp4a(w4[q], w4[q], S2);
+        }
+        n += 16;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const uint32_t u = (w4[q] >> (8 * b)) & 0xFFu;
+            if (!((skip >> (q * 4 + b)) & 1u)) {
+              n += 1;
+              S += u;
+              S2 += u * u;
+            }
+          }
+      }
+    }
+  }
+  unsigned long long n64 = n, S64 = S, S264 = S2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n64 += __shfl_xor_sync(0xffffffffu, n64, o);
+    S64 += __shfl_xor_sync(0xffffffffu, S64, o);
+    S264 += __shfl_xor_sync(0xffffffffu, S264, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = n64;
+    red[1][warp] = S64;
+    red[2][warp] = S264;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long tn = 0, tS = 0, tS2 = 0;
+#pragma unroll
+    for (int k = 0; k < kRowThreads / 32; ++k) {
+      tn += red[0][k];
+      tS += red[1][k];
+      tS2 += red[2][k];
+    }
+    const double dn = (double)tn;
+    const double mean = tn ? (double)tS / dn : __longlong_as_double(0x7ff8000000000000ll);
+    if (nobs_out) nobs_out[j] = (int32_t)tn;
+    if (S_out) S_out[j] = (long long)tS;
+    if (S2_out) S2_out[j] = (long long)tS2;
+    if (mean_out) mean_out[j] = mean;
+    if (gc2_out) {
+      const long long num = (long long)tS2 * (long long)tn - (long long)tS * (long long)tS;
+      gc2_out[j] = tn ? (double)num / dn : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    const double c = row_shift<ENC>(tn, mean);
+    if (shift_out) shift_out[j] = (float)c;
+    s_c = (float)c;
+    s_mh = (uint32_t)__bfloat16_as_ushort(__double2bfloat16((tn ? mean : 0.0) - c));
+  }
+  __syncthreads();
+  // pass 2: the operand row from registers, zeros past N
+  const float cf = s_c;
+  const uint32_t mhu = s_mh;
+  uint4* ah = reinterpret_cast<uint4*>(A + j * lda);
+  auto bits = [](float x) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)); };
+  const uint32_t lut0 = bits(2.0f - cf) | (mhu << 16);
+  const uint32_t lut1 = bits(1.0f - cf) | (bits(-cf) << 16);
+  const float c_plus = 8388608.0f + cf;
+  const uint32_t mh2 = mhu | (mhu << 16);
+#pragma unroll
+  for (int g = 0; g < GPT; ++g) {
+    const int t = tid + g * kRowThreads;
+    if (t >= nvalid) break;
+    uint32_t o[8];
+    if (ENC == TG_ENC_2BIT)
+      split16_2bit(w[g], lut0, lut1, o);
+    else
+      split16_u8(v[g], c_plus, ms[g], mh2, o);
+    if (t * 16 + 16 > N) zero_tail16(o, t * 16, N);
+    ah[2 * t] = make_uint4(o[0], o[1], o[2], o[3]);
+    ah[2 * t + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+  }
+  const long long groups = lda >> 4;
+  for (long long t = nvalid + tid; t < groups; t += kRowThreads) {
+    ah[2 * t] = make_uint4(0, 0, 0, 0);
+    ah[2 * t + 1] = make_uint4(0, 0, 0, 0);
+  }
+}
+
 template <int ENC, int PREC>
 cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32_t* missing,
                int64_t ldm, void* Ahi, float* shift, int64_t lda, int32_t* nobs, int64_t* S,
                int64_t* S2, double* mean, double* gc2, cudaStream_t st) {
+  // dosage rows (N bytes) take the block-per-row kernel; 2-bit rows are small enough that
+  // the warp-per-row kernel's second read hits in L2, and it measured faster for them
+  if constexpr (ENC == TG_ENC_U8_DOSAGE && PREC == TG_PREC_SPLIT_BF16) {
+    __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(Ahi);
+    long long* S64 = reinterpret_cast<long long*>(S);
+    long long* S264 = reinterpret_cast<long long*>(S2);
+    if (N <= kRowThreads * 6 * 16) {
+      k_decode_rows<ENC, 6><<<(unsigned)M, kRowThreads, 0, st>>>(G, ldg, (int)N, missing, ldm, A,
+                                                                 shift, lda, nobs, S64, S264,
+                                                                 mean, gc2);
+      return cudaGetLastError();
+    }
+    if (N <= kRowThreads * 12 * 16) {
+      k_decode_rows<ENC, 12><<<(unsigned)M, kRowThreads, 0, st>>>(G, ldg, (int)N, missing, ldm, A,
+                                                                  shift, lda, nobs, S64, S264,
+                                                                  mean, gc2);
+      return cudaGetLastError();
+    }
+  }
   const unsigned grid = (unsigned)((M + kWarps - 1) / kWarps);
   k_decode<ENC, PREC><<<grid, kWarps * 32, 0, st>>>(
       G, ldg, (int)N, M, missing, ldm, Ahi, shift, lda, nobs, reinterpret_cast<long long*>(S),

@@ -66,7 +66,7 @@ def _check_operand(a, shift, units, miss, mean, prec, N, enc):
         assert np.array_equal(np.where(miss, a[:, :N], 0), np.where(miss, f[:, None], 0))
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 63, 64, 65, 130, 1999, 23001])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 63, 64, 65, 130, 1999, 23001, 24576, 24577, 49153])
 @pytest.mark.parametrize("prec", [tg.TG_PREC_SPLIT_BF16, tg.TG_PREC_FP32])
 def test_decode_2bit_bit_exact(tgctx, N, prec):
     g = torch.Generator().manual_seed(N)
@@ -102,7 +102,9 @@ def test_decode_2bit_every_byte_value(tgctx):
     _check_operand(a, c, units, m, mean, tg.TG_PREC_SPLIT_BF16, N, tg.TG_ENC_2BIT)
 
 
-@pytest.mark.parametrize("N", [1, 15, 16, 17, 33, 2000, 23000])
+# dosage rows of N <= 24,576 and <= 49,152 take the block-per-row kernel, larger N the
+# warp-per-row kernel
+@pytest.mark.parametrize("N", [1, 15, 16, 17, 33, 2000, 23000, 24576, 24577, 49152, 49153])
 @pytest.mark.parametrize("masked", [False, True])
 @pytest.mark.parametrize("prec", [tg.TG_PREC_SPLIT_BF16, tg.TG_PREC_FP32])
 def test_decode_u8_bit_exact(tgctx, N, masked, prec):
