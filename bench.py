@@ -367,7 +367,7 @@ def _ours(args, dist, rank, ws):
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": _traffic(),
-                "kernel": "k_tc_scan (tcgen05 split-BF16 + fused epilogue)",
+                "kernel": "k_tc2_scan (tcgen05 cta_group::2 split-BF16 + fused epilogue)",
                 "issued_tflops": 2 * achieved, "peak_source": f"{peak_src} bf16 sustained",
                 "kernel_ms": gemm_ms,
                 "stage_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in stages.items()}}
@@ -532,16 +532,22 @@ def _ours_batched(args, dist, rank, ws):
 
 
 def _traffic():
-    """DRAM bytes per launch of the scan kernel from a committed ncu summary, if one exists
-    for the current kernel source."""
+    """DRAM bytes per launch of the contraction kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "tc_scan_traffic.json")
-    src = os.path.join(ROOT, "paper_2604_21095_gb300", "csrc", "k_tc.cu")
+    path = os.path.join(ROOT, "profiles", "tc2_scan_traffic_n23000_p20480_u8.md")
+    csrc = os.path.join(ROOT, "paper_2604_21095_gb300", "csrc")
     try:
-        with open(path) as f:
-            rec = json.load(f)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        return rec["bytes_per_launch"] if rec.get("k_tc_sha256") == h else None
+        h = hashlib.sha256(b"".join(open(os.path.join(csrc, f), "rb").read()
+                                    for f in ("k_tc2.cu", "tc_common.cuh"))).hexdigest()
+        rec = {}
+        for line in open(path):
+            if ":" in line and not line.startswith(("|", "#", " ")):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        if rec.get("source_sha256") != h:
+            return None
+        return int(rec["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
 

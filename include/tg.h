@@ -205,9 +205,12 @@ tg_status tg_scan_block_static(const tg_panel* panel, const uint8_t* G, int64_t 
                                const tg_outputs* out, void* stream);
 
 /* The scan of a whole genotype matrix held in HOST memory (pinned for overlap): blocks of
- * block_markers rows are copied to the device on the context's side stream, double
+ * at most block_markers rows are copied to the device on the context's side stream, double
  * buffered, while the previous block is scanned on `stream`; hits, their count and the
  * per-phenotype best keys are copied back to host memory at the end. Synchronous.
+ *   Blocking: when block_markers >= 2048 the first block has round_up(block_markers / 8, 256)
+ *   rows and each next block twice as many, up to block_markers, so that only a short first
+ *   copy is not hidden behind a scan. Results do not depend on the blocking.
  *   G_host: host uint8 [M][ldg]; hits_host: host [hit_capacity]; n_hits: host, total hit
  *   count (may exceed hit_capacity, then TG_ERR_CAPACITY); best_host: host [P] or NULL.
  * Only hit collection is supported here (opts->full_output must be 0). */

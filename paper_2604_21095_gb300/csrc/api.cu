@@ -614,10 +614,15 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
   o.hit_capacity = hit_capacity;
   o.n_hits = c->dnhits;
   o.best = best_host ? c->dbest : nullptr;
+  // Block sizes ramp up from about block_markers / 8, doubling, so that only a short first
+  // copy runs before the first scan; every later copy hides behind the previous block's scan.
+  int64_t next = block_markers;
+  if (block_markers >= 8 * 256) next = round_up(block_markers / 8, 256);
   // the first waits on ev_free find no recorded work and pass
-  for (int64_t m0 = 0, b = 0; m0 < M; m0 += block_markers, ++b) {
+  for (int64_t m0 = 0, b = 0, rows = 0; m0 < M; m0 += rows, ++b) {
     const int buf = (int)(b & 1);
-    const int64_t rows = std::min<int64_t>(block_markers, M - m0);
+    rows = std::min<int64_t>(next, M - m0);
+    next = std::min<int64_t>(block_markers, 2 * next);
     TG_CUDA(cudaStreamWaitEvent(c->side, c->ev_free[buf], 0));
     {
       StageScope s(c, STAGE_H2D, c->side, 0);

@@ -10,7 +10,8 @@ import torch
 import oracle
 import paper_2604_21095_gb300 as tg
 import synth
-from scan_util import compare_best, compare_full, compare_hits, oracle_panel, run_scan
+from scan_util import (HIT_DTYPE, compare_best, compare_full, compare_hits, enc_id, oracle_panel,
+                       run_scan)
 
 pytestmark = pytest.mark.gpu
 
@@ -179,3 +180,30 @@ def test_blocks_accumulate_hits_and_best(tgctx, panels):
     assert key(whole["hits"]) == sorted(key(a["hits"]) + key(b["hits"]))
     best = np.maximum(a["best_key"], b["best_key"])
     assert np.array_equal(best, whole["best_key"])
+
+
+@pytest.mark.parametrize("encoding,block", [("2bit", 2048), ("u8", 1000), ("2bit", 100_000)])
+def test_host_streamed_scan_matches_oracle(tgctx, panels, encoding, block):
+    """tg_scan_host from pinned host memory: blocks ramp up from block/8 (256, 512, 1024, 2048
+    ... for block = 2048) and the hits and best markers equal the oracle's."""
+    w, pan, blk, _ = _case(encoding, M=3000, P=300)
+    panel = _panel(tgctx, panels, ("host", encoding), pan, w.N, w.P)
+    G_host = blk["G"].pin_memory()
+    cap = 1 << 14
+    hits_h = torch.zeros(cap * HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    best_h = torch.zeros(w.P, dtype=torch.int64).pin_memory()
+    opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, THR)
+    nh = tg.tg_scan_host(tgctx, panel, G_host, w.N, w.M, enc_id(encoding), block, opts, hits_h,
+                         best_h, marker_offset=11)
+    assert 0 < nh <= cap
+    b = best_h.numpy().view(np.uint64)
+    res = {"n_hits": nh,
+           "hits": np.frombuffer(hits_h.numpy().tobytes(), dtype=HIT_DTYPE)[:nh],
+           "best_key": b,
+           "best_marker": np.where(b == 0, -1, (0xFFFFFFFF - (b & 0xFFFFFFFF)).astype(np.int64)),
+           "best_absr": np.frombuffer(((b >> 32).astype(np.uint32)).tobytes(), dtype=np.float32)}
+    ref = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]),
+                      mode="projected")
+    want, got = compare_hits(res, ref, THR, marker_offset=11)
+    assert want > 0 and got > 0
+    compare_best(res, ref, marker_offset=11)
