@@ -11,6 +11,11 @@ convert), with the genotype projected on Q as well (Frisch-Waugh-Lovell).
 
 Reading: degrees of freedom df = N - q - 1 (q = rank [1, C]); with an intercept
 only, q = 1 and df = N - 2 as in Eq. 3.
+
+`ols_paper` is the statistic exactly as Section 2.2 prints it: the marker is only centred
+and standardised (not projected on Q), r is its correlation with the residualised panel,
+and Eq. 3 uses N - 2 degrees of freedom whatever the covariates. It equals the OLS test
+when the covariates are an intercept only.
 """
 from __future__ import annotations
 
@@ -85,3 +90,34 @@ def ols_projected(Q: np.ndarray, g: np.ndarray, Yres: np.ndarray):
     for a in (r, beta, se, t):
         a[bad] = np.nan
     return r, beta, se, t, df, np.where(bad, np.nan, gres2)
+
+
+def ols_paper(g: np.ndarray, Yres: np.ndarray):
+    """Eq. 2 and Eq. 3 as printed in Section 2.2 (the genotype is not projected on Q).
+
+    g: [M][N] imputed genotypes; Yres: [N][P] residualised panel (Eq. 1).
+    r = g_c . y_res / (|g_c| |y_res|) with g_c = g - mean(g) (the standardised marker),
+    t = r sqrt((N - 2) / (1 - r^2)) (Eq. 3), df = N - 2.
+    Reading (the paper reports no effect size): beta = g_c . y_res / |g_c|^2, the slope of
+    the residualised phenotype on the centred marker, and se = |beta / t|.
+    A marker with no observed call or a constant one is untestable (NaN).
+    Returns (r, beta, se, t, df, gc2 [M] = |g_c|^2).
+    """
+    g = np.atleast_2d(np.asarray(g, dtype=np.float64))
+    Yres = np.asarray(Yres, dtype=np.float64)
+    N = g.shape[1]
+    df = N - 2
+    gc = g - g.mean(axis=1, keepdims=True)
+    gc2 = (gc * gc).sum(axis=1)
+    bad = ~(gc2 > 0.0)
+    ynorm = np.linalg.norm(Yres, axis=0)
+    num = gc @ Yres
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r = num / np.sqrt(gc2)[:, None] / ynorm[None, :]
+        r = np.clip(r, -1.0, 1.0)
+        t = r * np.sqrt(df / ((1.0 - r) * (1.0 + r)))
+        beta = num / gc2[:, None]
+        se = ynorm[None, :] * np.sqrt((1.0 - r) * (1.0 + r) / df) / np.sqrt(gc2)[:, None]
+    for a in (r, beta, se, t):
+        a[bad] = np.nan
+    return r, beta, se, t, df, np.where(bad, np.nan, gc2)

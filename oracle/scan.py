@@ -17,7 +17,7 @@ from __future__ import annotations
 import numpy as np
 
 from .decode import DOSAGE_SCALE, decode_2bit, decode_u8, impute, marker_stats
-from .ols import ols_direct, ols_projected
+from .ols import ols_direct, ols_paper, ols_projected
 from .panel import design_matrix, householder_basis, residualise
 from .pvalue import mlog10p_from_r, mlog10p_from_t
 
@@ -54,8 +54,11 @@ def decode(G: np.ndarray, encoding: str, N: int, missing_words=None) -> dict:
 def scan(G: np.ndarray, encoding: str, panel: dict, missing_words=None, mode: str = "projected") -> dict:
     """Statistics of every (marker, phenotype) pair of one genotype block.
 
-    Returns beta, se, t, mlog10p ([M][P]; r too in projected mode), df, the decode
-    record and gres2 (|g_res|^2 per marker, allele units, projected mode).
+    Modes: "direct" (OLS of y on [1, C, g], the definition), "projected" (Eq. 1-3 with the
+    marker projected on Q as well; the same numbers) and "paper" (Eq. 2-3 exactly as
+    printed: the marker only standardised, df = N - 2).
+    Returns beta, se, t, mlog10p ([M][P]; r too in projected and paper mode), df, the decode
+    record and gres2 (|g_res|^2 per marker in allele units; |g_c|^2 in paper mode).
     """
     dec = decode(G, encoding, panel["N"], missing_words)
     g = dec["g"]
@@ -70,6 +73,13 @@ def scan(G: np.ndarray, encoding: str, panel: dict, missing_words=None, mode: st
         r[:, ~ok] = np.nan
         out["r"] = r
         out["gres2"] = gres2
+    elif mode == "paper":
+        r, beta, se, t, df, gc2 = ols_paper(g, panel["Yres"])
+        mlp = mlog10p_from_r(r, df)
+        r[:, ~ok] = np.nan
+        out["r"] = r
+        out["gres2"] = gc2
+        out["df"] = df
     else:
         raise ValueError(mode)
     for a in (beta, se, t, mlp):

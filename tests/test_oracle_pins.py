@@ -215,6 +215,74 @@ def test_intercept_only_is_pearson_and_eq3():
             assert abs(t[j, p] - pear * math.sqrt((N - 2) / (1 - pear ** 2))) < 1e-9
 
 
+# ---------------------------------------------------------------- the paper's printed form
+
+def test_paper_form_is_pearson_with_residualised_phenotype():
+    """Eq. 2-3 as printed: r is the Pearson correlation of the raw marker with the
+    residualised phenotype (numpy.corrcoef), and the two-sided p-value is the one of a
+    correlation test with N - 2 degrees of freedom (scipy.stats.pearsonr), with covariates."""
+    stats = pytest.importorskip("scipy.stats")
+    C, X, g, Y = _tiny_case(51, N=60, n_cov=3, M=6, P=3)
+    Q, _ = oracle.householder_basis(X)
+    Yres, _, _ = oracle.residualise(Y, Q)
+    rr, beta, se, t, df, gc2 = oracle.ols_paper(g, Yres)
+    N = X.shape[0]
+    assert df == N - 2
+    mlp = oracle.mlog10p_from_r(rr, df)
+    for j in range(g.shape[0]):
+        assert abs(gc2[j] - ((g[j] - g[j].mean()) ** 2).sum()) <= 1e-12 * gc2[j]
+        for p in range(Y.shape[1]):
+            pear = np.corrcoef(g[j], Yres[:, p])[0, 1]
+            assert abs(rr[j, p] - pear) < 1e-12
+            ref = stats.pearsonr(g[j], Yres[:, p])
+            assert abs(mlp[j, p] + math.log10(ref.pvalue)) < 1e-9 * max(1.0, mlp[j, p])
+            # slope of the residualised phenotype on the centred marker (numpy.polyfit)
+            slope = np.polyfit(g[j] - g[j].mean(), Yres[:, p], 1)[0]
+            assert abs(beta[j, p] - slope) < 1e-10 * max(1.0, abs(slope))
+            assert abs(se[j, p] - abs(beta[j, p] / t[j, p])) < 1e-10 * se[j, p]
+
+
+def test_paper_form_equals_ols_with_intercept_only_and_differs_with_covariates():
+    """With an intercept only the printed form is the OLS test (q = 1, g_res = g_c); with
+    covariates it differs by the factor |g_res| / |g_c| in r and by df."""
+    C, X, g, Y = _tiny_case(52, N=50, n_cov=0, M=5, P=2)
+    Q, _ = oracle.householder_basis(X)
+    Yres, _, _ = oracle.residualise(Y, Q)
+    a = oracle.ols_paper(g, Yres)
+    b = oracle.ols_projected(Q, g, Yres)
+    assert a[4] == b[4] == X.shape[0] - 2
+    for x, y in zip(a[:4], b[:4]):
+        assert np.allclose(x, y, rtol=1e-12, atol=1e-14)
+    C, X, g, Y = _tiny_case(53, N=50, n_cov=3, M=5, P=2)
+    Q, _ = oracle.householder_basis(X)
+    Yres, _, _ = oracle.residualise(Y, Q)
+    rp, *_, dfp, gc2 = oracle.ols_paper(g, Yres)
+    rq, *_, dfq, gres2 = oracle.ols_projected(Q, g, Yres)
+    assert dfp == X.shape[0] - 2 and dfq == X.shape[0] - X.shape[1] - 1 == 45
+    assert np.allclose(rp, rq * np.sqrt(gres2 / gc2)[:, None], rtol=1e-12)
+
+
+def test_paper_form_scan_and_untestable_markers():
+    r = _rng(54)
+    N = 40
+    C = r.standard_normal((N, 2))
+    Y = r.standard_normal((N, 3))
+    panel = oracle.prepare_panel(Y, C)
+    counts = r.integers(0, 3, size=(3, N)).astype(np.int8)
+    counts[0] = 1                                     # constant: untestable
+    miss = np.zeros((3, N), dtype=bool)
+    miss[2, :5] = True
+    G = synth.pack_2bit(torch.from_numpy(counts), torch.from_numpy(miss)).numpy()
+    out = oracle.scan(G, "2bit", panel, mode="paper")
+    assert out["df"] == N - 2
+    assert np.all(np.isnan(out["r"][0])) and np.all(np.isnan(out["mlog10p"][0]))
+    assert np.all(np.isfinite(out["r"][1:]))
+    g = out["decode"]["g"]
+    for j in (1, 2):
+        for p in range(3):
+            assert abs(out["r"][j, p] - np.corrcoef(g[j], panel["Yres"][:, p])[0, 1]) < 1e-12
+
+
 def test_exact_fit_gives_unit_r_and_infinite_score():
     r = _rng(41)
     N = 40
