@@ -31,7 +31,7 @@
 extern "C" {
 #endif
 
-#define TG_ABI_VERSION 1
+#define TG_ABI_VERSION 2
 
 typedef struct tg_ctx tg_ctx;
 typedef struct tg_panel tg_panel;
@@ -60,11 +60,23 @@ typedef enum {
   TG_ENC_U8_DOSAGE = 1 /* one byte b per sample, allele-1 dosage 2b/255 */
 } tg_encoding;
 
+/* Which statistic the scan computes (Section 2.2). */
+typedef enum {
+  TG_MODE_PROJECTED = 0, /* the OLS test of y on [1, C, g]: the marker is projected on Q as well,
+                            r = g_res.y_res / (|g_res| |y_res|), df = N - q - 1 */
+  TG_MODE_PAPER = 1      /* Eq. 2-3 as printed: the marker is only centred and standardised,
+                            r = g_c.y_res / (|g_c| |y_res|), df = N - 2 whatever the covariates
+                            (identical to TG_MODE_PROJECTED when the covariates are an intercept
+                            only); beta = g_c.y_res / |g_c|^2, se = |beta / t| */
+} tg_mode;
+
 /* Per-call scan options. */
 typedef struct {
   int32_t precision;   /* tg_precision */
   int32_t full_output; /* nonzero: write beta, se, t, -log10 p of every (marker, phenotype) */
   double hit_mlog10p;  /* collect pairs with -log10 p >= this; <= 0 or NaN: no hit list */
+  int32_t mode;        /* tg_mode (0 = TG_MODE_PROJECTED) */
+  int32_t reserved;    /* must be 0 */
 } tg_scan_opts;
 
 /* One association above the hit threshold (24 bytes). */

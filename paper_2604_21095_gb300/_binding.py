@@ -17,6 +17,7 @@ TG_OK, TG_ERR_INVALID_ARG, TG_ERR_CUDA, TG_ERR_OOM, TG_ERR_NONFINITE, TG_ERR_RAN
     TG_ERR_CAPACITY, TG_ERR_TIMEOUT, TG_ERR_UNSUPPORTED = range(9)
 TG_PREC_FP32, TG_PREC_SPLIT_BF16 = 0, 1
 TG_ENC_2BIT, TG_ENC_U8_DOSAGE = 0, 1
+TG_MODE_PROJECTED, TG_MODE_PAPER = 0, 1
 TG_N_STAGES = 6
 STAGES = ("decode", "project", "norm", "scan", "h2d", "stats")
 
@@ -28,7 +29,8 @@ class TgError(RuntimeError):
 
 
 class tg_scan_opts(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("full_output", C.c_int32), ("hit_mlog10p", C.c_double)]
+    _fields_ = [("precision", C.c_int32), ("full_output", C.c_int32), ("hit_mlog10p", C.c_double),
+                ("mode", C.c_int32), ("reserved", C.c_int32)]
 
 
 class tg_hit(C.Structure):

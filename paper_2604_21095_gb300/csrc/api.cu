@@ -159,6 +159,9 @@ tg_status check_scan_args(const tg_ctx* c, const tg_panel* p, const ScanArgs& a)
   TG_ARG(a.encoding == TG_ENC_2BIT || a.encoding == TG_ENC_U8_DOSAGE, "unknown encoding");
   TG_ARG(a.opts.precision == TG_PREC_FP32 || a.opts.precision == TG_PREC_SPLIT_BF16,
          "unknown precision");
+  TG_ARG(a.opts.mode == TG_MODE_PROJECTED || a.opts.mode == TG_MODE_PAPER, "unknown mode");
+  TG_ARG(a.opts.reserved == 0, "tg_scan_opts.reserved must be 0");
+  TG_ARG(a.opts.mode == TG_MODE_PROJECTED || a.N > 2, "the paper's form needs N > 2");
   TG_ARG(a.N == p->N, "N differs from the panel's sample count");
   TG_ARG(a.M >= 0, "M < 0");
   TG_ARG(a.marker_offset >= 0 && a.marker_offset + a.M <= 0xFFFFFFFFll,
@@ -184,10 +187,9 @@ tg_status check_scan_args(const tg_ctx* c, const tg_panel* p, const ScanArgs& a)
 
 namespace {
 
-float r2_threshold(tg_panel* p, double mlog10p) {
+float r2_threshold(double mlog10p, double df, double lnB) {
   if (!(mlog10p > 0.0)) return 2.0f;  // never reached
-  const double r2 = host_r2_threshold(mlog10p, (double)p->df, p->lnB);
-  return (float)r2;
+  return (float)host_r2_threshold(mlog10p, df, lnB);
 }
 
 }  // namespace
@@ -209,7 +211,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   }
   TG_CUDA(ensure_markers(c, a.M));
   TG_CUDA(ensure_operands(c, a.M, p->Npad, prec));
-  const float kappa = a.encoding == TG_ENC_U8_DOSAGE ? (float)(2.0 / 255.0) : 1.0f;
+  const double kappa64 = a.encoding == TG_ENC_U8_DOSAGE ? 2.0 / 255.0 : 1.0;
+  const float kappa = (float)kappa64;
   void* Ahi = prec == TG_PREC_FP32 ? (void*)c->A32 : (void*)c->Ahi;
   {
     StageScope s(c, STAGE_DECODE, st, 1);
@@ -217,7 +220,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
                           split ? c->shift : nullptr, p->Npad, c->nobs, nullptr, nullptr, c->mean,
                           c->gc2, st));
   }
-  const int64_t nq = p->q - 1;
+  // the paper's printed form does not project the marker: |g_res|^2 is |g_c|^2
+  const int64_t nq = a.opts.mode == TG_MODE_PAPER ? 0 : p->q - 1;
   CUtensorMap tA;
   if (split && !make_tmap(&tA, c->Ahi, a.M, p->Npad, p->Npad, MT))
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
@@ -240,7 +244,7 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   }
   {
     StageScope s(c, STAGE_NORM, st, 1);
-    TG_CUDA(launch_marker_norm(a.M, c->nobs, c->gc2, c->qg, nq, kappa, c->gres2,
+    TG_CUDA(launch_marker_norm(a.M, c->nobs, c->gc2, c->qg, nq, kappa64, c->gres2,
                                a.out.marker_norm2, c->rinv, c->rinv64, st));
     if (a.out.marker_nobs)
       TG_CUDA(cudaMemcpyAsync(a.out.marker_nobs, c->nobs, sizeof(int32_t) * a.M,
@@ -253,12 +257,12 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   ep.M = (int)a.M;
   ep.P = (int)p->P;
   ep.marker_offset = a.marker_offset;
-  ep.df = (double)p->df;
-  ep.df_f = (float)p->df;
-  ep.lnB = p->lnB;
+  mode_df(p, a.opts.mode, &ep.df, &ep.lnB);
+  ep.df_f = (float)ep.df;
   ep.kappa = kappa;
+  ep.kappa64 = kappa64;
   ep.do_hits = a.opts.hit_mlog10p > 0.0 && a.out.n_hits != nullptr;
-  ep.r2_thr = ep.do_hits ? r2_threshold(p, a.opts.hit_mlog10p) : 2.0f;
+  ep.r2_thr = ep.do_hits ? r2_threshold(a.opts.hit_mlog10p, ep.df, ep.lnB) : 2.0f;
   ep.do_full = a.opts.full_output ? 1 : 0;
   ep.do_best = a.out.best != nullptr;
   ep.row_inv = c->rinv;
@@ -309,6 +313,16 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
 }  // namespace tg
 
 namespace tg {
+
+void mode_df(const tg_panel* p, int mode, double* df, double* lnB) {
+  if (mode == TG_MODE_PAPER) {
+    *df = (double)(p->N - 2);
+    *lnB = p->lnB_paper;
+  } else {
+    *df = (double)p->df;
+    *lnB = p->lnB;
+  }
+}
 
 tg_status fail(tg_status s, const std::string& msg) {
   g_err = msg;
@@ -489,6 +503,7 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
   if (flags & 1u) return cleanup(fail(TG_ERR_NONFINITE, "non-finite covariate"));
   if (flags & 2u) return cleanup(fail(TG_ERR_NONFINITE, "non-finite phenotype"));
   p->lnB = host_lnbeta_half((double)p->df);
+  p->lnB_paper = host_lnbeta_half((double)(N - 2));
   if (!make_tmap(&p->tmBhi, p->Bhi, p->Ppad, p->Npad, p->Npad, 256) ||
       !make_tmap(&p->tmBlo, p->Blo, p->Ppad, p->Npad, p->Npad, 256) ||
       !make_tmap(&p->tmBhi2, p->Bhi, p->Ppad, p->Npad, p->Npad, 128) ||
@@ -751,6 +766,7 @@ tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_pa
   r->Npad = p0->Npad;
   r->Ppad = round_up(std::max<int64_t>(P, 1), PPAD);
   r->lnB = p0->lnB;
+  r->lnB_paper = p0->lnB_paper;
   const int64_t Np = r->Npad, Pp = r->Ppad;
   cudaError_t e;
   if ((e = dalloc(&r->Q, (size_t)(q * N))) || (e = dalloc(&r->Yres, (size_t)(std::max<int64_t>(P, 1) * N))) ||

@@ -115,6 +115,8 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
     return fail(TG_ERR_INVALID_ARG, "unknown encoding");
   const int prec = opts->precision;
   if (prec != TG_PREC_FP32 && prec != TG_PREC_SPLIT_BF16) return fail(TG_ERR_INVALID_ARG, "unknown precision");
+  if ((opts->mode != TG_MODE_PROJECTED && opts->mode != TG_MODE_PAPER) || opts->reserved != 0)
+    return fail(TG_ERR_INVALID_ARG, "unknown mode (or tg_scan_opts.reserved != 0)");
   if (N != p->N) return fail(TG_ERR_INVALID_ARG, "N differs from the panel's sample count");
   if (M < 0 || marker_offset < 0 || marker_offset + M > 0xFFFFFFFFll)
     return fail(TG_ERR_INVALID_ARG, "bad M or marker_offset");
@@ -176,7 +178,8 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   void* Ahi = cv.take<unsigned char>((size_t)rows * p->Npad * elem);
 
   cudaStream_t st = (cudaStream_t)stream;
-  const float kappa = encoding == TG_ENC_U8_DOSAGE ? (float)(2.0 / 255.0) : 1.0f;
+  const double kappa64 = encoding == TG_ENC_U8_DOSAGE ? 2.0 / 255.0 : 1.0;
+  const float kappa = (float)kappa64;
 #define TGS_CUDA(call)                                    \
   do {                                                    \
     cudaError_t e_ = (call);                              \
@@ -189,7 +192,7 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   CUtensorMap tA;
   if (split && !tmap_static(&tA, Ahi, M, p->Npad, p->Npad, MT))
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
-  const int64_t nq = p->q - 1;
+  const int64_t nq = opts->mode == TG_MODE_PAPER ? 0 : p->q - 1;  // the paper's form: no projection
   if (nq > 0) {
     if (!split) {
       TGS_CUDA(launch_project(reinterpret_cast<const float*>(Ahi), p->Npad, M, p->Npad, p->QB, nq,
@@ -208,7 +211,7 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
                               st));
     }
   }
-  TGS_CUDA(launch_marker_norm(M, nobs, gc2, qg, nq, kappa, gres2, out->marker_norm2, rinv, rinv64, st));
+  TGS_CUDA(launch_marker_norm(M, nobs, gc2, qg, nq, kappa64, gres2, out->marker_norm2, rinv, rinv64, st));
   if (out->marker_nobs)
     TGS_CUDA(cudaMemcpyAsync(out->marker_nobs, nobs, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st));
   if (out->marker_mean)
@@ -217,12 +220,12 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   ep.M = (int)M;
   ep.P = (int)p->P;
   ep.marker_offset = marker_offset;
-  ep.df = (double)p->df;
-  ep.df_f = (float)p->df;
-  ep.lnB = p->lnB;
+  mode_df(p, opts->mode, &ep.df, &ep.lnB);
+  ep.df_f = (float)ep.df;
   ep.kappa = kappa;
+  ep.kappa64 = kappa64;
   ep.do_hits = want_hits ? 1 : 0;
-  ep.r2_thr = want_hits ? (float)host_r2_threshold(opts->hit_mlog10p, (double)p->df, p->lnB) : 2.0f;
+  ep.r2_thr = want_hits ? (float)host_r2_threshold(opts->hit_mlog10p, ep.df, ep.lnB) : 2.0f;
   ep.do_full = opts->full_output ? 1 : 0;
   ep.do_best = out->best != nullptr;
   ep.row_inv = rinv;

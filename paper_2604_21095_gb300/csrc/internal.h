@@ -34,7 +34,8 @@ struct EpiParams {
   double df;                   // N - q - 1
   float df_f;
   double lnB;                  // ln Beta(df/2, 1/2)
-  float kappa;                 // allele units per decode unit (1 or 2/255)
+  float kappa;                 // allele units per decode unit (1 or 2/255), FP32 kernels
+  double kappa64;              // the same in FP64 (hit statistics)
   float r2_thr;                // hit threshold on r^2 (> 1 disables)
   int do_full, do_hits, do_best;
   const float* row_inv;        // [M] 1/|a_res| (decode units), NaN = untestable
@@ -101,7 +102,8 @@ struct tg_panel {
   __nv_bfloat16* QBhi = nullptr; // [QCOLS][Npad] the same split into bf16 hi + lo
   __nv_bfloat16* QBlo = nullptr;
   float* qcs = nullptr;          // [QCOLS] sum_i (QBhi + QBlo)[k][i]
-  double lnB = 0;
+  double lnB = 0;                // ln B(df/2, 1/2), df = N - q - 1
+  double lnB_paper = 0;          // ln B((N-2)/2, 1/2) for the paper's printed form
   CUtensorMap tmBhi, tmBlo;      // phenotype panel, 256-row boxes
   CUtensorMap tmBhi2, tmBlo2;    // phenotype panel, 128-row boxes (one CTA's half of a pair tile)
   CUtensorMap tmQhi, tmQlo;      // covariate projection columns, 64-row boxes
@@ -156,6 +158,8 @@ tg_status fail(tg_status s, const std::string& msg);
 tg_status cuda_fail(cudaError_t e, const char* what);
 tg_status check_scan_args(const tg_ctx* c, const tg_panel* p, const ScanArgs& a);
 tg_status scan_impl(tg_ctx* c, const tg_panel* p, const ScanArgs& a, cudaStream_t st);
+// Degrees of freedom and ln B(df/2, 1/2) of the statistic a scan mode computes.
+void mode_df(const tg_panel* p, int mode, double* df, double* lnB);
 bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t ld,
                uint32_t box_rows);
 
@@ -181,7 +185,7 @@ cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N
 cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, const float* QB,
                            int64_t nq, float* qg, cudaStream_t st);
 cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
-                               int64_t nq, float kappa, double* gres2_units_out,
+                               int64_t nq, double kappa, double* gres2_units_out,
                                double* norm2_allele_out, float* rinv, double* rinv64,
                                cudaStream_t st);
 cudaError_t launch_sgemm_scan(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t K,

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ A, lo
 // ---------------------------------------------------------------- marker norms
 __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
                               const double* __restrict__ gc2, const float* __restrict__ qg, int nq,
-                              float kappa, double* __restrict__ gres2u,
+                              double kappa, double* __restrict__ gres2u,
                               double* __restrict__ norm2_allele, float* __restrict__ rinv,
                               double* __restrict__ rinv64) {
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -105,7 +105,7 @@ __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   const double inv = ok ? 1.0 / sqrt(r2) : nan;
   gres2u[j] = ok ? r2 : nan;
-  if (norm2_allele) norm2_allele[j] = ok ? r2 * (double)kappa * (double)kappa : nan;
+  if (norm2_allele) norm2_allele[j] = ok ? r2 * kappa * kappa : nan;
   rinv[j] = (float)inv;
   rinv64[j] = inv;
 }
@@ -231,7 +231,7 @@ cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, co
 }
 
 cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
-                               int64_t nq, float kappa, double* gres2_units_out,
+                               int64_t nq, double kappa, double* gres2_units_out,
                                double* norm2_allele_out, float* rinv, double* rinv64,
                                cudaStream_t st) {
   if (M == 0) return cudaSuccess;

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(128) k_hit_stats(EpiParams ep,
     double r = (double)h.beta * rinv;
     r = fmin(1.0, fmax(-1.0, r));
     const double omr2 = (1.0 - r) * (1.0 + r);
-    const double scale = ep.col_s64[h.pheno] * rinv / (double)ep.kappa;
+    const double scale = ep.col_s64[h.pheno] * rinv / ep.kappa64;
     h.beta = (float)(r * scale);
     h.se = (float)(scale * sqrt(omr2 / ep.df));
     h.t = (float)(r * sqrt(ep.df / omr2));

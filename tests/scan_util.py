@@ -38,7 +38,8 @@ def prec_id(precision: str) -> int:
 
 
 def run_scan(ctx, panel, G, N, P, encoding, precision, full=True, hit_mlog10p=0.0,
-             hit_capacity=1 << 16, missing=None, marker_offset=0, stream=None):
+             hit_capacity=1 << 16, missing=None, marker_offset=0, stream=None,
+             mode=tg.TG_MODE_PROJECTED):
     """One tg_scan_block call; returns a dict of numpy arrays."""
     dev = G.device
     M = G.shape[0]
@@ -55,7 +56,7 @@ def run_scan(ctx, panel, G, N, P, encoding, precision, full=True, hit_mlog10p=0.
     out = tg.make_outputs(beta=o.get("beta"), se=o.get("se"), t=o.get("t"),
                           mlog10p=o.get("mlog10p"), ldo=P, hits=hits, n_hits=n_hits, best=best,
                           marker_norm2=norm2, marker_nobs=nobs, marker_mean=mean)
-    opts = tg.tg_scan_opts(prec_id(precision), 1 if full else 0, float(hit_mlog10p))
+    opts = tg.tg_scan_opts(prec_id(precision), 1 if full else 0, float(hit_mlog10p), mode)
     tg.tg_scan_block(ctx, panel, G, N, M, enc_id(encoding), opts, out, marker_offset=marker_offset,
                      missing=missing, stream=stream)
     status = tg.tg_status_poll(ctx, stream)

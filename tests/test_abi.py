@@ -47,15 +47,40 @@ def test_binding_covers_the_header():
     assert sorted(_binding.exported_symbols()) == _declared()
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets the C compiler gives the
+    header's structures."""
+    import shutil
+    import subprocess
     assert ctypes.sizeof(_binding.tg_hit) == 24
-    assert ctypes.sizeof(_binding.tg_scan_opts) == 16
-    assert ctypes.sizeof(_binding.tg_outputs) == 12 * 8
+    structs = {"tg_hit": _binding.tg_hit, "tg_scan_opts": _binding.tg_scan_opts,
+               "tg_outputs": _binding.tg_outputs}
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "tg.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
 
 
 def test_version_and_status_strings(lib):
     assert "sm_103a" in tg.tg_version()
-    assert tg.tg_abi_version() == 1
+    assert tg.tg_abi_version() == 2
     assert tg.tg_status_string(tg.TG_ERR_TIMEOUT) == "device wait timed out"
 
 

@@ -11,7 +11,7 @@ import oracle
 import paper_2604_21095_gb300 as tg
 import synth
 from scan_util import (HIT_DTYPE, compare_best, compare_full, compare_hits, enc_id, oracle_panel,
-                       run_scan)
+                       r_tol, run_scan)
 
 pytestmark = pytest.mark.gpu
 
@@ -207,3 +207,61 @@ def test_host_streamed_scan_matches_oracle(tgctx, panels, encoding, block):
     want, got = compare_hits(res, ref, THR, marker_offset=11)
     assert want > 0 and got > 0
     compare_best(res, ref, marker_offset=11)
+
+
+@pytest.mark.parametrize("encoding,masked", [("2bit", False), ("u8", True)])
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_paper_mode_matches_oracle(tgctx, panels, encoding, masked, precision):
+    """Eq. 2-3 as printed (marker only standardised, df = N - 2) against the oracle's paper
+    form, with covariates present (where it differs from the OLS test)."""
+    w, pan, blk, miss = _case(encoding, masked=masked)
+    panel = _panel(tgctx, panels, ("main", encoding, masked), pan, w.N, w.P)
+    G = blk["G"].cuda()
+    res = run_scan(tgctx, panel, G, w.N, w.P, encoding, precision, full=True, hit_mlog10p=THR,
+                   missing=None if miss is None else miss.cuda(), marker_offset=3,
+                   mode=tg.TG_MODE_PAPER)
+    assert res["status"] == tg.TG_OK
+    ref = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]),
+                      None if miss is None else miss.numpy(), mode="paper")
+    assert ref["df"] == w.N - 2
+    err = compare_full(res, ref, label=f"paper {encoding}/{precision}")
+    want, got = compare_hits(res, ref, THR, marker_offset=3)
+    assert want > 0 and got > 0
+    compare_best(res, ref, marker_offset=3)
+    ok = np.isfinite(ref["gres2"])
+    assert np.array_equal(np.isfinite(res["norm2"]), ok)
+    assert np.allclose(res["norm2"][ok], ref["gres2"][ok], rtol=1e-10)
+    # the projected statistic differs measurably with 4 covariates
+    proj = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]),
+                       None if miss is None else miss.numpy(), mode="projected")
+    assert np.nanmax(np.abs(proj["r"] - ref["r"])) > 10 * r_tol(ref["df"])
+    print(f"\nmax |error| vs FP64 oracle, paper form {encoding}/{precision}: {err}")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+def test_paper_mode_is_projected_mode_with_intercept_only(tgctx, precision):
+    w = synth.Workload("paper_icpt", N=1500, M=700, P=130, n_cov=0, encoding="2bit",
+                       missing=0.02, seed=17, block=700, causal_per_pheno=2)
+    pan = synth.make_panel(w)
+    blk = synth.make_block(w, 0)
+    panel = tg.tg_prepare_panel(tgctx, pan["Yt"].cuda(), w.N, w.P, None)
+    try:
+        G = blk["G"].cuda()
+        a = run_scan(tgctx, panel, G, w.N, w.P, "2bit", precision, full=True, hit_mlog10p=THR,
+                     mode=tg.TG_MODE_PAPER)
+        b = run_scan(tgctx, panel, G, w.N, w.P, "2bit", precision, full=True, hit_mlog10p=THR)
+        for k in ("beta", "se", "t", "mlog10p", "best_key", "norm2"):
+            assert np.array_equal(a[k], b[k], equal_nan=True), k
+        assert sorted(a["hits"].tolist()) == sorted(b["hits"].tolist())
+    finally:
+        tg.tg_panel_free(panel)
+
+
+def test_mode_argument_checked(tgctx, panels):
+    w, pan, blk, _ = _case("2bit")
+    panel = _panel(tgctx, panels, ("main", "2bit", False), pan, w.N, w.P)
+    for opts in (tg.tg_scan_opts(1, 0, THR, 2), tg.tg_scan_opts(1, 0, THR, 0, 1)):
+        out = tg.make_outputs(hits=torch.zeros(24, dtype=torch.uint8, device="cuda"),
+                              n_hits=torch.zeros(1, dtype=torch.int64, device="cuda"))
+        with pytest.raises(tg.TgError):
+            tg.tg_scan_block(tgctx, panel, blk["G"].cuda(), w.N, w.M, tg.TG_ENC_2BIT, opts, out)
