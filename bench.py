@@ -51,6 +51,10 @@ def _args():
                         "or n23000_m500000_12panels_p8192_2bit (batched form)")
     a.add_argument("--phenotypes", type=int, default=None)
     a.add_argument("--block-markers", type=int, default=None)
+    a.add_argument("--sweep-p", action="store_true",
+                   help="instead of the bench line: time one block of the workload against panels "
+                        "of growing P (the paper's Section 3.2 scaling in the number of phenotypes) "
+                        "and print one JSON line with every point")
     return a.parse_args()
 
 
@@ -552,8 +556,63 @@ def _traffic():
         return None
 
 
+def _sweep_p(args):
+    """Per-block time of the whole scan path against the panel size P, on one GPU."""
+    import torch
+
+    import paper_2604_21095_gb300 as tg
+    import synth
+
+    dev = torch.device("cuda", 0)
+    tg.build()
+    w = _workload(args)
+    enc = tg.TG_ENC_U8_DOSAGE if w.encoding == "u8" else tg.TG_ENC_2BIT
+    ctx = tg.tg_create(0)
+    stream = torch.cuda.current_stream(dev)
+    pan = synth.make_panel(w, device=dev, planted_blocks=1)
+    G = synth.make_block(w, 0, device=dev)["G"]
+    M = G.shape[0]
+    hits = torch.zeros((1 << 20) * 24, dtype=torch.uint8, device=dev)
+    n_hits = torch.zeros(1, dtype=torch.int64, device=dev)
+    points = []
+    for P in (16, 64, 256, 1024, 2048, 4096, 8192, 20480):
+        if P > w.P:
+            break
+        Yt = pan["Yt"][:P].contiguous()
+        panel = tg.tg_prepare_panel(ctx, Yt, w.N, P, pan["cov_t"], stream=stream)
+        best = torch.zeros(P, dtype=torch.int64, device=dev)
+        out = tg.make_outputs(hits=hits, n_hits=n_hits, best=best)
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, THR)
+        reps = max(3, min(50, int(20480 * 5 / P)))
+        for _ in range(2):
+            tg.tg_scan_block(ctx, panel, G, w.N, M, enc, opts, out, stream=stream)
+        torch.cuda.synchronize()
+        tg.tg_stage_times(ctx, reset=True)
+        tg.tg_set_profiling(ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            tg.tg_scan_block(ctx, panel, G, w.N, M, enc, opts, out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tg.tg_set_profiling(ctx, False)
+        st = tg.tg_stage_times(ctx, reset=True)
+        ms = e0.elapsed_time(e1) / reps
+        points.append({"P": P, "ms_per_block": ms, "tests_per_s": M * P / (ms / 1000.0),
+                       "stage_ms": {k: v[0] / reps for k, v in st.items() if v[1]}})
+        n_hits.zero_()
+        tg.tg_panel_free(panel)
+    tg.tg_destroy(ctx)
+    print(json.dumps({"metric": "per-block scan time vs number of phenotypes", "unit": "ms",
+                      "workload": f"{w.name}: one {M}-marker block, N={w.N}, C={w.n_cov + 1}",
+                      "points": points}))
+
+
 def main():
     args = _args()
+    if args.sweep_p:
+        _sweep_p(args)
+        return
     dist, rank, ws = _dist()
     if args.impl == "reference":
         _reference(args, dist, rank, ws)
