@@ -232,6 +232,16 @@ tg_status tg_scan_host(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G_host
                        int64_t hit_capacity, int64_t* n_hits, unsigned long long* best_host,
                        void* stream);
 
+/* Whether split-form scans decode the genotypes inside the contraction kernels (enable != 0)
+ * or first write the decoded operand to device memory (enable == 0, the default). The fused
+ * form applies to 2-bit blocks and to dosage blocks without a missing mask (others always use
+ * the decoded operand); it needs no operand buffer (about 2 x round_up(N, 64) bytes per marker)
+ * and reads the packed rows instead, but its two decoder warps per CTA take about 3,000 cycles
+ * per 32-sample K block, against 512 for the products, so on GB300 it is slower at every panel
+ * size. Both forms compute bit-identical results. Not allowed while a captured scan graph uses
+ * the context (TG_ERR_INVALID_ARG). */
+tg_status tg_set_fused_decode(tg_ctx* ctx, int enable);
+
 /* ---- Batched form: many panels, ragged blocks, one captured graph, tuned tiles ----------- */
 
 /* One panel made of n panels that were prepared from the same N samples and the same

@@ -78,6 +78,7 @@ _SIGS = {
     "tg_tuning": (C.c_int, [_VP, _I64, C.POINTER(_I32), C.POINTER(_I32)]),
     "tg_set_tuning": (C.c_int, [_VP, _I64, _I32, _I32]),
     "tg_status_poll": (C.c_int, [_VP, _VP]),
+    "tg_set_fused_decode": (C.c_int, [_VP, C.c_int]),
     "tg_set_profiling": (C.c_int, [_VP, C.c_int]),
     "tg_stage_times": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_I64), C.c_int]),
     "tg_bounded_wait_test": (C.c_int, [_VP, _VP, _I64, _VP]),
@@ -313,6 +314,10 @@ def tg_set_tuning(ctx, M, kernel: str, group_m: int):
 def tg_status_poll(ctx, stream=None) -> int:
     """Synchronise and return the latched device status (0 = ok); does not raise."""
     return load().tg_status_poll(ctx, _stream(stream))
+
+
+def tg_set_fused_decode(ctx, enable: bool):
+    _check(load().tg_set_fused_decode(ctx, 1 if enable else 0))
 
 
 def tg_set_profiling(ctx, enable: bool):

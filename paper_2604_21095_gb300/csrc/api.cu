@@ -23,6 +23,7 @@ const char* kVersion = "tg 0.1.0 (sm_103a)";
 
 // The spin limit of device-side waits: generous enough for a FULL-output tile epilogue.
 constexpr long long kSpinNs = 4000000000ll;
+constexpr int kGroupDefault = 16;  // raster group (m-tiles) when the tuner has not chosen one
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -52,6 +53,18 @@ bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t
   cuuint32_t estr[2] = {1u, 1u};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+bool make_tmap_packed(CUtensorMap* m, const void* ptr, int64_t rows, int64_t ld, uint32_t box_bytes) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld};
+  cuuint32_t box[2] = {box_bytes, (cuuint32_t)MT};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(ptr), dims, strides, box,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -118,11 +131,12 @@ struct StageScope {
 cudaError_t ensure_markers(tg_ctx* c, int64_t M) {
   if (M <= c->cap_m) return cudaSuccess;
   const int64_t cap = round_up(M, MT);
-  dfree(c->nobs); dfree(c->mean); dfree(c->shift); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
-  dfree(c->rinv); dfree(c->rinv64);
+  dfree(c->nobs); dfree(c->mean); dfree(c->shift); dfree(c->mh); dfree(c->gc2); dfree(c->qg);
+  dfree(c->gres2); dfree(c->rinv); dfree(c->rinv64);
   c->cap_m = 0;
   cudaError_t e;
   if ((e = dalloc(&c->nobs, cap)) || (e = dalloc(&c->mean, cap)) || (e = dalloc(&c->shift, cap)) ||
+      (e = dalloc(&c->mh, cap)) ||
       (e = dalloc(&c->gc2, cap)) || (e = dalloc(&c->qg, cap * QCOLS)) ||
       (e = dalloc(&c->gres2, cap)) || (e = dalloc(&c->rinv, cap)) || (e = dalloc(&c->rinv64, cap)))
     return e;
@@ -201,29 +215,42 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   if (a.M == 0) return TG_OK;
   const int prec = a.opts.precision;
   const bool split = prec == TG_PREC_SPLIT_BF16;
+  // split-form 2-bit blocks and unmasked dosage blocks are decoded inside the contraction
+  // kernels; the rest go through a decoded operand in HBM
+  const bool fused = split && c->fuse_decode && a.missing == nullptr;
   if (c->graphs_alive > 0) {
-    const bool grow = a.M > c->cap_m || round_up(a.M, MT) > c->cap_rows || p->Npad > c->cap_npad ||
-                      (prec == TG_PREC_FP32 ? !c->A32 : !c->Ahi);
+    const bool grow = a.M > c->cap_m || (!fused && (round_up(a.M, MT) > c->cap_rows ||
+                                                    p->Npad > c->cap_npad ||
+                                                    (prec == TG_PREC_FP32 ? !c->A32 : !c->Ahi)));
     if (grow)
       return fail(TG_ERR_INVALID_ARG,
                   "the context's workspace is held by a captured scan graph: scan blocks no "
                   "larger than the graph's, or use another context");
   }
   TG_CUDA(ensure_markers(c, a.M));
-  TG_CUDA(ensure_operands(c, a.M, p->Npad, prec));
+  if (!fused) TG_CUDA(ensure_operands(c, a.M, p->Npad, prec));
   const double kappa64 = a.encoding == TG_ENC_U8_DOSAGE ? 2.0 / 255.0 : 1.0;
   const float kappa = (float)kappa64;
-  void* Ahi = prec == TG_PREC_FP32 ? (void*)c->A32 : (void*)c->Ahi;
+  void* Ahi = fused ? nullptr : prec == TG_PREC_FP32 ? (void*)c->A32 : (void*)c->Ahi;
   {
     StageScope s(c, STAGE_DECODE, st, 1);
     TG_CUDA(launch_decode(a.G, a.ldg, a.encoding, a.N, a.M, a.missing, a.ldm, prec, Ahi,
-                          split ? c->shift : nullptr, p->Npad, c->nobs, nullptr, nullptr, c->mean,
-                          c->gc2, st));
+                          split ? c->shift : nullptr, split ? c->mh : nullptr, p->Npad, c->nobs,
+                          nullptr, nullptr, c->mean, c->gc2, st));
   }
-  // the paper's printed form does not project the marker: |g_res|^2 is |g_c|^2
+  DecodeArgs da{};
+  if (fused) {
+    da.N = (int)a.N;
+    da.M = (int)a.M;
+    da.shift = c->shift;
+    da.mh = c->mh;
+    if (!make_tmap_packed(&da.tmG, a.G, a.M, a.ldg, a.encoding == TG_ENC_U8_DOSAGE ? 32u : 16u))
+      return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the packed genotypes");
+  }
+  const DecodeArgs* dec = fused ? &da : nullptr;
   const int64_t nq = a.opts.mode == TG_MODE_PAPER ? 0 : p->q - 1;
   CUtensorMap tA;
-  if (split && !make_tmap(&tA, c->Ahi, a.M, p->Npad, p->Npad, MT))
+  if (split && !fused && !make_tmap(&tA, c->Ahi, a.M, p->Npad, p->Npad, MT))
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
   if (nq > 0) {
     StageScope s(c, STAGE_PROJECT, st, 1);
@@ -239,7 +266,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       pp.raw_out = c->qg;
       pp.raw_cols = (int)nq;
       pp.raw_ld = QCOLS;
-      TG_CUDA(launch_tc_scan(&tA, &p->tmQhi, &p->tmQlo, p->Npad, pp, c->sm_count, kSpinNs, st));
+      TG_CUDA(launch_tc_scan(&tA, &p->tmQhi, &p->tmQlo, p->Npad, pp, c->sm_count, kSpinNs, st,
+                             kGroupDefault, dec, a.encoding));
     }
   }
   {
@@ -293,13 +321,13 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       TG_CUDA(launch_sgemm_scan(c->A32, p->Npad, p->B32, p->Npad, p->Npad, ep, st));
     } else {
       const int b = tune_bucket(a.M);
-      const int group = c->tune_group[b] > 0 ? c->tune_group[b] : 16;
+      const int group = c->tune_group[b] > 0 ? c->tune_group[b] : kGroupDefault;
       if (c->tune_kernel[b] == TUNE_SINGLE)
         TG_CUDA(launch_tc_scan(&tA, &p->tmBhi, &p->tmBlo, p->Npad, ep, c->sm_count, kSpinNs, st,
-                               group));
+                               group, dec, a.encoding));
       else
         TG_CUDA(launch_tc2_scan(&tA, &p->tmBhi2, &p->tmBlo2, p->Npad, ep, c->sm_count, kSpinNs, st,
-                                group));
+                                group, dec, a.encoding));
     }
   }
   if (ep.do_hits || ep.do_full) {
@@ -416,7 +444,7 @@ tg_status tg_destroy(tg_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   dfree(c->status); dfree(c->scratch);
-  dfree(c->Ahi); dfree(c->A32); dfree(c->shift);
+  dfree(c->Ahi); dfree(c->A32); dfree(c->shift); dfree(c->mh);
   dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
   dfree(c->rinv); dfree(c->rinv64);
   dfree(c->stage_buf[0]); dfree(c->stage_buf[1]);
@@ -571,8 +599,8 @@ tg_status tg_decode_block(tg_ctx* c, const uint8_t* G, int64_t ldg, int32_t enco
   TG_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
   StageScope s(c, STAGE_DECODE, st, 1);
-  TG_CUDA(launch_decode(G, ldg, encoding, N, M, missing, ldm, precision, A, shift, lda, n_obs,
-                        S, S2, mean, nullptr, st));
+  TG_CUDA(launch_decode(G, ldg, encoding, N, M, missing, ldm, precision, A, shift, nullptr, lda,
+                        n_obs, S, S2, mean, nullptr, st));
   return TG_OK;
 }
 
@@ -679,6 +707,13 @@ tg_status tg_status_poll(tg_ctx* c, void* stream) {
   TG_CUDA(cudaMemset(c->status, 0, sizeof(word)));
   if (word & ST_TIMEOUT) return fail(TG_ERR_TIMEOUT, "a bounded device wait ran out");
   if (word & ST_CAPACITY) return fail(TG_ERR_CAPACITY, "more hits than hit_capacity");
+  return TG_OK;
+}
+
+tg_status tg_set_fused_decode(tg_ctx* c, int enable) {
+  TG_ARG(c, "null context");
+  TG_ARG(c->graphs_alive == 0, "a captured scan graph uses this context");
+  c->fuse_decode = enable != 0;
   return TG_OK;
 }
 
@@ -844,8 +879,10 @@ tg_status tg_scan_graph_create(tg_ctx* c, const tg_panel* p, int n_blocks,
     maxM = std::max(maxM, M[b]);
   }
   // size the workspace now: nothing may allocate inside the capture
+  bool need_operand = opts->precision != TG_PREC_SPLIT_BF16 || !c->fuse_decode;
+  for (int b = 0; b < n_blocks; ++b) need_operand |= missing && missing[b];
   TG_CUDA(ensure_markers(c, maxM));
-  TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision));
+  if (need_operand) TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision));
   cudaStream_t cap = nullptr;
   TG_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   tg_graph* g = new tg_graph();
@@ -918,7 +955,9 @@ tg_status tg_autotune(tg_ctx* c, const tg_panel* p, int32_t encoding, int64_t M,
     cleanup();
     return cuda_fail(e, "tg_autotune allocation");
   }
-  if ((e = launch_fill_random(G, (size_t)(M * ldg), 0x5eed5eedull, st))) {
+  if ((e = launch_fill_random(G, (size_t)(M * ldg), 0x5eed5eedull, st)) ||
+      (e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st)) ||
+      (e = cudaMemsetAsync(best, 0, sizeof(unsigned long long) * (size_t)std::max<int64_t>(p->P, 1), st))) {
     cleanup();
     return cuda_fail(e, "tg_autotune fill");
   }
@@ -997,7 +1036,7 @@ tg_status tg_tuning(const tg_ctx* c, int64_t M, int32_t* kernel, int32_t* group)
   TG_ARG(c && M > 0, "bad arguments");
   const int b = tune_bucket(M);
   if (kernel) *kernel = c->tune_kernel[b] == TUNE_SINGLE ? 1 : 2;
-  if (group) *group = c->tune_group[b] > 0 ? c->tune_group[b] : 16;
+  if (group) *group = c->tune_group[b] > 0 ? c->tune_group[b] : kGroupDefault;
   return TG_OK;
 }
 

@@ -188,7 +188,8 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   // every call shares the scratch and it keeps the last call's contents: clear what must start at 0
   TGS_CUDA(cudaMemsetAsync(status, 0, sizeof(uint32_t), st));
   TGS_CUDA(launch_decode(G, ldg, encoding, N, M, missing, ldm, prec, Ahi,
-                         split ? shift : nullptr, p->Npad, nobs, nullptr, nullptr, mean, gc2, st));
+                         split ? shift : nullptr, nullptr, p->Npad, nobs, nullptr, nullptr, mean,
+                         gc2, st));
   CUtensorMap tA;
   if (split && !tmap_static(&tA, Ahi, M, p->Npad, p->Npad, MT))
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");

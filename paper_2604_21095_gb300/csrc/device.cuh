@@ -50,7 +50,7 @@ __device__ __forceinline__ float corr_nan(float D, float rinv, float rmul) {
 // statistics kernel that runs after the contraction turns it into beta, se, t, -log10 p.
 __device__ __forceinline__ void emit_hit_raw(const EpiParams& ep, float D, long long row, int col) {
   const unsigned long long slot = atomicAdd(ep.n_hits, 1ull);
-  if ((long long)slot >= ep.hit_cap) {
+  if (slot >= (unsigned long long)ep.hit_cap) {  // unsigned: any count past capacity, never a write
     atomicOr(ep.status, ST_CAPACITY);
     return;
   }

@@ -57,6 +57,17 @@ struct EpiParams {
   int raw_cols, raw_ld;
 };
 
+// Packed genotypes for a contraction kernel that decodes its A operand in the producer
+// (2-bit calls, or dosage bytes without a missing mask; split form only). The kernel loads the
+// packed rows through `tmG` (uint8, {ldg, M}, boxes of 32 or 16 bytes x 128 rows).
+struct DecodeArgs {
+  CUtensorMap tmG;
+  int N;                  // samples; K columns >= N are zero
+  int M;                  // rows of the block; rows >= M are zero
+  const float* shift;     // [M] row shift c
+  const uint32_t* mh;     // [M] bf16 bits of (mean - c), the missing-call value
+};
+
 struct Events {
   cudaEvent_t a, b;
   int stage;
@@ -123,6 +134,7 @@ struct tg_ctx {
   int32_t* nobs = nullptr;
   double* mean = nullptr;
   float* shift = nullptr;                       // [cap_m] per-row shift of the split operand
+  uint32_t* mh = nullptr;                       // [cap_m] bf16 bits of the missing-call value
   double* gc2 = nullptr;
   float* qg = nullptr;                          // [cap_m][QCOLS]
   double* gres2 = nullptr;
@@ -146,6 +158,9 @@ struct tg_ctx {
   int64_t launches[TG_N_STAGES] = {0, 0, 0, 0, 0, 0};
   // captured scan graphs that hold pointers into this workspace
   int graphs_alive = 0;
+  // split-form scans decode 2-bit / unmasked dosage blocks in the contraction producer
+  // (off by default: slower than the decoded operand on GB300, see tg_set_fused_decode)
+  bool fuse_decode = false;
   // autotuned kernel per block-size bucket
   int tune_kernel[tg::kTuneBuckets] = {};
   int tune_group[tg::kTuneBuckets] = {};
@@ -162,6 +177,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* p, const ScanArgs& a, cudaStream_
 void mode_df(const tg_panel* p, int mode, double* df, double* lnB);
 bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t ld,
                uint32_t box_rows);
+// uint8 map over packed genotype rows [rows][ld], boxes of box_bytes x 128 rows, zero fill.
+bool make_tmap_packed(CUtensorMap* m, const void* ptr, int64_t rows, int64_t ld, uint32_t box_bytes);
 
 // panel kernels (k_panel.cu)
 cudaError_t launch_build_design(double* X, const double* C, int64_t ldc, int64_t N, int64_t n_cov,
@@ -178,8 +195,8 @@ cudaError_t launch_qcols(const double* Q, int64_t N, int64_t q, int64_t Npad, fl
 // decode (k_decode.cu)
 cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,
                           const uint32_t* missing, int64_t ldm, int precision, void* Ahi,
-                          float* shift, int64_t lda, int32_t* nobs, int64_t* S, int64_t* S2,
-                          double* mean, double* gc2, cudaStream_t st);
+                          float* shift, uint32_t* mh, int64_t lda, int32_t* nobs, int64_t* S,
+                          int64_t* S2, double* mean, double* gc2, cudaStream_t st);
 
 // SIMT kernels (k_simt.cu)
 cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, const float* QB,
@@ -197,14 +214,17 @@ cudaError_t launch_hit_stats(const EpiParams& ep, const unsigned long long* star
 cudaError_t launch_fill_random(uint8_t* p, size_t n, unsigned long long seed, cudaStream_t st);
 
 // tensor-core kernel (k_tc.cu)
+// With `dec` non-NULL the A operand is decoded from packed genotypes in the kernel (tmA unused).
 cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                            const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
-                           long long spin_ns, cudaStream_t st, int group_m = 16);
+                           long long spin_ns, cudaStream_t st, int group_m = 16,
+                           const DecodeArgs* dec = nullptr, int encoding = 0);
 
 // tensor-core kernel on CTA pairs, 256 x 256 tiles (k_tc2.cu)
 cudaError_t launch_tc2_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                             const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
-                            long long spin_ns, cudaStream_t st, int group_m = 16);
+                            long long spin_ns, cudaStream_t st, int group_m = 16,
+                            const DecodeArgs* dec = nullptr, int encoding = 0);
 
 // bounded wait test (k_tc.cu)
 cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,

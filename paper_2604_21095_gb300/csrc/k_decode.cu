@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 
 #include "device.cuh"
+#include "genotype.cuh"
 #include "internal.h"
 
 namespace tg {
@@ -133,47 +134,6 @@ __device__ __forceinline__ void load8(const uint8_t* __restrict__ row, const uin
   if (i0 + 8 > N) miss &= (N > i0) ? ((1u << (N - i0)) - 1u) : 0u;
 }
 
-// 16 split-form values of 2-bit fields w (sample 16t + k in bits 2k..2k+1): eight bf16x2
-// words. lut0 = {field 00, field 01} and lut1 = {field 10, field 11} as bf16 pairs; the
-// permute selector for fields (f, g) is 0x1010 + 0x22 f + 0x2200 g (bytes 2f, 2f+1, 2g, 2g+1).
-__device__ __forceinline__ void split16_2bit(uint32_t w, uint32_t lut0, uint32_t lut1,
-                                             uint32_t (&o)[8]) {
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    const uint32_t f = (w >> (4 * p)) & 3u, g = (w >> (4 * p + 2)) & 3u;
-    o[p] = __byte_perm(lut0, lut1, 0x1010u + 0x22u * f + 0x2200u * g);
-  }
-}
-
-// 16 split-form values of dosage bytes v: b - c exactly, bf16x2 words; bits of `miss` take
-// the missing value mh (a bf16 in the low half of mh2 and in the high half).
-__device__ __forceinline__ void split16_u8(uint4 v, float c_plus, uint32_t miss, uint32_t mh2,
-                                           uint32_t (&o)[8]) {
-  const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    const uint32_t w = w4[p >> 1];
-    const uint32_t k = (uint32_t)(p & 1) * 2u;
-    const float a = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + k)) - c_plus;
-    const float b = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7441u + k)) - c_plus;
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    uint32_t r = *reinterpret_cast<uint32_t*>(&h);
-    const uint32_t m = (miss >> (2 * p)) & 3u;
-    if (m) r = __byte_perm(r, mh2, (m & 1u ? 0x0054u : 0x0010u) | (m & 2u ? 0x7600u : 0x3200u));
-    o[p] = r;
-  }
-}
-
-// Zero the values of samples >= N in a 16-sample group starting at i0 (i0 < N < i0 + 16).
-__device__ __forceinline__ void zero_tail16(uint32_t (&o)[8], int i0, int N) {
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    const int i = i0 + 2 * p;
-    if (i >= N) o[p] = 0u;
-    else if (i + 1 >= N) o[p] &= 0xFFFFu;
-  }
-}
-
 // Shift of a marker row for the split form (see above); 0 when no call is observed.
 template <int ENC>
 __device__ __forceinline__ double row_shift(unsigned long long n, double mean) {
@@ -185,9 +145,9 @@ template <int ENC, int PREC>
 __global__ void __launch_bounds__(kWarps * 32) k_decode(
     const uint8_t* __restrict__ G, long long ldg, int N, long long M,
     const uint32_t* __restrict__ miss, long long ldm, void* __restrict__ Ahi,
-    float* __restrict__ shift_out, long long lda, int32_t* __restrict__ nobs_out,
-    long long* __restrict__ S_out, long long* __restrict__ S2_out, double* __restrict__ mean_out,
-    double* __restrict__ gc2_out) {
+    float* __restrict__ shift_out, uint32_t* __restrict__ mh_out, long long lda,
+    int32_t* __restrict__ nobs_out, long long* __restrict__ S_out, long long* __restrict__ S2_out,
+    double* __restrict__ mean_out, double* __restrict__ gc2_out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long j = (long long)blockIdx.x * kWarps + warp;
   if (j >= M) return;
@@ -207,15 +167,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_decode(
       gc2_out[j] = n ? (double)num / dn : __longlong_as_double(0x7ff8000000000000ll);
     }
   }
-  // pass 2: operand row
+  // pass 2: operand row (skipped when Ahi is NULL: the statistics and the split form's
+  // per-row shift and missing value only, for the contraction that decodes in its producer)
   const double m_imp = n ? mean : 0.0;
   const long long steps = lda >> 3;
   if (PREC == TG_PREC_SPLIT_BF16) {
     const double c = row_shift<ENC>(n, mean);
-    if (lane == 0 && shift_out) shift_out[j] = (float)c;
     const float cf = (float)c;  // exact: a multiple of 2^-7 in [0, 2] or an integer in [0, 255]
     const __nv_bfloat16 mh = __double2bfloat16(m_imp - c);
     const uint32_t mhu = (uint32_t)__bfloat16_as_ushort(mh);
+    if (lane == 0 && shift_out) shift_out[j] = cf;
+    if (lane == 0 && mh_out) mh_out[j] = mhu;
+    if (!Ahi) return;
     uint4* ah = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(Ahi) + j * lda);
     const long long groups = lda >> 4;  // 16 samples each
     if (ENC == TG_ENC_2BIT) {
@@ -416,21 +379,22 @@ __global__ void __launch_bounds__(kRowThreads, GPT <= 6 ? 4 : 2) k_decode_rows(
 
 template <int ENC, int PREC>
 cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32_t* missing,
-               int64_t ldm, void* Ahi, float* shift, int64_t lda, int32_t* nobs, int64_t* S,
-               int64_t* S2, double* mean, double* gc2, cudaStream_t st) {
+               int64_t ldm, void* Ahi, float* shift, uint32_t* mh, int64_t lda, int32_t* nobs,
+               int64_t* S, int64_t* S2, double* mean, double* gc2, cudaStream_t st) {
   // dosage rows (N bytes) take the block-per-row kernel; 2-bit rows are small enough that
-  // the warp-per-row kernel's second read hits in L2, and it measured faster for them
+  // the warp-per-row kernel's second read hits in L2, and it measured faster for them. The
+  // statistics-only form (Ahi NULL) reads each row once in the warp-per-row kernel.
   if constexpr (ENC == TG_ENC_U8_DOSAGE && PREC == TG_PREC_SPLIT_BF16) {
     __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(Ahi);
     long long* S64 = reinterpret_cast<long long*>(S);
     long long* S264 = reinterpret_cast<long long*>(S2);
-    if (N <= kRowThreads * 6 * 16) {
+    if (A && N <= kRowThreads * 6 * 16) {
       k_decode_rows<ENC, 6><<<(unsigned)M, kRowThreads, 0, st>>>(G, ldg, (int)N, missing, ldm, A,
                                                                  shift, lda, nobs, S64, S264,
                                                                  mean, gc2);
       return cudaGetLastError();
     }
-    if (N <= kRowThreads * 12 * 16) {
+    if (A && N <= kRowThreads * 12 * 16) {
       k_decode_rows<ENC, 12><<<(unsigned)M, kRowThreads, 0, st>>>(G, ldg, (int)N, missing, ldm, A,
                                                                   shift, lda, nobs, S64, S264,
                                                                   mean, gc2);
@@ -439,7 +403,7 @@ cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32
   }
   const unsigned grid = (unsigned)((M + kWarps - 1) / kWarps);
   k_decode<ENC, PREC><<<grid, kWarps * 32, 0, st>>>(
-      G, ldg, (int)N, M, missing, ldm, Ahi, shift, lda, nobs, reinterpret_cast<long long*>(S),
+      G, ldg, (int)N, M, missing, ldm, Ahi, shift, mh, lda, nobs, reinterpret_cast<long long*>(S),
       reinterpret_cast<long long*>(S2), mean, gc2);
   return cudaGetLastError();
 }
@@ -448,17 +412,18 @@ cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32
 
 cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,
                           const uint32_t* missing, int64_t ldm, int precision, void* Ahi,
-                          float* shift, int64_t lda, int32_t* nobs, int64_t* S, int64_t* S2,
-                          double* mean, double* gc2, cudaStream_t st) {
+                          float* shift, uint32_t* mh, int64_t lda, int32_t* nobs, int64_t* S,
+                          int64_t* S2, double* mean, double* gc2, cudaStream_t st) {
   if (M == 0) return cudaSuccess;
+  if (!Ahi && precision != TG_PREC_SPLIT_BF16) return cudaErrorInvalidValue;
   if (encoding == TG_ENC_2BIT) {
     return precision == TG_PREC_SPLIT_BF16
-               ? go<TG_ENC_2BIT, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, shift, lda, nobs, S, S2, mean, gc2, st)
-               : go<TG_ENC_2BIT, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, shift, lda, nobs, S, S2, mean, gc2, st);
+               ? go<TG_ENC_2BIT, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, shift, mh, lda, nobs, S, S2, mean, gc2, st)
+               : go<TG_ENC_2BIT, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, shift, mh, lda, nobs, S, S2, mean, gc2, st);
   }
   return precision == TG_PREC_SPLIT_BF16
-             ? go<TG_ENC_U8_DOSAGE, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, shift, lda, nobs, S, S2, mean, gc2, st)
-             : go<TG_ENC_U8_DOSAGE, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, shift, lda, nobs, S, S2, mean, gc2, st);
+             ? go<TG_ENC_U8_DOSAGE, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, shift, mh, lda, nobs, S, S2, mean, gc2, st)
+             : go<TG_ENC_U8_DOSAGE, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, shift, mh, lda, nobs, S, S2, mean, gc2, st);
 }
 
 }  // namespace tg

@@ -9,6 +9,9 @@
 // Persistent kernel, one CTA per SM, 384 threads (3 warpgroups), warp-specialised:
 //   warp 0 lane 0  TMA producer: 128x32 A tiles and 256x32 B tiles (64-byte swizzle) into a
 //                  ring of shared-memory stages, completion tracked by mbarrier transaction bytes
+//   warps 2, 3     with packed genotypes instead of a decoded operand (OPA_2BIT / OPA_U8): the
+//                  decoders, which expand each A tile from the packed rows (tc_common.cuh) and
+//                  join the stage's full barrier
 //   warp 1 lane 0  MMA issuer: per 32-wide K step, 2 x 2 tcgen05.mma 128x256x16 into an
 //                  FP32 accumulator in TMEM
 //   warps 4..11    epilogue: tcgen05.ld of the accumulator (thread = marker row, each warp one
@@ -35,19 +38,24 @@ namespace {
 
 using namespace tcx;
 
+template <int OPA>
 struct Cfg {
-  static constexpr int kStageBytes = A_BYTES + 2 * B_BYTES;  // 40 KB
+  // A, B_hi, B_lo and (when decoding here) the CTA's packed rows: 40 KB (+ 2 or 4 KB)
+  static constexpr int kStageBytes = A_BYTES + 2 * B_BYTES + DecCfg<OPA>::kPackBytes;
   static constexpr int kStages = 5;
   static constexpr int kBarBytes = 256;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;  // + alignment slack
 };
 
+template <int OPA>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmBhi,
               const __grid_constant__ CUtensorMap tmBlo, int num_kb, int n_mt, int n_nt, int bn,
-              int group_m, long long spin_ns, EpiParams ep) {
+              int group_m, long long spin_ns, EpiParams ep,
+              const __grid_constant__ DecodeArgs da) {
   // bn = B rows per tile: 256 for the phenotype panel, 64 for the covariate projection
-  using C = Cfg;
+  using C = Cfg<OPA>;
+  constexpr bool kFused = OPA != OPA_TMA;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -59,18 +67,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto cfull_bar = [&](int a) { return bars + 8u * (2 * S + a); };
   auto cempty_bar = [&](int a) { return bars + 8u * (2 * S + 2 + a); };
   const uint32_t drain_bar = bars + 8u * (2 * S + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * C::kStageBytes + 8 * (2 * S + 5));
+  auto pfull_bar = [&](int s) { return bars + 8u * (2 * S + 5 + s); };  // packed rows landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * C::kStageBytes + 8 * (3 * S + 5));
+  static_assert(8 * (3 * S + 5) + 8 <= C::kBarBytes, "barrier area");
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   auto sA = [&](int s) { return base + s * C::kStageBytes; };
   auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
   auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + B_BYTES; };
+  auto sPk = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * B_BYTES; };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full_bar(s), 1);
+      mbar_init(full_bar(s), kFused ? 1 + kDecThreads / 32 : 1);  // + one arrival per decoder warp
       mbar_init(empty_bar(s), 1);
+      mbar_init(pfull_bar(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(cfull_bar(a), 1);
@@ -94,7 +106,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
   const int num_tiles = n_mt * n_nt;
   if (warp < 4) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kLow));
     if (warp == 0 && lane == 0) {
     // ------------------------------------------------------------ TMA producer
     int stage = 0;
@@ -106,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
       tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
-      const uint32_t bytes = A_BYTES + 2u * (uint32_t)bn * (TBK * 2);
+      const uint32_t bytes = (kFused ? 0u : (uint32_t)A_BYTES) + 2u * (uint32_t)bn * (TBK * 2);
       for (int kb = 0; kb < num_kb; ++kb) {
         if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, spin_ns, ep.status)) {
           ok = false;
@@ -114,7 +126,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_expect_tx(full_bar(stage), bytes);
         armed[stage] = (int)phase;
-        tma_load_2d(&tmAhi, sA(stage), full_bar(stage), kb * TBK, mt * TBM);
+        if (!kFused) tma_load_2d(&tmAhi, sA(stage), full_bar(stage), kb * TBK, mt * TBM);
+        if (kFused) {
+          mbar_expect_tx(pfull_bar(stage), (uint32_t)DecCfg<OPA>::kPackBytes);
+          tma_load_2d(&da.tmG, sPk(stage), pfull_bar(stage), dec_box_x<OPA>(kb), mt * TBM);
+        }
         tma_load_2d(&tmBhi, sBhi(stage), full_bar(stage), kb * TBK, nt * bn);
         tma_load_2d(&tmBlo, sBlo(stage), full_bar(stage), kb * TBK, nt * bn);
         if (++stage == S) {
@@ -125,7 +141,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // copies still in flight land before the CTA leaves (bounded)
     for (int s = 0; s < S; ++s)
-      if (armed[s] >= 0) mbar_wait(full_bar(s), (uint32_t)armed[s], abort_flag, spin_ns, ep.status);
+      if (armed[s] >= 0) {
+        if (kFused) mbar_wait(pfull_bar(s), (uint32_t)armed[s], abort_flag, spin_ns, ep.status);
+        mbar_wait(full_bar(s), (uint32_t)armed[s], abort_flag, spin_ns, ep.status);
+      }
     } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     // Each chunk of kChunkKB K blocks starts a fresh accumulator (no chained accumulation
@@ -174,9 +193,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     // every product issued so far completes before TMEM is released (bounded)
     tc_commit(drain_bar);
     mbar_wait(drain_bar, 0u, abort_flag, spin_ns, ep.status);
+    } else if (kFused && warp >= 2) {
+    // ------------------------------------------------------------ decoders (warps 2, 3)
+    const int t = threadIdx.x - 64;  // rows t and t + 64 of each A tile
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      int mt, nt;
+      tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
+      const long long r0 = (long long)mt * TBM + t;
+      const uint2 k0 = dec_row_consts<OPA>(da, r0), k1 = dec_row_consts<OPA>(da, r0 + 64);
+      for (int kb = 0; kb < num_kb; ++kb) {
+        if (!mbar_wait(pfull_bar(stage), phase, abort_flag, spin_ns, ep.status)) {
+          ok = false;
+          break;
+        }
+        dec_expand_store<OPA>(sPk(stage), k0, r0 < da.M, t, kb, da.N, sA(stage));
+        dec_expand_store<OPA>(sPk(stage), k1, r0 + 64 < da.M, t + 64, kb, da.N, sA(stage));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMA
+        __syncwarp();
+        if (lane == 0) mbar_arrive(full_bar(stage));
+        if (++stage == S) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
     }
   } else {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kHigh));
     // ------------------------------------------------------------ epilogue
     // 8 warps: (TMEM lane quarter, column half) pairs; FP32 running totals in registers.
     const int quarter = warp & 3;
@@ -257,12 +303,15 @@ __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, u
   }
 }
 
+template <int OPA>
 cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* bl, int64_t K,
-               const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st) {
-  static bool attr_set = false;  // per process; the attribute is per function
+               const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st,
+               const DecodeArgs& da) {
+  static bool attr_set = false;  // per process and instantiation; the attribute is per function
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_scan<OPA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<OPA>::kSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -271,8 +320,8 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* b
   const int n_nt = (ep.P + bn - 1) / bn;
   const int tiles = n_mt * n_nt;
   const int grid = tiles < sm_count ? tiles : sm_count;
-  k_tc_scan<<<grid, kThreads, Cfg::kSmem, st>>>(*a, *bh, *bl, (int)(K / TBK), n_mt, n_nt, bn,
-                                                group_m, spin_ns, ep);
+  k_tc_scan<OPA><<<grid, kThreads, Cfg<OPA>::kSmem, st>>>(*a, *bh, *bl, (int)(K / TBK), n_mt, n_nt,
+                                                          bn, group_m, spin_ns, ep, da);
   return cudaGetLastError();
 }
 
@@ -280,10 +329,15 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* b
 
 cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                            const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
-                           long long spin_ns, cudaStream_t st, int group_m) {
+                           long long spin_ns, cudaStream_t st, int group_m, const DecodeArgs* dec,
+                           int encoding) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   if (K % TBK || group_m < 1) return cudaErrorInvalidValue;
-  return go(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st);
+  if (!dec) return go<OPA_TMA>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{});
+  if (dec->M != ep.M) return cudaErrorInvalidValue;
+  if (encoding == TG_ENC_2BIT)
+    return go<OPA_2BIT>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
+  return go<OPA_U8>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
 }
 
 cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,

@@ -14,6 +14,9 @@
 //   warp 1 lane 0 (leader only) MMA issuer; commits are multicast to both CTAs' barriers
 //   warps 4..11 (both CTAs)     epilogue on the local 128 rows; the drained signal goes to
 //                               the leader's chunk-empty barrier (16 arrivals: 8 per CTA)
+//   warps 2, 3 (both CTAs)      with packed genotypes (OPA_2BIT / OPA_U8): decoders of the
+//                               local 128 A rows (tc_common.cuh); each warp arrives once on the
+//                               leader's full barrier after its stores
 // Accumulation is chunked exactly as in k_tc.cu (fresh accumulator every 1024 samples, FP32
 // totals in registers). Every wait is bounded; a timeout raises the abort flag in both CTAs.
 #include <cuda.h>
@@ -30,11 +33,15 @@ using namespace tcx;
 
 constexpr int HB_BYTES = 128 * TBK * 2;  // one CTA's half of a B tile: 8 KB
 
+template <int OPA>
 struct Cfg2 {
-  static constexpr int kStageBytes = A_BYTES + 2 * HB_BYTES;  // 24 KB
+  // A, this CTA's halves of B_hi and B_lo and (when decoding here) its packed rows:
+  // 24 KB (+ 2 or 4 KB)
+  static constexpr int kStageBytes = A_BYTES + 2 * HB_BYTES + DecCfg<OPA>::kPackBytes;
   static constexpr int kStages = 8;
   static constexpr int kBarBytes = 256;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;
+  static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
 constexpr uint32_t kIdesc2 = idesc_bf16_m(256, 256);
@@ -117,11 +124,14 @@ __device__ __forceinline__ void tile_coord2(int tile, int n_mp, int n_nt, int gr
   nt = idx / gm;
 }
 
+template <int OPA>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     k_tc2_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmBhi,
                const __grid_constant__ CUtensorMap tmBlo, int num_kb, int n_mt, int n_nt,
-               int group_p, long long spin_ns, EpiParams ep) {
-  using C = Cfg2;
+               int group_p, long long spin_ns, EpiParams ep,
+              const __grid_constant__ DecodeArgs da) {
+  using C = Cfg2<OPA>;
+  constexpr bool kFused = OPA != OPA_TMA;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -133,12 +143,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   auto cfull_bar = [&](int a) { return bars + 8u * (2 * S + a); };
   auto cempty_bar = [&](int a) { return bars + 8u * (2 * S + 2 + a); };
   const uint32_t drain_bar = bars + 8u * (2 * S + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * C::kStageBytes + 8 * (2 * S + 5));
+  auto pfull_bar = [&](int s) { return bars + 8u * (2 * S + 5 + s); };  // local packed rows landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * C::kStageBytes + 8 * (3 * S + 5));
+  static_assert(8 * (3 * S + 5) + 8 <= C::kBarBytes, "barrier area");
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   auto sA = [&](int s) { return base + s * C::kStageBytes; };
   auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
   auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + HB_BYTES; };
+  auto sPk = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * HB_BYTES; };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
@@ -146,8 +159,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   const uint32_t peer_abort = map_to_rank(smem_u32((const void*)abort_flag), rank ^ 1u);
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(full_bar(s), 1);
+      // the leader's full barrier: its own arrive.expect_tx, plus one arrival per decoder warp
+      // of both CTAs when the A tiles are decoded here
+      mbar_init(full_bar(s), kFused ? 1 + 2 * (kDecThreads / 32) : 1);
       mbar_init(empty_bar(s), 1);
+      mbar_init(pfull_bar(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(cfull_bar(a), 1);
@@ -181,7 +197,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   };
 
   if (warp < 4) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsLow));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kLow));
     if (warp == 0 && lane == 0) {
       // ---------------------------------------------------------- TMA producer (both CTAs)
       int stage = 0;
@@ -194,7 +210,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         int mp, nt;
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
         const int mt0 = 2 * mp;
-        const uint32_t pair_bytes = 2u * (A_BYTES + 2 * HB_BYTES);
+        const uint32_t pair_bytes = 2u * ((kFused ? 0u : (uint32_t)A_BYTES) + 2 * HB_BYTES);
         const int arow = (mt0 + (int)rank) * TBM;
         const int brow = nt * TBN + (int)rank * 128;
         for (int kb = 0; kb < num_kb; ++kb) {
@@ -206,12 +222,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          if (leader) {
-            mbar_expect_tx(full_bar(stage), pair_bytes);
-            armed[stage] = (int)phase;
-          }
+          if (leader) mbar_expect_tx(full_bar(stage), pair_bytes);
+          armed[stage] = (int)phase;
           const uint32_t fb = map_to_rank(full_bar(stage), 0u);
-          tma_load_2d_pair(&tmAhi, sA(stage), fb, kb * TBK, arow);
+          if (!kFused) tma_load_2d_pair(&tmAhi, sA(stage), fb, kb * TBK, arow);
+          if (kFused) {  // this CTA's packed rows, completing on its own barrier
+            mbar_expect_tx(pfull_bar(stage), (uint32_t)DecCfg<OPA>::kPackBytes);
+            tma_load_2d(&da.tmG, sPk(stage), pfull_bar(stage), dec_box_x<OPA>(kb), arow);
+          }
           tma_load_2d_pair(&tmBhi, sBhi(stage), fb, kb * TBK, brow);
           tma_load_2d_pair(&tmBlo, sBlo(stage), fb, kb * TBK, brow);
           if (++stage == S) {
@@ -220,10 +238,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           }
         }
       }
-      // the leader's armed stages complete only when both CTAs' copies have landed (bounded)
-      if (leader)
-        for (int s = 0; s < S; ++s)
-          if (armed[s] >= 0) mbar_wait(full_bar(s), (uint32_t)armed[s], abort_flag, spin_ns, ep.status);
+      // the leader's armed stages complete only when both CTAs' copies have landed; the packed
+      // rows of every CTA land in its own barrier (bounded)
+      for (int s = 0; s < S; ++s) {
+        if (armed[s] < 0) continue;
+        if (kFused) mbar_wait(pfull_bar(s), (uint32_t)armed[s], abort_flag, spin_ns, ep.status);
+        if (leader) mbar_wait(full_bar(s), (uint32_t)armed[s], abort_flag, spin_ns, ep.status);
+      }
     } else if (warp == 1 && lane == 0 && leader) {
       // ---------------------------------------------------------- MMA issuer (leader)
       int stage = 0;
@@ -268,9 +289,38 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       }
       tc2_commit_local(drain_bar);
       mbar_wait(drain_bar, 0u, abort_flag, spin_ns, ep.status);
+    } else if (kFused && warp >= 2) {
+      // ---------------------------------------------------------- decoders (both CTAs)
+      const int t = threadIdx.x - 64;  // rows t and t + 64 of this CTA's A tile
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
+        int mp, nt;
+        tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
+        const long long r0 = (long long)(2 * mp + (int)rank) * TBM + t;
+        const uint2 k0 = dec_row_consts<OPA>(da, r0), k1 = dec_row_consts<OPA>(da, r0 + 64);
+        for (int kb = 0; kb < num_kb; ++kb) {
+          if (!wait(pfull_bar(stage), phase)) {
+            ok = false;
+            break;
+          }
+          dec_expand_store<OPA>(sPk(stage), k0, r0 < da.M, t, kb, da.N, sA(stage));
+          dec_expand_store<OPA>(sPk(stage), k1, r0 + 64 < da.M, t + 64, kb, da.N, sA(stage));
+          // the leader's tensor core reads this CTA's tile: make the stores visible to the
+          // async proxy at cluster scope before signalling
+          asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(map_to_rank(full_bar(stage), 0u));
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
     }
   } else {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsHigh));
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kHigh));
     // ------------------------------------------------------------ epilogue (both CTAs)
     const int quarter = warp & 3;
     const int half = (warp - 4) >> 2;
@@ -329,12 +379,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   }
 }
 
+template <int OPA>
 cudaError_t go2(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* bl, int64_t K,
-                const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st) {
+                const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st,
+                const DecodeArgs& da) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc2_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg2::kSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_tc2_scan<OPA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg2<OPA>::kSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -343,8 +396,8 @@ cudaError_t go2(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* 
   const int tiles = ((n_mt + 1) / 2) * n_nt;
   const int pairs = tiles < sm_count / 2 ? tiles : sm_count / 2;
   const int group_p = group_m / 2 > 0 ? group_m / 2 : 1;
-  k_tc2_scan<<<2 * pairs, kThreads, Cfg2::kSmem, st>>>(*a, *bh, *bl, (int)(K / TBK), n_mt, n_nt,
-                                                      group_p, spin_ns, ep);
+  k_tc2_scan<OPA><<<2 * pairs, kThreads, Cfg2<OPA>::kSmem, st>>>(
+      *a, *bh, *bl, (int)(K / TBK), n_mt, n_nt, group_p, spin_ns, ep, da);
   return cudaGetLastError();
 }
 
@@ -352,10 +405,16 @@ cudaError_t go2(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* 
 
 cudaError_t launch_tc2_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                             const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
-                            long long spin_ns, cudaStream_t st, int group_m) {
+                            long long spin_ns, cudaStream_t st, int group_m, const DecodeArgs* dec,
+                            int encoding) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   if (K % TBK || group_m < 1) return cudaErrorInvalidValue;
-  return go2(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st);
+  if (!dec)
+    return go2<OPA_TMA>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{});
+  if (dec->M != ep.M) return cudaErrorInvalidValue;
+  if (encoding == TG_ENC_2BIT)
+    return go2<OPA_2BIT>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
+  return go2<OPA_U8>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
 }
 
 }  // namespace tg

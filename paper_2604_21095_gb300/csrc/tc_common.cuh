@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 
 #include "device.cuh"
+#include "genotype.cuh"
 #include "internal.h"
 
 namespace tg {
@@ -16,14 +17,19 @@ constexpr int TBM = 128, TBN = 256, TBK = 32;  // TBK bf16 = 64 bytes = one swiz
 constexpr int A_BYTES = TBM * TBK * 2;         // 8 KB
 constexpr int B_BYTES = TBN * TBK * 2;         // 16 KB
 constexpr int kEpiWarps = 8;
-// Three warpgroups: warpgroup 0 = producer warp, MMA warp and two idle warps; warpgroups 1-2 =
-// the 8 epilogue warps. At launch every thread gets 168 registers (384 x 168 = 64,512); then
+// Three warpgroups: warpgroup 0 = producer warp, MMA warp and two decoder warps (idle when the
+// A operand comes by TMA); warpgroups 1-2 = the 8 epilogue warps. At launch every thread gets 168 registers (384 x 168 = 64,512); then
 // warpgroup 0 gives registers back (56 each) and the epilogue warpgroups take them
 // (224 each): 128 x 56 + 256 x 224 = 64,512, the launch total, so the increase cannot stall.
+// When warps 2-3 decode the A operand (see below) they need more: 64 / 216
+// (128 x 64 + 256 x 216 = 63,488).
 constexpr int kThreads = 384;
-constexpr int kRegsLow = 56;
-constexpr int kRegsHigh = 224;
-static_assert(128 * kRegsLow + 256 * kRegsHigh <= kThreads * 168, "register split exceeds launch");
+template <int OPA>
+struct RegSplit {
+  static constexpr int kLow = OPA == 0 ? 56 : 64;
+  static constexpr int kHigh = OPA == 0 ? 224 : 216;
+  static_assert(128 * kLow + 256 * kHigh <= kThreads * 168, "register split exceeds launch");
+};
 constexpr int kTmemCols = 512;                 // two 128 x 256 FP32 chunk accumulators
 constexpr int kChunkKB = 32;                   // K blocks per accumulation chunk (1024 samples)
 constexpr int kGroupM = 16;                    // default raster: 16 m-tiles per group
@@ -142,6 +148,82 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float v[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------ decode in the producer
+// Operand kinds of the contraction kernels: A by TMA from a decoded operand in HBM, or decoded
+// from packed genotypes (OPA_2BIT, OPA_U8). In the second case the producer thread also loads,
+// by TMA, the CTA's 128 packed rows for each K block into the stage (a box of 32 bytes per row
+// for dosages, one K block; 16 bytes for 2-bit calls, two K blocks of which the stage uses one
+// half), completing on the stage's packed-full barrier; the decoder warps (warps 2 and 3, 64
+// threads, two rows each) wait on it, expand the rows to the centred split operand
+// (genotype.cuh), store each row's four 16-byte chunks where the TMA's 64-byte swizzle would
+// put them (chunk j of row r at r * 64 + 16 * (j ^ ((r >> 1) & 3))) and join the stage's full
+// barrier. The packed load is issued after the stage's empty barrier, so a completed
+// packed-full barrier also means the A tile may be overwritten.
+enum { OPA_TMA = 0, OPA_2BIT = 1, OPA_U8 = 2 };
+constexpr int kDecThreads = 64;
+template <int OPA>
+struct DecCfg {
+  static constexpr int kBox = OPA == OPA_U8 ? 32 : 16;  // packed bytes per row in a stage
+  static constexpr int kPackBytes = OPA == OPA_TMA ? 0 : TBM * kBox;
+};
+
+// Per-row constants of the expansion: 2-bit {lut0, lut1}, dosage {2^23 + c as float bits, mh2}.
+template <int OPA>
+__device__ __forceinline__ uint2 dec_row_consts(const DecodeArgs& da, long long row) {
+  if (row >= da.M) return make_uint2(0u, 0u);
+  const float c = da.shift[row];
+  const uint32_t mh = da.mh[row] & 0xFFFFu;
+  if (OPA == OPA_2BIT)
+    return make_uint2(bf16_bits(2.0f - c) | (mh << 16), bf16_bits(1.0f - c) | (bf16_bits(-c) << 16));
+  return make_uint2(__float_as_uint(8388608.0f + c), mh | (mh << 16));
+}
+
+// Expand row r's K block kb from the stage's packed rows and store it, swizzled, into the A
+// tile; one 16-sample half (two 16-byte chunks) at a time.
+template <int OPA>
+__device__ __forceinline__ void dec_expand_store(uint32_t packed, uint2 k, bool row_ok, int r,
+                                                 int kb, int N, uint32_t a_tile) {
+  constexpr int BOX = DecCfg<OPA>::kBox;
+  const uint32_t src = packed + (uint32_t)(r * BOX) + (OPA == OPA_2BIT ? 8u * (uint32_t)(kb & 1) : 0u);
+  const uint32_t row_base = a_tile + (uint32_t)r * 64u;
+  const uint32_t sw = (uint32_t)((r >> 1) & 3);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t o[8];
+    if (OPA == OPA_2BIT) {
+      uint32_t w;
+      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(w) : "r"(src + 4 * h));
+      split16_2bit(w, k.x, k.y, o);
+    } else {
+      uint4 v;
+      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                   : "r"(src + 16 * h));
+      split16_u8(v, __uint_as_float(k.x), 0u, k.y, o);
+    }
+    const int i0 = kb * TBK + 16 * h;
+    if (!row_ok) {
+#pragma unroll
+      for (int p = 0; p < 8; ++p) o[p] = 0u;
+    } else if (i0 + 16 > N) {
+      zero_tail16(o, i0, N);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const uint32_t j = (uint32_t)(2 * h + c);
+      asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(row_base + ((j ^ sw) << 4)),
+                   "r"(o[4 * c]), "r"(o[4 * c + 1]), "r"(o[4 * c + 2]), "r"(o[4 * c + 3])
+                   : "memory");
+    }
+  }
+}
+
+// x coordinate (bytes) of the packed box of K block kb: 16-byte aligned, as TMA requires.
+template <int OPA>
+__device__ __forceinline__ int dec_box_x(int kb) {
+  return OPA == OPA_U8 ? kb * 32 : (kb >> 1) * 16;
 }
 
 // Raster: tiles go down group_m m-tiles (markers) first, then across the n-tiles (phenotypes),

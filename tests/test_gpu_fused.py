@@ -1,0 +1,70 @@
+"""Decoding the genotypes inside the contraction kernels (tg_set_fused_decode, for split-form
+2-bit blocks and unmasked dosage blocks) against the default path that first writes the
+decoded operand to device memory: every output must be bit-identical, for both kernels (CTA
+pairs and one CTA per tile), both encodings, sample counts that end inside a K block and blocks
+whose last m-tiles are partly or wholly past M. The decoded-operand path itself is checked
+against the oracle by the scan tests."""
+import numpy as np
+import pytest
+
+import paper_2604_21095_gb300 as tg
+import synth
+from scan_util import run_scan
+
+pytestmark = pytest.mark.gpu
+
+
+def _outputs_equal(a, b):
+    for k in ("beta", "se", "t", "mlog10p", "best_key", "norm2", "nobs", "mean"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    key = lambda r: sorted(tuple(h) for h in r["hits"].tolist())
+    assert a["n_hits"] == b["n_hits"] and key(a) == key(b)
+
+
+@pytest.mark.parametrize("encoding", ["2bit", "u8"])
+@pytest.mark.parametrize("kernel", ["pair", "single"])
+@pytest.mark.parametrize("N,M,P", [(2000, 1000, 300), (1999, 777, 513), (257, 300, 40),
+                                   (23000, 520, 600)])
+def test_fused_decode_is_bit_identical(encoding, kernel, N, M, P):
+    w = synth.Workload(f"fused_{encoding}_{N}_{M}_{P}", N=N, M=M, P=P, n_cov=4,
+                       encoding=encoding, missing=0.03 if encoding == "2bit" else 0.0, seed=29,
+                       block=M, causal_per_pheno=1)
+    pan = synth.make_panel(w)
+    G = synth.make_block(w, 0)["G"].cuda()
+    ctx = tg.tg_create(0)
+    panel = tg.tg_prepare_panel(ctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+    try:
+        tg.tg_set_tuning(ctx, M, kernel, 4)
+        res = {}
+        for fused in (True, False):
+            tg.tg_set_fused_decode(ctx, fused)
+            res[fused] = run_scan(ctx, panel, G, N, P, encoding, "split", full=True,
+                                  hit_mlog10p=3.0, marker_offset=5)
+            assert res[fused]["status"] == tg.TG_OK
+        assert res[True]["n_hits"] > 0
+        _outputs_equal(res[True], res[False])
+    finally:
+        tg.tg_panel_free(panel)
+        tg.tg_destroy(ctx)
+
+
+def test_masked_dosage_blocks_use_the_decoded_operand():
+    """A dosage block with a missing mask is scanned through the decoded operand whatever the
+    setting; the result does not depend on it."""
+    w = synth.Workload("fused_masked", N=1500, M=600, P=200, n_cov=2, encoding="u8",
+                       missing=0.0, seed=31, block=600, causal_per_pheno=1)
+    pan = synth.make_panel(w)
+    G = synth.make_block(w, 0)["G"].cuda()
+    miss = synth.missing_words(31, 0, w.M, w.N, 0.05).cuda()
+    ctx = tg.tg_create(0)
+    panel = tg.tg_prepare_panel(ctx, pan["Yt"].cuda(), w.N, w.P, pan["cov_t"].cuda())
+    try:
+        res = {}
+        for fused in (True, False):
+            tg.tg_set_fused_decode(ctx, fused)
+            res[fused] = run_scan(ctx, panel, G, w.N, w.P, "u8", "split", full=True,
+                                  hit_mlog10p=3.0, missing=miss)
+        _outputs_equal(res[True], res[False])
+    finally:
+        tg.tg_panel_free(panel)
+        tg.tg_destroy(ctx)
