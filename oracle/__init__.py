@@ -14,7 +14,8 @@ nothing from them. It is plain NumPy in float64, slow and direct:
 * pvalue.py  - two-sided Student-t p-values through the regularised incomplete beta
                function, evaluated in log space (Section 2.2: t converted to P values).
 * scan.py    - the whole scan: statistics for every (marker, phenotype), hits above a
-               -log10 p threshold and the best marker per phenotype.
+               -log10 p threshold and the best marker per phenotype; a panel may be
+               prepared on the subset of samples its phenotypes are observed on.
 
 Every function is pinned by tests under tests/ against closed forms, brute force on
 tiny inputs, invariants or published table values; none is marked "parity unpinned".

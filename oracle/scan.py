@@ -22,17 +22,31 @@ from .panel import design_matrix, householder_basis, residualise
 from .pvalue import mlog10p_from_r, mlog10p_from_t
 
 
-def prepare_panel(Y: np.ndarray, C: np.ndarray | None) -> dict:
-    """Y: [N][P] phenotypes; C: [N][n_cov] covariates (intercept not included)."""
+def prepare_panel(Y: np.ndarray, C: np.ndarray | None, samples: np.ndarray | None = None) -> dict:
+    """Y: [N][P] phenotypes; C: [N][n_cov] covariates (intercept not included).
+
+    samples: optional bool [N], the samples these phenotypes are observed on (a group of
+    phenotypes sharing one missingness pattern). Reading (the paper has no missing
+    phenotypes): the panel is then Eq. 1 and the standardisation applied to those rows only,
+    X = [1, C] restricted to them, and every test below uses only those rows (df = N_S - q - 1);
+    phenotype values outside them are never read. Genotype imputation stays a property of the
+    marker: a missing call is imputed with the marker's mean over all N samples.
+    """
     Y = np.asarray(Y, dtype=np.float64)
     N = Y.shape[0]
-    X = design_matrix(C, N)
+    rows = None if samples is None else np.asarray(samples, dtype=bool)
+    if rows is not None:
+        assert rows.shape == (N,)
+        Y = Y[rows]
+        C = None if C is None or np.size(C) == 0 else np.asarray(C, dtype=np.float64).reshape(N, -1)[rows]
+    NS = Y.shape[0]
+    X = design_matrix(C, NS)
     Q, kept = householder_basis(X)
     Yres, s, Yt = residualise(Y, Q)
     q = Q.shape[1]
-    return {"N": N, "P": Y.shape[1], "X": X, "Xk": X[:, kept], "kept": kept, "Q": Q, "q": q,
-            "df": N - q - 1, "Y": Y, "Yres": Yres, "s": s, "Yt": Yt,
-            "pheno_ok": np.isfinite(Yt).all(axis=0)}
+    return {"N": N, "NS": NS, "rows": rows, "P": Y.shape[1], "X": X, "Xk": X[:, kept],
+            "kept": kept, "Q": Q, "q": q, "df": NS - q - 1, "Y": Y, "Yres": Yres, "s": s,
+            "Yt": Yt, "pheno_ok": np.isfinite(Yt).all(axis=0)}
 
 
 def decode(G: np.ndarray, encoding: str, N: int, missing_words=None) -> dict:
@@ -61,7 +75,9 @@ def scan(G: np.ndarray, encoding: str, panel: dict, missing_words=None, mode: st
     record and gres2 (|g_res|^2 per marker in allele units; |g_c|^2 in paper mode).
     """
     dec = decode(G, encoding, panel["N"], missing_words)
-    g = dec["g"]
+    g = dec["g"]                       # imputed over all N samples
+    if panel.get("rows") is not None:  # a panel of a sample subset tests those rows only
+        g = g[:, panel["rows"]]
     ok = panel["pheno_ok"]
     out = {"df": panel["df"], "decode": dec}
     if mode == "direct":

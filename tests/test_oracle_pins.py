@@ -215,6 +215,92 @@ def test_intercept_only_is_pearson_and_eq3():
             assert abs(t[j, p] - pear * math.sqrt((N - 2) / (1 - pear ** 2))) < 1e-9
 
 
+# ---------------------------------------------------------------- phenotypes observed on a subset
+
+def _subset_case(seed, N=48, n_cov=2, M=5, P=3, frac=0.7):
+    r = _rng(seed)
+    C = r.standard_normal((N, n_cov))
+    counts = r.integers(0, 3, size=(M, N)).astype(np.int8)
+    miss = r.random((M, N)) < 0.15
+    G = synth.pack_2bit(torch.from_numpy(counts), torch.from_numpy(miss)).numpy()
+    rows = r.random(N) < frac
+    Y = r.standard_normal((N, P)) + 0.4 * counts[0][:, None]
+    return C, G, rows, Y
+
+
+def test_subset_panel_is_ols_on_the_observed_rows_by_lstsq():
+    """The test of a phenotype observed on rows S is the OLS of y_S on [1, C_S, g_S] with the
+    genotype imputed by its mean over all N samples (numpy.linalg.lstsq on the subset)."""
+    C, G, rows, Y = _subset_case(61)
+    N = Y.shape[0]
+    Ynan = Y.copy()
+    Ynan[~rows] = np.nan                       # values outside S are never read
+    panel = oracle.prepare_panel(Ynan, C, rows)
+    assert panel["NS"] == rows.sum() and panel["df"] == rows.sum() - 3 - 1
+    out = oracle.scan(G, "2bit", panel, mode="projected")
+    direct = oracle.scan(G, "2bit", panel, mode="direct")
+    counts, miss = oracle.decode_2bit(G, N)
+    for j in range(G.shape[0]):
+        obs = ~miss[j]
+        g = np.where(miss[j], counts[j][obs].mean(), counts[j]).astype(float)  # all-N mean
+        W = np.column_stack([np.ones(rows.sum()), C[rows], g[rows]])
+        coef, *_ = np.linalg.lstsq(W, Y[rows], rcond=None)
+        resid = Y[rows] - W @ coef
+        df = rows.sum() - W.shape[1]
+        se = np.sqrt((resid ** 2).sum(0) / df * np.linalg.inv(W.T @ W)[-1, -1])
+        assert np.allclose(out["beta"][j], coef[-1], rtol=1e-9, atol=1e-12)
+        assert np.allclose(out["se"][j], se, rtol=1e-9)
+        assert np.allclose(direct["beta"][j], coef[-1], rtol=1e-9, atol=1e-12)
+        assert np.allclose(out["t"][j], coef[-1] / se, rtol=1e-8)
+
+
+def test_subset_panel_full_mask_and_outside_values():
+    C, G, rows, Y = _subset_case(62)
+    N = Y.shape[0]
+    full = oracle.scan(G, "2bit", oracle.prepare_panel(Y, C, np.ones(N, bool)))
+    plain = oracle.scan(G, "2bit", oracle.prepare_panel(Y, C))
+    for k in ("beta", "se", "t", "mlog10p", "r"):   # equal up to BLAS summation order
+        assert np.allclose(full[k], plain[k], rtol=1e-12, atol=1e-15, equal_nan=True), k
+    Y2 = Y.copy()
+    Y2[~rows] = 1e6 * _rng(63).standard_normal(((~rows).sum(), Y.shape[1]))
+    a = oracle.scan(G, "2bit", oracle.prepare_panel(Y, C, rows))
+    b = oracle.scan(G, "2bit", oracle.prepare_panel(Y2, C, rows))
+    for k in ("beta", "se", "t", "mlog10p", "r"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+
+
+def test_subset_panel_imputation_uses_the_all_sample_mean():
+    """A missing call inside S takes the marker's mean over all N observed calls: moving a
+    marker's calls outside S changes the imputed value inside S, and so the statistic."""
+    C, G, rows, Y = _subset_case(64, M=1)
+    N = Y.shape[0]
+    counts, miss = oracle.decode_2bit(G, N)
+    assert (miss[0] & rows).any()
+    counts2 = counts.copy()
+    out_s = np.nonzero(~rows & ~miss[0])[0]
+    counts2[0, out_s] = 2 - counts2[0, out_s]          # change calls outside S only
+    G2 = synth.pack_2bit(torch.from_numpy(counts2.astype(np.int8)), torch.from_numpy(miss)).numpy()
+    panel = oracle.prepare_panel(Y, C, rows)
+    a, b = oracle.scan(G, "2bit", panel), oracle.scan(G2, "2bit", panel)
+    assert counts[0][~miss[0]].mean() != counts2[0][~miss[0]].mean()
+    assert not np.allclose(a["r"], b["r"])
+    # the same pair with the missing calls inside S turned into observed calls of the all-N mean
+    # is not expressible in codes, so check the value directly: g_S at missing calls
+    g = oracle.scan(G, "2bit", panel)["decode"]["g"][0]
+    assert np.allclose(g[miss[0]], counts[0][~miss[0]].mean())
+
+
+def test_subset_panel_paper_form_is_pearson_on_the_subset():
+    C, G, rows, Y = _subset_case(65)
+    panel = oracle.prepare_panel(Y, C, rows)
+    out = oracle.scan(G, "2bit", panel, mode="paper")
+    assert out["df"] == rows.sum() - 2
+    g = out["decode"]["g"][:, rows]
+    for j in range(G.shape[0]):
+        for p in range(Y.shape[1]):
+            assert abs(out["r"][j, p] - np.corrcoef(g[j], panel["Yres"][:, p])[0, 1]) < 1e-12
+
+
 # ---------------------------------------------------------------- the paper's printed form
 
 def test_paper_form_is_pearson_with_residualised_phenotype():
