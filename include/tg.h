@@ -139,6 +139,34 @@ tg_status tg_prepare_panel(tg_ctx* ctx, const float* Y, int64_t ldy, int64_t N, 
                            void* stream);
 
 /* Panel shape: samples, phenotypes, covariate rank q (intercept included), df = N - q - 1. */
+/* The panel of a group of phenotypes observed on a subset S of the N samples (phenotypes that
+ * share one missingness pattern; the paper has no missing phenotypes, this is the reading
+ * taken for them). Eq. 1 and the standardisation are applied to the rows in S only, with
+ * X = [1, C] restricted to S, and every scan of the panel tests the OLS of y_S on
+ * [1, C_S, g_S] (or Eq. 2-3 on S in TG_MODE_PAPER), df = N_S - q - 1 (N_S - 2). A genotype's
+ * missing calls are still imputed with its mean over all N samples.
+ *   Y, ldy, N, P, C, ldc, n_cov: as tg_prepare_panel; phenotype values outside S are never
+ *   read (NaN allowed there), inside S they must be finite.
+ *   samples: device, uint32 [ceil(N/32)], bit i%32 of word i/32 set = sample i in S (bits
+ *   past N ignored); N_S >= 3.
+ * The panel keeps the full sample axis (its arrays are zero outside S), so blocks of all N
+ * samples are scanned against it with tg_scan_block, tg_scan_host and the captured graphs;
+ * tg_scan_block_static rejects it (TG_ERR_UNSUPPORTED). Subset panels concatenate only with
+ * panels of the same subset. Synchronous. */
+tg_status tg_prepare_panel_subset(tg_ctx* ctx, const float* Y, int64_t ldy, int64_t N, int64_t P,
+                                  const double* C, int64_t ldc, int64_t n_cov,
+                                  const uint32_t* samples, tg_panel** out, void* stream);
+
+/* The samples a panel uses: n_used = N_S (N for a panel of all samples) and a borrowed device
+ * pointer to its sample mask (NULL for a panel of all samples). */
+tg_status tg_panel_samples(const tg_panel* panel, int64_t* n_used, const uint32_t** samples);
+
+/* Per-phenotype masks of finite values, the input for grouping phenotypes by missingness:
+ * masks[p * ldm + w] bit b set = Y[p * ldy + 32 w + b] is finite (bits past N are 0).
+ * Y: device float [P][ldy]; masks: device uint32 [P][ldm], ldm >= ceil(N/32). Asynchronous. */
+tg_status tg_phenotype_masks(tg_ctx* ctx, const float* Y, int64_t ldy, int64_t N, int64_t P,
+                             uint32_t* masks, int64_t ldm, void* stream);
+
 tg_status tg_panel_info(const tg_panel* panel, int64_t* N, int64_t* P, int64_t* q, int64_t* df);
 
 /* Borrowed device pointer to Q: double column-major N x q (column k at Q + k*ldq). */

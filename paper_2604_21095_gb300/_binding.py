@@ -79,6 +79,10 @@ _SIGS = {
     "tg_set_tuning": (C.c_int, [_VP, _I64, _I32, _I32]),
     "tg_status_poll": (C.c_int, [_VP, _VP]),
     "tg_set_fused_decode": (C.c_int, [_VP, C.c_int]),
+    "tg_prepare_panel_subset": (C.c_int, [_VP, _VP, _I64, _I64, _I64, _VP, _I64, _I64, _VP,
+                                          C.POINTER(_VP), _VP]),
+    "tg_panel_samples": (C.c_int, [_VP, C.POINTER(_I64), C.POINTER(_VP)]),
+    "tg_phenotype_masks": (C.c_int, [_VP, _VP, _I64, _I64, _I64, _VP, _I64, _VP]),
     "tg_set_profiling": (C.c_int, [_VP, C.c_int]),
     "tg_stage_times": (C.c_int, [_VP, C.POINTER(_D), C.POINTER(_I64), C.c_int]),
     "tg_bounded_wait_test": (C.c_int, [_VP, _VP, _I64, _VP]),
@@ -314,6 +318,29 @@ def tg_set_tuning(ctx, M, kernel: str, group_m: int):
 def tg_status_poll(ctx, stream=None) -> int:
     """Synchronise and return the latched device status (0 = ok); does not raise."""
     return load().tg_status_poll(ctx, _stream(stream))
+
+
+def tg_prepare_panel_subset(ctx, Y, N, P, C_cov, samples, stream=None):
+    """As tg_prepare_panel, for phenotypes observed on the samples whose bits are set in
+    `samples` (int32/uint32 device words [ceil(N/32)])."""
+    out = _VP()
+    n_cov = 0 if C_cov is None else C_cov.shape[0]
+    ldc = N if C_cov is None else _ld(C_cov)
+    _check(load().tg_prepare_panel_subset(ctx, _ptr(Y), _ld(Y), N, P, _ptr(C_cov), ldc, n_cov,
+                                          _ptr(samples), C.byref(out), _stream(stream)))
+    return out
+
+
+def tg_panel_samples(panel):
+    n = _I64()
+    m = _VP()
+    _check(load().tg_panel_samples(panel, C.byref(n), C.byref(m)))
+    return n.value, m.value
+
+
+def tg_phenotype_masks(ctx, Yt, N, P, masks, stream=None):
+    _check(load().tg_phenotype_masks(ctx, _ptr(Yt), _ld(Yt), N, P, _ptr(masks), _ld(masks),
+                                     _stream(stream)))
 
 
 def tg_set_fused_decode(ctx, enable: bool):

@@ -131,12 +131,12 @@ struct StageScope {
 cudaError_t ensure_markers(tg_ctx* c, int64_t M) {
   if (M <= c->cap_m) return cudaSuccess;
   const int64_t cap = round_up(M, MT);
-  dfree(c->nobs); dfree(c->mean); dfree(c->shift); dfree(c->mh); dfree(c->gc2); dfree(c->qg);
+  dfree(c->nobs); dfree(c->mean); dfree(c->shift); dfree(c->mh); dfree(c->gc2s); dfree(c->gc2); dfree(c->qg);
   dfree(c->gres2); dfree(c->rinv); dfree(c->rinv64);
   c->cap_m = 0;
   cudaError_t e;
   if ((e = dalloc(&c->nobs, cap)) || (e = dalloc(&c->mean, cap)) || (e = dalloc(&c->shift, cap)) ||
-      (e = dalloc(&c->mh, cap)) ||
+      (e = dalloc(&c->mh, cap)) || (e = dalloc(&c->gc2s, cap)) ||
       (e = dalloc(&c->gc2, cap)) || (e = dalloc(&c->qg, cap * QCOLS)) ||
       (e = dalloc(&c->gres2, cap)) || (e = dalloc(&c->rinv, cap)) || (e = dalloc(&c->rinv64, cap)))
     return e;
@@ -270,9 +270,14 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
                              kGroupDefault, dec, a.encoding));
     }
   }
+  if (p->samples) {  // a subset panel: |g_c|^2 over its samples
+    StageScope s(c, STAGE_NORM, st, 1);
+    TG_CUDA(launch_subset_stats(a.G, a.ldg, a.encoding, a.N, a.M, a.missing, a.ldm, p->samples,
+                                c->mean, c->gc2s, st));
+  }
   {
     StageScope s(c, STAGE_NORM, st, 1);
-    TG_CUDA(launch_marker_norm(a.M, c->nobs, c->gc2, c->qg, nq, kappa64, c->gres2,
+    TG_CUDA(launch_marker_norm(a.M, c->nobs, p->samples ? c->gc2s : c->gc2, c->qg, nq, kappa64, c->gres2,
                                a.out.marker_norm2, c->rinv, c->rinv64, st));
     if (a.out.marker_nobs)
       TG_CUDA(cudaMemcpyAsync(a.out.marker_nobs, c->nobs, sizeof(int32_t) * a.M,
@@ -344,7 +349,7 @@ namespace tg {
 
 void mode_df(const tg_panel* p, int mode, double* df, double* lnB) {
   if (mode == TG_MODE_PAPER) {
-    *df = (double)(p->N - 2);
+    *df = (double)(p->NS - 2);
     *lnB = p->lnB_paper;
   } else {
     *df = (double)p->df;
@@ -444,7 +449,7 @@ tg_status tg_destroy(tg_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   dfree(c->status); dfree(c->scratch);
-  dfree(c->Ahi); dfree(c->A32); dfree(c->shift); dfree(c->mh);
+  dfree(c->Ahi); dfree(c->A32); dfree(c->shift); dfree(c->mh); dfree(c->gc2s);
   dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
   dfree(c->rinv); dfree(c->rinv64);
   dfree(c->stage_buf[0]); dfree(c->stage_buf[1]);
@@ -478,6 +483,7 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
   p->N = N;
   p->P = P;
   p->n_cov = n_cov;
+  p->NS = N;
   p->Npad = round_up(N, KPAD);
   p->Ppad = round_up(std::max<int64_t>(P, 1), PPAD);
   const int64_t k = 1 + n_cov;
@@ -543,6 +549,133 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
   return TG_OK;
 }
 
+tg_status tg_prepare_panel_subset(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, int64_t P,
+                                  const double* C, int64_t ldc, int64_t n_cov,
+                                  const uint32_t* samples, tg_panel** out, void* stream) {
+  TG_ARG(c && out && samples, "null context, output or sample mask");
+  *out = nullptr;
+  TG_ARG(N > 0 && P >= 0 && n_cov >= 0, "bad sizes");
+  TG_ARG(N <= (1ll << 30), "N too large");
+  TG_ARG(Y != nullptr || P == 0, "null Y");
+  TG_ARG(ldy >= N, "ldy < N");
+  if (n_cov > 0) TG_ARG(C != nullptr && ldc >= N, "null C or ldc < N");
+  TG_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nw = (N + 31) / 32;
+  std::vector<uint32_t> hm((size_t)nw);
+  TG_CUDA(cudaMemcpyAsync(hm.data(), samples, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost, st));
+  TG_CUDA(cudaStreamSynchronize(st));
+  std::vector<int> idx;
+  for (int64_t i = 0; i < N; ++i)
+    if ((hm[(size_t)(i >> 5)] >> (i & 31)) & 1u) idx.push_back((int)i);
+  const int64_t NS = (int64_t)idx.size();
+  if (NS < 3) return fail(TG_ERR_RANK, "a subset panel needs at least 3 samples");
+  int* didx = nullptr;
+  float* Yc = nullptr;
+  double* Cc = nullptr;
+  tg_panel* pc = nullptr;
+  tg_panel* r = nullptr;
+  auto cleanup = [&](tg_status s) {
+    dfree(didx); dfree(Yc); dfree(Cc);
+    if (pc) tg_panel_free(pc);
+    if (r) tg_panel_free(r);
+    return s;
+  };
+  cudaError_t e;
+  if ((e = dalloc(&didx, (size_t)NS)) || (e = dalloc(&Yc, (size_t)(std::max<int64_t>(P, 1) * NS))) ||
+      (n_cov > 0 && (e = dalloc(&Cc, (size_t)(n_cov * NS)))))
+    return cleanup(cuda_fail(e, "tg_prepare_panel_subset allocation"));
+  if ((e = cudaMemcpyAsync(didx, idx.data(), sizeof(int) * NS, cudaMemcpyHostToDevice, st)) ||
+      (e = launch_gather_f32(Y, ldy, Yc, NS, didx, NS, P, st)) ||
+      (n_cov > 0 && (e = launch_gather_f64(C, ldc, Cc, NS, didx, NS, n_cov, st))))
+    return cleanup(cuda_fail(e, "tg_prepare_panel_subset gather"));
+  // the panel on the gathered rows, then its sample-indexed arrays back on the full axis
+  tg_status s = tg_prepare_panel(c, Yc, NS, NS, P, Cc, NS, n_cov, &pc, stream);
+  if (s != TG_OK) return cleanup(s);
+  r = new tg_panel();
+  r->device = c->device;
+  r->N = N;
+  r->NS = NS;
+  r->P = P;
+  r->n_cov = n_cov;
+  r->q = pc->q;
+  r->df = pc->df;
+  r->Npad = round_up(N, KPAD);
+  r->Ppad = pc->Ppad;
+  r->lnB = pc->lnB;
+  r->lnB_paper = pc->lnB_paper;
+  const int64_t Np = r->Npad, Pp = r->Ppad, q = r->q, P1 = std::max<int64_t>(P, 1);
+  if ((e = dalloc(&r->Q, (size_t)(q * N))) || (e = dalloc(&r->Yres, (size_t)(P1 * N))) ||
+      (e = dalloc(&r->s, (size_t)P1)) || (e = dalloc(&r->col_s, (size_t)P1)) ||
+      (e = dalloc(&r->col_rmul, (size_t)Pp)) || (e = dalloc(&r->col_cs, (size_t)Pp)) ||
+      (e = dalloc(&r->qcs, (size_t)QCOLS)) || (e = dalloc(&r->Bhi, (size_t)(Pp * Np))) ||
+      (e = dalloc(&r->Blo, (size_t)(Pp * Np))) || (e = dalloc(&r->B32, (size_t)(Pp * Np))) ||
+      (e = dalloc(&r->QB, (size_t)(QCOLS * Np))) || (e = dalloc(&r->QBhi, (size_t)(QCOLS * Np))) ||
+      (e = dalloc(&r->QBlo, (size_t)(QCOLS * Np))) || (e = dalloc(&r->samples, (size_t)nw)))
+    return cleanup(cuda_fail(e, "tg_prepare_panel_subset allocation"));
+  auto run = [&]() -> cudaError_t {
+    cudaError_t x;
+    const int64_t Nc = pc->Npad;
+    if ((x = cudaMemsetAsync(r->Q, 0, sizeof(double) * q * N, st)) ||
+        (x = cudaMemsetAsync(r->Yres, 0, sizeof(double) * P1 * N, st)) ||
+        (x = cudaMemsetAsync(r->Bhi, 0, 2 * Pp * Np, st)) ||
+        (x = cudaMemsetAsync(r->Blo, 0, 2 * Pp * Np, st)) ||
+        (x = cudaMemsetAsync(r->B32, 0, 4 * Pp * Np, st)) ||
+        (x = cudaMemsetAsync(r->QB, 0, 4 * QCOLS * Np, st)) ||
+        (x = cudaMemsetAsync(r->QBhi, 0, 2 * QCOLS * Np, st)) ||
+        (x = cudaMemsetAsync(r->QBlo, 0, 2 * QCOLS * Np, st)))
+      return x;
+    if ((x = launch_scatter(pc->Q, NS, r->Q, N, didx, NS, q, 8, st)) ||
+        (x = launch_scatter(pc->Yres, NS, r->Yres, N, didx, NS, P, 8, st)) ||
+        (x = launch_scatter(pc->Bhi, Nc, r->Bhi, Np, didx, NS, Pp, 2, st)) ||
+        (x = launch_scatter(pc->Blo, Nc, r->Blo, Np, didx, NS, Pp, 2, st)) ||
+        (x = launch_scatter(pc->B32, Nc, r->B32, Np, didx, NS, Pp, 4, st)) ||
+        (x = launch_scatter(pc->QB, Nc, r->QB, Np, didx, NS, QCOLS, 4, st)) ||
+        (x = launch_scatter(pc->QBhi, Nc, r->QBhi, Np, didx, NS, QCOLS, 2, st)) ||
+        (x = launch_scatter(pc->QBlo, Nc, r->QBlo, Np, didx, NS, QCOLS, 2, st)))
+      return x;
+    if ((x = cudaMemcpyAsync(r->s, pc->s, sizeof(double) * P1, cudaMemcpyDeviceToDevice, st)) ||
+        (x = cudaMemcpyAsync(r->col_s, pc->col_s, sizeof(float) * P1, cudaMemcpyDeviceToDevice, st)) ||
+        (x = cudaMemcpyAsync(r->col_rmul, pc->col_rmul, sizeof(float) * Pp, cudaMemcpyDeviceToDevice, st)) ||
+        (x = cudaMemcpyAsync(r->col_cs, pc->col_cs, sizeof(float) * Pp, cudaMemcpyDeviceToDevice, st)) ||
+        (x = cudaMemcpyAsync(r->qcs, pc->qcs, sizeof(float) * QCOLS, cudaMemcpyDeviceToDevice, st)) ||
+        (x = cudaMemcpyAsync(r->samples, hm.data(), sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, st)))
+      return x;
+    return cudaStreamSynchronize(st);
+  };
+  if ((e = run())) return cleanup(cuda_fail(e, "tg_prepare_panel_subset scatter"));
+  if (N % 32) {  // bits past N are not samples
+    const uint32_t last = hm[(size_t)(nw - 1)] & ((1u << (N % 32)) - 1u);
+    TG_CUDA(cudaMemcpy(r->samples + nw - 1, &last, sizeof(uint32_t), cudaMemcpyHostToDevice));
+  }
+  if (!make_tmap(&r->tmBhi, r->Bhi, Pp, Np, Np, 256) || !make_tmap(&r->tmBlo, r->Blo, Pp, Np, Np, 256) ||
+      !make_tmap(&r->tmBhi2, r->Bhi, Pp, Np, Np, 128) || !make_tmap(&r->tmBlo2, r->Blo, Pp, Np, Np, 128) ||
+      !make_tmap(&r->tmQhi, r->QBhi, QCOLS, Np, Np, 64) || !make_tmap(&r->tmQlo, r->QBlo, QCOLS, Np, Np, 64))
+    return cleanup(fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the subset panel"));
+  tg_panel* done = r;
+  r = nullptr;
+  cleanup(TG_OK);
+  *out = done;
+  return TG_OK;
+}
+
+tg_status tg_panel_samples(const tg_panel* p, int64_t* n_used, const uint32_t** samples) {
+  TG_ARG(p, "null panel");
+  if (n_used) *n_used = p->NS;
+  if (samples) *samples = p->samples;
+  return TG_OK;
+}
+
+tg_status tg_phenotype_masks(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, int64_t P,
+                             uint32_t* masks, int64_t ldm, void* stream) {
+  TG_ARG(c && N > 0 && P >= 0, "bad arguments");
+  TG_ARG((Y && masks) || P == 0, "null Y or masks");
+  TG_ARG(ldy >= N && ldm >= (N + 31) / 32, "ldy < N or ldm < ceil(N/32)");
+  TG_CUDA(cudaSetDevice(c->device));
+  TG_CUDA(launch_pheno_masks(Y, ldy, N, P, masks, ldm, (cudaStream_t)stream));
+  return TG_OK;
+}
+
 tg_status tg_panel_info(const tg_panel* p, int64_t* N, int64_t* P, int64_t* q, int64_t* df) {
   TG_ARG(p, "null panel");
   if (N) *N = p->N;
@@ -573,7 +706,7 @@ tg_status tg_panel_free(tg_panel* p) {
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   dfree(p->X); dfree(p->Q); dfree(p->Yres); dfree(p->s); dfree(p->col_s); dfree(p->col_rmul);
-  dfree(p->col_cs); dfree(p->qcs);
+  dfree(p->col_cs); dfree(p->qcs); dfree(p->samples);
   dfree(p->Bhi); dfree(p->Blo); dfree(p->B32); dfree(p->QB); dfree(p->QBhi); dfree(p->QBlo);
   delete p;
   return TG_OK;
@@ -774,7 +907,8 @@ tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_pa
   for (int i = 0; i < n; ++i) {
     TG_ARG(panels[i] != nullptr, "null panel");
     const tg_panel* pi = panels[i];
-    TG_ARG(pi->N == p0->N && pi->q == p0->q && pi->n_cov == p0->n_cov && pi->device == p0->device,
+    TG_ARG(pi->N == p0->N && pi->NS == p0->NS && pi->q == p0->q && pi->n_cov == p0->n_cov &&
+               pi->device == p0->device && (pi->samples != nullptr) == (p0->samples != nullptr),
            "panels differ in samples or covariate rank");
     P += pi->P;
   }
@@ -791,6 +925,17 @@ tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_pa
         return fail(TG_ERR_INVALID_ARG, "panels were prepared with different covariates");
     }
   }
+  const int64_t nw = (N + 31) / 32;
+  std::vector<uint32_t> mask0;
+  if (p0->samples) {  // subset panels: the same samples
+    mask0.resize((size_t)nw);
+    std::vector<uint32_t> mi((size_t)nw);
+    TG_CUDA(cudaMemcpy(mask0.data(), p0->samples, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost));
+    for (int i = 1; i < n; ++i) {
+      TG_CUDA(cudaMemcpy(mi.data(), panels[i]->samples, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost));
+      if (mi != mask0) return fail(TG_ERR_INVALID_ARG, "subset panels use different samples");
+    }
+  }
   tg_panel* r = new tg_panel();
   r->device = p0->device;
   r->N = N;
@@ -802,8 +947,16 @@ tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_pa
   r->Ppad = round_up(std::max<int64_t>(P, 1), PPAD);
   r->lnB = p0->lnB;
   r->lnB_paper = p0->lnB_paper;
+  r->NS = p0->NS;
   const int64_t Np = r->Npad, Pp = r->Ppad;
   cudaError_t e;
+  if (!mask0.empty()) {
+    if ((e = dalloc(&r->samples, (size_t)nw)) ||
+        (e = cudaMemcpy(r->samples, mask0.data(), sizeof(uint32_t) * nw, cudaMemcpyHostToDevice))) {
+      tg_panel_free(r);
+      return cuda_fail(e, "tg_panel_concat allocation");
+    }
+  }
   if ((e = dalloc(&r->Q, (size_t)(q * N))) || (e = dalloc(&r->Yres, (size_t)(std::max<int64_t>(P, 1) * N))) ||
       (e = dalloc(&r->s, (size_t)std::max<int64_t>(P, 1))) ||
       (e = dalloc(&r->col_s, (size_t)std::max<int64_t>(P, 1))) || (e = dalloc(&r->col_rmul, (size_t)Pp)) ||

@@ -117,6 +117,8 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   if (prec != TG_PREC_FP32 && prec != TG_PREC_SPLIT_BF16) return fail(TG_ERR_INVALID_ARG, "unknown precision");
   if ((opts->mode != TG_MODE_PROJECTED && opts->mode != TG_MODE_PAPER) || opts->reserved != 0)
     return fail(TG_ERR_INVALID_ARG, "unknown mode (or tg_scan_opts.reserved != 0)");
+  if (p->samples)
+    return fail(TG_ERR_UNSUPPORTED, "subset panels are scanned with tg_scan_block, not the static form");
   if (N != p->N) return fail(TG_ERR_INVALID_ARG, "N differs from the panel's sample count");
   if (M < 0 || marker_offset < 0 || marker_offset + M > 0xFFFFFFFFll)
     return fail(TG_ERR_INVALID_ARG, "bad M or marker_offset");

@@ -99,6 +99,8 @@ inline int tune_bucket(int64_t M) {
 struct tg_panel {
   int device = 0;
   int64_t N = 0, P = 0, n_cov = 0, q = 0, df = 0, Npad = 0, Ppad = 0;
+  int64_t NS = 0;               // samples the panel's phenotypes use (N unless a subset)
+  uint32_t* samples = nullptr;  // [ceil(N/32)] bit mask of those samples (subset panels only)
   double* X = nullptr;        // [(1+n_cov)][N] design, reduced in place by the QR
   double* Q = nullptr;        // [q][N] (column-major N x q)
   double* Yres = nullptr;     // [P][N]
@@ -134,6 +136,7 @@ struct tg_ctx {
   int32_t* nobs = nullptr;
   double* mean = nullptr;
   float* shift = nullptr;                       // [cap_m] per-row shift of the split operand
+  double* gc2s = nullptr;                       // [cap_m] |g_c|^2 over a subset panel's samples
   uint32_t* mh = nullptr;                       // [cap_m] bf16 bits of the missing-call value
   double* gc2 = nullptr;
   float* qg = nullptr;                          // [cap_m][QCOLS]
@@ -191,12 +194,27 @@ cudaError_t launch_residualise(const float* Y, int64_t ldy, const double* Q, int
                                float* col_cs, uint32_t* flags, cudaStream_t st);
 cudaError_t launch_qcols(const double* Q, int64_t N, int64_t q, int64_t Npad, float* QB,
                          __nv_bfloat16* QBhi, __nv_bfloat16* QBlo, float* qcs, cudaStream_t st);
+// subset panels: rows gathered to a compact copy and scattered back (elements of 2, 4 or 8
+// bytes), and per-phenotype finite-value masks
+cudaError_t launch_gather_f32(const float* src, int64_t lds, float* dst, int64_t ldd, const int* idx,
+                              int64_t ns, int64_t R, cudaStream_t st);
+cudaError_t launch_gather_f64(const double* src, int64_t lds, double* dst, int64_t ldd,
+                              const int* idx, int64_t ns, int64_t R, cudaStream_t st);
+cudaError_t launch_scatter(const void* src, int64_t lds, void* dst, int64_t ldd, const int* idx,
+                           int64_t ns, int64_t R, int elem_bytes, cudaStream_t st);
+cudaError_t launch_pheno_masks(const float* Y, int64_t ldy, int64_t N, int64_t P, uint32_t* masks,
+                               int64_t ldm, cudaStream_t st);
 
 // decode (k_decode.cu)
 cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,
                           const uint32_t* missing, int64_t ldm, int precision, void* Ahi,
                           float* shift, uint32_t* mh, int64_t lda, int32_t* nobs, int64_t* S,
                           int64_t* S2, double* mean, double* gc2, cudaStream_t st);
+// |g_c|^2 over the samples of a subset panel (decode units; the imputed value is the marker's
+// all-sample mean)
+cudaError_t launch_subset_stats(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,
+                                const uint32_t* missing, int64_t ldm, const uint32_t* samples,
+                                const double* mean, double* gc2s, cudaStream_t st);
 
 // SIMT kernels (k_simt.cu)
 cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, const float* QB,

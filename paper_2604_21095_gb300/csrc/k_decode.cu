@@ -377,6 +377,83 @@ __global__ void __launch_bounds__(kRowThreads, GPT <= 6 ? 4 : 2) k_decode_rows(
   }
 }
 
+// |g_c|^2 of each marker over the samples of a subset panel, in decode units, the marker's
+// missing calls imputed with its all-sample mean m (one warp per marker). With n observed
+// calls in the subset (sum T, sum of squares U, exact integers), k imputed ones and N_S = n + k,
+// the subset mean is gbar = (T + k m) / N_S and
+//   |g_c|^2 = (n U - T^2) / n + n (T / n - gbar)^2 + k (m - gbar)^2,
+// the first term exact in integers, the others small and well conditioned.
+__device__ __forceinline__ uint32_t spread16(uint32_t m) {  // bit b -> bit 2b
+  m = (m | (m << 8)) & 0x00FF00FFu;
+  m = (m | (m << 4)) & 0x0F0F0F0Fu;
+  m = (m | (m << 2)) & 0x33333333u;
+  m = (m | (m << 1)) & 0x55555555u;
+  return m;
+}
+
+template <int ENC>
+__global__ void __launch_bounds__(kWarps * 32) k_subset_stats(
+    const uint8_t* __restrict__ G, long long ldg, int N, long long M,
+    const uint32_t* __restrict__ miss, long long ldm, const uint32_t* __restrict__ samples,
+    const double* __restrict__ mean, double* __restrict__ gc2s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long j = (long long)blockIdx.x * kWarps + warp;
+  if (j >= M) return;
+  const uint8_t* row = G + j * ldg;
+  const uint32_t* mrow = miss ? miss + j * ldm : nullptr;
+  unsigned long long n = 0, T = 0, U = 0, k = 0;
+  const int groups = (N + 15) >> 4;  // 16 samples each
+  for (int t = lane; t < groups; t += 32) {
+    const int left = N - t * 16;
+    const uint32_t in_n = left >= 16 ? 0xFFFFu : ((1u << left) - 1u);
+    const uint32_t s16 = (samples[t >> 1] >> ((t & 1) * 16)) & in_n;
+    if (!s16) continue;
+    if (ENC == TG_ENC_2BIT) {
+      const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(row) + t);
+      const uint32_t sm = spread16(s16);
+      const uint32_t lo = w & 0x55555555u, hi = (w >> 1) & 0x55555555u;
+      const uint32_t c2 = __popc(~lo & ~hi & sm), c1 = __popc(hi & ~lo & sm);
+      n += c2 + c1 + __popc(lo & hi & sm);
+      T += 2 * c2 + c1;
+      U += 4 * c2 + c1;
+      k += __popc(lo & ~hi & sm);
+    } else {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + t);
+      const uint32_t m16 = mrow ? (mrow[t >> 1] >> ((t & 1) * 16)) & 0xFFFFu : 0u;
+      const uint32_t use = s16 & ~m16;
+      k += __popc(s16 & m16);
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if ((use >> (q * 4 + b)) & 1u) {
+            const uint32_t u = (w4[q] >> (8 * b)) & 0xFFu;
+            n += 1;
+            T += u;
+            U += u * u;
+          }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+    T += __shfl_xor_sync(0xffffffffu, T, o);
+    U += __shfl_xor_sync(0xffffffffu, U, o);
+    k += __shfl_xor_sync(0xffffffffu, k, o);
+  }
+  if (lane) return;
+  if (n == 0) {  // every call of the subset imputed: constant there
+    gc2s[j] = 0.0;
+    return;
+  }
+  const double m = mean[j], dn = (double)n, dk = (double)k;
+  const double gbar = ((double)T + dk * m) / (dn + dk);
+  const long long num = (long long)U * (long long)n - (long long)T * (long long)T;
+  const double d1 = (double)T / dn - gbar, d2 = m - gbar;
+  gc2s[j] = (double)num / dn + dn * d1 * d1 + (k ? dk * d2 * d2 : 0.0);
+}
+
 template <int ENC, int PREC>
 cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32_t* missing,
                int64_t ldm, void* Ahi, float* shift, uint32_t* mh, int64_t lda, int32_t* nobs,
@@ -424,6 +501,20 @@ cudaError_t launch_decode(const uint8_t* G, int64_t ldg, int encoding, int64_t N
   return precision == TG_PREC_SPLIT_BF16
              ? go<TG_ENC_U8_DOSAGE, TG_PREC_SPLIT_BF16>(G, ldg, N, M, missing, ldm, Ahi, shift, mh, lda, nobs, S, S2, mean, gc2, st)
              : go<TG_ENC_U8_DOSAGE, TG_PREC_FP32>(G, ldg, N, M, missing, ldm, Ahi, shift, mh, lda, nobs, S, S2, mean, gc2, st);
+}
+
+cudaError_t launch_subset_stats(const uint8_t* G, int64_t ldg, int encoding, int64_t N, int64_t M,
+                                const uint32_t* missing, int64_t ldm, const uint32_t* samples,
+                                const double* mean, double* gc2s, cudaStream_t st) {
+  if (M == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((M + kWarps - 1) / kWarps);
+  if (encoding == TG_ENC_2BIT)
+    k_subset_stats<TG_ENC_2BIT><<<grid, kWarps * 32, 0, st>>>(G, ldg, (int)N, M, missing, ldm,
+                                                               samples, mean, gc2s);
+  else
+    k_subset_stats<TG_ENC_U8_DOSAGE><<<grid, kWarps * 32, 0, st>>>(G, ldg, (int)N, M, missing, ldm,
+                                                                    samples, mean, gc2s);
+  return cudaGetLastError();
 }
 
 }  // namespace tg

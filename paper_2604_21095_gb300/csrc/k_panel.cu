@@ -9,6 +9,10 @@
 //      marker projection.
 //   5. Per column of the BF16 pairs, sum_i (hi + lo) in FP64: the scan adds c * sum back for a
 //      marker row shifted by c (the split operand is centred; see k_decode.cu).
+// A panel of phenotypes observed on a subset of the samples is prepared on the gathered rows
+// (steps 1-5 with N_S samples) and its sample-indexed arrays are then scattered back to the
+// full sample axis with zeros elsewhere (k_gather, k_scatter); k_pheno_masks gives each
+// phenotype's finite-value mask, from which such subsets are formed.
 #include <cuda_bf16.h>
 
 #include "device.cuh"
@@ -212,7 +216,89 @@ __global__ void k_qcols(const double* __restrict__ Q, long long N, int q, long l
   QBlo[o] = __double2bfloat16(v - (double)__bfloat162float(h));
 }
 
+// dst[r][i] = src[r * lds + idx[i]] for r < R, i < ns (rows of a compact copy).
+template <class T>
+__global__ void k_gather(const T* __restrict__ src, long long lds, T* __restrict__ dst, long long ldd,
+                         const int* __restrict__ idx, int ns, int R) {
+  const long long total = (long long)R * ns;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / ns;
+    const int i = (int)(e - r * ns);
+    dst[r * ldd + i] = src[r * lds + idx[i]];
+  }
+}
+
+// dst[r * ldd + idx[i]] = src[r][i] (dst zeroed beforehand).
+template <class T>
+__global__ void k_scatter(const T* __restrict__ src, long long lds, T* __restrict__ dst, long long ldd,
+                          const int* __restrict__ idx, int ns, int R) {
+  const long long total = (long long)R * ns;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / ns;
+    const int i = (int)(e - r * ns);
+    dst[r * ldd + idx[i]] = src[r * lds + i];
+  }
+}
+
+// masks[p][w] bit b = Y[p][32 w + b] is finite (bits past N are 0).
+__global__ void k_pheno_masks(const float* __restrict__ Y, long long ldy, long long N, long long P,
+                              uint32_t* __restrict__ masks, long long ldm) {
+  const long long nw = (N + 31) / 32;
+  const long long total = P * nw;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / nw, w = e - p * nw;
+    uint32_t m = 0;
+    for (int b = 0; b < 32; ++b) {
+      const long long i = 32 * w + b;
+      if (i < N && isfinite(Y[p * ldy + i])) m |= 1u << b;
+    }
+    masks[p * ldm + w] = m;
+  }
+}
+
+template <class T>
+unsigned grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (unsigned)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
+}
+
 }  // namespace
+
+cudaError_t launch_gather_f32(const float* src, int64_t lds, float* dst, int64_t ldd, const int* idx,
+                              int64_t ns, int64_t R, cudaStream_t st) {
+  if (ns == 0 || R == 0) return cudaSuccess;
+  k_gather<float><<<grid_for<float>(R * ns), 256, 0, st>>>(src, lds, dst, ldd, idx, (int)ns, (int)R);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_f64(const double* src, int64_t lds, double* dst, int64_t ldd,
+                              const int* idx, int64_t ns, int64_t R, cudaStream_t st) {
+  if (ns == 0 || R == 0) return cudaSuccess;
+  k_gather<double><<<grid_for<double>(R * ns), 256, 0, st>>>(src, lds, dst, ldd, idx, (int)ns, (int)R);
+  return cudaGetLastError();
+}
+cudaError_t launch_scatter(const void* src, int64_t lds, void* dst, int64_t ldd, const int* idx,
+                           int64_t ns, int64_t R, int elem_bytes, cudaStream_t st) {
+  if (ns == 0 || R == 0) return cudaSuccess;
+  const unsigned g = grid_for<char>(R * ns);
+  if (elem_bytes == 8)
+    k_scatter<double><<<g, 256, 0, st>>>(static_cast<const double*>(src), lds, static_cast<double*>(dst), ldd, idx, (int)ns, (int)R);
+  else if (elem_bytes == 4)
+    k_scatter<float><<<g, 256, 0, st>>>(static_cast<const float*>(src), lds, static_cast<float*>(dst), ldd, idx, (int)ns, (int)R);
+  else if (elem_bytes == 2)
+    k_scatter<unsigned short><<<g, 256, 0, st>>>(static_cast<const unsigned short*>(src), lds, static_cast<unsigned short*>(dst), ldd, idx, (int)ns, (int)R);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+cudaError_t launch_pheno_masks(const float* Y, int64_t ldy, int64_t N, int64_t P, uint32_t* masks,
+                               int64_t ldm, cudaStream_t st) {
+  if (P == 0) return cudaSuccess;
+  k_pheno_masks<<<grid_for<char>(P * ((N + 31) / 32)), 256, 0, st>>>(Y, ldy, N, P, masks, ldm);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_build_design(double* X, const double* C, int64_t ldc, int64_t N, int64_t n_cov,
                                 uint32_t* flags, cudaStream_t st) {

@@ -76,10 +76,19 @@ def run_scan(ctx, panel, G, N, P, encoding, precision, full=True, hit_mlog10p=0.
     return res
 
 
-def oracle_panel(Yt: torch.Tensor, cov_t):
+def oracle_panel(Yt: torch.Tensor, cov_t, samples=None):
     Y = Yt.cpu().numpy().T.astype(np.float64)
     C = None if cov_t is None or cov_t.shape[0] == 0 else cov_t.cpu().numpy().T
-    return oracle.prepare_panel(Y, C)
+    return oracle.prepare_panel(Y, C, samples)
+
+
+def sample_words(rows: np.ndarray) -> torch.Tensor:
+    """bool [N] -> int32 words [ceil(N/32)], bit i%32 of word i/32 = rows[i]."""
+    N = rows.shape[0]
+    w = np.zeros((N + 31) // 32, dtype=np.uint32)
+    for i in np.nonzero(rows)[0]:
+        w[i // 32] |= np.uint32(1) << np.uint32(i % 32)
+    return torch.from_numpy(w.view(np.int32).copy())
 
 
 def compare_full(res, ref, label="", rtol=None):
