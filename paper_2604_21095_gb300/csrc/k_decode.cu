@@ -237,19 +237,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_decode(
   }
 }
 
-// Split form for rows of up to kRowThreads * GPT * 16 samples: one block per marker row, the
+// Split form for rows of up to THREADS * GPT * 16 samples: one block per marker row, the
 // packed row held in registers between the two passes (one read of the row from HBM, every
 // load of a thread in flight at once). Used for dosage rows, where the warp-per-row kernel's
 // second read of a 23 KB row misses L2 under load.
-constexpr int kRowThreads = 256;
 
-template <int ENC, int GPT>
-__global__ void __launch_bounds__(kRowThreads, GPT <= 6 ? 4 : 2) k_decode_rows(
+template <int ENC, int GPT, int THREADS>
+__global__ void __launch_bounds__(THREADS, GPT * THREADS <= 1536 ? 4 : 2) k_decode_rows(
     const uint8_t* __restrict__ G, long long ldg, int N, const uint32_t* __restrict__ miss,
     long long ldm, __nv_bfloat16* __restrict__ A, float* __restrict__ shift_out, long long lda,
     int32_t* __restrict__ nobs_out, long long* __restrict__ S_out, long long* __restrict__ S2_out,
     double* __restrict__ mean_out, double* __restrict__ gc2_out) {
-  __shared__ unsigned long long red[3][kRowThreads / 32];
+  __shared__ unsigned long long red[3][THREADS / 32];
   __shared__ float s_c;
   __shared__ uint32_t s_mh;
   const long long j = blockIdx.x;
@@ -264,7 +263,7 @@ __global__ void __launch_bounds__(kRowThreads, GPT <= 6 ? 4 : 2) k_decode_rows(
   uint32_t n = 0, S = 0, S2 = 0;
 #pragma unroll
   for (int g = 0; g < GPT; ++g) {
-    const int t = tid + g * kRowThreads;
+    const int t = tid + g * THREADS;
     if (ENC == TG_ENC_2BIT) {
       w[g] = t < nvalid ? __ldg(reinterpret_cast<const uint32_t*>(row) + t) : 0u;
     } else {
@@ -274,7 +273,7 @@ __global__ void __launch_bounds__(kRowThreads, GPT <= 6 ? 4 : 2) k_decode_rows(
   }
 #pragma unroll
   for (int g = 0; g < GPT; ++g) {
-    const int t = tid + g * kRowThreads;
+    const int t = tid + g * THREADS;
     if (t >= nvalid) continue;
     const int left = N - t * 16;  // >= 1
     if (ENC == TG_ENC_2BIT) {
@@ -327,7 +326,7 @@ __global__ void __launch_bounds__(kRowThreads, GPT <= 6 ? 4 : 2) k_decode_rows(
   if (tid == 0) {
     unsigned long long tn = 0, tS = 0, tS2 = 0;
 #pragma unroll
-    for (int k = 0; k < kRowThreads / 32; ++k) {
+    for (int k = 0; k < THREADS / 32; ++k) {
       tn += red[0][k];
       tS += red[1][k];
       tS2 += red[2][k];
@@ -359,7 +358,7 @@ __global__ void __launch_bounds__(kRowThreads, GPT <= 6 ? 4 : 2) k_decode_rows(
   const uint32_t mh2 = mhu | (mhu << 16);
 #pragma unroll
   for (int g = 0; g < GPT; ++g) {
-    const int t = tid + g * kRowThreads;
+    const int t = tid + g * THREADS;
     if (t >= nvalid) break;
     uint32_t o[8];
     if (ENC == TG_ENC_2BIT)
@@ -371,7 +370,7 @@ __global__ void __launch_bounds__(kRowThreads, GPT <= 6 ? 4 : 2) k_decode_rows(
     ah[2 * t + 1] = make_uint4(o[4], o[5], o[6], o[7]);
   }
   const long long groups = lda >> 4;
-  for (long long t = nvalid + tid; t < groups; t += kRowThreads) {
+  for (long long t = nvalid + tid; t < groups; t += THREADS) {
     ah[2 * t] = make_uint4(0, 0, 0, 0);
     ah[2 * t + 1] = make_uint4(0, 0, 0, 0);
   }
@@ -458,23 +457,25 @@ template <int ENC, int PREC>
 cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32_t* missing,
                int64_t ldm, void* Ahi, float* shift, uint32_t* mh, int64_t lda, int32_t* nobs,
                int64_t* S, int64_t* S2, double* mean, double* gc2, cudaStream_t st) {
-  // dosage rows (N bytes) take the block-per-row kernel; 2-bit rows are small enough that
-  // the warp-per-row kernel's second read hits in L2, and it measured faster for them. The
-  // statistics-only form (Ahi NULL) reads each row once in the warp-per-row kernel.
-  if constexpr (ENC == TG_ENC_U8_DOSAGE && PREC == TG_PREC_SPLIT_BF16) {
+  // Split form: one block per marker row with the row in registers (read from HBM once):
+  // 256 threads x 6 groups of 16 samples for dosage rows, 128 x 12 for 2-bit rows; 12 and 24
+  // groups up to twice those N. The statistics-only form (Ahi NULL) and longer rows read each
+  // row twice in the warp-per-row kernel.
+  if constexpr (PREC == TG_PREC_SPLIT_BF16) {
+    constexpr int T = ENC == TG_ENC_2BIT ? 128 : 256;
+    constexpr int G1 = ENC == TG_ENC_2BIT ? 12 : 6;
     __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(Ahi);
     long long* S64 = reinterpret_cast<long long*>(S);
     long long* S264 = reinterpret_cast<long long*>(S2);
-    if (A && N <= kRowThreads * 6 * 16) {
-      k_decode_rows<ENC, 6><<<(unsigned)M, kRowThreads, 0, st>>>(G, ldg, (int)N, missing, ldm, A,
-                                                                 shift, lda, nobs, S64, S264,
-                                                                 mean, gc2);
+    if (A && N <= T * G1 * 16) {
+      k_decode_rows<ENC, G1, T><<<(unsigned)M, T, 0, st>>>(G, ldg, (int)N, missing, ldm, A, shift,
+                                                          lda, nobs, S64, S264, mean, gc2);
       return cudaGetLastError();
     }
-    if (A && N <= kRowThreads * 12 * 16) {
-      k_decode_rows<ENC, 12><<<(unsigned)M, kRowThreads, 0, st>>>(G, ldg, (int)N, missing, ldm, A,
-                                                                  shift, lda, nobs, S64, S264,
-                                                                  mean, gc2);
+    if (A && N <= T * 2 * G1 * 16) {
+      k_decode_rows<ENC, 2 * G1, T><<<(unsigned)M, T, 0, st>>>(G, ldg, (int)N, missing, ldm, A,
+                                                              shift, lda, nobs, S64, S264, mean,
+                                                              gc2);
       return cudaGetLastError();
     }
   }

@@ -102,7 +102,7 @@ def test_decode_2bit_every_byte_value(tgctx):
     _check_operand(a, c, units, m, mean, tg.TG_PREC_SPLIT_BF16, N, tg.TG_ENC_2BIT)
 
 
-# dosage rows of N <= 24,576 and <= 49,152 take the block-per-row kernel, larger N the
+# split-form rows of N <= 24,576 and <= 49,152 take the block-per-row kernels, larger N the
 # warp-per-row kernel
 @pytest.mark.parametrize("N", [1, 15, 16, 17, 33, 2000, 23000, 24576, 24577, 49152, 49153])
 @pytest.mark.parametrize("masked", [False, True])
