@@ -23,7 +23,7 @@ const char* kVersion = "tg 0.1.0 (sm_103a)";
 
 // The spin limit of device-side waits: generous enough for a FULL-output tile epilogue.
 constexpr long long kSpinNs = 4000000000ll;
-constexpr int kGroupDefault = 16;  // raster group (m-tiles) when the tuner has not chosen one
+constexpr int kGroupDefault = 32;  // raster group (m-tiles) when the tuner has not chosen one
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

@@ -32,7 +32,6 @@ struct RegSplit {
 };
 constexpr int kTmemCols = 512;                 // two 128 x 256 FP32 chunk accumulators
 constexpr int kChunkKB = 32;                   // K blocks per accumulation chunk (1024 samples)
-constexpr int kGroupM = 16;                    // default raster: 16 m-tiles per group
 
 
 
