@@ -241,51 +241,30 @@ __device__ __forceinline__ void tile_coord(int tile, int n_mt, int n_nt, int gro
 // Statistics of the 128 totals one thread holds: its marker row against 128 consecutive
 // phenotype columns starting at col0, in groups of 16 columns.
 // D of a column is tot + shift * col_cs[col] (the marker row was shifted by `shift`).
+// Per column: r, the hit test, optionally every statistic's r, and the column's best marker
+// over the warp's 32 rows: one warp max (redux.sync) of the ordered key bits(|r|) + 1 (0 for
+// NaN; non-negative floats order like their bits), the lowest lane holding it (the smallest
+// marker) offering it to the global per-phenotype best.
 __device__ __forceinline__ void epilogue_tile(const EpiParams& ep, const float (&tot)[128],
                                               long long row, long long row_base, bool row_ok,
                                               float rinv, float shift, int col0, int lane) {
 #pragma unroll
-  for (int grp = 0; grp < 8; ++grp) {
-    float m[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const int col = col0 + grp * 16 + e;
-      const float D = (col < ep.P) ? fmaf(shift, ep.col_cs[col], tot[grp * 16 + e]) : 0.0f;
-      float r = __int_as_float(0x7fc00000);
-      if (row_ok && col < ep.P) r = corr_nan(D, rinv, ep.col_rmul[col]);
-      m[e] = (r == r) ? fabsf(r) : -1.0f;
+  for (int e = 0; e < 128; ++e) {
+    const int col = col0 + e;
+    float r = __int_as_float(0x7fc00000);
+    if (row_ok && col < ep.P) {
+      const float D = fmaf(shift, ep.col_cs[col], tot[e]);
+      r = corr_nan(D, rinv, ep.col_rmul[col]);
       if (ep.do_hits && r * r >= ep.r2_thr) emit_hit_raw(ep, D, row, col);
-      if (ep.do_full && row_ok && col < ep.P) ep.rstore[row * ep.ldo + col] = r;
+      if (ep.do_full) ep.rstore[row * ep.ldo + col] = r;
     }
-    if (!ep.do_best) continue;
-    // max over the warp's 32 rows: lanes l and l^16 first, then a reduce-scatter over 16
-    // lanes after which lane l holds the column max for column grp*16 + (l & 15)
-#pragma unroll
-    for (int i = 0; i < 16; ++i) m[i] = fmaxf(m[i], __shfl_xor_sync(0xffffffffu, m[i], 16));
-#pragma unroll
-    for (int s = 8; s >= 1; s >>= 1) {
-      const bool upper = (lane & s) != 0;
-#pragma unroll
-      for (int i = 0; i < s; ++i) {
-        const float send = upper ? m[i] : m[i + s];
-        const float keep = upper ? m[i + s] : m[i];
-        m[i] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, send, s));
-      }
-    }
-    const float cmax = m[0];
-    // the lowest lane (smallest marker) reaching the column max owns the candidate
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const float ce = __shfl_sync(0xffffffffu, cmax, e);
-      const int col = col0 + grp * 16 + e;
-      float r = __int_as_float(0x7fc00000);
-      if (row_ok && col < ep.P)
-        r = corr_nan(fmaf(shift, ep.col_cs[col], tot[grp * 16 + e]), rinv, ep.col_rmul[col]);
-      const float a = (r == r) ? fabsf(r) : -1.0f;
-      const unsigned b = __ballot_sync(0xffffffffu, ce >= 0.0f && a == ce);
-      if (lane == e && b != 0u) {
-        const long long marker = ep.marker_offset + row_base + (__ffs(b) - 1);
-        atomicMax(ep.best + col, best_key(ce, marker));
+    if (ep.do_best) {
+      const uint32_t u = (r == r) ? __float_as_uint(fabsf(r)) + 1u : 0u;
+      const uint32_t cmax = __reduce_max_sync(0xffffffffu, u);
+      if (cmax) {
+        const uint32_t owners = __ballot_sync(0xffffffffu, u == cmax);
+        if (lane == __ffs(owners) - 1)
+          atomicMax(ep.best + col, best_key(r, ep.marker_offset + row_base + lane));
       }
     }
   }

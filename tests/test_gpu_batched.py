@@ -8,7 +8,7 @@ import torch
 import oracle
 import paper_2604_21095_gb300 as tg
 import synth
-from scan_util import HIT_DTYPE, compare_best, compare_full, oracle_panel, run_scan
+from scan_util import HIT_DTYPE, compare_best, compare_full, oracle_panel, run_scan, sample_words
 
 pytestmark = pytest.mark.gpu
 
@@ -76,10 +76,18 @@ def _hitset(hits, n):
     return {(int(x["marker"]), int(x["pheno"])): float(x["mlog10p"]) for x in h}
 
 
-def test_graph_replay_equals_eager_scans_of_ragged_blocks(tgctx):
+@pytest.mark.parametrize("subset", [False, True])
+def test_graph_replay_equals_eager_scans_of_ragged_blocks(tgctx, subset):
+    """Captured scans of ragged blocks replay to the eager result, for a panel of all samples
+    and for a subset panel (whose marker norms come from the subset statistics kernel)."""
     P = 300
     cov = synth.covariates(84, N, 3)
-    panel = tg.tg_prepare_panel(tgctx, synth.phenotypes(84, cov, P).cuda(), N, P, cov.cuda())
+    Y = synth.phenotypes(84, cov, P).cuda()
+    if subset:
+        rows = np.random.default_rng(84).random(N) < 0.8
+        panel = tg.tg_prepare_panel_subset(tgctx, Y, N, P, cov.cuda(), sample_words(rows).cuda())
+    else:
+        panel = tg.tg_prepare_panel(tgctx, Y, N, P, cov.cuda())
     ctx2 = tg.tg_create(0)  # the graph holds its context's workspace
     try:
         w = synth.Workload("ragged", N=N, M=3000, P=P, n_cov=3, encoding="2bit", missing=0.01,
