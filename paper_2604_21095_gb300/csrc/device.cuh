@@ -39,6 +39,12 @@ __device__ __forceinline__ unsigned long long best_key(float r, long long marker
          (unsigned long long)(0xFFFFFFFFu - (uint32_t)marker);
 }
 
+// Offer a key to a per-phenotype best: a global max reduction that returns nothing, so the
+// thread does not wait for the round trip (atomicMax would).
+__device__ __forceinline__ void best_offer(unsigned long long* best, unsigned long long key) {
+  asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(best), "l"(key) : "memory");
+}
+
 // r from the raw product D of a marker row and a unit-norm phenotype column (NaN kept).
 __device__ __forceinline__ float corr_nan(float D, float rinv, float rmul) {
   const float r = D * rinv * rmul;

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256, 1) k_sgemm_scan(const float* __restrict__
       }
     }
     __syncthreads();
-    if (tid < BN && n0 + tid < ep.P && colbest[tid]) atomicMax(ep.best + n0 + tid, colbest[tid]);
+    if (tid < BN && n0 + tid < ep.P && colbest[tid]) best_offer(ep.best + n0 + tid, colbest[tid]);
   }
 }
 

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    // Each chunk of kChunkKB K blocks starts a fresh accumulator (no chained accumulation
+    // Each chunk (chunk_end) starts a fresh accumulator (no chained accumulation
     // across chunks); the two chunk accumulators alternate.
     int stage = 0;
     uint32_t phase = 0;
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
       tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
-      for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kChunkKB, ++g) {
+      for (int kb0 = 0; kb0 < num_kb && ok; kb0 = chunk_end(kb0, num_kb), ++g) {
         const int acc = (int)(g & 1u);
         const uint32_t ph = (g >> 1) & 1u;
         if (!mbar_wait(cempty_bar(acc), ph ^ 1u, abort_flag, spin_ns, ep.status)) {
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
-        const int kb1 = min(num_kb, kb0 + kChunkKB);
+        const int kb1 = chunk_end(kb0, num_kb);
         for (int kb = kb0; kb < kb1; ++kb) {
           if (!mbar_wait(full_bar(stage), phase, abort_flag, spin_ns, ep.status)) {
             ok = false;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       float tot[128];
 #pragma unroll
       for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
-      for (int kb0 = 0; kb0 < num_kb; kb0 += kChunkKB, ++g) {
+      for (int kb0 = 0; kb0 < num_kb; kb0 = chunk_end(kb0, num_kb), ++g) {
         const int acc = (int)(g & 1u);
         const uint32_t ph = (g >> 1) & 1u;
         if (!mbar_wait(cfull_bar(acc), ph, abort_flag, spin_ns, ep.status)) {

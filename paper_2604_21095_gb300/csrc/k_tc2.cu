@@ -254,7 +254,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
         int mp, nt;
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
-        for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kChunkKB, ++g) {
+        for (int kb0 = 0; kb0 < num_kb && ok; kb0 = chunk_end(kb0, num_kb), ++g) {
           const int acc = (int)(g & 1u);
           const uint32_t ph = (g >> 1) & 1u;
           if (!wait(cempty_bar(acc), ph ^ 1u)) {
@@ -263,7 +263,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
-          const int kb1 = min(num_kb, kb0 + kChunkKB);
+          const int kb1 = chunk_end(kb0, num_kb);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!wait(full_bar(stage), phase)) {
               ok = false;
@@ -334,7 +334,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       float tot[128];
 #pragma unroll
       for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
-      for (int kb0 = 0; kb0 < num_kb; kb0 += kChunkKB, ++g) {
+      for (int kb0 = 0; kb0 < num_kb; kb0 = chunk_end(kb0, num_kb), ++g) {
         const int acc = (int)(g & 1u);
         const uint32_t ph = (g >> 1) & 1u;
         if (!wait(cfull_bar(acc), ph)) {

@@ -32,6 +32,16 @@ struct RegSplit {
 };
 constexpr int kTmemCols = 512;                 // two 128 x 256 FP32 chunk accumulators
 constexpr int kChunkKB = 32;                   // K blocks per accumulation chunk (1024 samples)
+// The first chunk of each tile is kFirstChunks chunks long: the epilogue warps finish the
+// previous tile's statistics while it runs, and a longer first chunk gives them that time
+// before the products need a drained accumulator again (one longer chunk in ~20 changes the
+// accumulation little).
+constexpr int kFirstChunks = 1;
+__host__ __device__ constexpr int chunk_end(int kb0, int num_kb) {
+  return (kb0 == 0 ? kFirstChunks * kChunkKB : kb0 + kChunkKB) < num_kb
+             ? (kb0 == 0 ? kFirstChunks * kChunkKB : kb0 + kChunkKB)
+             : num_kb;
+}
 
 
 
@@ -245,28 +255,47 @@ __device__ __forceinline__ void tile_coord(int tile, int n_mt, int n_nt, int gro
 // over the warp's 32 rows: one warp max (redux.sync) of the ordered key bits(|r|) + 1 (0 for
 // NaN; non-negative floats order like their bits), the lowest lane holding it (the smallest
 // marker) offering it to the global per-phenotype best.
-__device__ __forceinline__ void epilogue_tile(const EpiParams& ep, const float (&tot)[128],
+// The 128 columns go in 8 rolled groups of 16, the totals shifted down by 16 registers after
+// each group: fully unrolled, this runs once per tile through tens of KB of straight-line code
+// and stalls on instruction fetch long enough to hold up the products.
+__device__ __forceinline__ void epilogue_tile(const EpiParams& ep, float (&tot)[128],
                                               long long row, long long row_base, bool row_ok,
                                               float rinv, float shift, int col0, int lane) {
+#pragma unroll 1
+  for (int g = 0; g < 8; ++g) {
+    // keys of the group's 16 columns, then 16 independent warp maxima, then the ballots: the
+    // collective operations of different columns overlap instead of forming one chain
+    uint32_t u[16];
 #pragma unroll
-  for (int e = 0; e < 128; ++e) {
-    const int col = col0 + e;
-    float r = __int_as_float(0x7fc00000);
-    if (row_ok && col < ep.P) {
-      const float D = fmaf(shift, ep.col_cs[col], tot[e]);
-      r = corr_nan(D, rinv, ep.col_rmul[col]);
-      if (ep.do_hits && r * r >= ep.r2_thr) emit_hit_raw(ep, D, row, col);
-      if (ep.do_full) ep.rstore[row * ep.ldo + col] = r;
+    for (int k = 0; k < 16; ++k) {
+      const int col = col0 + 16 * g + k;
+      float r = __int_as_float(0x7fc00000);
+      if (row_ok && col < ep.P) {
+        const float D = fmaf(shift, ep.col_cs[col], tot[k]);
+        r = corr_nan(D, rinv, ep.col_rmul[col]);
+        if (ep.do_hits && r * r >= ep.r2_thr) emit_hit_raw(ep, D, row, col);
+        if (ep.do_full) ep.rstore[row * ep.ldo + col] = r;
+      }
+      u[k] = (r == r) ? __float_as_uint(fabsf(r)) + 1u : 0u;
     }
     if (ep.do_best) {
-      const uint32_t u = (r == r) ? __float_as_uint(fabsf(r)) + 1u : 0u;
-      const uint32_t cmax = __reduce_max_sync(0xffffffffu, u);
-      if (cmax) {
-        const uint32_t owners = __ballot_sync(0xffffffffu, u == cmax);
-        if (lane == __ffs(owners) - 1)
-          atomicMax(ep.best + col, best_key(r, ep.marker_offset + row_base + lane));
+      uint32_t cmax[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) cmax[k] = __reduce_max_sync(0xffffffffu, u[k]);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (!cmax[k]) continue;  // warp-uniform
+        const uint32_t owners = __ballot_sync(0xffffffffu, u[k] == cmax[k]);
+        if (lane == __ffs(owners) - 1) {
+          const long long marker = ep.marker_offset + row_base + lane;
+          best_offer(ep.best + col0 + 16 * g + k,
+                     ((unsigned long long)(u[k] - 1u) << 32) |
+                         (unsigned long long)(0xFFFFFFFFu - (uint32_t)marker));
+        }
       }
     }
+#pragma unroll
+    for (int i = 0; i < 112; ++i) tot[i] = tot[i + 16];
   }
 }
 
