@@ -330,9 +330,12 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       if (c->tune_kernel[b] == TUNE_SINGLE)
         TG_CUDA(launch_tc_scan(&tA, &p->tmBhi, &p->tmBlo, p->Npad, ep, c->sm_count, kSpinNs, st,
                                group, dec, a.encoding));
-      else
+      else {
+        ep.wave_ctr = reinterpret_cast<unsigned long long*>(c->scratch + 32);
+        TG_CUDA(cudaMemsetAsync(ep.wave_ctr, 0, sizeof(unsigned long long), st));
         TG_CUDA(launch_tc2_scan(&tA, &p->tmBhi2, &p->tmBlo2, p->Npad, ep, c->sm_count, kSpinNs, st,
                                 group, dec, a.encoding));
+      }
     }
   }
   if (ep.do_hits || ep.do_full) {

@@ -53,6 +53,7 @@ struct EpiParams {
   unsigned long long* n_hits;
   unsigned long long* best;
   uint32_t* status;
+  unsigned long long* wave_ctr;  // CTA-pair lockstep counter (zeroed per launch), NULL = off
   float* raw_out;              // projection mode: D of the first raw_cols columns, [M][raw_ld]
   int raw_cols, raw_ld;
 };

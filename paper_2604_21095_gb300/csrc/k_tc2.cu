@@ -111,6 +111,24 @@ __device__ __forceinline__ void tc2_commit_local(uint32_t bar) {
       : "memory");
 }
 
+// Soft lockstep of the CTA pairs. The tiles in flight at once share their A rows and panel
+// columns through L2 only while they stream the same K range at about the same time; pairs that
+// drift apart read their slabs from DRAM again (4x the traffic, and the power, at full size).
+// So a pair's producers start loading their tile of wave w once every pair has begun wave w
+// (the leader counts its pair in), or after kLockstepNs, whichever comes first: a pair that is
+// slow or not resident delays the others by at most that much and never causes an error.
+constexpr long long kLockstepNs = 30000;
+__device__ __forceinline__ void lockstep(unsigned long long* ctr, bool leader, int w, int ncl,
+                                         int num_tiles) {
+  if (leader) atomicAdd(ctr, 1ull);
+  const long long need = min((long long)num_tiles, (long long)(w + 1) * ncl);
+  const uint64_t t0 = globaltimer_ns();
+  while ((long long)*reinterpret_cast<volatile unsigned long long*>(ctr) < need) {
+    if ((long long)(globaltimer_ns() - t0) > kLockstepNs) break;
+    __nanosleep(64);
+  }
+}
+
 // Tile (pair of m-tiles, n-tile) of cluster-level tile index `tile`; group_p m-tile pairs
 // per raster group.
 __device__ __forceinline__ void tile_coord2(int tile, int n_mp, int n_nt, int group_p, int& mp,
@@ -206,7 +224,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int s = 0; s < S; ++s) armed[s] = -1;
       bool ok = true;
-      for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
+      for (int tile = cid, w = 0; tile < num_tiles && ok; tile += ncl, ++w) {
+        if (ep.wave_ctr) lockstep(ep.wave_ctr, leader, w, ncl, num_tiles);
         int mp, nt;
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
         const int mt0 = 2 * mp;
