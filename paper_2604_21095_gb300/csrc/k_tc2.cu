@@ -10,7 +10,9 @@
 //
 // Roles (384 threads, three warpgroups, as in k_tc.cu):
 //   warp 0 lane 0 (both CTAs)   TMA producer into the local stage ring; every copy signals
-//                               the leader's full barrier (cta_group::2 completion)
+//                               the leader's full barrier (cta_group::2 completion). The
+//                               leader's producer also takes the pair's next tile (next_tile)
+//                               and publishes its index to every role of both CTAs
 //   warp 1 lane 0 (leader only) MMA issuer; commits are multicast to both CTAs' barriers
 //   warps 4..11 (both CTAs)     epilogue on the local 128 rows; the drained signal goes to
 //                               the leader's chunk-empty barrier (16 arrivals: 8 per CTA)
@@ -39,10 +41,15 @@ struct Cfg2 {
   // 24 KB (+ 2 or 4 KB)
   static constexpr int kStageBytes = A_BYTES + 2 * HB_BYTES + DecCfg<OPA>::kPackBytes;
   static constexpr int kStages = 8;
-  static constexpr int kBarBytes = 256;
+  static constexpr int kBarBytes = 512;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
+
+// Tile indices pass from the leader's producer to every other role of both CTAs through a
+// ring of kTileRing shared-memory slots (a full barrier per slot in each CTA, an empty
+// barrier per slot in the leader).
+constexpr int kTileRing = 4;
 
 constexpr uint32_t kIdesc2 = idesc_bf16_m(256, 256);
 
@@ -111,21 +118,62 @@ __device__ __forceinline__ void tc2_commit_local(uint32_t bar) {
       : "memory");
 }
 
-// Soft lockstep of the CTA pairs. The tiles in flight at once share their A rows and panel
-// columns through L2 only while they stream the same K range at about the same time; pairs that
-// drift apart read their slabs from DRAM again (4x the traffic, and the power, at full size).
-// So a pair's producers start loading their tile of wave w once every pair has begun wave w
-// (the leader counts its pair in), or after kLockstepNs, whichever comes first: a pair that is
-// slow or not resident delays the others by at most that much and never causes an error.
+// Tile order and soft lockstep of the CTA pairs. The tiles in flight at once share their A rows
+// and panel columns through L2 only while they stream the same K range at about the same time;
+// pairs that drift apart read their slabs from DRAM again (4x the traffic, and the power, at
+// full size). With a counter (zeroed per launch), a pair takes the next tile of the raster
+// when it is ready for one, and starts loading it once all but kLockstepSlack tiles of that
+// tile's wave (the ncl tiles in flight together) have been taken, or after kLockstepNs: a pair
+// that runs slower than the others takes fewer tiles instead of holding every wave back (with
+// a fixed order, pair c taking every ncl-th tile, the last pair to start set the pace of every
+// wave), and a pair that is not resident delays the others by at most the time limit and never
+// causes an error. Without a counter, pair c takes tiles c, c + ncl, c + 2 ncl, ... without
+// waiting. Indices past the last tile (returned as num_tiles) end the pair's work.
 constexpr long long kLockstepNs = 30000;
-__device__ __forceinline__ void lockstep(unsigned long long* ctr, bool leader, int w, int ncl,
+constexpr int kLockstepSlack = 2;
+__device__ __forceinline__ int next_tile(unsigned long long* ctr, int i, int cid, int ncl,
                                          int num_tiles) {
-  if (leader) atomicAdd(ctr, 1ull);
-  const long long need = min((long long)num_tiles, (long long)(w + 1) * ncl);
+  if (!ctr) return min(cid + i * ncl, num_tiles);
+  const unsigned long long t = atomicAdd(ctr, 1ull);
+  if (t >= (unsigned long long)num_tiles) return num_tiles;
+  const long long need = min((long long)num_tiles,
+                             (long long)(t / ncl + 1) * ncl - kLockstepSlack);
   const uint64_t t0 = globaltimer_ns();
   while ((long long)*reinterpret_cast<volatile unsigned long long*>(ctr) < need) {
     if ((long long)(globaltimer_ns() - t0) > kLockstepNs) break;
     __nanosleep(64);
+  }
+  return (int)t;
+}
+
+// mbarrier wait with acquire at cluster scope (the phase may be completed by the other CTA),
+// bounded like mbar_wait.
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
+                                                  volatile int* abort_flag, long long limit_ns,
+                                                  uint32_t* status) {
+  if (mbar_try_cluster(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
+#pragma unroll 1
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_cluster(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if ((long long)(globaltimer_ns() - t0) > limit_ns) {
+      *abort_flag = 1;
+      atomicOr(status, ST_TIMEOUT);
+      return false;
+    }
   }
 }
 
@@ -162,9 +210,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   auto cempty_bar = [&](int a) { return bars + 8u * (2 * S + 2 + a); };
   const uint32_t drain_bar = bars + 8u * (2 * S + 4);
   auto pfull_bar = [&](int s) { return bars + 8u * (2 * S + 5 + s); };  // local packed rows landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * C::kStageBytes + 8 * (3 * S + 5));
-  static_assert(8 * (3 * S + 5) + 8 <= C::kBarBytes, "barrier area");
+  auto tfull_bar = [&](int r) { return bars + 8u * (3 * S + 5 + r); };   // tile slot written
+  auto tempty_bar = [&](int r) { return bars + 8u * (3 * S + 5 + kTileRing + r); };  // leader's
+  constexpr int kBarEnd = 8 * (3 * S + 5 + 2 * kTileRing);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * C::kStageBytes + kBarEnd);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* tile_slot = reinterpret_cast<volatile int*>(tmem_slot + 2);
+  static_assert(kBarEnd + 8 + 4 * kTileRing <= C::kBarBytes, "barrier area");
+  // consumers of each tile slot: the leader's MMA thread, the peer's producer, the epilogue
+  // warps of both CTAs and, when decoding here, the decoder warps of both CTAs
+  constexpr int kRingConsumers = 2 + 2 * kEpiWarps + (kFused ? 2 * (kDecThreads / 32) : 0);
 
   auto sA = [&](int s) { return base + s * C::kStageBytes; };
   auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
@@ -186,6 +241,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     for (int a = 0; a < 2; ++a) {
       mbar_init(cfull_bar(a), 1);
       mbar_init(cempty_bar(a), 2 * kEpiWarps);
+    }
+    for (int r = 0; r < kTileRing; ++r) {
+      mbar_init(tfull_bar(r), 1);
+      mbar_init(tempty_bar(r), kRingConsumers);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -213,6 +272,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     if (!ok) st_cluster_u32(peer_abort, 1u);
     return ok;
   };
+  // Tile `i` of this pair's sequence from the ring, for every consumer role: a single thread
+  // (whole_warp false) or a whole warp, whose lane 0 then arrives for it. Returns num_tiles at
+  // the end of the work, and -1 on timeout or abort.
+  auto take_tile = [&](int i, bool whole_warp) -> int {
+    const int r = i % kTileRing;
+    if (!mbar_wait_cluster(tfull_bar(r), (uint32_t)(i / kTileRing) & 1u, abort_flag, spin_ns,
+                           ep.status)) {
+      st_cluster_u32(peer_abort, 1u);
+      return -1;
+    }
+    const int t = tile_slot[r];
+    if (whole_warp) __syncwarp();
+    if (!whole_warp || lane == 0) mbar_arrive_cluster(map_to_rank(tempty_bar(r), 0u));
+    return t;
+  };
 
   if (warp < 4) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kLow));
@@ -224,8 +298,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int s = 0; s < S; ++s) armed[s] = -1;
       bool ok = true;
-      for (int tile = cid, w = 0; tile < num_tiles && ok; tile += ncl, ++w) {
-        if (ep.wave_ctr) lockstep(ep.wave_ctr, leader, w, ncl, num_tiles);
+      for (int i = 0; ok; ++i) {
+        int tile;
+        if (leader) {  // take the next tile and publish it to both CTAs
+          const int r = i % kTileRing;
+          if (!mbar_wait_cluster(tempty_bar(r), ((uint32_t)(i / kTileRing) & 1u) ^ 1u, abort_flag,
+                                 spin_ns, ep.status)) {
+            st_cluster_u32(peer_abort, 1u);
+            break;
+          }
+          tile = next_tile(ep.wave_ctr, i, cid, ncl, num_tiles);
+          tile_slot[r] = tile;
+          st_cluster_u32(map_to_rank(smem_u32((const void*)(tile_slot + r)), 1u), (uint32_t)tile);
+          mbar_arrive(tfull_bar(r));
+          mbar_arrive_cluster(map_to_rank(tfull_bar(r), 1u));
+        } else {
+          tile = take_tile(i, false);
+          if (tile < 0) break;
+        }
+        if (tile >= num_tiles) break;
         int mp, nt;
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
         const int mt0 = 2 * mp;
@@ -270,9 +361,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       uint32_t g = 0;
       bool ok = true;
-      for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
-        int mp, nt;
-        tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
+      for (int i = 0; ok; ++i) {
+        const int tile = take_tile(i, false);
+        if (tile < 0 || tile >= num_tiles) break;
         for (int kb0 = 0; kb0 < num_kb && ok; kb0 = chunk_end(kb0, num_kb), ++g) {
           const int acc = (int)(g & 1u);
           const uint32_t ph = (g >> 1) & 1u;
@@ -314,7 +405,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
+      for (int i = 0; ok; ++i) {
+        const int tile = take_tile(i, true);
+        if (tile < 0 || tile >= num_tiles) break;
         int mp, nt;
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
         const long long r0 = (long long)(2 * mp + (int)rank) * TBM + t;
@@ -347,7 +440,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const uint32_t leader_cempty1 = map_to_rank(cempty_bar(1), 0u);
     uint32_t g = 0;
     bool ok = true;
-    for (int tile = cid; tile < num_tiles && ok; tile += ncl) {
+    for (int i = 0; ok; ++i) {
+      const int tile = take_tile(i, true);
+      if (tile < 0 || tile >= num_tiles) break;
       int mp, nt;
       tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
       float tot[128];

@@ -138,6 +138,58 @@ def test_degenerate_markers_and_phenotypes(tgctx, precision):
     assert np.array_equal(ok, np.isfinite(res["t"]))
 
 
+@pytest.mark.parametrize("precision", ["fp32", "split"])
+@pytest.mark.parametrize("encoding", ["2bit", "u8"])
+def test_exact_fit_is_a_hit_with_unit_r(tgctx, precision, encoding):
+    """A phenotype that is exactly b*g_j + (covariates) has |r| = 1 at marker j (r clamped to
+    [-1, 1], t and -log10 p infinite or beyond any threshold, never NaN); it is the hit and the
+    best marker of that phenotype with beta = b, and the other phenotypes keep oracle parity."""
+    N, M, P, n_cov = 700, 40, 4, 3
+    cov = synth.covariates(51, N, n_cov)
+    if encoding == "2bit":
+        counts, miss = synth.hard_calls(51, 0, synth.maf(51, 0, M, lo=0.2), N, 0.0)
+        G = synth.pack_2bit(counts, miss)
+        g = counts.double()
+    else:
+        G = torch.zeros(M, (N + 15) // 16 * 16, dtype=torch.uint8)  # rows padded to 16 bytes
+        G[:, :N] = torch.randint(0, 256, (M, N), generator=torch.Generator().manual_seed(51),
+                                 dtype=torch.uint8)
+        g = G[:, :N].double() * (2.0 / 255.0)
+    fits = {0: (5, 0.7), 1: (17, -1.3)}
+    Yt = synth.phenotypes(51, cov, P)
+    for p, (j, b) in fits.items():
+        y = b * g[j] + 0.5 + cov.T @ torch.tensor([0.3, -0.2, 0.1], dtype=torch.float64)
+        Yt[p] = y.float()
+    panel = tg.tg_prepare_panel(tgctx, Yt.cuda(), N, P, cov.cuda())
+    try:
+        res = run_scan(tgctx, panel, G.cuda(), N, P, encoding, precision, full=True,
+                       hit_mlog10p=50.0)
+    finally:
+        tg.tg_panel_free(panel)
+    assert res["status"] == tg.TG_OK
+    for k in ("beta", "se", "t", "mlog10p"):
+        assert not np.isnan(res[k]).any(), k
+    got = {(int(h["marker"]), int(h["pheno"])): h for h in res["hits"]}
+    for p, (j, b) in fits.items():
+        h = got[(j, p)]
+        assert abs(h["beta"] - b) <= 1e-4 * abs(b), (p, h["beta"], b)
+        assert math.copysign(1.0, h["t"]) == math.copysign(1.0, b) and abs(h["t"]) >= 1e3
+        assert h["mlog10p"] >= 1e3
+        assert res["best_marker"][p] == j and res["best_absr"][p] >= 1.0 - 1e-5
+        assert abs(res["t"][j, p]) >= 1e3 and res["mlog10p"][j, p] >= 1e3
+        assert abs(res["beta"][j, p] - b) <= 1e-4 * abs(b)
+    ref = oracle.scan(G.numpy(), encoding, oracle_panel(Yt, cov))
+    keep = [2, 3]
+
+    def sub(d):
+        return {k: (v[:, keep] if isinstance(v, np.ndarray) and v.ndim == 2 else v)
+                for k, v in d.items()}
+
+    compare_full(sub(res), sub(ref), label=f"exact fit/{encoding}/{precision}")
+    for p, (j, b) in fits.items():  # the oracle agrees: r = +-1 up to the FP32 rounding of Y
+        assert abs(abs(ref["r"][j, p]) - 1.0) <= 1e-9 and abs(ref["beta"][j, p] - b) <= 1e-6
+
+
 @pytest.mark.parametrize("M,P", [(1, 1), (129, 257), (256, 256), (5, 1000)])
 @pytest.mark.parametrize("precision", ["fp32", "split"])
 def test_tile_edges(tgctx, M, P, precision):
