@@ -369,10 +369,13 @@ def _ours(args, dist, rank, ws):
     flops = 2.0 * w.N * M * w.P                      # Eq. 2, algorithmic
     achieved = flops / (gemm_ms / 1000.0) / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    prof = _kernel_profile()
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": _traffic(),
+                "frac": achieved / peak, "traffic": prof.get("dram_bytes_per_launch"),
                 "kernel": "k_tc2_scan (tcgen05 cta_group::2 split-BF16 + fused epilogue)",
-                "issued_tflops": 2 * achieved, "peak_source": f"{peak_src} bf16 sustained",
+                "issued_tflops": 2 * achieved, "issued_frac": 2 * achieved / peak,
+                "tensor_pipe_active": prof.get("tensor_pipe_active"),
+                "peak_source": f"{peak_src} bf16 sustained",
                 "kernel_ms": gemm_ms,
                 "stage_ms_per_step": {k: v[0] / max(1, args.steps) for k, v in stages.items()}}
 
@@ -535,9 +538,10 @@ def _ours_batched(args, dist, rank, ws):
     tg.tg_destroy(ctx)
 
 
-def _traffic():
-    """DRAM bytes per launch of the contraction kernel from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+def _kernel_profile():
+    """DRAM bytes per launch and the tensor pipe's active fraction of the elapsed cycles of the
+    contraction kernel, from the committed full-size ncu summary, if it was taken on the current
+    kernel sources (else an empty dict)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "tc2_scan_traffic_n23000_p20480_u8.md")
     csrc = os.path.join(ROOT, "paper_2604_21095_gb300", "csrc")
@@ -550,10 +554,11 @@ def _traffic():
                 k, v = line.split(":", 1)
                 rec[k.strip()] = v.strip()
         if rec.get("source_sha256") != h:
-            return None
-        return int(rec["dram_bytes_per_launch"])
+            return {}
+        return {"dram_bytes_per_launch": int(rec["dram_bytes_per_launch"]),
+                "tensor_pipe_active": float(rec["tensor_pipe_active_pct"]) / 100.0}
     except (OSError, KeyError, ValueError):
-        return None
+        return {}
 
 
 def _sweep_p(args):
