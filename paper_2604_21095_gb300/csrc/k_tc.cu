@@ -47,7 +47,11 @@ struct Cfg {
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;  // + alignment slack
 };
 
-template <int OPA>
+// KS = K blocks per stage. The 64-column covariate projection streams the 3 GB operand and is
+// bound by HBM, where two consecutive 64-byte row segments requested back to back use the DRAM
+// pages better than one: it loads two K blocks per stage into the 40 KB slot (A halves at 0 and
+// 8 KB, B_hi halves at 16 and 20 KB, B_lo halves at 24 and 28 KB; 64 B rows).
+template <int OPA, int KS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmBhi,
               const __grid_constant__ CUtensorMap tmBlo, int num_kb, int n_mt, int n_nt, int bn,
@@ -76,6 +80,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
   auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + B_BYTES; };
   auto sPk = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * B_BYTES; };
+  static_assert(KS == 1 || (KS == 2 && !kFused && 2 * A_BYTES + 4 * 4096 <= C::kStageBytes),
+                "two K blocks per stage: decoded operand and at most 64 B rows");
+  auto sAk = [&](int s, int h) { return KS == 1 ? sA(s) : sA(s) + (uint32_t)(h * A_BYTES); };
+  auto sBhik = [&](int s, int h) {
+    return KS == 1 ? sBhi(s) : sA(s) + (uint32_t)(2 * A_BYTES + h * 4096);
+  };
+  auto sBlok = [&](int s, int h) {
+    return KS == 1 ? sBlo(s) : sA(s) + (uint32_t)(2 * A_BYTES + 2 * 4096 + h * 4096);
+  };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -118,21 +131,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       int mt, nt;
       tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
-      const uint32_t bytes = (kFused ? 0u : (uint32_t)A_BYTES) + 2u * (uint32_t)bn * (TBK * 2);
-      for (int kb = 0; kb < num_kb; ++kb) {
+      const uint32_t bytes =
+          (uint32_t)KS * ((kFused ? 0u : (uint32_t)A_BYTES) + 2u * (uint32_t)bn * (TBK * 2));
+      for (int kb = 0; kb < num_kb; kb += KS) {
         if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, spin_ns, ep.status)) {
           ok = false;
           break;
         }
         mbar_expect_tx(full_bar(stage), bytes);
         armed[stage] = (int)phase;
-        if (!kFused) tma_load_2d(&tmAhi, sA(stage), full_bar(stage), kb * TBK, mt * TBM);
         if (kFused) {
           mbar_expect_tx(pfull_bar(stage), (uint32_t)DecCfg<OPA>::kPackBytes);
           tma_load_2d(&da.tmG, sPk(stage), pfull_bar(stage), dec_box_x<OPA>(kb), mt * TBM);
         }
-        tma_load_2d(&tmBhi, sBhi(stage), full_bar(stage), kb * TBK, nt * bn);
-        tma_load_2d(&tmBlo, sBlo(stage), full_bar(stage), kb * TBK, nt * bn);
+#pragma unroll
+        for (int h = 0; h < KS; ++h) {
+          if (!kFused)
+            tma_load_2d(&tmAhi, sAk(stage, h), full_bar(stage), (kb + h) * TBK, mt * TBM);
+          tma_load_2d(&tmBhi, sBhik(stage, h), full_bar(stage), (kb + h) * TBK, nt * bn);
+          tma_load_2d(&tmBlo, sBlok(stage, h), full_bar(stage), (kb + h) * TBK, nt * bn);
+        }
         if (++stage == S) {
           stage = 0;
           phase ^= 1u;
@@ -167,20 +185,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
         const int kb1 = chunk_end(kb0, num_kb);
-        for (int kb = kb0; kb < kb1; ++kb) {
+        for (int kb = kb0; kb < kb1; kb += KS) {
           if (!mbar_wait(full_bar(stage), phase, abort_flag, spin_ns, ep.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
 #pragma unroll
-          for (int k = 0; k < TBK / 16; ++k) {
-            const uint64_t a = sdesc_sw64(sA(stage) + 32u * k);
-            const uint64_t bh = sdesc_sw64(sBhi(stage) + 32u * k);
-            const uint64_t bl = sdesc_sw64(sBlo(stage) + 32u * k);
-            tc_mma(d, a, bh, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
-            tc_mma(d, a, bl, idesc, 1u);
-          }
+          for (int h = 0; h < KS; ++h)
+#pragma unroll
+            for (int k = 0; k < TBK / 16; ++k) {
+              const uint64_t a = sdesc_sw64(sAk(stage, h) + 32u * k);
+              const uint64_t bh = sdesc_sw64(sBhik(stage, h) + 32u * k);
+              const uint64_t bl = sdesc_sw64(sBlok(stage, h) + 32u * k);
+              tc_mma(d, a, bh, idesc, (kb > kb0 || h > 0 || k > 0) ? 1u : 0u);
+              tc_mma(d, a, bl, idesc, 1u);
+            }
           tc_commit(empty_bar(stage));
           if (++stage == S) {
             stage = 0;
@@ -303,13 +323,13 @@ __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, u
   }
 }
 
-template <int OPA>
+template <int OPA, int KS>
 cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* bl, int64_t K,
                const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st,
                const DecodeArgs& da) {
   static bool attr_set = false;  // per process and instantiation; the attribute is per function
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_scan<OPA>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_scan<OPA, KS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg<OPA>::kSmem);
     if (e != cudaSuccess) return e;
@@ -320,8 +340,9 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* b
   const int n_nt = (ep.P + bn - 1) / bn;
   const int tiles = n_mt * n_nt;
   const int grid = tiles < sm_count ? tiles : sm_count;
-  k_tc_scan<OPA><<<grid, kThreads, Cfg<OPA>::kSmem, st>>>(*a, *bh, *bl, (int)(K / TBK), n_mt, n_nt,
-                                                          bn, group_m, spin_ns, ep, da);
+  if (KS == 2 && (bn > 64 || (K / TBK) % 2)) return cudaErrorInvalidValue;
+  k_tc_scan<OPA, KS><<<grid, kThreads, Cfg<OPA>::kSmem, st>>>(
+      *a, *bh, *bl, (int)(K / TBK), n_mt, n_nt, bn, group_m, spin_ns, ep, da);
   return cudaGetLastError();
 }
 
@@ -333,11 +354,15 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                            int encoding) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   if (K % TBK || group_m < 1) return cudaErrorInvalidValue;
-  if (!dec) return go<OPA_TMA>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{});
+  if (!dec) {
+    if (ep.raw_out)  // the covariate projection
+      return go<OPA_TMA, 2>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{});
+    return go<OPA_TMA, 1>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{});
+  }
   if (dec->M != ep.M) return cudaErrorInvalidValue;
   if (encoding == TG_ENC_2BIT)
-    return go<OPA_2BIT>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
-  return go<OPA_U8>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
+    return go<OPA_2BIT, 1>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
+  return go<OPA_U8, 1>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
 }
 
 cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,

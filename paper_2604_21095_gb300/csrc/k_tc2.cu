@@ -35,12 +35,19 @@ using namespace tcx;
 
 constexpr int HB_BYTES = 128 * TBK * 2;  // one CTA's half of a B tile: 8 KB
 
+// K blocks per stage: two with the decoded operand, so that each row's two consecutive 64-byte
+// segments are requested back to back (better DRAM page use where the kernel streams HBM, at
+// small P); one when the A tiles are decoded here.
+template <int OPA>
+constexpr int kStageKB = OPA == OPA_TMA ? 2 : 1;
+
 template <int OPA>
 struct Cfg2 {
-  // A, this CTA's halves of B_hi and B_lo and (when decoding here) its packed rows:
-  // 24 KB (+ 2 or 4 KB)
-  static constexpr int kStageBytes = A_BYTES + 2 * HB_BYTES + DecCfg<OPA>::kPackBytes;
-  static constexpr int kStages = 8;
+  // per K block: A, this CTA's halves of B_hi and B_lo (24 KB); when decoding here, plus the
+  // CTA's packed rows (2 or 4 KB)
+  static constexpr int KS = kStageKB<OPA>;
+  static constexpr int kStageBytes = KS * (A_BYTES + 2 * HB_BYTES) + DecCfg<OPA>::kPackBytes;
+  static constexpr int kStages = 8 / KS;
   static constexpr int kBarBytes = 512;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;
   static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
@@ -221,10 +228,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   // warps of both CTAs and, when decoding here, the decoder warps of both CTAs
   constexpr int kRingConsumers = 2 + 2 * kEpiWarps + (kFused ? 2 * (kDecThreads / 32) : 0);
 
-  auto sA = [&](int s) { return base + s * C::kStageBytes; };
-  auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
-  auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + HB_BYTES; };
-  auto sPk = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * HB_BYTES; };
+  // stage layout: KS A tiles, KS B_hi halves, KS B_lo halves, then the packed rows
+  constexpr int KS = C::KS;
+  static_assert(KS == 1 || !kFused, "decoding here loads one K block per stage");
+  auto sA = [&](int s, int h) { return base + s * C::kStageBytes + h * A_BYTES; };
+  auto sBhi = [&](int s, int h) { return base + s * C::kStageBytes + KS * A_BYTES + h * HB_BYTES; };
+  auto sBlo = [&](int s, int h) {
+    return base + s * C::kStageBytes + KS * (A_BYTES + HB_BYTES) + h * HB_BYTES;
+  };
+  auto sPk = [&](int s) { return base + s * C::kStageBytes + KS * (A_BYTES + 2 * HB_BYTES); };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_rank();
@@ -320,10 +332,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         int mp, nt;
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
         const int mt0 = 2 * mp;
-        const uint32_t pair_bytes = 2u * ((kFused ? 0u : (uint32_t)A_BYTES) + 2 * HB_BYTES);
+        const uint32_t pair_bytes = 2u * KS * ((kFused ? 0u : (uint32_t)A_BYTES) + 2 * HB_BYTES);
         const int arow = (mt0 + (int)rank) * TBM;
         const int brow = nt * TBN + (int)rank * 128;
-        for (int kb = 0; kb < num_kb; ++kb) {
+        for (int kb = 0; kb < num_kb; kb += KS) {
           if (!wait(empty_bar(stage), phase ^ 1u)) {
             ok = false;
             break;
@@ -335,13 +347,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           if (leader) mbar_expect_tx(full_bar(stage), pair_bytes);
           armed[stage] = (int)phase;
           const uint32_t fb = map_to_rank(full_bar(stage), 0u);
-          if (!kFused) tma_load_2d_pair(&tmAhi, sA(stage), fb, kb * TBK, arow);
           if (kFused) {  // this CTA's packed rows, completing on its own barrier
             mbar_expect_tx(pfull_bar(stage), (uint32_t)DecCfg<OPA>::kPackBytes);
             tma_load_2d(&da.tmG, sPk(stage), pfull_bar(stage), dec_box_x<OPA>(kb), arow);
           }
-          tma_load_2d_pair(&tmBhi, sBhi(stage), fb, kb * TBK, brow);
-          tma_load_2d_pair(&tmBlo, sBlo(stage), fb, kb * TBK, brow);
+#pragma unroll
+          for (int h = 0; h < KS; ++h) {
+            if (!kFused) tma_load_2d_pair(&tmAhi, sA(stage, h), fb, (kb + h) * TBK, arow);
+            tma_load_2d_pair(&tmBhi, sBhi(stage, h), fb, (kb + h) * TBK, brow);
+            tma_load_2d_pair(&tmBlo, sBlo(stage, h), fb, (kb + h) * TBK, brow);
+          }
           if (++stage == S) {
             stage = 0;
             phase ^= 1u;
@@ -374,20 +389,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
           const int kb1 = chunk_end(kb0, num_kb);
-          for (int kb = kb0; kb < kb1; ++kb) {
+          for (int kb = kb0; kb < kb1; kb += KS) {
             if (!wait(full_bar(stage), phase)) {
               ok = false;
               break;
             }
             tc_fence_after();
 #pragma unroll
-            for (int k = 0; k < TBK / 16; ++k) {
-              const uint64_t a = sdesc_sw64(sA(stage) + 32u * k);
-              const uint64_t bh = sdesc_sw64(sBhi(stage) + 32u * k);
-              const uint64_t bl = sdesc_sw64(sBlo(stage) + 32u * k);
-              tc2_mma(d, a, bh, (kb > kb0 || k > 0) ? 1u : 0u);
-              tc2_mma(d, a, bl, 1u);
-            }
+            for (int h = 0; h < KS; ++h)
+#pragma unroll
+              for (int k = 0; k < TBK / 16; ++k) {
+                const uint64_t a = sdesc_sw64(sA(stage, h) + 32u * k);
+                const uint64_t bh = sdesc_sw64(sBhi(stage, h) + 32u * k);
+                const uint64_t bl = sdesc_sw64(sBlo(stage, h) + 32u * k);
+                tc2_mma(d, a, bh, (kb > kb0 || h > 0 || k > 0) ? 1u : 0u);
+                tc2_mma(d, a, bl, 1u);
+              }
             tc2_commit_both(empty_bar(stage));
             if (++stage == S) {
               stage = 0;
@@ -417,8 +434,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          dec_expand_store<OPA>(sPk(stage), k0, r0 < da.M, t, kb, da.N, sA(stage));
-          dec_expand_store<OPA>(sPk(stage), k1, r0 + 64 < da.M, t + 64, kb, da.N, sA(stage));
+          dec_expand_store<OPA>(sPk(stage), k0, r0 < da.M, t, kb, da.N, sA(stage, 0));
+          dec_expand_store<OPA>(sPk(stage), k1, r0 + 64 < da.M, t + 64, kb, da.N, sA(stage, 0));
           // the leader's tensor core reads this CTA's tile: make the stores visible to the
           // async proxy at cluster scope before signalling
           asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
@@ -510,6 +527,7 @@ cudaError_t go2(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* 
   const int tiles = ((n_mt + 1) / 2) * n_nt;
   const int pairs = tiles < sm_count / 2 ? tiles : sm_count / 2;
   const int group_p = group_m / 2 > 0 ? group_m / 2 : 1;
+  if ((K / TBK) % Cfg2<OPA>::KS) return cudaErrorInvalidValue;
   k_tc2_scan<OPA><<<2 * pairs, kThreads, Cfg2<OPA>::kSmem, st>>>(
       *a, *bh, *bl, (int)(K / TBK), n_mt, n_nt, group_p, spin_ns, ep, da);
   return cudaGetLastError();
