@@ -649,7 +649,8 @@ tg_status tg_prepare_panel_subset(tg_ctx* c, const float* Y, int64_t ldy, int64_
   if ((e = run())) return cleanup(cuda_fail(e, "tg_prepare_panel_subset scatter"));
   if (N % 32) {  // bits past N are not samples
     const uint32_t last = hm[(size_t)(nw - 1)] & ((1u << (N % 32)) - 1u);
-    TG_CUDA(cudaMemcpy(r->samples + nw - 1, &last, sizeof(uint32_t), cudaMemcpyHostToDevice));
+    if ((e = cudaMemcpy(r->samples + nw - 1, &last, sizeof(uint32_t), cudaMemcpyHostToDevice)))
+      return cleanup(cuda_fail(e, "tg_prepare_panel_subset sample mask"));
   }
   if (!make_tmap(&r->tmBhi, r->Bhi, Pp, Np, Np, 256) || !make_tmap(&r->tmBlo, r->Blo, Pp, Np, Np, 256) ||
       !make_tmap(&r->tmBhi2, r->Bhi, Pp, Np, Np, 128) || !make_tmap(&r->tmBlo2, r->Blo, Pp, Np, Np, 128) ||
@@ -1106,7 +1107,10 @@ tg_status tg_autotune(tg_ctx* c, const tg_panel* p, int32_t encoding, int64_t M,
   unsigned long long* best = nullptr;
   cudaError_t e;
   auto cleanup = [&]() { dfree(G); dfree(hits); dfree(cnt); dfree(best); };
-  if ((e = dalloc(&G, (size_t)(M * ldg))) || (e = dalloc(&hits, 1024)) || (e = dalloc(&cnt, 1)) ||
+  // chance hits of the random trial block (about 5e-8 of M x P tests per scan) stay far below
+  // the trial capacity, so the trials never latch a capacity error in the context's status
+  constexpr int64_t kTrialHits = 1 << 16;
+  if ((e = dalloc(&G, (size_t)(M * ldg))) || (e = dalloc(&hits, kTrialHits)) || (e = dalloc(&cnt, 1)) ||
       (e = dalloc(&best, (size_t)std::max<int64_t>(p->P, 1)))) {
     cleanup();
     return cuda_fail(e, "tg_autotune allocation");
@@ -1119,7 +1123,7 @@ tg_status tg_autotune(tg_ctx* c, const tg_panel* p, int32_t encoding, int64_t M,
   }
   tg_outputs o{};
   o.hits = hits;
-  o.hit_capacity = 1024;
+  o.hit_capacity = kTrialHits;
   o.n_hits = cnt;
   o.best = best;
   const tg_scan_opts opts{TG_PREC_SPLIT_BF16, 0, 7.30103};
@@ -1149,7 +1153,10 @@ tg_status tg_autotune(tg_ctx* c, const tg_panel* p, int32_t encoding, int64_t M,
     int64_t n_before[TG_N_STAGES];
     tg_stage_times(c, ms_before, n_before, 0);
     c->prof = true;
-    for (int r = 0; r < 2 && s == TG_OK; ++r) s = scan_impl(c, p, a, st);
+    for (int r = 0; r < 2 && s == TG_OK; ++r) {
+      if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st))) { s = cuda_fail(e, "autotune"); break; }
+      s = scan_impl(c, p, a, st);
+    }
     c->prof = false;
     double ms_after[TG_N_STAGES];
     int64_t n_after[TG_N_STAGES];
