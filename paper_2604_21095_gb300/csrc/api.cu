@@ -132,13 +132,14 @@ cudaError_t ensure_markers(tg_ctx* c, int64_t M) {
   if (M <= c->cap_m) return cudaSuccess;
   const int64_t cap = round_up(M, MT);
   dfree(c->nobs); dfree(c->mean); dfree(c->shift); dfree(c->mh); dfree(c->gc2s); dfree(c->gc2); dfree(c->qg);
-  dfree(c->gres2); dfree(c->rinv); dfree(c->rinv64);
+  dfree(c->gres2); dfree(c->rinv); dfree(c->rinv64); dfree(c->refine_list);
   c->cap_m = 0;
   cudaError_t e;
   if ((e = dalloc(&c->nobs, cap)) || (e = dalloc(&c->mean, cap)) || (e = dalloc(&c->shift, cap)) ||
       (e = dalloc(&c->mh, cap)) || (e = dalloc(&c->gc2s, cap)) ||
       (e = dalloc(&c->gc2, cap)) || (e = dalloc(&c->qg, cap * QCOLS)) ||
-      (e = dalloc(&c->gres2, cap)) || (e = dalloc(&c->rinv, cap)) || (e = dalloc(&c->rinv64, cap)))
+      (e = dalloc(&c->gres2, cap)) || (e = dalloc(&c->rinv, cap)) || (e = dalloc(&c->rinv64, cap)) ||
+      (e = dalloc(&c->refine_list, cap)))
     return e;
   c->cap_m = cap;
   return cudaSuccess;
@@ -276,9 +277,11 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
                                 c->mean, c->gc2s, st));
   }
   {
-    StageScope s(c, STAGE_NORM, st, 1);
+    StageScope s(c, STAGE_NORM, st, nq > 0 ? 2 : 1);
+    const MarkerRefine rf{a.G, a.ldg, a.encoding, a.N, a.missing, a.ldm, c->mean, p->Q, (int)p->q,
+                          c->refine_list, c->scratch + 40};
     TG_CUDA(launch_marker_norm(a.M, c->nobs, p->samples ? c->gc2s : c->gc2, c->qg, nq, kappa64, c->gres2,
-                               a.out.marker_norm2, c->rinv, c->rinv64, st));
+                               a.out.marker_norm2, c->rinv, c->rinv64, &rf, st));
     if (a.out.marker_nobs)
       TG_CUDA(cudaMemcpyAsync(a.out.marker_nobs, c->nobs, sizeof(int32_t) * a.M,
                               cudaMemcpyDeviceToDevice, st));
@@ -454,7 +457,7 @@ tg_status tg_destroy(tg_ctx* c) {
   dfree(c->status); dfree(c->scratch);
   dfree(c->Ahi); dfree(c->A32); dfree(c->shift); dfree(c->mh); dfree(c->gc2s);
   dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
-  dfree(c->rinv); dfree(c->rinv64);
+  dfree(c->rinv); dfree(c->rinv64); dfree(c->refine_list);
   dfree(c->stage_buf[0]); dfree(c->stage_buf[1]);
   dfree(c->dhits); dfree(c->dnhits); dfree(c->dbest);
   for (auto& ev : c->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }

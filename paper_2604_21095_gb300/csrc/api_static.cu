@@ -149,6 +149,7 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   probe.take<double>((size_t)rows);
   probe.take<float>((size_t)rows);
   probe.take<double>((size_t)rows);
+  probe.take<int>((size_t)rows);
   probe.take<unsigned char>((size_t)rows * p->Npad * elem);
   if (probe.used > kStaticScratchBytes) {
     const size_t per = (size_t)p->Npad * elem + 4 * QCOLS + 64;
@@ -167,7 +168,7 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   if (s != TG_OK) return s;
 
   Carver cv{ds->base};
-  uint32_t* status = cv.take<uint32_t>(4);
+  uint32_t* status = cv.take<uint32_t>(4);  // [0] status word, [1] count of re-projected markers
   unsigned long long* hit_start = cv.take<unsigned long long>(1);
   float* shift = cv.take<float>((size_t)rows);
   int32_t* nobs = cv.take<int32_t>((size_t)rows);
@@ -177,6 +178,7 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   double* gres2 = cv.take<double>((size_t)rows);
   float* rinv = cv.take<float>((size_t)rows);
   double* rinv64 = cv.take<double>((size_t)rows);
+  int* refine_list = cv.take<int>((size_t)rows);
   void* Ahi = cv.take<unsigned char>((size_t)rows * p->Npad * elem);
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -214,7 +216,10 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
                               st));
     }
   }
-  TGS_CUDA(launch_marker_norm(M, nobs, gc2, qg, nq, kappa64, gres2, out->marker_norm2, rinv, rinv64, st));
+  const MarkerRefine rf{G, ldg, encoding, N, missing, ldm, mean, p->Q, (int)p->q, refine_list,
+                        status + 1};
+  TGS_CUDA(launch_marker_norm(M, nobs, gc2, qg, nq, kappa64, gres2, out->marker_norm2, rinv, rinv64,
+                              &rf, st));
   if (out->marker_nobs)
     TGS_CUDA(cudaMemcpyAsync(out->marker_nobs, nobs, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st));
   if (out->marker_mean)

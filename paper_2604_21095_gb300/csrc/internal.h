@@ -144,6 +144,7 @@ struct tg_ctx {
   double* gres2 = nullptr;
   float* rinv = nullptr;
   double* rinv64 = nullptr;
+  int* refine_list = nullptr;                   // [cap_m] markers re-projected in FP64
   // host-streamed scan
   uint8_t* stage_buf[2] = {nullptr, nullptr};
   size_t stage_bytes = 0;
@@ -220,10 +221,26 @@ cudaError_t launch_subset_stats(const uint8_t* G, int64_t ldg, int encoding, int
 // SIMT kernels (k_simt.cu)
 cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, const float* QB,
                            int64_t nq, float* qg, cudaStream_t st);
+// What the FP64 re-projection of markers close to the covariate span needs: the packed block,
+// the FP64 means (units) and the panel's FP64 basis Q ([q][N], column 0 the intercept), and a
+// list of at least M ints with its counter (4 bytes of device memory).
+struct MarkerRefine {
+  const uint8_t* G;
+  int64_t ldg;
+  int encoding;
+  int64_t N;
+  const uint32_t* missing;
+  int64_t ldm;
+  const double* mean;
+  const double* Q;
+  int q;
+  int* list;
+  unsigned* count;
+};
 cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
                                int64_t nq, double kappa, double* gres2_units_out,
                                double* norm2_allele_out, float* rinv, double* rinv64,
-                               cudaStream_t st);
+                               const MarkerRefine* refine, cudaStream_t st);
 cudaError_t launch_sgemm_scan(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t K,
                               const EpiParams& ep, cudaStream_t st);
 

@@ -87,11 +87,17 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ A, lo
 }
 
 // ---------------------------------------------------------------- marker norms
+// A marker is re-projected in FP64 (k_marker_refine) when the covariates explain more than
+// this share of its variance: |g_res|^2 = |g_c|^2 - sum_k (q_k . g_c)^2 then amplifies the
+// rounding of the projections by |g_c|^2 / |g_res|^2 (>= 2 here).
+constexpr double kRefineShare = 0.5;
+
 __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
                               const double* __restrict__ gc2, const float* __restrict__ qg, int nq,
                               double kappa, double* __restrict__ gres2u,
                               double* __restrict__ norm2_allele, float* __restrict__ rinv,
-                              double* __restrict__ rinv64) {
+                              double* __restrict__ rinv64, int* __restrict__ refine_list,
+                              unsigned* __restrict__ refine_count) {
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (j >= M) return;
   const double c2 = gc2[j];
@@ -108,6 +114,65 @@ __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
   if (norm2_allele) norm2_allele[j] = ok ? r2 * kappa * kappa : nan;
   rinv[j] = (float)inv;
   rinv64[j] = inv;
+  if (refine_list && nobs[j] > 0 && c2 > 0.0 && r2 < (1.0 - kRefineShare) * c2)
+    refine_list[atomicAdd(refine_count, 1u)] = (int)j;
+}
+
+// FP64 re-projection of the listed markers, one block of 256 threads per marker:
+// sum_k (q_k . g_c)^2 over the non-intercept columns of Q from the packed genotypes (missing
+// calls at the marker's mean, which is also its centre, so they add nothing) and the FP64 mean,
+// then the marker's norm outputs again. q_0 . g_c = 0 exactly (q_0 is constant and g_c has zero
+// sum), as in the tensor-core projection, which leaves column 0 out.
+__global__ void __launch_bounds__(256) k_marker_refine(MarkerRefine rf, const int32_t* __restrict__ nobs,
+                                                       const double* __restrict__ gc2, double kappa,
+                                                       double* __restrict__ gres2u,
+                                                       double* __restrict__ norm2_allele,
+                                                       float* __restrict__ rinv,
+                                                       double* __restrict__ rinv64) {
+  __shared__ double red[8];
+  const unsigned n = *rf.count;
+  for (unsigned li = blockIdx.x; li < n; li += gridDim.x) {
+    const long long j = rf.list[li];
+    const double mu = rf.mean[j];
+    const uint8_t* row = rf.G + j * rf.ldg;
+    const uint32_t* mrow = rf.missing ? rf.missing + j * rf.ldm : nullptr;
+    double s = 0.0;  // thread 0's copy is the sum
+    for (int k = 1; k < rf.q; ++k) {
+      const double* qk = rf.Q + (long long)k * rf.N;
+      double acc = 0.0;
+      for (long long i = threadIdx.x; i < rf.N; i += blockDim.x) {
+        double v;
+        if (rf.encoding == TG_ENC_2BIT) {
+          const unsigned f = (row[i >> 2] >> (2 * (i & 3))) & 3u;  // 00 = 2, 10 = 1, 11 = 0, 01 missing
+          v = f == 0u ? 2.0 : f == 2u ? 1.0 : f == 3u ? 0.0 : mu;
+        } else {
+          const bool miss = mrow && ((mrow[i >> 5] >> (i & 31)) & 1u);
+          v = miss ? mu : (double)row[i];
+        }
+        acc = fma(qk[i], v - mu, acc);
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        s += t * t;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const double c2 = gc2[j];
+      const double r2 = c2 - s;
+      const bool ok = nobs[j] > 0 && c2 > 0.0 && r2 > 1e-5 * c2;
+      const double nan = __longlong_as_double(0x7ff8000000000000ll);
+      const double inv = ok ? 1.0 / sqrt(r2) : nan;
+      gres2u[j] = ok ? r2 : nan;
+      if (norm2_allele) norm2_allele[j] = ok ? r2 * kappa * kappa : nan;
+      rinv[j] = (float)inv;
+      rinv64[j] = inv;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- FP32 scan
@@ -233,11 +298,20 @@ cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, co
 cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
                                int64_t nq, double kappa, double* gres2_units_out,
                                double* norm2_allele_out, float* rinv, double* rinv64,
-                               cudaStream_t st) {
+                               const MarkerRefine* refine, cudaStream_t st) {
   if (M == 0) return cudaSuccess;
-  k_marker_norm<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, nobs, gc2, qg, (int)nq, kappa,
-                                                             gres2_units_out, norm2_allele_out,
-                                                             rinv, rinv64);
+  const bool rf = refine != nullptr && nq > 0;
+  if (rf) {
+    cudaError_t e = cudaMemsetAsync(refine->count, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+  }
+  k_marker_norm<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(
+      M, nobs, gc2, qg, (int)nq, kappa, gres2_units_out, norm2_allele_out, rinv, rinv64,
+      rf ? refine->list : nullptr, rf ? refine->count : nullptr);
+  if (!rf) return cudaGetLastError();
+  // a fixed grid, so that the launch does not depend on the count (graph capture)
+  k_marker_refine<<<304, 256, 0, st>>>(*refine, nobs, gc2, kappa, gres2_units_out,
+                                       norm2_allele_out, rinv, rinv64);
   return cudaGetLastError();
 }
 

@@ -370,3 +370,50 @@ def test_few_samples(N, kernel, precision):
                 assert abs(mlp[j, q] - 1.0) <= max(1e-3, 1e-5 * mlp[j, q]), (j, q, mlp[j, q])
     finally:
         tg.tg_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", ["split", "fp32"])
+@pytest.mark.parametrize("encoding", ["2bit", "u8"])
+def test_markers_close_to_the_covariate_span(tgctx, precision, encoding):
+    """Covariates that nearly reproduce some markers (|g_c|^2 / |g_res|^2 up to ~1e4): their
+    residual norms are recomputed in FP64 (the tensor-core projection's rounding would be
+    amplified by that ratio), so the norms match the oracle to FP64 accuracy and r stays within
+    the tolerance scaled by sqrt(|g_c|^2 / |g_res|^2), the amplification the product itself
+    carries."""
+    N, M, P = 2000, 64, 40
+    w = synth.Workload(f"collinear_{encoding}", N=N, M=M, P=P, n_cov=4, encoding=encoding,
+                       missing=0.01 if encoding == "2bit" else 0.0, seed=77, block=M,
+                       causal_per_pheno=1)
+    pan = synth.make_panel(w)
+    blk = synth.make_block(w, 0)
+    dec = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))["decode"]
+    g = torch.from_numpy(dec["g"])
+    cov = pan["cov_t"].clone()
+    noise = synth.covariates(78, N, 3)
+    for k, (j, eps) in enumerate([(3, 0.1), (17, 0.03), (40, 0.01)]):
+        gc = g[j] - g[j].mean()
+        cov[k] = gc + eps * gc.std() * noise[k]
+    Yt = synth.phenotypes(79, cov, P)
+    panel = tg.tg_prepare_panel(tgctx, Yt.cuda(), N, P, cov.cuda())
+    try:
+        res = run_scan(tgctx, panel, blk["G"].cuda(), N, P, encoding, precision, full=True)
+    finally:
+        tg.tg_panel_free(panel)
+    assert res["status"] == tg.TG_OK
+    ref = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(Yt, cov))
+    gc2 = ((dec["g"] - dec["g"].mean(axis=1, keepdims=True)) ** 2).sum(axis=1)
+    cond = gc2 / ref["gres2"]
+    assert np.nanmax(cond) > 3e3  # the construction reached the regime it is about
+    ok = np.isfinite(ref["gres2"])
+    assert np.array_equal(np.isfinite(res["norm2"]), ok)
+    rel = np.abs(res["norm2"][ok] - ref["gres2"][ok]) / ref["gres2"][ok]
+    refined = cond[ok] >= 2.0  # the FP64 re-projection; the rest come from the fast projection
+    assert np.all(rel[refined] <= 1e-10 * cond[ok][refined]), rel[refined].max()
+    assert np.all(rel[~refined] <= 1e-6), rel[~refined].max()
+    df = ref["df"]
+    rb = res["t"] / np.sqrt(df + res["t"].astype(np.float64) ** 2)
+    dr = np.abs(rb - ref["r"])
+    bound = np.broadcast_to(r_tol(df) * np.sqrt(np.maximum(cond, 1.0))[:, None], dr.shape)
+    fin = np.isfinite(ref["r"])
+    assert np.array_equal(np.isfinite(res["t"]), fin)
+    assert np.all(dr[fin] <= bound[fin]), (dr[fin].max(), np.argmax(np.where(fin, dr / bound, 0)))
