@@ -417,3 +417,26 @@ def test_markers_close_to_the_covariate_span(tgctx, precision, encoding):
     fin = np.isfinite(ref["r"])
     assert np.array_equal(np.isfinite(res["t"]), fin)
     assert np.all(dr[fin] <= bound[fin]), (dr[fin].max(), np.argmax(np.where(fin, dr / bound, 0)))
+
+
+@pytest.mark.parametrize("precision", ["split", "fp32"])
+def test_panel_without_phenotypes(tgctx, precision):
+    """P = 0: the scan still decodes, projects and reports every marker's norm, with no hit."""
+    N, M = 700, 100
+    cov = synth.covariates(91, N, 2)
+    counts, miss = synth.hard_calls(91, 0, synth.maf(91, 0, M), N, 0.02)
+    G = synth.pack_2bit(counts, miss)
+    panel = tg.tg_prepare_panel(tgctx, torch.zeros(0, N, dtype=torch.float32, device="cuda"), N, 0,
+                                cov.cuda())
+    try:
+        assert tg.tg_panel_info(panel)[:3] == (N, 0, 3)
+        res = run_scan(tgctx, panel, G.cuda(), N, 0, "2bit", precision, full=False,
+                       hit_mlog10p=0.5)
+    finally:
+        tg.tg_panel_free(panel)
+    assert res["status"] == tg.TG_OK and res["n_hits"] == 0
+    ref = oracle.scan(G.numpy(), "2bit", oracle_panel(synth.phenotypes(91, cov, 1), cov))
+    ok = np.isfinite(ref["gres2"])
+    assert np.array_equal(np.isfinite(res["norm2"]), ok)
+    assert np.allclose(res["norm2"][ok], ref["gres2"][ok], rtol=1e-6)
+    assert np.array_equal(res["nobs"], ref["decode"]["n_obs"])
