@@ -183,6 +183,36 @@ def _oracle_sample(Yt, cov_t, G, seconds: float, encoding: str = "u8"):
     return done, t_total, Yt.shape[0]
 
 
+def _oracle_one_core(w, seconds: float):
+    """The same oracle timing on one core: a child process with the BLAS and OpenMP pools at one
+    thread and no GPU, on a slice of the workload (at most 2,048 phenotypes and 4,096 markers of
+    block 0; the oracle's cost per test does not depend on P at these sizes). Returns
+    (tests/s, sample description) or None if the child fails."""
+    import subprocess
+    import sys
+    Pp = min(w.P, 2048)
+    code = (
+        "import dataclasses, sys, time\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import bench, synth\n"
+        f"w = dataclasses.replace(synth.WORKLOADS[{w.name.replace('_reduced', '')!r}], P={Pp}, "
+        f"N={w.N}, block=4096)\n"
+        "pan = synth.make_panel(w)\n"
+        "G = synth.make_block(w, 0)['G']\n"
+        f"done, secs, P = bench._oracle_sample(pan['Yt'], pan['cov_t'], G, {seconds}, w.encoding)\n"
+        "print(done, secs, P)\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=max(120.0, 10 * seconds))
+        done, secs, P = r.stdout.strip().splitlines()[-1].split()
+        done, secs, P = int(done), float(secs), int(P)
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+        return None
+    return done * P / secs, f"{done} markers x {P} phenotypes on 1 thread, {secs:.1f} s"
+
+
 def _reference(args, dist, rank, ws):
     """--impl reference: the FP64 CPU oracle, rank 0 only."""
     if rank != 0:
@@ -397,6 +427,9 @@ def _ours(args, dist, rank, ws):
         cpu = {"value": done * P / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{done} markers x {P} phenotypes of block 0, FP64 projected OLS with "
                          f"p-values, {secs:.1f} s (panel preparation excluded, as on the GPU)"}
+        one = _oracle_one_core(w, args.cpu_seconds / 3)
+        if one:
+            cpu["one_core"] = {"value": one[0], "unit": UNIT, "sample": one[1]}
 
     if rank == 0:
         print(json.dumps({
