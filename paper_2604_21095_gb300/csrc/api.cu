@@ -330,7 +330,10 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     } else {
       const int b = tune_bucket(a.M);
       const int group = c->tune_group[b] > 0 ? c->tune_group[b] : kGroupDefault;
-      if (c->tune_kernel[b] == TUNE_SINGLE)
+      if (p->P <= 64)  // a small panel: 64-column tiles, bound by HBM
+        TG_CUDA(launch_tc_scan(&tA, &p->tmBhi64, &p->tmBlo64, p->Npad, ep, c->sm_count, kSpinNs,
+                               st, group, dec, a.encoding, true));
+      else if (c->tune_kernel[b] == TUNE_SINGLE)
         TG_CUDA(launch_tc_scan(&tA, &p->tmBhi, &p->tmBlo, p->Npad, ep, c->sm_count, kSpinNs, st,
                                group, dec, a.encoding));
       else {
@@ -549,7 +552,9 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
       !make_tmap(&p->tmBhi2, p->Bhi, p->Ppad, p->Npad, p->Npad, 128) ||
       !make_tmap(&p->tmBlo2, p->Blo, p->Ppad, p->Npad, p->Npad, 128) ||
       !make_tmap(&p->tmQhi, p->QBhi, QCOLS, p->Npad, p->Npad, 64) ||
-      !make_tmap(&p->tmQlo, p->QBlo, QCOLS, p->Npad, p->Npad, 64))
+      !make_tmap(&p->tmQlo, p->QBlo, QCOLS, p->Npad, p->Npad, 64) ||
+      !make_tmap(&p->tmBhi64, p->Bhi, p->Ppad, p->Npad, p->Npad, 64) ||
+      !make_tmap(&p->tmBlo64, p->Blo, p->Ppad, p->Npad, p->Npad, 64))
     return cleanup(fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panel"));
   *out = p;
   return TG_OK;
@@ -657,7 +662,8 @@ tg_status tg_prepare_panel_subset(tg_ctx* c, const float* Y, int64_t ldy, int64_
   }
   if (!make_tmap(&r->tmBhi, r->Bhi, Pp, Np, Np, 256) || !make_tmap(&r->tmBlo, r->Blo, Pp, Np, Np, 256) ||
       !make_tmap(&r->tmBhi2, r->Bhi, Pp, Np, Np, 128) || !make_tmap(&r->tmBlo2, r->Blo, Pp, Np, Np, 128) ||
-      !make_tmap(&r->tmQhi, r->QBhi, QCOLS, Np, Np, 64) || !make_tmap(&r->tmQlo, r->QBlo, QCOLS, Np, Np, 64))
+      !make_tmap(&r->tmQhi, r->QBhi, QCOLS, Np, Np, 64) || !make_tmap(&r->tmQlo, r->QBlo, QCOLS, Np, Np, 64) ||
+      !make_tmap(&r->tmBhi64, r->Bhi, Pp, Np, Np, 64) || !make_tmap(&r->tmBlo64, r->Blo, Pp, Np, Np, 64))
     return cleanup(fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the subset panel"));
   tg_panel* done = r;
   r = nullptr;
@@ -1011,7 +1017,8 @@ tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_pa
   }
   if (!make_tmap(&r->tmBhi, r->Bhi, Pp, Np, Np, 256) || !make_tmap(&r->tmBlo, r->Blo, Pp, Np, Np, 256) ||
       !make_tmap(&r->tmBhi2, r->Bhi, Pp, Np, Np, 128) || !make_tmap(&r->tmBlo2, r->Blo, Pp, Np, Np, 128) ||
-      !make_tmap(&r->tmQhi, r->QBhi, QCOLS, Np, Np, 64) || !make_tmap(&r->tmQlo, r->QBlo, QCOLS, Np, Np, 64)) {
+      !make_tmap(&r->tmQhi, r->QBhi, QCOLS, Np, Np, 64) || !make_tmap(&r->tmQlo, r->QBlo, QCOLS, Np, Np, 64) ||
+      !make_tmap(&r->tmBhi64, r->Bhi, Pp, Np, Np, 64) || !make_tmap(&r->tmBlo64, r->Blo, Pp, Np, Np, 64)) {
     tg_panel_free(r);
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the concatenated panel");
   }

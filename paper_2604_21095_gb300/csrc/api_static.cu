@@ -261,8 +261,9 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
     TGS_CUDA(launch_sgemm_scan(reinterpret_cast<const float*>(Ahi), p->Npad, p->B32, p->Npad,
                                p->Npad, ep, st));
   } else {
-    TGS_CUDA(launch_tc_scan(&tA, &p->tmBhi, &p->tmBlo, p->Npad, ep, ds->sm_count, kStaticSpinNs,
-                            st));
+    const bool narrow = p->P <= 64;  // a small panel: 64-column tiles, bound by HBM
+    TGS_CUDA(launch_tc_scan(&tA, narrow ? &p->tmBhi64 : &p->tmBhi, narrow ? &p->tmBlo64 : &p->tmBlo,
+                            p->Npad, ep, ds->sm_count, kStaticSpinNs, st, 16, nullptr, 0, narrow));
   }
   if (ep.do_hits) TGS_CUDA(launch_hit_stats(ep, hit_start, st));
   if (ep.do_full) TGS_CUDA(launch_full_stats(ep, st));

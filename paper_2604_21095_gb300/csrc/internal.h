@@ -121,6 +121,7 @@ struct tg_panel {
   CUtensorMap tmBhi, tmBlo;      // phenotype panel, 256-row boxes
   CUtensorMap tmBhi2, tmBlo2;    // phenotype panel, 128-row boxes (one CTA's half of a pair tile)
   CUtensorMap tmQhi, tmQlo;      // covariate projection columns, 64-row boxes
+  CUtensorMap tmBhi64, tmBlo64;  // phenotype panel, 64-row boxes (64-column tiles, P <= 64)
 };
 
 struct tg_ctx {
@@ -251,10 +252,12 @@ cudaError_t launch_fill_random(uint8_t* p, size_t n, unsigned long long seed, cu
 
 // tensor-core kernel (k_tc.cu)
 // With `dec` non-NULL the A operand is decoded from packed genotypes in the kernel (tmA unused).
+// `narrow`: 64-column tiles for a panel of at most 64 phenotypes (B maps with 64-row boxes);
+// the covariate projection (ep.raw_out) always uses them.
 cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                            const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
                            long long spin_ns, cudaStream_t st, int group_m = 16,
-                           const DecodeArgs* dec = nullptr, int encoding = 0);
+                           const DecodeArgs* dec = nullptr, int encoding = 0, bool narrow = false);
 
 // tensor-core kernel on CTA pairs, 256 x 256 tiles (k_tc2.cu)
 cudaError_t launch_tc2_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,

@@ -47,10 +47,11 @@ struct Cfg {
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;  // + alignment slack
 };
 
-// KS = K blocks per stage. The 64-column covariate projection streams the 3 GB operand and is
-// bound by HBM, where two consecutive 64-byte row segments requested back to back use the DRAM
-// pages better than one: it loads two K blocks per stage into the 40 KB slot (A halves at 0 and
-// 8 KB, B_hi halves at 16 and 20 KB, B_lo halves at 24 and 28 KB; 64 B rows).
+// KS = K blocks per stage. With 64-column tiles (the covariate projection, and panels of at most
+// 64 phenotypes) the kernel streams the 3 GB operand and is bound by HBM, where two consecutive
+// 64-byte row segments requested back to back use the DRAM pages better than one: it then loads
+// two K blocks per stage into the 40 KB slot (A halves at 0 and 8 KB, B_hi halves at 16 and
+// 20 KB, B_lo halves at 24 and 28 KB; 64 B rows).
 template <int OPA, int KS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmBhi,
@@ -326,7 +327,7 @@ __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, u
 template <int OPA, int KS>
 cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* bl, int64_t K,
                const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st,
-               const DecodeArgs& da) {
+               const DecodeArgs& da, int bn) {
   static bool attr_set = false;  // per process and instantiation; the attribute is per function
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_scan<OPA, KS>,
@@ -336,7 +337,6 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* b
     attr_set = true;
   }
   const int n_mt = (ep.M + TBM - 1) / TBM;
-  const int bn = ep.raw_out ? 64 : TBN;
   const int n_nt = (ep.P + bn - 1) / bn;
   const int tiles = n_mt * n_nt;
   const int grid = tiles < sm_count ? tiles : sm_count;
@@ -351,18 +351,22 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* b
 cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                            const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
                            long long spin_ns, cudaStream_t st, int group_m, const DecodeArgs* dec,
-                           int encoding) {
+                           int encoding, bool narrow) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   if (K % TBK || group_m < 1) return cudaErrorInvalidValue;
+  const int bn = ep.raw_out || narrow ? 64 : TBN;
+  if (narrow && ep.P > 64) return cudaErrorInvalidValue;
   if (!dec) {
-    if (ep.raw_out)  // the covariate projection
-      return go<OPA_TMA, 2>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{});
-    return go<OPA_TMA, 1>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{});
+    if (bn == 64)  // the covariate projection, or a panel of at most 64 phenotypes
+      return go<OPA_TMA, 2>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{},
+                            bn);
+    return go<OPA_TMA, 1>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{},
+                          bn);
   }
   if (dec->M != ep.M) return cudaErrorInvalidValue;
   if (encoding == TG_ENC_2BIT)
-    return go<OPA_2BIT, 1>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
-  return go<OPA_U8, 1>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec);
+    return go<OPA_2BIT, 1>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec, bn);
+  return go<OPA_U8, 1>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec, bn);
 }
 
 cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,
