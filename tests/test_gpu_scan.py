@@ -440,3 +440,29 @@ def test_panel_without_phenotypes(tgctx, precision):
     assert np.array_equal(np.isfinite(res["norm2"]), ok)
     assert np.allclose(res["norm2"][ok], ref["gres2"][ok], rtol=1e-6)
     assert np.array_equal(res["nobs"], ref["decode"]["n_obs"])
+
+
+@pytest.mark.parametrize("N", [30000, 50000])
+@pytest.mark.parametrize("encoding", ["2bit", "u8"])
+def test_long_sample_axis(tgctx, N, encoding):
+    """Sample counts past the one-pass decode's limits (N > 24,576 takes the row-in-registers
+    kernel with twice the groups, N > 49,152 the two-pass one) and a long K loop (up to 49
+    accumulation chunks), in both kernels' tile widths (P = 70: 256-column tiles)."""
+    M, P = 200, 70
+    w = synth.Workload(f"longN_{encoding}_{N}", N=N, M=M, P=P, n_cov=3, encoding=encoding,
+                       missing=0.01 if encoding == "2bit" else 0.0, seed=N % 97, block=M,
+                       causal_per_pheno=1)
+    pan = synth.make_panel(w)
+    blk = synth.make_block(w, 0)
+    panel = tg.tg_prepare_panel(tgctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+    try:
+        res = run_scan(tgctx, panel, blk["G"].cuda(), N, P, encoding, "split", full=True,
+                       hit_mlog10p=THR)
+    finally:
+        tg.tg_panel_free(panel)
+    assert res["status"] == tg.TG_OK
+    ref = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
+    compare_full(res, ref, label=f"N={N}/{encoding}")
+    compare_hits(res, ref, THR)
+    compare_best(res, ref)
+    assert np.array_equal(res["nobs"], ref["decode"]["n_obs"])
