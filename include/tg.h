@@ -296,6 +296,19 @@ tg_status tg_scan_graph_create(tg_ctx* ctx, const tg_panel* panel, int n_blocks,
                                const int64_t* marker_offset, const uint32_t* const* missing,
                                int64_t ldg, int64_t ldm, int32_t encoding, int64_t N,
                                const tg_scan_opts* opts, const tg_outputs* out, tg_graph** graph);
+/* The same with the genotype blocks in host memory: G_host[b] holds M[b] rows of ldg bytes in
+ * page-locked host memory (no missing masks: 2-bit calls carry theirs in-band, dosage blocks
+ * are scanned unmasked). The graph owns two device staging buffers of the largest block; each
+ * replay copies every block into one of them on a stream forked inside the graph, so that the
+ * copy of block b+1 runs while block b is scanned (Section 2.2, batches streamed in), and
+ * joins that stream before it ends. The host blocks are read at every replay: refill them
+ * between replays to stream new markers through the same graph. Same output rules as
+ * tg_scan_graph_create. */
+tg_status tg_scan_graph_create_host(tg_ctx* ctx, const tg_panel* panel, int n_blocks,
+                                    const uint8_t* const* G_host, const int64_t* M,
+                                    const int64_t* marker_offset, int64_t ldg, int32_t encoding,
+                                    int64_t N, const tg_scan_opts* opts, const tg_outputs* out,
+                                    tg_graph** graph);
 /* Replay the captured scans on `stream` (asynchronous). */
 tg_status tg_scan_graph_launch(tg_graph* graph, void* stream);
 tg_status tg_scan_graph_free(tg_graph* graph);

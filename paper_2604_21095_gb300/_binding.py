@@ -72,6 +72,10 @@ _SIGS = {
                                        C.POINTER(_I64), C.POINTER(_VP), _I64, _I64, _I32, _I64,
                                        C.POINTER(tg_scan_opts), C.POINTER(tg_outputs),
                                        C.POINTER(_VP)]),
+    "tg_scan_graph_create_host": (C.c_int, [_VP, _VP, C.c_int, C.POINTER(_VP), C.POINTER(_I64),
+                                            C.POINTER(_I64), _I64, _I32, _I64,
+                                            C.POINTER(tg_scan_opts), C.POINTER(tg_outputs),
+                                            C.POINTER(_VP)]),
     "tg_scan_graph_launch": (C.c_int, [_VP, _VP]),
     "tg_scan_graph_free": (C.c_int, [_VP]),
     "tg_autotune": (C.c_int, [_VP, _VP, _I32, _I64, _VP]),
@@ -290,6 +294,20 @@ def tg_scan_graph_create(ctx, panel, blocks, N, encoding, opts: tg_scan_opts, ou
     g = _VP()
     _check(load().tg_scan_graph_create(ctx, panel, n, G, M, off, miss, _ld(blocks[0]), ldm,
                                        encoding, N, C.byref(opts), C.byref(out), C.byref(g)))
+    return g
+
+
+def tg_scan_graph_create_host(ctx, panel, blocks_host, N, encoding, opts: tg_scan_opts,
+                              out: tg_outputs, marker_offsets):
+    """blocks_host: list of uint8 CPU tensors [M_b][ldg] in page-locked memory (same ldg); the
+    graph copies them to the device at every replay. Returns a graph handle."""
+    n = len(blocks_host)
+    G = (_VP * n)(*[b.data_ptr() for b in blocks_host])
+    M = (_I64 * n)(*[b.shape[0] for b in blocks_host])
+    off = (_I64 * n)(*marker_offsets)
+    g = _VP()
+    _check(load().tg_scan_graph_create_host(ctx, panel, n, G, M, off, _ld(blocks_host[0]),
+                                            encoding, N, C.byref(opts), C.byref(out), C.byref(g)))
     return g
 
 

@@ -400,6 +400,7 @@ struct tg_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t launches[TG_N_STAGES] = {0, 0, 0, 0, 0, 0};
+  uint8_t* stage[2] = {nullptr, nullptr};  // device staging of host blocks (host-block graphs)
 };
 
 extern "C" {
@@ -1087,6 +1088,109 @@ tg_status tg_scan_graph_create(tg_ctx* c, const tg_panel* p, int n_blocks,
   return TG_OK;
 }
 
+tg_status tg_scan_graph_create_host(tg_ctx* c, const tg_panel* p, int n_blocks,
+                                    const uint8_t* const* G_host, const int64_t* M,
+                                    const int64_t* marker_offset, int64_t ldg, int32_t encoding,
+                                    int64_t N, const tg_scan_opts* opts, const tg_outputs* out,
+                                    tg_graph** graph) {
+  TG_ARG(c && p && G_host && M && marker_offset && opts && out && graph && n_blocks >= 1,
+         "bad arguments");
+  *graph = nullptr;
+  TG_ARG(!opts->full_output, "captured scan graphs collect hits and best markers only");
+  TG_ARG(!out->marker_norm2 && !out->marker_nobs && !out->marker_mean,
+         "per-marker outputs are not supported in captured scan graphs");
+  TG_CUDA(cudaSetDevice(c->device));
+  int64_t maxM = 0;
+  for (int b = 0; b < n_blocks; ++b) {
+    TG_ARG(M[b] == 0 || G_host[b] != nullptr, "null host block");
+    // the arguments of the scan as it will run, from a device staging buffer
+    ScanArgs a{reinterpret_cast<const uint8_t*>(uintptr_t(256)), ldg, encoding, N, M[b],
+               marker_offset[b], nullptr, 0, *opts, *out};
+    tg_status s = check_scan_args(c, p, a);
+    if (s != TG_OK) return s;
+    maxM = std::max(maxM, M[b]);
+  }
+  const bool need_operand = opts->precision != TG_PREC_SPLIT_BF16 || !c->fuse_decode;
+  TG_CUDA(ensure_markers(c, maxM));
+  if (need_operand) TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision));
+  tg_graph* g = new tg_graph();
+  g->ctx = c;
+  const size_t blk_bytes = (size_t)std::max<int64_t>(maxM, 1) * (size_t)ldg;
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // ev: 0 fork, 1 join, 2-3 block copied into staging buffer 0/1, 4-5 buffer 0/1 free again
+  auto release = [&](tg_status s) {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    if (side) cudaStreamDestroy(side);
+    if (cap) cudaStreamDestroy(cap);
+    if (s != TG_OK) {
+      if (g->exec) cudaGraphExecDestroy(g->exec);
+      if (g->graph) cudaGraphDestroy(g->graph);
+      dfree(g->stage[0]);
+      dfree(g->stage[1]);
+      delete g;
+    }
+    return s;
+  };
+  cudaError_t e;
+  if ((e = dalloc(&g->stage[0], blk_bytes)) || (e = dalloc(&g->stage[1], blk_bytes)) ||
+      (e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) ||
+      (e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)))
+    return release(cuda_fail(e, "tg_scan_graph_create_host set-up"));
+  for (auto& x : ev)
+    if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)))
+      return release(cuda_fail(e, "tg_scan_graph_create_host events"));
+  int64_t before[TG_N_STAGES];
+  std::memcpy(before, c->launches, sizeof(before));
+  const bool prof = c->prof;
+  c->prof = false;
+  tg_status s = TG_OK;
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    auto step = [&]() -> tg_status {
+      // the copy stream joins the capture, then every block: copy (side) -> scan (cap)
+      TG_CUDA(cudaEventRecord(ev[0], cap));
+      TG_CUDA(cudaStreamWaitEvent(side, ev[0], 0));
+      bool used[2] = {false, false};
+      for (int b = 0, nb = 0; b < n_blocks; ++b) {
+        if (M[b] == 0) continue;
+        const int buf = (nb++) & 1;
+        if (used[buf]) TG_CUDA(cudaStreamWaitEvent(side, ev[4 + buf], 0));  // its last scan is done
+        used[buf] = true;
+        TG_CUDA(cudaMemcpyAsync(g->stage[buf], G_host[b], (size_t)M[b] * (size_t)ldg,
+                                cudaMemcpyHostToDevice, side));
+        TG_CUDA(cudaEventRecord(ev[2 + buf], side));
+        TG_CUDA(cudaStreamWaitEvent(cap, ev[2 + buf], 0));
+        ScanArgs a{g->stage[buf], ldg, encoding, N, M[b], marker_offset[b], nullptr, 0, *opts,
+                   *out};
+        tg_status r = scan_impl(c, p, a, cap);
+        if (r != TG_OK) return r;
+        TG_CUDA(cudaEventRecord(ev[4 + buf], cap));
+      }
+      TG_CUDA(cudaEventRecord(ev[1], side));  // the copy stream rejoins before the capture ends
+      TG_CUDA(cudaStreamWaitEvent(cap, ev[1], 0));
+      return TG_OK;
+    };
+    s = step();
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g->graph);
+    if (s == TG_OK && e2 != cudaSuccess) s = cuda_fail(e2, "tg_scan_graph_create_host capture");
+  } else {
+    s = cuda_fail(e, "tg_scan_graph_create_host capture");
+  }
+  c->prof = prof;
+  for (int i = 0; i < TG_N_STAGES; ++i) {
+    g->launches[i] = c->launches[i] - before[i];
+    c->launches[i] = before[i];
+  }
+  if (s == TG_OK && (e = cudaGraphInstantiate(&g->exec, g->graph, 0)))
+    s = cuda_fail(e, "tg_scan_graph_create_host instantiate");
+  if (s != TG_OK) return release(s);
+  c->graphs_alive += 1;
+  *graph = g;
+  return release(TG_OK);
+}
+
 tg_status tg_scan_graph_launch(tg_graph* g, void* stream) {
   TG_ARG(g && g->exec, "null graph");
   TG_CUDA(cudaSetDevice(g->ctx->device));
@@ -1100,6 +1204,11 @@ tg_status tg_scan_graph_free(tg_graph* g) {
   cudaSetDevice(g->ctx->device);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->stage[0] || g->stage[1]) {
+    cudaDeviceSynchronize();  // a replay may still read the staging buffers
+    dfree(g->stage[0]);
+    dfree(g->stage[1]);
+  }
   g->ctx->graphs_alive -= 1;
   delete g;
   return TG_OK;

@@ -169,3 +169,53 @@ def test_each_tuning_choice_matches_the_oracle(tgctx, kernel, group):
     finally:
         tg.tg_destroy(ctx2)
         tg.tg_panel_free(panel)
+
+
+@pytest.mark.parametrize("encoding", ["2bit", "u8"])
+def test_graph_with_host_blocks_equals_eager_scans(tgctx, encoding):
+    """A graph whose replay copies ragged pinned host blocks to the device on a forked stream
+    gives the eager scans' hits and best markers; refilled host blocks stream new markers
+    through the same graph."""
+    P = 300
+    cov = synth.covariates(87, N, 3)
+    panel = tg.tg_prepare_panel(tgctx, synth.phenotypes(87, cov, P).cuda(), N, P, cov.cuda())
+    ctx2 = tg.tg_create(0)
+    try:
+        w = synth.Workload("ragged_host", N=N, M=3000, P=P, n_cov=3, encoding=encoding,
+                           missing=0.01 if encoding == "2bit" else 0.0, seed=87, block=1024)
+        sizes = [700, 1500, 0, 333, 129]
+        offs = [int(x) for x in np.cumsum([0] + sizes[:-1])]
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, 3.0)
+        enc = tg.TG_ENC_2BIT if encoding == "2bit" else tg.TG_ENC_U8_DOSAGE
+
+        def blocks_for(seed_shift):  # an empty block keeps its row stride
+            return [synth.make_ragged_block(w, i + seed_shift, max(m, 1))[:m].clone()
+                    for i, m in enumerate(sizes)]
+
+        host = [b.pin_memory() for b in blocks_for(0)]
+        hits2, n2, best2, out2 = _accum_outputs(P)
+        g = tg.tg_scan_graph_create_host(ctx2, panel, host, N, enc, opts, out2, offs)
+        try:
+            for round_ in range(2):
+                if round_ == 1:  # refill the pinned blocks in place: new markers, same graph
+                    for h, b in zip(host, blocks_for(20)):
+                        h.copy_(b)
+                hits, n, best, out = _accum_outputs(P)
+                for b, o in zip(host, offs):
+                    if b.shape[0]:
+                        tg.tg_scan_block(tgctx, panel, b.cuda(), N, b.shape[0], enc, opts, out,
+                                         marker_offset=o)
+                assert tg.tg_status_poll(tgctx) == tg.TG_OK
+                eager = (_hitset(hits, n), best.cpu().numpy().copy())
+                n2.zero_()
+                best2.zero_()
+                tg.tg_scan_graph_launch(g)
+                assert tg.tg_status_poll(ctx2) == tg.TG_OK
+                got = _hitset(hits2, n2)
+                assert set(got) == set(eager[0]) and len(got) > 0
+                assert np.array_equal(best2.cpu().numpy(), eager[1])
+        finally:
+            tg.tg_scan_graph_free(g)
+    finally:
+        tg.tg_destroy(ctx2)
+        tg.tg_panel_free(panel)
