@@ -54,8 +54,9 @@ def _close(a, b):
     assert np.array_equal(a["nobs"], b["nobs"])
 
 
-def test_static_entry_matches_scan_block_on_two_calls_in_a_row(tgctx):
-    N, P = 1999, 300
+@pytest.mark.parametrize("P,thr", [(300, 4.0), (40, 3.0)])  # 256- and 64-column tiles
+def test_static_entry_matches_scan_block_on_two_calls_in_a_row(tgctx, P, thr):
+    N = 1999
     cov = synth.covariates(71, N, 3)
     panel = tg.tg_prepare_panel(tgctx, synth.phenotypes(71, cov, P).cuda(), N, P, cov.cuda())
     try:
@@ -65,7 +66,7 @@ def test_static_entry_matches_scan_block_on_two_calls_in_a_row(tgctx):
             (synth.dosage_bytes(71, 1, synth.maf(71, 1, 513), N).cuda(), tg.TG_ENC_U8_DOSAGE,
              synth.missing_words(71, 1, 513, N, 0.03).cuda(), 513),
         ]
-        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 1, 4.0)
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 1, thr)
         for G, enc, missing, M in calls:
             ref_b, ref_o = _buffers(M, P)
             tg.tg_scan_block(tgctx, panel, G, N, M, enc, opts, ref_o, marker_offset=11,
