@@ -325,6 +325,13 @@ tg_status tg_tuning(const tg_ctx* ctx, int64_t M, int32_t* kernel, int32_t* grou
 /* Set the choice for M-marker blocks by hand (e.g. from a saved tuning): kernel 1 or 2, group
  * in [1, 1024]. */
 tg_status tg_set_tuning(tg_ctx* ctx, int64_t M, int32_t kernel, int32_t group);
+/* Split-K of the one-CTA kernel for M-marker blocks of panels wider than 64 phenotypes: 1, 2
+ * or 4 chunk-aligned ranges of the samples, whose partial sums the tile's first range adds in
+ * order (so results do not depend on scheduling). tg_autotune tries 2 and 4 when that kernel's
+ * tiles are fewer than half the SMs; panels of at most 64 phenotypes split by the same rule
+ * without tuning. */
+tg_status tg_set_tuning_split(tg_ctx* ctx, int64_t M, int32_t splits);
+tg_status tg_tuning_split(const tg_ctx* ctx, int64_t M, int32_t* splits);
 
 /* Synchronise `stream`, then return and clear the latched device status
  * (TG_ERR_CAPACITY, TG_ERR_TIMEOUT) of work queued so far. */

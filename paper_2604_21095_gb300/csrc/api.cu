@@ -165,6 +165,56 @@ cudaError_t ensure_operands(tg_ctx* c, int64_t M, int64_t Npad, int prec) {
   return cudaSuccess;
 }
 
+// Split-K of the one-CTA kernel for a block of M markers: for a panel of at most 64 phenotypes
+// (64-column tiles) it is chosen by rule, for wider panels it is the tuned value. A split pays
+// only while the tiles are fewer than the SMs; every split keeps at least one 1,024-sample chunk.
+struct SplitChoice {
+  int ks = 1;
+  int64_t tiles = 0;
+};
+SplitChoice pick_split(const tg_ctx* c, const tg_panel* p, int64_t M, bool single,
+                       bool projection = false) {
+  SplitChoice r;
+  const int64_t n_mt = (M + MT - 1) / MT;
+  const bool narrow = projection || p->P <= 64;  // the projection has one 64-column tile
+  r.tiles = n_mt * (narrow ? 1 : (p->P + 255) / 256);
+  int ks = 1;
+  if (narrow) {
+    while (ks < 4 && r.tiles * ks * 2 <= c->sm_count) ks *= 2;
+  } else if (single) {
+    const int t = c->tune_split[tune_bucket(M)];
+    ks = t > 1 ? t : 1;
+  }
+  const int chunks = (int)((p->Npad / 32 + kAccumChunkKB - 1) / kAccumChunkKB);
+  while (ks > 1 && (ks > chunks || ks > c->sm_count)) ks /= 2;
+  r.ks = ks;
+  return r;
+}
+size_t split_bytes(const SplitChoice& sc) {
+  return sc.ks > 1 ? (size_t)sc.tiles * (size_t)(sc.ks - 1) * (size_t)(MT * 256) * sizeof(float) : 0;
+}
+cudaError_t ensure_split(tg_ctx* c, const SplitChoice& sc) {
+  const size_t need = split_bytes(sc);
+  if (need > c->sk_ws_bytes) {
+    dfree(c->sk_ws);
+    c->sk_ws_bytes = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c->sk_ws), need);
+    if (e != cudaSuccess) return e;
+    c->sk_ws_bytes = need;
+  }
+  if (sc.ks > 1 && sc.tiles > c->sk_cnt_cap) {
+    dfree(c->sk_cnt);
+    c->sk_cnt_cap = 0;
+    cudaError_t e = dalloc(&c->sk_cnt, (size_t)sc.tiles);
+    if (e != cudaSuccess) return e;
+    c->sk_cnt_cap = sc.tiles;
+  }
+  return cudaSuccess;
+}
+bool split_fits(const tg_ctx* c, const SplitChoice& sc) {
+  return split_bytes(sc) <= c->sk_ws_bytes && (sc.ks <= 1 || sc.tiles <= c->sk_cnt_cap);
+}
+
 }  // namespace
 
 namespace tg {
@@ -223,7 +273,11 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     const bool grow = a.M > c->cap_m || (!fused && (round_up(a.M, MT) > c->cap_rows ||
                                                     p->Npad > c->cap_npad ||
                                                     (prec == TG_PREC_FP32 ? !c->A32 : !c->Ahi)));
-    if (grow)
+    const int bq = tune_bucket(a.M);
+    const bool single = split && (p->P <= 64 || c->tune_kernel[bq] == TUNE_SINGLE);
+    const bool proj = split && a.opts.mode == TG_MODE_PROJECTED && p->q > 1;
+    if (grow || (single && !split_fits(c, pick_split(c, p, a.M, true))) ||
+        (proj && !split_fits(c, pick_split(c, p, a.M, true, true))))
       return fail(TG_ERR_INVALID_ARG,
                   "the context's workspace is held by a captured scan graph: scan blocks no "
                   "larger than the graph's, or use another context");
@@ -267,6 +321,14 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       pp.raw_out = c->qg;
       pp.raw_cols = (int)nq;
       pp.raw_ld = QCOLS;
+      const SplitChoice sc = pick_split(c, p, a.M, true, true);
+      if (sc.ks > 1) {  // a small block: split K so that more SMs stream the operand
+        TG_CUDA(ensure_split(c, sc));
+        pp.ksplit = sc.ks;
+        pp.sk_ws = c->sk_ws;
+        pp.sk_cnt = c->sk_cnt;
+        TG_CUDA(cudaMemsetAsync(pp.sk_cnt, 0, sizeof(unsigned) * (size_t)sc.tiles, st));
+      }
       TG_CUDA(launch_tc_scan(&tA, &p->tmQhi, &p->tmQlo, p->Npad, pp, c->sm_count, kSpinNs, st,
                              kGroupDefault, dec, a.encoding));
     }
@@ -330,12 +392,19 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     } else {
       const int b = tune_bucket(a.M);
       const int group = c->tune_group[b] > 0 ? c->tune_group[b] : kGroupDefault;
-      if (p->P <= 64)  // a small panel: 64-column tiles, bound by HBM
-        TG_CUDA(launch_tc_scan(&tA, &p->tmBhi64, &p->tmBlo64, p->Npad, ep, c->sm_count, kSpinNs,
-                               st, group, dec, a.encoding, true));
-      else if (c->tune_kernel[b] == TUNE_SINGLE)
-        TG_CUDA(launch_tc_scan(&tA, &p->tmBhi, &p->tmBlo, p->Npad, ep, c->sm_count, kSpinNs, st,
-                               group, dec, a.encoding));
+      const bool narrow = p->P <= 64;  // a small panel: 64-column tiles, bound by HBM
+      if (narrow || c->tune_kernel[b] == TUNE_SINGLE) {
+        const SplitChoice sc = pick_split(c, p, a.M, true);
+        if (sc.ks > 1) {  // split-K while the tiles are fewer than the SMs
+          TG_CUDA(ensure_split(c, sc));
+          ep.ksplit = sc.ks;
+          ep.sk_ws = c->sk_ws;
+          ep.sk_cnt = c->sk_cnt;
+          TG_CUDA(cudaMemsetAsync(ep.sk_cnt, 0, sizeof(unsigned) * (size_t)sc.tiles, st));
+        }
+        TG_CUDA(launch_tc_scan(&tA, narrow ? &p->tmBhi64 : &p->tmBhi, narrow ? &p->tmBlo64 : &p->tmBlo,
+                               p->Npad, ep, c->sm_count, kSpinNs, st, group, dec, a.encoding, narrow));
+      }
       else {
         ep.wave_ctr = reinterpret_cast<unsigned long long*>(c->scratch + 32);
         TG_CUDA(cudaMemsetAsync(ep.wave_ctr, 0, sizeof(unsigned long long), st));
@@ -462,6 +531,7 @@ tg_status tg_destroy(tg_ctx* c) {
   dfree(c->Ahi); dfree(c->A32); dfree(c->shift); dfree(c->mh); dfree(c->gc2s);
   dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
   dfree(c->rinv); dfree(c->rinv64); dfree(c->refine_list);
+  dfree(c->sk_ws); dfree(c->sk_cnt);
   dfree(c->stage_buf[0]); dfree(c->stage_buf[1]);
   dfree(c->dhits); dfree(c->dnhits); dfree(c->dbest);
   for (auto& ev : c->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
@@ -1051,6 +1121,13 @@ tg_status tg_scan_graph_create(tg_ctx* c, const tg_panel* p, int n_blocks,
   for (int b = 0; b < n_blocks; ++b) need_operand |= missing && missing[b];
   TG_CUDA(ensure_markers(c, maxM));
   if (need_operand) TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision));
+  for (int b = 0; b < n_blocks; ++b) {
+    const bool single = opts->precision == TG_PREC_SPLIT_BF16 &&
+                        (p->P <= 64 || c->tune_kernel[tune_bucket(M[b])] == TUNE_SINGLE);
+    if (single) TG_CUDA(ensure_split(c, pick_split(c, p, M[b], true)));
+    if (opts->precision == TG_PREC_SPLIT_BF16 && opts->mode == TG_MODE_PROJECTED && p->q > 1)
+      TG_CUDA(ensure_split(c, pick_split(c, p, M[b], true, true)));
+  }
   cudaStream_t cap = nullptr;
   TG_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   tg_graph* g = new tg_graph();
@@ -1113,6 +1190,13 @@ tg_status tg_scan_graph_create_host(tg_ctx* c, const tg_panel* p, int n_blocks,
   const bool need_operand = opts->precision != TG_PREC_SPLIT_BF16 || !c->fuse_decode;
   TG_CUDA(ensure_markers(c, maxM));
   if (need_operand) TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision));
+  for (int b = 0; b < n_blocks; ++b) {
+    const bool single = opts->precision == TG_PREC_SPLIT_BF16 &&
+                        (p->P <= 64 || c->tune_kernel[tune_bucket(M[b])] == TUNE_SINGLE);
+    if (single) TG_CUDA(ensure_split(c, pick_split(c, p, M[b], true)));
+    if (opts->precision == TG_PREC_SPLIT_BF16 && opts->mode == TG_MODE_PROJECTED && p->q > 1)
+      TG_CUDA(ensure_split(c, pick_split(c, p, M[b], true, true)));
+  }
   tg_graph* g = new tg_graph();
   g->ctx = c;
   const size_t blk_bytes = (size_t)std::max<int64_t>(maxM, 1) * (size_t)ldg;
@@ -1248,9 +1332,15 @@ tg_status tg_autotune(tg_ctx* c, const tg_panel* p, int32_t encoding, int64_t M,
   const tg_scan_opts opts{TG_PREC_SPLIT_BF16, 0, 7.30103};
   ScanArgs a{G, ldg, encoding, p->N, M, 0, nullptr, 0, opts, o};
   const int b = tune_bucket(M);
-  const int kinds[] = {TUNE_PAIR, TUNE_PAIR, TUNE_PAIR, TUNE_PAIR, TUNE_SINGLE, TUNE_SINGLE, TUNE_SINGLE};
-  const int groups[] = {4, 8, 16, 32, 8, 16, 32};
-  const int save_k = c->tune_kernel[b], save_g = c->tune_group[b];
+  // kernel, raster group, split-K (the one-CTA kernel splits K when its tiles are fewer than
+  // the SMs; panels of at most 64 phenotypes take 64-column tiles whatever the choice)
+  const int kinds[] = {TUNE_PAIR, TUNE_PAIR, TUNE_PAIR, TUNE_PAIR, TUNE_SINGLE, TUNE_SINGLE,
+                       TUNE_SINGLE, TUNE_SINGLE, TUNE_SINGLE};
+  const int groups[] = {4, 8, 16, 32, 8, 16, 32, 16, 16};
+  const int splits[] = {1, 1, 1, 1, 1, 1, 1, 2, 4};
+  const int64_t single_tiles = ((M + MT - 1) / MT) * ((p->P + 255) / 256);
+  const int n_cand = p->P > 64 && single_tiles * 2 <= c->sm_count ? 9 : 7;
+  const int save_k = c->tune_kernel[b], save_g = c->tune_group[b], save_s = c->tune_split[b];
   const bool prof = c->prof;
   // the trial launches do not count in the caller's stage statistics
   tg_stage_times(c, nullptr, nullptr, 0);
@@ -1261,9 +1351,10 @@ tg_status tg_autotune(tg_ctx* c, const tg_panel* p, int32_t encoding, int64_t M,
   double best_ms = 1e30;
   int best_i = -1;
   tg_status s = TG_OK;
-  for (int i = 0; i < 7 && s == TG_OK; ++i) {
+  for (int i = 0; i < n_cand && s == TG_OK; ++i) {
     c->tune_kernel[b] = kinds[i];
     c->tune_group[b] = groups[i];
+    c->tune_split[b] = splits[i];
     c->prof = false;
     s = scan_impl(c, p, a, st);  // warm-up (and first-use set-up)
     if (s != TG_OK) break;
@@ -1296,9 +1387,11 @@ tg_status tg_autotune(tg_ctx* c, const tg_panel* p, int32_t encoding, int64_t M,
   if (s != TG_OK || best_i < 0) {
     c->tune_kernel[b] = save_k;
     c->tune_group[b] = save_g;
+    c->tune_split[b] = save_s;
   } else {
     c->tune_kernel[b] = kinds[best_i];
     c->tune_group[b] = groups[best_i];
+    c->tune_split[b] = splits[best_i];
   }
   cleanup();
   return s;
@@ -1311,6 +1404,20 @@ tg_status tg_set_tuning(tg_ctx* c, int64_t M, int32_t kernel, int32_t group) {
   const int b = tune_bucket(M);
   c->tune_kernel[b] = kernel == 1 ? TUNE_SINGLE : TUNE_PAIR;
   c->tune_group[b] = group;
+  return TG_OK;
+}
+
+tg_status tg_set_tuning_split(tg_ctx* c, int64_t M, int32_t splits) {
+  TG_ARG(c && M > 0, "bad arguments");
+  TG_ARG(splits == 1 || splits == 2 || splits == 4, "splits must be 1, 2 or 4");
+  c->tune_split[tune_bucket(M)] = splits;
+  return TG_OK;
+}
+
+tg_status tg_tuning_split(const tg_ctx* c, int64_t M, int32_t* splits) {
+  TG_ARG(c && M > 0 && splits, "bad arguments");
+  const int t = c->tune_split[tune_bucket(M)];
+  *splits = t > 1 ? t : 1;
   return TG_OK;
 }
 

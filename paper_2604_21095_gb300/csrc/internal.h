@@ -17,6 +17,7 @@ namespace tg {
 enum : uint32_t { ST_CAPACITY = 1u, ST_TIMEOUT = 2u };
 
 constexpr int KPAD = 64;     // sample dimension (GEMM K) padding of every operand row
+constexpr int kAccumChunkKB = 32;  // tensor-core accumulation chunk: 32 K blocks of 32 samples
 constexpr int PPAD = 256;    // phenotype rows padding of the panel operands (tensor-core N tile)
 constexpr int QMAX = 64;     // intercept + at most 63 covariates
 constexpr int QCOLS = 64;    // projection columns (Q columns 1..q-1), zero padded
@@ -56,6 +57,12 @@ struct EpiParams {
   unsigned long long* wave_ctr;  // CTA-pair lockstep counter (zeroed per launch), NULL = off
   float* raw_out;              // projection mode: D of the first raw_cols columns, [M][raw_ld]
   int raw_cols, raw_ld;
+  // split-K (one-CTA kernel): K split in `ksplit` chunk-aligned ranges (0 or 1 = none); the
+  // partial sums of splits 1.. go through sk_ws ([tiles][ksplit-1][128][256] floats) and
+  // sk_cnt ([tiles], zeroed per launch) to the tile's split 0, which adds them in split order
+  int ksplit;
+  float* sk_ws;
+  unsigned* sk_cnt;
 };
 
 // Packed genotypes for a contraction kernel that decodes its A operand in the producer
@@ -170,6 +177,11 @@ struct tg_ctx {
   // autotuned kernel per block-size bucket
   int tune_kernel[tg::kTuneBuckets] = {};
   int tune_group[tg::kTuneBuckets] = {};
+  int tune_split[tg::kTuneBuckets] = {};        // split-K of the one-CTA kernel (0 = none)
+  float* sk_ws = nullptr;                       // split-K partial sums and per-tile counters
+  size_t sk_ws_bytes = 0;
+  unsigned* sk_cnt = nullptr;
+  int64_t sk_cnt_cap = 0;
 };
 
 namespace tg {

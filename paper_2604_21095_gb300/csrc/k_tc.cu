@@ -52,6 +52,22 @@ struct Cfg {
 // 64-byte row segments requested back to back use the DRAM pages better than one: it then loads
 // two K blocks per stage into the 40 KB slot (A halves at 0 and 8 KB, B_hi halves at 16 and
 // 20 KB, B_lo halves at 24 and 28 KB; 64 B rows).
+static_assert(kChunkKB == kAccumChunkKB, "the host's split choice counts the same chunks");
+
+// K-block range [lo, hi) of split `sp` of `ks`: whole accumulation chunks, the earlier splits
+// one chunk longer when they do not divide evenly (a split may be empty).
+__device__ __forceinline__ void split_range(int num_kb, int ks, int sp, int& lo, int& hi) {
+  const int chunks = (num_kb + kChunkKB - 1) / kChunkKB;
+  const int per = (chunks + ks - 1) / ks;
+  lo = min(num_kb, sp * per * kChunkKB);
+  hi = min(num_kb, (sp + 1) * per * kChunkKB);
+}
+// End of the accumulation chunk that starts at kb0 within [lo, hi); chunk_end for a whole range.
+__device__ __forceinline__ int chunk_end_in(int kb0, int lo, int hi) {
+  const int e = kb0 == lo ? lo + kFirstChunks * kChunkKB : kb0 + kChunkKB;
+  return e < hi ? e : hi;
+}
+
 template <int OPA, int KS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmBhi,
@@ -119,6 +135,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
   const int num_tiles = n_mt * n_nt;
+  // work items: (tile, split); a tile's ks items are consecutive and run in the same round
+  // (the grid is a multiple of ks and every CTA is resident)
+  const int ks = ep.ksplit > 1 ? ep.ksplit : 1;
+  const int num_items = num_tiles * ks;
   if (warp < 4) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kLow));
     if (warp == 0 && lane == 0) {
@@ -129,12 +149,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int s = 0; s < S; ++s) armed[s] = -1;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-      int mt, nt;
+    for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+      const int tile = item / ks;
+      int mt, nt, kb_lo, kb_hi;
       tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
+      split_range(num_kb, ks, item - tile * ks, kb_lo, kb_hi);
       const uint32_t bytes =
           (uint32_t)KS * ((kFused ? 0u : (uint32_t)A_BYTES) + 2u * (uint32_t)bn * (TBK * 2));
-      for (int kb = 0; kb < num_kb; kb += KS) {
+      for (int kb = kb_lo; kb < kb_hi; kb += KS) {
         if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, spin_ns, ep.status)) {
           ok = false;
           break;
@@ -173,10 +195,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t g = 0;
     bool ok = true;
     const uint32_t idesc = idesc_bf16(bn);
-    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-      int mt, nt;
-      tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
-      for (int kb0 = 0; kb0 < num_kb && ok; kb0 = chunk_end(kb0, num_kb), ++g) {
+    for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+      const int tile = item / ks;
+      int kb_lo, kb_hi;
+      split_range(num_kb, ks, item - tile * ks, kb_lo, kb_hi);
+      for (int kb0 = kb_lo; kb0 < kb_hi && ok; kb0 = chunk_end_in(kb0, kb_lo, kb_hi), ++g) {
         const int acc = (int)(g & 1u);
         const uint32_t ph = (g >> 1) & 1u;
         if (!mbar_wait(cempty_bar(acc), ph ^ 1u, abort_flag, spin_ns, ep.status)) {
@@ -185,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
-        const int kb1 = chunk_end(kb0, num_kb);
+        const int kb1 = chunk_end_in(kb0, kb_lo, kb_hi);
         for (int kb = kb0; kb < kb1; kb += KS) {
           if (!mbar_wait(full_bar(stage), phase, abort_flag, spin_ns, ep.status)) {
             ok = false;
@@ -220,12 +243,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-      int mt, nt;
+    for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+      const int tile = item / ks;
+      int mt, nt, kb_lo, kb_hi;
       tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
+      split_range(num_kb, ks, item - tile * ks, kb_lo, kb_hi);
       const long long r0 = (long long)mt * TBM + t;
       const uint2 k0 = dec_row_consts<OPA>(da, r0), k1 = dec_row_consts<OPA>(da, r0 + 64);
-      for (int kb = 0; kb < num_kb; ++kb) {
+      for (int kb = kb_lo; kb < kb_hi; ++kb) {
         if (!mbar_wait(pfull_bar(stage), phase, abort_flag, spin_ns, ep.status)) {
           ok = false;
           break;
@@ -250,13 +275,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int half = (warp - 4) >> 2;
     uint32_t g = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-      int mt, nt;
+    for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+      const int tile = item / ks, split = item - tile * ks;
+      int mt, nt, kb_lo, kb_hi;
       tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
+      split_range(num_kb, ks, split, kb_lo, kb_hi);
       float tot[128];
 #pragma unroll
       for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
-      for (int kb0 = 0; kb0 < num_kb; kb0 = chunk_end(kb0, num_kb), ++g) {
+      for (int kb0 = kb_lo; kb0 < kb_hi; kb0 = chunk_end_in(kb0, kb_lo, kb_hi), ++g) {
         const int acc = (int)(g & 1u);
         const uint32_t ph = (g >> 1) & 1u;
         if (!mbar_wait(cfull_bar(acc), ph, abort_flag, spin_ns, ep.status)) {
@@ -279,6 +306,58 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(cempty_bar(acc));
       }
       if (!ok) break;
+      if (ks > 1) {
+        // this thread's row and 128 columns of the tile's partial sums
+        const int rc = (quarter * 32 + lane) * TBN + half * 128;
+        float* wsp = ep.sk_ws + (size_t)tile * (size_t)(ks - 1) * (TBM * TBN);
+        if (split > 0) {  // hand the partial sums to the tile's split 0, warp by warp
+          float4* dst = reinterpret_cast<float4*>(wsp + (size_t)(split - 1) * (TBM * TBN) + rc);
+#pragma unroll
+          for (int e = 0; e < 32; ++e)
+            dst[e] = make_float4(tot[4 * e], tot[4 * e + 1], tot[4 * e + 2], tot[4 * e + 3]);
+          __threadfence();
+          __syncwarp();
+          if (lane == 0) atomicAdd(ep.sk_cnt + tile, 1u);
+          continue;
+        }
+        // split 0: each warp waits (bounded) for the other splits' warps, then adds their sums
+        // in split order; no CTA-wide barrier, so a warp that gave up cannot hold the others
+        bool got = true;
+        if (lane == 0) {
+          const unsigned need = (unsigned)((ks - 1) * kEpiWarps);
+          const uint64_t t0 = globaltimer_ns();
+          while (*reinterpret_cast<volatile unsigned*>(ep.sk_cnt + tile) < need) {
+            if (*abort_flag || (long long)(globaltimer_ns() - t0) > spin_ns) {
+              if (!*abort_flag) {
+                *abort_flag = 1;
+                atomicOr(ep.status, ST_TIMEOUT);
+              }
+              got = false;
+              break;
+            }
+            __nanosleep(128);
+          }
+          __threadfence();
+        }
+        got = __shfl_sync(0xffffffffu, got, 0);
+        __syncwarp();  // the partial sums are read after lane 0 saw them complete
+        if (!got) {
+          ok = false;
+          break;
+        }
+        for (int sp = 1; sp < ks; ++sp) {
+          const float4* src =
+              reinterpret_cast<const float4*>(wsp + (size_t)(sp - 1) * (TBM * TBN) + rc);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const float4 v = __ldcg(src + e);
+            tot[4 * e] += v.x;
+            tot[4 * e + 1] += v.y;
+            tot[4 * e + 2] += v.z;
+            tot[4 * e + 3] += v.w;
+          }
+        }
+      }
       const long long row_base = (long long)mt * TBM + quarter * 32;
       const long long row = row_base + lane;
       const bool row_ok = row < ep.M;
@@ -338,8 +417,12 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* b
   }
   const int n_mt = (ep.M + TBM - 1) / TBM;
   const int n_nt = (ep.P + bn - 1) / bn;
-  const int tiles = n_mt * n_nt;
-  const int grid = tiles < sm_count ? tiles : sm_count;
+  const int ks = ep.ksplit > 1 ? ep.ksplit : 1;
+  if (ks > 1 && (!ep.sk_ws || !ep.sk_cnt || sm_count < ks))
+    return cudaErrorInvalidValue;
+  const int items = n_mt * n_nt * ks;
+  // a multiple of ks, so that the splits of a tile run in the same round
+  const int grid = (items < sm_count ? items : sm_count) / ks * ks;
   if (KS == 2 && (bn > 64 || (K / TBK) % 2)) return cudaErrorInvalidValue;
   k_tc_scan<OPA, KS><<<grid, kThreads, Cfg<OPA>::kSmem, st>>>(
       *a, *bh, *bl, (int)(K / TBK), n_mt, n_nt, bn, group_m, spin_ns, ep, da);

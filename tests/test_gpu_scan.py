@@ -466,3 +466,39 @@ def test_long_sample_axis(tgctx, N, encoding):
     compare_hits(res, ref, THR)
     compare_best(res, ref)
     assert np.array_equal(res["nobs"], ref["decode"]["n_obs"])
+
+
+@pytest.mark.parametrize("P,kernel,splits", [(40, "pair", 0), (300, "single", 2),
+                                             (300, "single", 4), (300, "single", 1)])
+@pytest.mark.parametrize("encoding", ["2bit", "u8"])
+def test_split_k(P, kernel, splits, encoding):
+    """Blocks with fewer tiles than SMs: the one-CTA kernel splits the samples into 2 or 4
+    chunk-aligned ranges (P <= 64: by rule, here 4 ranges over 5 chunks, the last one empty;
+    wider panels: as tuned) and the tile's first range adds the others' partial sums in order."""
+    N, M = 5000, 600
+    ctx = tg.tg_create(0)
+    try:
+        tg.tg_set_tuning(ctx, M, kernel, 16)
+        if splits:
+            tg.tg_set_tuning_split(ctx, M, splits)
+            assert tg.tg_tuning_split(ctx, M) == splits
+        w = synth.Workload(f"splitk_{encoding}_{P}", N=N, M=M, P=P, n_cov=3, encoding=encoding,
+                           missing=0.01 if encoding == "2bit" else 0.0, seed=P + 5, block=M,
+                           causal_per_pheno=1)
+        pan = synth.make_panel(w)
+        blk = synth.make_block(w, 0)
+        panel = tg.tg_prepare_panel(ctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+        try:
+            res = [run_scan(ctx, panel, blk["G"].cuda(), N, P, encoding, "split", full=True,
+                            hit_mlog10p=THR) for _ in range(2)]
+        finally:
+            tg.tg_panel_free(panel)
+        assert res[0]["status"] == tg.TG_OK
+        for k in ("beta", "se", "t", "mlog10p"):  # the same order of additions every run
+            assert np.array_equal(res[0][k], res[1][k], equal_nan=True), k
+        ref = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
+        compare_full(res[0], ref, label=f"split-K {P}/{kernel}/{splits}/{encoding}")
+        compare_hits(res[0], ref, THR)
+        compare_best(res[0], ref)
+    finally:
+        tg.tg_destroy(ctx)
