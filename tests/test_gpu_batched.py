@@ -76,11 +76,11 @@ def _hitset(hits, n):
     return {(int(x["marker"]), int(x["pheno"])): float(x["mlog10p"]) for x in h}
 
 
-@pytest.mark.parametrize("subset", [False, True])
-def test_graph_replay_equals_eager_scans_of_ragged_blocks(tgctx, subset):
-    """Captured scans of ragged blocks replay to the eager result, for a panel of all samples
-    and for a subset panel (whose marker norms come from the subset statistics kernel)."""
-    P = 300
+@pytest.mark.parametrize("subset,P", [(False, 300), (True, 300), (False, 40)])
+def test_graph_replay_equals_eager_scans_of_ragged_blocks(tgctx, subset, P):
+    """Captured scans of ragged blocks replay to the eager result, for a panel of all samples,
+    for a subset panel (whose marker norms come from the subset statistics kernel) and for a
+    small panel (64-column tiles, split-K on these few-tile blocks, inside the capture)."""
     cov = synth.covariates(84, N, 3)
     Y = synth.phenotypes(84, cov, P).cuda()
     if subset:
