@@ -1,0 +1,71 @@
+"""Host logic of bench.py (no GPU): the paper's throughput used for vs_baseline, the parser of
+the committed full-size ncu summary and its source check, the workload description and the
+partition of marker blocks over replicas."""
+import hashlib
+import os
+
+import bench
+import synth
+
+
+def test_paper_rate_is_the_section_3_1_figure():
+    w = synth.WORKLOADS["n23000_m8900000_p20480_c20_u8"]
+    assert abs(bench._paper_rate(w) - 8.9e6 * 20480 / 1108.0) < 1.0
+    w2 = synth.WORKLOADS["n23000_m1000000_p2048_c10_2bit"]
+    assert abs(bench._paper_rate(w2) - 8.9e6 * 2048 / 940.0) < 1.0
+    assert bench._paper_rate(synth.WORKLOADS["n2000_m10000_p16_c5_2bit"]) is None  # N=2,000
+    assert bench._paper_rate(synth.WORKLOADS["n23000_m500000_12panels_p8192_2bit"]) is None
+
+
+def _fake_repo(tmp_path, sha):
+    csrc = tmp_path / "paper_2604_21095_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k_tc2.cu").write_bytes(b"kernel a")
+    (csrc / "tc_common.cuh").write_bytes(b"header b")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "tc2_scan_traffic_n23000_p20480_u8.md").write_text(
+        "# title: with a colon\n\n| metric | value |\n|---|---|\n| a: b | c |\n\n"
+        "Workload: something\n"
+        "dram_bytes_per_launch: 123456\n"
+        "tensor_pipe_active_pct: 91.20\n"
+        f"source_sha256: {sha}\n"
+        "Reading. text with a colon: here\n")
+    return str(tmp_path)
+
+
+def test_kernel_profile_needs_the_sources_it_was_taken_on(tmp_path, monkeypatch):
+    good = hashlib.sha256(b"kernel a" + b"header b").hexdigest()
+    monkeypatch.setattr(bench, "ROOT", _fake_repo(tmp_path / "a", good))
+    assert bench._kernel_profile() == {"dram_bytes_per_launch": 123456, "tensor_pipe_active": 0.912}
+    monkeypatch.setattr(bench, "ROOT", _fake_repo(tmp_path / "b", "0" * 64))
+    assert bench._kernel_profile() == {}
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path / "missing"))
+    assert bench._kernel_profile() == {}
+
+
+def test_committed_profile_parses():
+    rec = {}
+    path = os.path.join(os.path.dirname(bench.__file__), "profiles",
+                        "tc2_scan_traffic_n23000_p20480_u8.md")
+    for line in open(path):
+        if ":" in line and not line.startswith(("|", "#", " ")):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    assert int(rec["dram_bytes_per_launch"]) > 4.9e9  # at least the compulsory operand bytes
+    assert 0.0 < float(rec["tensor_pipe_active_pct"]) <= 100.0
+    assert len(rec["source_sha256"]) == 64
+
+
+def test_config_names_the_workload_and_its_l2_relation():
+    w = synth.WORKLOADS["n23000_m8900000_p20480_c20_u8"]
+    cfg = bench._config(w)
+    assert cfg["workload"].startswith("n23000_m8900000_p20480_c20_u8")
+    assert (cfg["N"], cfg["P"], cfg["C"]) == (23000, 20480, 20)
+    assert "larger than L2" in cfg["l2"]
+
+
+def test_replicas_partition_the_blocks():
+    for ws in (1, 2, 3, 8):
+        got = sorted(b for r in range(ws) for b in bench.rank_blocks(r, ws, 5))
+        assert got == list(range(5 * ws))
