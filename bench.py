@@ -487,7 +487,8 @@ def _ours_batched(args, dist, rank, ws):
         b = int(sizes[i]).bit_length() - 1
         if b not in tuned:
             tg.tg_autotune(ctx, panel, enc, int(sizes[i]), stream=stream)
-            tuned[b] = tg.tg_tuning(ctx, int(sizes[i]))
+            tuned[b] = dict(tg.tg_tuning(ctx, int(sizes[i])),
+                            splits=tg.tg_tuning_split(ctx, int(sizes[i])))
     cap = 1 << 20
     hits = torch.zeros(cap * 24, dtype=torch.uint8, device=dev)
     n_hits = torch.zeros(1, dtype=torch.int64, device=dev)
