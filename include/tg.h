@@ -332,6 +332,13 @@ tg_status tg_set_tuning(tg_ctx* ctx, int64_t M, int32_t kernel, int32_t group);
  * without tuning. */
 tg_status tg_set_tuning_split(tg_ctx* ctx, int64_t M, int32_t splits);
 tg_status tg_tuning_split(const tg_ctx* ctx, int64_t M, int32_t* splits);
+/* Keep a tuning: write every tuned block-size bucket of the context to a small JSON file
+ * ({"format": "tg-tuning", "version": 1, "buckets": [{"min_markers", "kernel": "pair" or
+ * "single", "group_m", "splits"}, ...]}), and read such a file into a context (a tuning taken
+ * once on a GB300 reused by later runs). Loading checks every entry first and changes nothing
+ * if one is malformed (TG_ERR_INVALID_ARG). Host file I/O only; synchronous. */
+tg_status tg_tuning_save(const tg_ctx* ctx, const char* path);
+tg_status tg_tuning_load(tg_ctx* ctx, const char* path);
 
 /* Synchronise `stream`, then return and clear the latched device status
  * (TG_ERR_CAPACITY, TG_ERR_TIMEOUT) of work queued so far. */

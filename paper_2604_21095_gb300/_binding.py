@@ -68,6 +68,8 @@ _SIGS = {
     "tg_scan_host": (C.c_int, [_VP, _VP, _VP, _I64, _I32, _I64, _I64, _I64, _I64,
                                C.POINTER(tg_scan_opts), _VP, _I64, C.POINTER(_I64), _VP, _VP]),
     "tg_panel_concat": (C.c_int, [_VP, C.POINTER(_VP), C.c_int, C.POINTER(_VP), _VP]),
+    "tg_tuning_save": (C.c_int, [_VP, C.c_char_p]),
+    "tg_tuning_load": (C.c_int, [_VP, C.c_char_p]),
     "tg_set_tuning_split": (C.c_int, [_VP, _I64, _I32]),
     "tg_tuning_split": (C.c_int, [_VP, _I64, C.POINTER(_I32)]),
     "tg_scan_graph_create": (C.c_int, [_VP, _VP, C.c_int, C.POINTER(_VP), C.POINTER(_I64),
@@ -343,6 +345,14 @@ def tg_tuning_split(ctx, M) -> int:
     v = _I32()
     _check(load().tg_tuning_split(ctx, M, C.byref(v)))
     return v.value
+
+
+def tg_tuning_save(ctx, path: str):
+    _check(load().tg_tuning_save(ctx, os.fsencode(path)))
+
+
+def tg_tuning_load(ctx, path: str):
+    _check(load().tg_tuning_load(ctx, os.fsencode(path)))
 
 
 def tg_status_poll(ctx, stream=None) -> int:

@@ -1421,6 +1421,85 @@ tg_status tg_tuning_split(const tg_ctx* c, int64_t M, int32_t* splits) {
   return TG_OK;
 }
 
+tg_status tg_tuning_save(const tg_ctx* c, const char* path) {
+  TG_ARG(c && path, "null context or path");
+  std::string j = "{\"format\": \"tg-tuning\", \"version\": 1, \"buckets\": [";
+  bool first = true;
+  for (int b = 0; b < kTuneBuckets; ++b) {
+    if (c->tune_kernel[b] == TUNE_DEFAULT) continue;
+    char line[192];
+    std::snprintf(line, sizeof(line),
+                  "%s\n  {\"min_markers\": %lld, \"kernel\": \"%s\", \"group_m\": %d, "
+                  "\"splits\": %d}",
+                  first ? "" : ",", 1ll << b, c->tune_kernel[b] == TUNE_SINGLE ? "single" : "pair",
+                  c->tune_group[b] > 0 ? c->tune_group[b] : kGroupDefault,
+                  c->tune_split[b] > 1 ? c->tune_split[b] : 1);
+    j += line;
+    first = false;
+  }
+  j += "\n]}\n";
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(TG_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  const bool ok = std::fwrite(j.data(), 1, j.size(), f) == j.size();
+  if (std::fclose(f) != 0 || !ok) return fail(TG_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  return TG_OK;
+}
+
+tg_status tg_tuning_load(tg_ctx* c, const char* path) {
+  TG_ARG(c && path, "null context or path");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(TG_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  std::string j;
+  char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) j.append(buf, n);
+  std::fclose(f);
+  if (j.find("\"tg-tuning\"") == std::string::npos)
+    return fail(TG_ERR_INVALID_ARG, "not a tuning file written by tg_tuning_save");
+  // every entry first, then applied together, so that a bad file changes nothing
+  int kern[kTuneBuckets], grp[kTuneBuckets], spl[kTuneBuckets];
+  std::memcpy(kern, c->tune_kernel, sizeof(kern));
+  std::memcpy(grp, c->tune_group, sizeof(grp));
+  std::memcpy(spl, c->tune_split, sizeof(spl));
+  // the integer after "key": in one entry; false if absent or not a number
+  auto num_in = [](const std::string& e, const char* key, long long* v) -> bool {
+    const size_t k = e.find(key);
+    if (k == std::string::npos) return false;
+    const size_t colon = e.find(':', k);
+    if (colon == std::string::npos) return false;
+    const char* start = e.c_str() + colon + 1;
+    char* end = nullptr;
+    *v = std::strtoll(start, &end, 10);
+    return end != start;
+  };
+  size_t pos = j.find('[');
+  int entries = 0;
+  while (pos != std::string::npos && (pos = j.find('{', pos + 1)) != std::string::npos) {
+    const size_t close = j.find('}', pos);
+    if (close == std::string::npos) break;
+    const std::string e = j.substr(pos, close - pos + 1);
+    long long mm = 0, gm = 0, sp = 0;
+    const bool single = e.find("\"single\"") != std::string::npos;
+    const bool pair = e.find("\"pair\"") != std::string::npos;
+    if (!num_in(e, "\"min_markers\"", &mm) || !num_in(e, "\"group_m\"", &gm) ||
+        !num_in(e, "\"splits\"", &sp) || single == pair || mm < 1 || gm < 1 || gm > 1024 ||
+        (sp != 1 && sp != 2 && sp != 4))
+      return fail(TG_ERR_INVALID_ARG, "malformed tuning entry in " + std::string(path));
+    const int b = tune_bucket(mm);
+    kern[b] = single ? TUNE_SINGLE : TUNE_PAIR;
+    grp[b] = (int)gm;
+    spl[b] = (int)sp;
+    ++entries;
+    pos = close;
+  }
+  if (entries == 0 && j.find("\"min_markers\"") != std::string::npos)
+    return fail(TG_ERR_INVALID_ARG, "malformed tuning file " + std::string(path));
+  std::memcpy(c->tune_kernel, kern, sizeof(kern));
+  std::memcpy(c->tune_group, grp, sizeof(grp));
+  std::memcpy(c->tune_split, spl, sizeof(spl));
+  return TG_OK;
+}
+
 tg_status tg_tuning(const tg_ctx* c, int64_t M, int32_t* kernel, int32_t* group) {
   TG_ARG(c && M > 0, "bad arguments");
   const int b = tune_bucket(M);

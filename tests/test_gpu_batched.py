@@ -219,3 +219,31 @@ def test_graph_with_host_blocks_equals_eager_scans(tgctx, encoding):
     finally:
         tg.tg_destroy(ctx2)
         tg.tg_panel_free(panel)
+
+
+def test_tuning_file_roundtrip(tmp_path):
+    """A tuning saved to JSON loads into another context unchanged; a malformed file is refused
+    and changes nothing."""
+    a, b = tg.tg_create(0), tg.tg_create(0)
+    try:
+        tg.tg_set_tuning(a, 3000, "single", 8)
+        tg.tg_set_tuning_split(a, 3000, 4)
+        tg.tg_set_tuning(a, 70000, "pair", 32)
+        path = tmp_path / "tuning.json"
+        tg.tg_tuning_save(a, str(path))
+        text = path.read_text()
+        assert '"tg-tuning"' in text and '"single"' in text
+        tg.tg_tuning_load(b, str(path))
+        for m in (3000, 70000):
+            assert tg.tg_tuning(b, m) == tg.tg_tuning(a, m)
+            assert tg.tg_tuning_split(b, m) == tg.tg_tuning_split(a, m)
+        bad = tmp_path / "bad.json"
+        bad.write_text(text.replace('"splits": 4', '"splits": 3'))
+        with pytest.raises(tg.TgError):
+            tg.tg_tuning_load(b, str(bad))
+        assert tg.tg_tuning_split(b, 3000) == 4  # unchanged by the refused file
+        with pytest.raises(tg.TgError):
+            tg.tg_tuning_load(b, str(tmp_path / "missing.json"))
+    finally:
+        tg.tg_destroy(a)
+        tg.tg_destroy(b)
