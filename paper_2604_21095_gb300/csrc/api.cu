@@ -1,6 +1,7 @@
 // C ABI of the genome-scan library: argument checks, device memory of contexts and panels,
 // tensor maps, stage timing and the orchestration of the kernels of one block scan.
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -99,12 +100,17 @@ bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
   } while (0)
 
 // ---------------------------------------------------------------- profiling
+// Each stage is also an NVTX range on the calling thread (named for profilers and timelines;
+// a no-op when no tool is attached).
+const char* const kStageNames[TG_N_STAGES] = {"tg.decode", "tg.project", "tg.norm",
+                                              "tg.scan",   "tg.h2d",     "tg.stats"};
 struct StageScope {
   tg_ctx* c;
   int stage;
   cudaStream_t st;
   cudaEvent_t a = nullptr, b = nullptr;
   StageScope(tg_ctx* c_, int s_, cudaStream_t st_, int nlaunch) : c(c_), stage(s_), st(st_) {
+    nvtxRangePushA(kStageNames[stage]);
     c->launches[stage] += nlaunch;
     if (!c->prof) return;
     a = take();
@@ -112,6 +118,7 @@ struct StageScope {
     cudaEventRecord(a, st);
   }
   ~StageScope() {
+    nvtxRangePop();
     if (!c->prof || !a) return;
     cudaEventRecord(b, st);
     c->pending.push_back({a, b, stage});
