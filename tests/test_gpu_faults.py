@@ -77,3 +77,31 @@ def test_arguments_are_refused_before_launch(tgctx):
         assert tg.tg_status_poll(tgctx) == tg.TG_OK
     finally:
         tg.tg_panel_free(panel)
+
+
+def test_allocation_failure_is_reported_and_the_context_survives(tgctx):
+    """Host-side fault injection by size: a panel and a block whose device buffers cannot be
+    allocated (hundreds of GB) give TG_ERR_OOM before any kernel reads the inputs; the same
+    context then prepares and scans normally."""
+    N, P = 23000, 3
+    cov = synth.covariates(53, N, 1)
+    Y = synth.phenotypes(53, cov, P).cuda()
+    with pytest.raises(tg.TgError) as e:  # Y_res alone would need P * N * 8 = 736 GB
+        tg.tg_prepare_panel(tgctx, Y[:1], N, 4_000_000, cov.cuda())
+    assert e.value.status == tg.TG_ERR_OOM
+    panel = tg.tg_prepare_panel(tgctx, Y, N, P, cov.cuda())
+    try:
+        counts, miss = synth.hard_calls(53, 0, synth.maf(53, 0, 64), N)
+        G = synth.pack_2bit(counts, miss).cuda()
+        huge_M = 20_000_000  # the decoded operand alone would need huge_M * 23,040 * 2 = 920 GB
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, 7.3)
+        n_hits = torch.zeros(1, dtype=torch.int64, device="cuda")
+        hits = torch.zeros(24 * 16, dtype=torch.uint8, device="cuda")
+        out = tg.make_outputs(hits=hits, n_hits=n_hits)
+        with pytest.raises(tg.TgError) as e:
+            tg.tg_scan_block(tgctx, panel, G, N, huge_M, tg.TG_ENC_2BIT, opts, out)
+        assert e.value.status == tg.TG_ERR_OOM
+        res = run_scan(tgctx, panel, G, N, P, "2bit", "split")
+        assert res["status"] == tg.TG_OK and np.isfinite(res["t"]).all()
+    finally:
+        tg.tg_panel_free(panel)
