@@ -222,6 +222,37 @@ bool split_fits(const tg_ctx* c, const SplitChoice& sc) {
   return split_bytes(sc) <= c->sk_ws_bytes && (sc.ks <= 1 || sc.tiles <= c->sk_cnt_cap);
 }
 
+// Size the context's workspace for the scans a graph will capture: nothing may allocate inside
+// a capture. A workspace that another live graph has captured cannot move, so while one exists
+// only a graph whose blocks fit the current buffers is accepted.
+tg_status reserve_graph_workspace(tg_ctx* c, const tg_panel* p, int n_blocks, const int64_t* M,
+                                  int64_t maxM, bool need_operand, const tg_scan_opts& opts) {
+  const bool split = opts.precision == TG_PREC_SPLIT_BF16;
+  std::vector<SplitChoice> need;
+  for (int b = 0; b < n_blocks; ++b) {
+    if (split && (p->P <= 64 || c->tune_kernel[tune_bucket(M[b])] == TUNE_SINGLE))
+      need.push_back(pick_split(c, p, M[b], true));
+    if (split && opts.mode == TG_MODE_PROJECTED && p->q > 1)
+      need.push_back(pick_split(c, p, M[b], true, true));
+  }
+  if (c->graphs_alive > 0) {
+    bool fits = maxM <= c->cap_m;
+    if (need_operand)
+      fits = fits && round_up(maxM, MT) <= c->cap_rows && p->Npad <= c->cap_npad &&
+             (opts.precision == TG_PREC_FP32 ? c->A32 != nullptr : c->Ahi != nullptr);
+    for (const SplitChoice& sc : need) fits = fits && split_fits(c, sc);
+    if (!fits)
+      return fail(TG_ERR_INVALID_ARG,
+                  "another captured scan graph holds this context's workspace: capture the "
+                  "largest blocks first, or use another context");
+    return TG_OK;
+  }
+  TG_CUDA(ensure_markers(c, maxM));
+  if (need_operand) TG_CUDA(ensure_operands(c, maxM, p->Npad, opts.precision));
+  for (const SplitChoice& sc : need) TG_CUDA(ensure_split(c, sc));
+  return TG_OK;
+}
+
 }  // namespace
 
 namespace tg {
@@ -1126,14 +1157,9 @@ tg_status tg_scan_graph_create(tg_ctx* c, const tg_panel* p, int n_blocks,
   // size the workspace now: nothing may allocate inside the capture
   bool need_operand = opts->precision != TG_PREC_SPLIT_BF16 || !c->fuse_decode;
   for (int b = 0; b < n_blocks; ++b) need_operand |= missing && missing[b];
-  TG_CUDA(ensure_markers(c, maxM));
-  if (need_operand) TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision));
-  for (int b = 0; b < n_blocks; ++b) {
-    const bool single = opts->precision == TG_PREC_SPLIT_BF16 &&
-                        (p->P <= 64 || c->tune_kernel[tune_bucket(M[b])] == TUNE_SINGLE);
-    if (single) TG_CUDA(ensure_split(c, pick_split(c, p, M[b], true)));
-    if (opts->precision == TG_PREC_SPLIT_BF16 && opts->mode == TG_MODE_PROJECTED && p->q > 1)
-      TG_CUDA(ensure_split(c, pick_split(c, p, M[b], true, true)));
+  {
+    tg_status ws = reserve_graph_workspace(c, p, n_blocks, M, maxM, need_operand, *opts);
+    if (ws != TG_OK) return ws;
   }
   cudaStream_t cap = nullptr;
   TG_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -1195,14 +1221,9 @@ tg_status tg_scan_graph_create_host(tg_ctx* c, const tg_panel* p, int n_blocks,
     maxM = std::max(maxM, M[b]);
   }
   const bool need_operand = opts->precision != TG_PREC_SPLIT_BF16 || !c->fuse_decode;
-  TG_CUDA(ensure_markers(c, maxM));
-  if (need_operand) TG_CUDA(ensure_operands(c, maxM, p->Npad, opts->precision));
-  for (int b = 0; b < n_blocks; ++b) {
-    const bool single = opts->precision == TG_PREC_SPLIT_BF16 &&
-                        (p->P <= 64 || c->tune_kernel[tune_bucket(M[b])] == TUNE_SINGLE);
-    if (single) TG_CUDA(ensure_split(c, pick_split(c, p, M[b], true)));
-    if (opts->precision == TG_PREC_SPLIT_BF16 && opts->mode == TG_MODE_PROJECTED && p->q > 1)
-      TG_CUDA(ensure_split(c, pick_split(c, p, M[b], true, true)));
+  {
+    tg_status ws = reserve_graph_workspace(c, p, n_blocks, M, maxM, need_operand, *opts);
+    if (ws != TG_OK) return ws;
   }
   tg_graph* g = new tg_graph();
   g->ctx = c;

@@ -247,3 +247,47 @@ def test_tuning_file_roundtrip(tmp_path):
     finally:
         tg.tg_destroy(a)
         tg.tg_destroy(b)
+
+
+def test_second_graph_cannot_move_the_first_graphs_workspace(tgctx):
+    """While a graph holds the context's buffers, another graph on the same context is accepted
+    only if its blocks fit them; both then replay to the eager results."""
+    P = 300
+    cov = synth.covariates(88, N, 3)
+    panel = tg.tg_prepare_panel(tgctx, synth.phenotypes(88, cov, P).cuda(), N, P, cov.cuda())
+    ctx2 = tg.tg_create(0)
+    try:
+        w = synth.Workload("two_graphs", N=N, M=3000, P=P, n_cov=3, encoding="2bit",
+                           missing=0.01, seed=88, block=1024)
+        big = [synth.make_ragged_block(w, i, m, device="cuda") for i, m in enumerate([900, 700])]
+        small = [synth.make_ragged_block(w, 5 + i, m, device="cuda") for i, m in enumerate([500, 300])]
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, 3.0)
+        h1, n1, b1, o1 = _accum_outputs(P)
+        g1 = tg.tg_scan_graph_create(ctx2, panel, small, N, tg.TG_ENC_2BIT, opts, o1, [0, 500])
+        try:
+            h2, n2, b2, o2 = _accum_outputs(P)
+            with pytest.raises(tg.TgError) as e:
+                tg.tg_scan_graph_create(ctx2, panel, big, N, tg.TG_ENC_2BIT, opts, o2, [0, 900])
+            assert e.value.status == tg.TG_ERR_INVALID_ARG
+            g2 = tg.tg_scan_graph_create(ctx2, panel, small[1:], N, tg.TG_ENC_2BIT, opts, o2, [500])
+            try:
+                for g, n, b, blocks, offs in ((g1, n1, b1, small, [0, 500]),
+                                              (g2, n2, b2, small[1:], [500])):
+                    n.zero_()
+                    b.zero_()
+                    tg.tg_scan_graph_launch(g)
+                    assert tg.tg_status_poll(ctx2) == tg.TG_OK
+                    hits, nn, best, out = _accum_outputs(P)
+                    for blk, o in zip(blocks, offs):
+                        tg.tg_scan_block(tgctx, panel, blk, N, blk.shape[0], tg.TG_ENC_2BIT, opts,
+                                         out, marker_offset=o)
+                    assert tg.tg_status_poll(tgctx) == tg.TG_OK
+                    assert np.array_equal(b.cpu().numpy(), best.cpu().numpy())
+                    assert int(n.item()) == int(nn.item())
+            finally:
+                tg.tg_scan_graph_free(g2)
+        finally:
+            tg.tg_scan_graph_free(g1)
+    finally:
+        tg.tg_destroy(ctx2)
+        tg.tg_panel_free(panel)
