@@ -442,12 +442,12 @@ def test_panel_without_phenotypes(tgctx, precision):
     assert np.array_equal(res["nobs"], ref["decode"]["n_obs"])
 
 
-@pytest.mark.parametrize("N", [30000, 50000])
+@pytest.mark.parametrize("N", [30000, 50000, 200000])
 @pytest.mark.parametrize("encoding", ["2bit", "u8"])
 def test_long_sample_axis(tgctx, N, encoding):
     """Sample counts past the one-pass decode's limits (N > 24,576 takes the row-in-registers
-    kernel with twice the groups, N > 49,152 the two-pass one) and a long K loop (up to 49
-    accumulation chunks), in both kernels' tile widths (P = 70: 256-column tiles)."""
+    kernel with twice the groups, N > 49,152 the two-pass one) and long K loops (up to 196
+    accumulation chunks at a biobank-like N = 200,000), with 256-column tiles (P = 70)."""
     M, P = 200, 70
     w = synth.Workload(f"longN_{encoding}_{N}", N=N, M=M, P=P, n_cov=3, encoding=encoding,
                        missing=0.01 if encoding == "2bit" else 0.0, seed=N % 97, block=M,
