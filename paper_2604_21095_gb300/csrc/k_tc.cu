@@ -23,9 +23,12 @@
 // toward zero at each chained addition, which over 23,000 samples biases |r| low by about
 // 5e-5 relative; chunks of 1024 keep that bias near 2e-6. Two chunk accumulators (512 TMEM
 // columns) alternate, so draining one overlaps the products of the next.
-// Every mbarrier wait is bounded: past the limit the kernel latches ST_TIMEOUT, raises a
-// shared abort flag, lets in-flight copies and products finish (again bounded), frees its
-// TMEM and returns.
+// Tiles are 128 x 256, or 128 x 64 for the covariate projection and panels of at most 64
+// phenotypes. With split-K (ep.ksplit > 1, for blocks with fewer tiles than SMs) a work item is
+// a tile and a chunk-aligned range of the samples; the tile's first range adds the other
+// ranges' partial sums (handed over in global memory) in range order before its epilogue.
+// Every wait is bounded: past the limit the kernel latches ST_TIMEOUT, raises a shared abort
+// flag, lets in-flight copies and products finish (again bounded), frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
