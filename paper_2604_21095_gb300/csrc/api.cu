@@ -345,6 +345,9 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   CUtensorMap tA;
   if (split && !fused && !make_tmap(&tA, c->Ahi, a.M, p->Npad, p->Npad, MT))
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
+  // a small panel in the projected form: one pass over the operand gives the projection and the
+  // panel's products (raw, into qg after the projection columns); the statistics follow the norms
+  const bool joint = split && nq > 0 && p->QYhi != nullptr;
   if (nq > 0) {
     StageScope s(c, STAGE_PROJECT, st, 1);
     if (!split) {
@@ -352,12 +355,12 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     } else {
       EpiParams pp{};
       pp.M = (int)a.M;
-      pp.P = (int)nq;
+      pp.P = (int)(joint ? nq + p->P : nq);
       pp.status = c->status;
       pp.row_shift = c->shift;
-      pp.col_cs = p->qcs;
+      pp.col_cs = joint ? p->qycs : p->qcs;
       pp.raw_out = c->qg;
-      pp.raw_cols = (int)nq;
+      pp.raw_cols = pp.P;
       pp.raw_ld = QCOLS;
       const SplitChoice sc = pick_split(c, p, a.M, true, true);
       if (sc.ks > 1) {  // a small block: split K so that more SMs stream the operand
@@ -367,8 +370,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
         pp.sk_cnt = c->sk_cnt;
         TG_CUDA(cudaMemsetAsync(pp.sk_cnt, 0, sizeof(unsigned) * (size_t)sc.tiles, st));
       }
-      TG_CUDA(launch_tc_scan(&tA, &p->tmQhi, &p->tmQlo, p->Npad, pp, c->sm_count, kSpinNs, st,
-                             kGroupDefault, dec, a.encoding));
+      TG_CUDA(launch_tc_scan(&tA, joint ? &p->tmQYhi : &p->tmQhi, joint ? &p->tmQYlo : &p->tmQlo,
+                             p->Npad, pp, c->sm_count, kSpinNs, st, kGroupDefault, dec, a.encoding));
     }
   }
   if (p->samples) {  // a subset panel: |g_c|^2 over its samples
@@ -427,6 +430,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     StageScope s(c, STAGE_GEMM, st, 1);
     if (prec == TG_PREC_FP32) {
       TG_CUDA(launch_sgemm_scan(c->A32, p->Npad, p->B32, p->Npad, p->Npad, ep, st));
+    } else if (joint) {  // the products came with the projection
+      TG_CUDA(launch_raw_stats(c->qg + nq, QCOLS, ep, st));
     } else {
       const int b = tune_bucket(a.M);
       const int group = c->tune_group[b] > 0 ? c->tune_group[b] : kGroupDefault;
@@ -583,6 +588,34 @@ tg_status tg_destroy(tg_ctx* c) {
   return TG_OK;
 }
 
+// The joint operand of a small panel (tg_panel::QYhi): the q - 1 projection rows, then the P
+// phenotype rows, copied from the panel's own split operands. Nothing for a panel without
+// covariate columns or with P + q - 1 > 64. Synchronous on st.
+tg_status build_joint(tg_panel* p, cudaStream_t st) {
+  const int64_t nq = p->q - 1, P = p->P, Np = p->Npad;
+  if (nq <= 0 || P <= 0 || P + nq > QCOLS) return TG_OK;
+  const size_t row = sizeof(__nv_bfloat16) * (size_t)Np;
+  const auto d2d = cudaMemcpyDeviceToDevice;
+  cudaError_t e;
+  if ((e = dalloc(&p->QYhi, (size_t)(QCOLS * Np))) || (e = dalloc(&p->QYlo, (size_t)(QCOLS * Np))) ||
+      (e = dalloc(&p->qycs, (size_t)QCOLS)) ||
+      (e = cudaMemsetAsync(p->QYhi, 0, row * QCOLS, st)) ||
+      (e = cudaMemsetAsync(p->QYlo, 0, row * QCOLS, st)) ||
+      (e = cudaMemsetAsync(p->qycs, 0, sizeof(float) * QCOLS, st)) ||
+      (e = cudaMemcpyAsync(p->QYhi, p->QBhi, row * nq, d2d, st)) ||
+      (e = cudaMemcpyAsync(p->QYlo, p->QBlo, row * nq, d2d, st)) ||
+      (e = cudaMemcpyAsync(p->QYhi + nq * Np, p->Bhi, row * P, d2d, st)) ||
+      (e = cudaMemcpyAsync(p->QYlo + nq * Np, p->Blo, row * P, d2d, st)) ||
+      (e = cudaMemcpyAsync(p->qycs, p->qcs, sizeof(float) * nq, d2d, st)) ||
+      (e = cudaMemcpyAsync(p->qycs + nq, p->col_cs, sizeof(float) * P, d2d, st)) ||
+      (e = cudaStreamSynchronize(st)))
+    return cuda_fail(e, "joint projection and panel operand");
+  if (!make_tmap(&p->tmQYhi, p->QYhi, QCOLS, Np, Np, 64) ||
+      !make_tmap(&p->tmQYlo, p->QYlo, QCOLS, Np, Np, 64))
+    return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the joint operand");
+  return TG_OK;
+}
+
 tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, int64_t P,
                            const double* C, int64_t ldc, int64_t n_cov, tg_panel** out,
                            void* stream) {
@@ -665,6 +698,8 @@ tg_status tg_prepare_panel(tg_ctx* c, const float* Y, int64_t ldy, int64_t N, in
       !make_tmap(&p->tmBhi64, p->Bhi, p->Ppad, p->Npad, p->Npad, 64) ||
       !make_tmap(&p->tmBlo64, p->Blo, p->Ppad, p->Npad, p->Npad, 64))
     return cleanup(fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the panel"));
+  const tg_status js = build_joint(p, st);
+  if (js != TG_OK) return cleanup(js);
   *out = p;
   return TG_OK;
 }
@@ -774,6 +809,8 @@ tg_status tg_prepare_panel_subset(tg_ctx* c, const float* Y, int64_t ldy, int64_
       !make_tmap(&r->tmQhi, r->QBhi, QCOLS, Np, Np, 64) || !make_tmap(&r->tmQlo, r->QBlo, QCOLS, Np, Np, 64) ||
       !make_tmap(&r->tmBhi64, r->Bhi, Pp, Np, Np, 64) || !make_tmap(&r->tmBlo64, r->Blo, Pp, Np, Np, 64))
     return cleanup(fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the subset panel"));
+  const tg_status js = build_joint(r, st);
+  if (js != TG_OK) return cleanup(js);
   tg_panel* done = r;
   r = nullptr;
   cleanup(TG_OK);
@@ -830,6 +867,7 @@ tg_status tg_panel_free(tg_panel* p) {
   dfree(p->X); dfree(p->Q); dfree(p->Yres); dfree(p->s); dfree(p->col_s); dfree(p->col_rmul);
   dfree(p->col_cs); dfree(p->qcs); dfree(p->samples);
   dfree(p->Bhi); dfree(p->Blo); dfree(p->B32); dfree(p->QB); dfree(p->QBhi); dfree(p->QBlo);
+  dfree(p->QYhi); dfree(p->QYlo); dfree(p->qycs);
   delete p;
   return TG_OK;
 }
@@ -1130,6 +1168,11 @@ tg_status tg_panel_concat(tg_ctx* c, const tg_panel* const* panels, int n, tg_pa
       !make_tmap(&r->tmBhi64, r->Bhi, Pp, Np, Np, 64) || !make_tmap(&r->tmBlo64, r->Blo, Pp, Np, Np, 64)) {
     tg_panel_free(r);
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the concatenated panel");
+  }
+  const tg_status js = build_joint(r, st);
+  if (js != TG_OK) {
+    tg_panel_free(r);
+    return js;
   }
   *out = r;
   return TG_OK;

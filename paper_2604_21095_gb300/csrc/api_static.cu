@@ -198,6 +198,8 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   if (split && !tmap_static(&tA, Ahi, M, p->Npad, p->Npad, MT))
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
   const int64_t nq = opts->mode == TG_MODE_PAPER ? 0 : p->q - 1;  // the paper's form: no projection
+  // a small panel: the projection and the panel's products in one pass (raw, into qg)
+  const bool joint = split && nq > 0 && p->QYhi != nullptr;
   if (nq > 0) {
     if (!split) {
       TGS_CUDA(launch_project(reinterpret_cast<const float*>(Ahi), p->Npad, M, p->Npad, p->QB, nq,
@@ -205,15 +207,15 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
     } else {
       EpiParams pp{};
       pp.M = (int)M;
-      pp.P = (int)nq;
+      pp.P = (int)(joint ? nq + p->P : nq);
       pp.status = status;
       pp.row_shift = shift;
-      pp.col_cs = p->qcs;
+      pp.col_cs = joint ? p->qycs : p->qcs;
       pp.raw_out = qg;
-      pp.raw_cols = (int)nq;
+      pp.raw_cols = pp.P;
       pp.raw_ld = QCOLS;
-      TGS_CUDA(launch_tc_scan(&tA, &p->tmQhi, &p->tmQlo, p->Npad, pp, ds->sm_count, kStaticSpinNs,
-                              st));
+      TGS_CUDA(launch_tc_scan(&tA, joint ? &p->tmQYhi : &p->tmQhi, joint ? &p->tmQYlo : &p->tmQlo,
+                              p->Npad, pp, ds->sm_count, kStaticSpinNs, st));
     }
   }
   const MarkerRefine rf{G, ldg, encoding, N, missing, ldm, mean, p->Q, (int)p->q, refine_list,
@@ -260,6 +262,8 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   if (!split) {
     TGS_CUDA(launch_sgemm_scan(reinterpret_cast<const float*>(Ahi), p->Npad, p->B32, p->Npad,
                                p->Npad, ep, st));
+  } else if (joint) {  // the products came with the projection
+    TGS_CUDA(launch_raw_stats(qg + nq, QCOLS, ep, st));
   } else {
     const bool narrow = p->P <= 64;  // a small panel: 64-column tiles, bound by HBM
     TGS_CUDA(launch_tc_scan(&tA, narrow ? &p->tmBhi64 : &p->tmBhi, narrow ? &p->tmBlo64 : &p->tmBlo,

@@ -129,6 +129,13 @@ struct tg_panel {
   CUtensorMap tmBhi2, tmBlo2;    // phenotype panel, 128-row boxes (one CTA's half of a pair tile)
   CUtensorMap tmQhi, tmQlo;      // covariate projection columns, 64-row boxes
   CUtensorMap tmBhi64, tmBlo64;  // phenotype panel, 64-row boxes (64-column tiles, P <= 64)
+  // Small panels (P + q - 1 <= 64): the projection columns and the phenotypes in one operand,
+  // rows [0, q-1) = QB rows, rows [q-1, q-1+P) = the panel, rest zero, so that one pass over a
+  // block's operand gives both Q^T a and the panel's products (NULL when the panel is larger).
+  __nv_bfloat16* QYhi = nullptr;  // [QCOLS][Npad]
+  __nv_bfloat16* QYlo = nullptr;
+  float* qycs = nullptr;          // [QCOLS] qcs then col_cs
+  CUtensorMap tmQYhi, tmQYlo;     // 64-row boxes
 };
 
 struct tg_ctx {
@@ -270,6 +277,11 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                            const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
                            long long spin_ns, cudaStream_t st, int group_m = 16,
                            const DecodeArgs* dec = nullptr, int encoding = 0, bool narrow = false);
+
+// The statistics of a small panel from the joint pass's raw products (k_tc.cu): D of marker row
+// m and phenotype p at raw[m * ld + p] (the shift's add-back included), the same per-element
+// epilogue as the contraction kernels.
+cudaError_t launch_raw_stats(const float* raw, int64_t ld, const EpiParams& ep, cudaStream_t st);
 
 // tensor-core kernel on CTA pairs, 256 x 256 tiles (k_tc2.cu)
 cudaError_t launch_tc2_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,

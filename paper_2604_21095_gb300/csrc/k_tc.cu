@@ -391,6 +391,28 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Statistics of a small panel from its raw products: each warp takes 32 consecutive marker
+// rows (a lane per row, as in the contraction epilogue) and runs the same per-element code on
+// the row's P <= 64 products, whose shift add-back is already in (shift 0 here).
+__global__ void __launch_bounds__(128) k_raw_stats(const float* __restrict__ raw, long long ld,
+                                                   EpiParams ep) {
+  const int lane = threadIdx.x & 31;
+  const long long row_base = ((long long)blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
+  if (row_base >= ep.M) return;  // warp-uniform
+  const long long row = row_base + lane;
+  const bool row_ok = row < ep.M;
+  float tot[128];
+#pragma unroll
+  for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
+  if (row_ok) {
+#pragma unroll
+    for (int e = 0; e < 64; ++e)
+      if (e < ep.P) tot[e] = raw[row * ld + e];
+  }
+  const float rinv = row_ok ? ep.row_inv[row] : __int_as_float(0x7fc00000);
+  epilogue_tile(ep, tot, row, row_base, row_ok, rinv, 0.0f, 0, lane);
+}
+
 __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, uint32_t* result) {
   const uint64_t t0 = globaltimer_ns();
   for (;;) {
@@ -453,6 +475,14 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
   if (encoding == TG_ENC_2BIT)
     return go<OPA_2BIT, 1>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec, bn);
   return go<OPA_U8, 1>(tmBhi, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, *dec, bn);
+}
+
+cudaError_t launch_raw_stats(const float* raw, int64_t ld, const EpiParams& ep, cudaStream_t st) {
+  if (ep.M == 0 || ep.P == 0) return cudaSuccess;
+  if (ep.P > 64) return cudaErrorInvalidValue;
+  const long long blocks = ((long long)ep.M + 127) / 128;
+  k_raw_stats<<<(unsigned)blocks, 128, 0, st>>>(raw, (long long)ld, ep);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_wait_test(const uint32_t* flag, long long limit_ns, uint32_t* result,
