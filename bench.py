@@ -642,7 +642,7 @@ def _sweep_p(args):
     hits = torch.zeros((1 << 20) * 24, dtype=torch.uint8, device=dev)
     n_hits = torch.zeros(1, dtype=torch.int64, device=dev)
     points = []
-    for P in (16, 40, 64, 256, 1024, 2048, 4096, 8192, 20480):
+    for P in (16, 40, 64, 100, 200, 256, 1024, 2048, 4096, 8192, 20480):
         if P > w.P:
             break
         Yt = pan["Yt"][:P].contiguous()

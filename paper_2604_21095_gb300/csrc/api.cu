@@ -144,7 +144,7 @@ cudaError_t ensure_markers(tg_ctx* c, int64_t M) {
   cudaError_t e;
   if ((e = dalloc(&c->nobs, cap)) || (e = dalloc(&c->mean, cap)) || (e = dalloc(&c->shift, cap)) ||
       (e = dalloc(&c->mh, cap)) || (e = dalloc(&c->gc2s, cap)) ||
-      (e = dalloc(&c->gc2, cap)) || (e = dalloc(&c->qg, cap * QCOLS)) ||
+      (e = dalloc(&c->gc2, cap)) || (e = dalloc(&c->qg, cap * JCOLS)) ||
       (e = dalloc(&c->gres2, cap)) || (e = dalloc(&c->rinv, cap)) || (e = dalloc(&c->rinv64, cap)) ||
       (e = dalloc(&c->refine_list, cap)))
     return e;
@@ -347,7 +347,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
   // a small panel in the projected form: one pass over the operand gives the projection and the
   // panel's products (raw, into qg after the projection columns); the statistics follow the norms
-  const bool joint = split && nq > 0 && p->QYhi != nullptr;
+  const bool joint = split && nq > 0 && p->joint_cols > 0;
+  const int64_t ldq = joint ? p->joint_cols : QCOLS;  // qg row stride
   if (nq > 0) {
     StageScope s(c, STAGE_PROJECT, st, 1);
     if (!split) {
@@ -361,7 +362,7 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       pp.col_cs = joint ? p->qycs : p->qcs;
       pp.raw_out = c->qg;
       pp.raw_cols = pp.P;
-      pp.raw_ld = QCOLS;
+      pp.raw_ld = (int)ldq;
       const SplitChoice sc = pick_split(c, p, a.M, true, true);
       if (sc.ks > 1) {  // a small block: split K so that more SMs stream the operand
         TG_CUDA(ensure_split(c, sc));
@@ -383,7 +384,7 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     StageScope s(c, STAGE_NORM, st, nq > 0 ? 2 : 1);
     const MarkerRefine rf{a.G, a.ldg, a.encoding, a.N, a.missing, a.ldm, c->mean, p->Q, (int)p->q,
                           c->refine_list, c->scratch + 40};
-    TG_CUDA(launch_marker_norm(a.M, c->nobs, p->samples ? c->gc2s : c->gc2, c->qg, nq, kappa64, c->gres2,
+    TG_CUDA(launch_marker_norm(a.M, c->nobs, p->samples ? c->gc2s : c->gc2, c->qg, ldq, nq, kappa64, c->gres2,
                                a.out.marker_norm2, c->rinv, c->rinv64, &rf, st));
     if (a.out.marker_nobs)
       TG_CUDA(cudaMemcpyAsync(a.out.marker_nobs, c->nobs, sizeof(int32_t) * a.M,
@@ -431,7 +432,7 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     if (prec == TG_PREC_FP32) {
       TG_CUDA(launch_sgemm_scan(c->A32, p->Npad, p->B32, p->Npad, p->Npad, ep, st));
     } else if (joint) {  // the products came with the projection
-      TG_CUDA(launch_raw_stats(c->qg + nq, QCOLS, ep, st));
+      TG_CUDA(launch_raw_stats(c->qg + nq, ldq, ep, st));
     } else {
       const int b = tune_bucket(a.M);
       const int group = c->tune_group[b] > 0 ? c->tune_group[b] : kGroupDefault;
@@ -589,19 +590,21 @@ tg_status tg_destroy(tg_ctx* c) {
 }
 
 // The joint operand of a small panel (tg_panel::QYhi): the q - 1 projection rows, then the P
-// phenotype rows, copied from the panel's own split operands. Nothing for a panel without
-// covariate columns or with P + q - 1 > 64. Synchronous on st.
+// phenotype rows, copied from the panel's own split operands, in the fewest of 64, 128 or 256
+// rows that hold them. Nothing for a panel without covariate columns or with P + q - 1 > 256.
+// Synchronous on st.
 tg_status build_joint(tg_panel* p, cudaStream_t st) {
   const int64_t nq = p->q - 1, P = p->P, Np = p->Npad;
-  if (nq <= 0 || P <= 0 || P + nq > QCOLS) return TG_OK;
+  if (nq <= 0 || P <= 0 || P + nq > JCOLS) return TG_OK;
+  const int64_t jc = P + nq <= 64 ? 64 : P + nq <= 128 ? 128 : 256;
   const size_t row = sizeof(__nv_bfloat16) * (size_t)Np;
   const auto d2d = cudaMemcpyDeviceToDevice;
   cudaError_t e;
-  if ((e = dalloc(&p->QYhi, (size_t)(QCOLS * Np))) || (e = dalloc(&p->QYlo, (size_t)(QCOLS * Np))) ||
-      (e = dalloc(&p->qycs, (size_t)QCOLS)) ||
-      (e = cudaMemsetAsync(p->QYhi, 0, row * QCOLS, st)) ||
-      (e = cudaMemsetAsync(p->QYlo, 0, row * QCOLS, st)) ||
-      (e = cudaMemsetAsync(p->qycs, 0, sizeof(float) * QCOLS, st)) ||
+  if ((e = dalloc(&p->QYhi, (size_t)(jc * Np))) || (e = dalloc(&p->QYlo, (size_t)(jc * Np))) ||
+      (e = dalloc(&p->qycs, (size_t)jc)) ||
+      (e = cudaMemsetAsync(p->QYhi, 0, row * jc, st)) ||
+      (e = cudaMemsetAsync(p->QYlo, 0, row * jc, st)) ||
+      (e = cudaMemsetAsync(p->qycs, 0, sizeof(float) * jc, st)) ||
       (e = cudaMemcpyAsync(p->QYhi, p->QBhi, row * nq, d2d, st)) ||
       (e = cudaMemcpyAsync(p->QYlo, p->QBlo, row * nq, d2d, st)) ||
       (e = cudaMemcpyAsync(p->QYhi + nq * Np, p->Bhi, row * P, d2d, st)) ||
@@ -610,9 +613,10 @@ tg_status build_joint(tg_panel* p, cudaStream_t st) {
       (e = cudaMemcpyAsync(p->qycs + nq, p->col_cs, sizeof(float) * P, d2d, st)) ||
       (e = cudaStreamSynchronize(st)))
     return cuda_fail(e, "joint projection and panel operand");
-  if (!make_tmap(&p->tmQYhi, p->QYhi, QCOLS, Np, Np, 64) ||
-      !make_tmap(&p->tmQYlo, p->QYlo, QCOLS, Np, Np, 64))
+  if (!make_tmap(&p->tmQYhi, p->QYhi, jc, Np, Np, (uint32_t)jc) ||
+      !make_tmap(&p->tmQYlo, p->QYlo, jc, Np, Np, (uint32_t)jc))
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the joint operand");
+  p->joint_cols = (int)jc;
   return TG_OK;
 }
 

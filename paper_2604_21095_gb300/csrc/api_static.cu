@@ -199,7 +199,7 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
   const int64_t nq = opts->mode == TG_MODE_PAPER ? 0 : p->q - 1;  // the paper's form: no projection
   // a small panel: the projection and the panel's products in one pass (raw, into qg)
-  const bool joint = split && nq > 0 && p->QYhi != nullptr;
+  const bool joint = split && nq > 0 && p->joint_cols == QCOLS;  // the scratch holds 64 columns
   if (nq > 0) {
     if (!split) {
       TGS_CUDA(launch_project(reinterpret_cast<const float*>(Ahi), p->Npad, M, p->Npad, p->QB, nq,
@@ -220,7 +220,7 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   }
   const MarkerRefine rf{G, ldg, encoding, N, missing, ldm, mean, p->Q, (int)p->q, refine_list,
                         status + 1};
-  TGS_CUDA(launch_marker_norm(M, nobs, gc2, qg, nq, kappa64, gres2, out->marker_norm2, rinv, rinv64,
+  TGS_CUDA(launch_marker_norm(M, nobs, gc2, qg, QCOLS, nq, kappa64, gres2, out->marker_norm2, rinv, rinv64,
                               &rf, st));
   if (out->marker_nobs)
     TGS_CUDA(cudaMemcpyAsync(out->marker_nobs, nobs, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st));

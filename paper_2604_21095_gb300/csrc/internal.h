@@ -21,6 +21,7 @@ constexpr int kAccumChunkKB = 32;  // tensor-core accumulation chunk: 32 K block
 constexpr int PPAD = 256;    // phenotype rows padding of the panel operands (tensor-core N tile)
 constexpr int QMAX = 64;     // intercept + at most 63 covariates
 constexpr int QCOLS = 64;    // projection columns (Q columns 1..q-1), zero padded
+constexpr int JCOLS = 256;   // widest joint operand: projection columns + panel in one tile
 constexpr int MT = 128;      // marker rows per tensor-core tile
 
 enum Stage { STAGE_DECODE = 0, STAGE_PROJECT = 1, STAGE_NORM = 2, STAGE_GEMM = 3, STAGE_H2D = 4,
@@ -129,13 +130,15 @@ struct tg_panel {
   CUtensorMap tmBhi2, tmBlo2;    // phenotype panel, 128-row boxes (one CTA's half of a pair tile)
   CUtensorMap tmQhi, tmQlo;      // covariate projection columns, 64-row boxes
   CUtensorMap tmBhi64, tmBlo64;  // phenotype panel, 64-row boxes (64-column tiles, P <= 64)
-  // Small panels (P + q - 1 <= 64): the projection columns and the phenotypes in one operand,
-  // rows [0, q-1) = QB rows, rows [q-1, q-1+P) = the panel, rest zero, so that one pass over a
-  // block's operand gives both Q^T a and the panel's products (NULL when the panel is larger).
-  __nv_bfloat16* QYhi = nullptr;  // [QCOLS][Npad]
+  // Small panels (P + q - 1 <= 256): the projection columns and the phenotypes in one operand
+  // of joint_cols = 64, 128 or 256 rows, rows [0, q-1) = QB rows, rows [q-1, q-1+P) = the panel, rest
+  // zero, so that one pass over a block's operand gives both Q^T a and the panel's products
+  // (joint_cols = 0 and NULL buffers when the panel is larger).
+  int joint_cols = 0;
+  __nv_bfloat16* QYhi = nullptr;  // [joint_cols][Npad]
   __nv_bfloat16* QYlo = nullptr;
-  float* qycs = nullptr;          // [QCOLS] qcs then col_cs
-  CUtensorMap tmQYhi, tmQYlo;     // 64-row boxes
+  float* qycs = nullptr;          // [joint_cols] qcs then col_cs
+  CUtensorMap tmQYhi, tmQYlo;     // boxes of joint_cols rows
 };
 
 struct tg_ctx {
@@ -258,7 +261,7 @@ struct MarkerRefine {
   unsigned* count;
 };
 cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
-                               int64_t nq, double kappa, double* gres2_units_out,
+                               int64_t ldq, int64_t nq, double kappa, double* gres2_units_out,
                                double* norm2_allele_out, float* rinv, double* rinv64,
                                const MarkerRefine* refine, cudaStream_t st);
 cudaError_t launch_sgemm_scan(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t K,
@@ -271,16 +274,17 @@ cudaError_t launch_fill_random(uint8_t* p, size_t n, unsigned long long seed, cu
 
 // tensor-core kernel (k_tc.cu)
 // With `dec` non-NULL the A operand is decoded from packed genotypes in the kernel (tmA unused).
-// `narrow`: 64-column tiles for a panel of at most 64 phenotypes (B maps with 64-row boxes);
-// the covariate projection (ep.raw_out) always uses them.
+// `narrow`: 64-column tiles for a panel of at most 64 phenotypes (B maps with 64-row boxes).
+// Raw mode (ep.raw_out: the covariate projection, alone or joint with a small panel) uses the
+// narrowest of 64-, 128- and 256-column tiles that holds the raw columns.
 cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                            const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
                            long long spin_ns, cudaStream_t st, int group_m = 16,
                            const DecodeArgs* dec = nullptr, int encoding = 0, bool narrow = false);
 
-// The statistics of a small panel from the joint pass's raw products (k_tc.cu): D of marker row
-// m and phenotype p at raw[m * ld + p] (the shift's add-back included), the same per-element
-// epilogue as the contraction kernels.
+// The statistics of a small panel (P <= 256) from the joint pass's raw products (k_tc.cu): D of
+// marker row m and phenotype p at raw[m * ld + p] (the shift's add-back included), the same
+// per-element epilogue as the contraction kernels.
 cudaError_t launch_raw_stats(const float* raw, int64_t ld, const EpiParams& ep, cudaStream_t st);
 
 // tensor-core kernel on CTA pairs, 256 x 256 tiles (k_tc2.cu)

@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ A, lo
 constexpr double kRefineShare = 0.5;
 
 __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
-                              const double* __restrict__ gc2, const float* __restrict__ qg, int nq,
+                              const double* __restrict__ gc2, const float* __restrict__ qg,
+                              long long ldq, int nq,
                               double kappa, double* __restrict__ gres2u,
                               double* __restrict__ norm2_allele, float* __restrict__ rinv,
                               double* __restrict__ rinv64, int* __restrict__ refine_list,
@@ -103,7 +104,7 @@ __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
   const double c2 = gc2[j];
   double s = 0.0;
   for (int k = 0; k < nq; ++k) {
-    const double v = (double)qg[j * QCOLS + k];
+    const double v = (double)qg[j * ldq + k];
     s += v * v;
   }
   const double r2 = c2 - s;
@@ -296,7 +297,7 @@ cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, co
 }
 
 cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
-                               int64_t nq, double kappa, double* gres2_units_out,
+                               int64_t ldq, int64_t nq, double kappa, double* gres2_units_out,
                                double* norm2_allele_out, float* rinv, double* rinv64,
                                const MarkerRefine* refine, cudaStream_t st) {
   if (M == 0) return cudaSuccess;
@@ -306,7 +307,7 @@ cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2
     if (e != cudaSuccess) return e;
   }
   k_marker_norm<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(
-      M, nobs, gc2, qg, (int)nq, kappa, gres2_units_out, norm2_allele_out, rinv, rinv64,
+      M, nobs, gc2, qg, (long long)ldq, (int)nq, kappa, gres2_units_out, norm2_allele_out, rinv, rinv64,
       rf ? refine->list : nullptr, rf ? refine->count : nullptr);
   if (!rf) return cudaGetLastError();
   // a fixed grid, so that the launch does not depend on the count (graph capture)

@@ -41,20 +41,25 @@ namespace {
 
 using namespace tcx;
 
-template <int OPA>
+template <int OPA, int KS = 1, int BR = 64>
 struct Cfg {
-  // A, B_hi, B_lo and (when decoding here) the CTA's packed rows: 40 KB (+ 2 or 4 KB)
-  static constexpr int kStageBytes = A_BYTES + 2 * B_BYTES + DecCfg<OPA>::kPackBytes;
-  static constexpr int kStages = 5;
+  // A, B_hi, B_lo and (when decoding here) the CTA's packed rows: 40 KB (+ 2 or 4 KB), 5 stages;
+  // two K blocks of up to 64 B rows use the same slot; two K blocks of 128 B rows take
+  // 2 x (8 + 2 x 8) = 48 KB, 4 stages
+  static constexpr bool kWide = KS == 2 && BR > 64;
+  static constexpr int kStageBytes =
+      kWide ? KS * (A_BYTES + 2 * BR * TBK * 2) : A_BYTES + 2 * B_BYTES + DecCfg<OPA>::kPackBytes;
+  static constexpr int kStages = kWide ? 4 : 5;
   static constexpr int kBarBytes = 256;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;  // + alignment slack
 };
 
-// KS = K blocks per stage. With 64-column tiles (the covariate projection, and panels of at most
-// 64 phenotypes) the kernel streams the 3 GB operand and is bound by HBM, where two consecutive
-// 64-byte row segments requested back to back use the DRAM pages better than one: it then loads
-// two K blocks per stage into the 40 KB slot (A halves at 0 and 8 KB, B_hi halves at 16 and
-// 20 KB, B_lo halves at 24 and 28 KB; 64 B rows).
+// KS = K blocks per stage, BR = B rows per K block when KS = 2. With 64- or 128-column tiles (the
+// covariate projection, alone or joint with a small panel, and panels of at most 64 phenotypes)
+// the kernel streams the 3 GB operand and is bound by HBM, where two consecutive 64-byte row
+// segments requested back to back use the DRAM pages better than one: it then loads two K
+// blocks per stage (A halves at 0 and 8 KB, then the two B_hi halves, then the two B_lo halves,
+// BR x 64 B each).
 static_assert(kChunkKB == kAccumChunkKB, "the host's split choice counts the same chunks");
 
 // K-block range [lo, hi) of split `sp` of `ks`: whole accumulation chunks, the earlier splits
@@ -71,14 +76,14 @@ __device__ __forceinline__ int chunk_end_in(int kb0, int lo, int hi) {
   return e < hi ? e : hi;
 }
 
-template <int OPA, int KS>
+template <int OPA, int KS, int BR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmBhi,
               const __grid_constant__ CUtensorMap tmBlo, int num_kb, int n_mt, int n_nt, int bn,
               int group_m, long long spin_ns, EpiParams ep,
               const __grid_constant__ DecodeArgs da) {
-  // bn = B rows per tile: 256 for the phenotype panel, 64 for the covariate projection
-  using C = Cfg<OPA>;
+  // bn = B rows per tile: 256 for the phenotype panel, 64 or 128 (<= BR) with KS = 2
+  using C = Cfg<OPA, KS, BR>;
   constexpr bool kFused = OPA != OPA_TMA;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -100,14 +105,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
   auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + B_BYTES; };
   auto sPk = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * B_BYTES; };
-  static_assert(KS == 1 || (KS == 2 && !kFused && 2 * A_BYTES + 4 * 4096 <= C::kStageBytes),
-                "two K blocks per stage: decoded operand and at most 64 B rows");
+  constexpr int kBk = BR * TBK * 2;  // one K block of B rows (KS = 2)
+  static_assert(KS == 1 || (KS == 2 && !kFused && 2 * A_BYTES + 4 * kBk <= C::kStageBytes),
+                "two K blocks per stage: decoded operand and at most BR B rows");
   auto sAk = [&](int s, int h) { return KS == 1 ? sA(s) : sA(s) + (uint32_t)(h * A_BYTES); };
   auto sBhik = [&](int s, int h) {
-    return KS == 1 ? sBhi(s) : sA(s) + (uint32_t)(2 * A_BYTES + h * 4096);
+    return KS == 1 ? sBhi(s) : sA(s) + (uint32_t)(2 * A_BYTES + h * kBk);
   };
   auto sBlok = [&](int s, int h) {
-    return KS == 1 ? sBlo(s) : sA(s) + (uint32_t)(2 * A_BYTES + 2 * 4096 + h * 4096);
+    return KS == 1 ? sBlo(s) : sA(s) + (uint32_t)(2 * A_BYTES + 2 * kBk + h * kBk);
   };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -367,12 +373,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float rinv = (row_ok && ep.row_inv) ? ep.row_inv[row] : __int_as_float(0x7fc00000);
       const float shift = (row_ok && ep.row_shift) ? ep.row_shift[row] : 0.0f;
       if (ep.raw_out) {
-        // covariate projection: the first raw_cols columns of the tile, unnormalised
-        if (row_ok && half == 0) {
+        // covariate projection (and a small panel's products): the first raw_cols columns of
+        // the tile, unnormalised
+        if (row_ok) {
 #pragma unroll
-          for (int e = 0; e < 64; ++e)
-            if (e < ep.raw_cols)
-              ep.raw_out[row * ep.raw_ld + e] = fmaf(shift, ep.col_cs[e], tot[e]);
+          for (int e = 0; e < 128; ++e) {  // fully unrolled: tot stays in registers
+            const int col = half * 128 + e;
+            if (col < ep.raw_cols)
+              ep.raw_out[row * ep.raw_ld + col] = fmaf(shift, ep.col_cs[col], tot[e]);
+          }
         }
       } else {
         epilogue_tile(ep, tot, row, row_base, row_ok, rinv, shift, nt * TBN + half * 128, lane);
@@ -393,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // Statistics of a small panel from its raw products: each warp takes 32 consecutive marker
 // rows (a lane per row, as in the contraction epilogue) and runs the same per-element code on
-// the row's P <= 64 products, whose shift add-back is already in (shift 0 here).
+// the row's P <= 256 products, 128 at a time, whose shift add-back is already in (shift 0).
 __global__ void __launch_bounds__(128) k_raw_stats(const float* __restrict__ raw, long long ld,
                                                    EpiParams ep) {
   const int lane = threadIdx.x & 31;
@@ -401,16 +410,14 @@ __global__ void __launch_bounds__(128) k_raw_stats(const float* __restrict__ raw
   if (row_base >= ep.M) return;  // warp-uniform
   const long long row = row_base + lane;
   const bool row_ok = row < ep.M;
-  float tot[128];
-#pragma unroll
-  for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
-  if (row_ok) {
-#pragma unroll
-    for (int e = 0; e < 64; ++e)
-      if (e < ep.P) tot[e] = raw[row * ld + e];
-  }
   const float rinv = row_ok ? ep.row_inv[row] : __int_as_float(0x7fc00000);
-  epilogue_tile(ep, tot, row, row_base, row_ok, rinv, 0.0f, 0, lane);
+  for (int col0 = 0; col0 < ep.P; col0 += 128) {
+    float tot[128];
+#pragma unroll
+    for (int e = 0; e < 128; ++e)
+      tot[e] = (row_ok && col0 + e < ep.P) ? raw[row * ld + col0 + e] : 0.0f;
+    epilogue_tile(ep, tot, row, row_base, row_ok, rinv, 0.0f, col0, lane);
+  }
 }
 
 __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, uint32_t* result) {
@@ -428,15 +435,15 @@ __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, u
   }
 }
 
-template <int OPA, int KS>
+template <int OPA, int KS, int BR = 64>
 cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* bl, int64_t K,
                const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st,
                const DecodeArgs& da, int bn) {
   static bool attr_set = false;  // per process and instantiation; the attribute is per function
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_scan<OPA, KS>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_scan<OPA, KS, BR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg<OPA>::kSmem);
+                                         Cfg<OPA, KS, BR>::kSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -448,8 +455,8 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* b
   const int items = n_mt * n_nt * ks;
   // a multiple of ks, so that the splits of a tile run in the same round
   const int grid = (items < sm_count ? items : sm_count) / ks * ks;
-  if (KS == 2 && (bn > 64 || (K / TBK) % 2)) return cudaErrorInvalidValue;
-  k_tc_scan<OPA, KS><<<grid, kThreads, Cfg<OPA>::kSmem, st>>>(
+  if (KS == 2 && (bn > BR || (K / TBK) % 2)) return cudaErrorInvalidValue;
+  k_tc_scan<OPA, KS, BR><<<grid, kThreads, Cfg<OPA, KS, BR>::kSmem, st>>>(
       *a, *bh, *bl, (int)(K / TBK), n_mt, n_nt, bn, group_m, spin_ns, ep, da);
   return cudaGetLastError();
 }
@@ -462,12 +469,19 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                            int encoding, bool narrow) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   if (K % TBK || group_m < 1) return cudaErrorInvalidValue;
-  const int bn = ep.raw_out || narrow ? 64 : TBN;
+  // raw mode: the narrowest tile that holds the raw columns (the B maps' boxes match)
+  const int bn = narrow ? 64
+                 : ep.raw_out ? (ep.raw_cols <= 64 ? 64 : ep.raw_cols <= 128 ? 128 : TBN)
+                              : TBN;
   if (narrow && ep.P > 64) return cudaErrorInvalidValue;
+  if (ep.raw_out && (ep.raw_cols > TBN || ep.P != ep.raw_cols)) return cudaErrorInvalidValue;
   if (!dec) {
     if (bn == 64)  // the covariate projection, or a panel of at most 64 phenotypes
-      return go<OPA_TMA, 2>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{},
-                            bn);
+      return go<OPA_TMA, 2, 64>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st,
+                                DecodeArgs{}, bn);
+    if (bn == 128)  // the projection joint with a panel of at most 128 - (q - 1) phenotypes
+      return go<OPA_TMA, 2, 128>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st,
+                                 DecodeArgs{}, bn);
     return go<OPA_TMA, 1>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{},
                           bn);
   }
@@ -479,7 +493,7 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
 
 cudaError_t launch_raw_stats(const float* raw, int64_t ld, const EpiParams& ep, cudaStream_t st) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
-  if (ep.P > 64) return cudaErrorInvalidValue;
+  if (ep.P > JCOLS) return cudaErrorInvalidValue;
   const long long blocks = ((long long)ep.M + 127) / 128;
   k_raw_stats<<<(unsigned)blocks, 128, 0, st>>>(raw, (long long)ld, ep);
   return cudaGetLastError();

@@ -505,31 +505,34 @@ def test_split_k(P, kernel, splits, encoding):
 
 
 @pytest.mark.parametrize("encoding", ["2bit", "u8"])
-def test_joint_pass_at_the_small_panel_boundary(tgctx, encoding):
-    """A panel whose phenotypes and covariate columns fit one 64-column tile (P + q - 1 <= 64)
-    gets its products from the projection's pass; one phenotype more and the panel goes through
-    its own contraction. Both match the oracle, and the shared phenotypes agree bit for bit."""
-    N, M, n_cov = 3000, 1100, 19  # q - 1 = 19 projection columns: the joint pass holds P <= 45
-    w = synth.Workload(f"joint_{encoding}", N=N, M=M, P=46, n_cov=n_cov, encoding=encoding,
-                       missing=0.01 if encoding == "2bit" else 0.0, seed=91, block=M,
-                       causal_per_pheno=1)
+def test_joint_pass_at_the_small_panel_boundaries(tgctx, encoding):
+    """A panel whose phenotypes and covariate columns fit one tile (P + q - 1 <= 64, 128 or 256
+    columns) gets its products from the projection's pass; one phenotype more and it goes
+    through the next form (the next joint tile width, then its own contraction). Every form
+    matches the oracle, and the phenotypes they share agree bit for bit."""
+    N, M, n_cov = 3000, 1100, 19  # q - 1 = 19: joint tiles hold P <= 45, 109 and 237
+    sizes = (45, 46, 109, 110, 237, 238)
+    w = synth.Workload(f"joint_{encoding}", N=N, M=M, P=max(sizes), n_cov=n_cov,
+                       encoding=encoding, missing=0.01 if encoding == "2bit" else 0.0, seed=91,
+                       block=M, causal_per_pheno=1)
     pan = synth.make_panel(w)
     blk = synth.make_block(w, 0)
     cov = pan["cov_t"]
     res = {}
-    for P in (45, 46):
-        Yt = pan["Yt"][:P].contiguous()
-        panel = tg.tg_prepare_panel(tgctx, Yt.cuda(), N, P, cov.cuda())
+    for P in sizes:
+        panel = tg.tg_prepare_panel(tgctx, pan["Yt"][:P].contiguous().cuda(), N, P, cov.cuda())
         try:
             res[P] = run_scan(tgctx, panel, blk["G"].cuda(), N, P, encoding, "split", full=True,
                               hit_mlog10p=THR)
         finally:
             tg.tg_panel_free(panel)
         assert res[P]["status"] == tg.TG_OK
-        ref = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(Yt, cov))
+        ref = oracle.scan(blk["G"].numpy(), encoding,
+                          oracle_panel(pan["Yt"][:P].contiguous(), cov))
         compare_full(res[P], ref, label=f"P={P}/{encoding}")
         compare_hits(res[P], ref, THR)
         compare_best(res[P], ref)
-    for k in ("beta", "se", "t", "mlog10p"):
-        assert np.array_equal(res[45][k], res[46][k][:, :45], equal_nan=True), k
-    assert np.array_equal(res[45]["best_key"], res[46]["best_key"][:45])
+    for a, b in zip(sizes, sizes[1:]):
+        for k in ("beta", "se", "t", "mlog10p"):
+            assert np.array_equal(res[a][k], res[b][k][:, :a], equal_nan=True), (a, b, k)
+        assert np.array_equal(res[a]["best_key"], res[b]["best_key"][:a]), (a, b)
