@@ -249,8 +249,12 @@ tg_status tg_scan_block_static(const tg_panel* panel, const uint8_t* G, int64_t 
  * buffered, while the previous block is scanned on `stream`; hits, their count and the
  * per-phenotype best keys are copied back to host memory at the end. Synchronous.
  *   Blocking: when block_markers >= 2048 the first block has round_up(block_markers / 8, 256)
- *   rows and each next block twice as many, up to block_markers, so that only a short first
- *   copy is not hidden behind a scan. Results do not depend on the blocking.
+ *   rows and each next block f times as many (rounded up to 256), up to block_markers, so that
+ *   only a short first copy is not hidden behind a scan. f = 2 on a context's first host scan;
+ *   each call times its second block's copy and scan, and later calls use their ratio
+ *   (scan / copy) clamped to [1, 2], so that a slow host link keeps the blocks small instead
+ *   of leaving the scan waiting on a copy twice its own length. Results do not depend on the
+ *   blocking.
  *   G_host: host uint8 [M][ldg]; hits_host: host [hit_capacity]; n_hits: host, total hit
  *   count (may exceed hit_capacity, then TG_ERR_CAPACITY); best_host: host [P] or NULL.
  * Only hit collection is supported here (opts->full_output must be 0). */
@@ -259,6 +263,15 @@ tg_status tg_scan_host(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G_host
                        int64_t marker_offset, const tg_scan_opts* opts, tg_hit* hits_host,
                        int64_t hit_capacity, int64_t* n_hits, unsigned long long* best_host,
                        void* stream);
+
+/* The block growth factor f of tg_scan_host: factor = 0 (the default) picks it from the
+ * previous call's measured scan / copy ratio as described there; 1 <= factor <= 8 fixes it.
+ * TG_ERR_INVALID_ARG for other values. */
+tg_status tg_set_host_ramp(tg_ctx* ctx, double factor);
+
+/* The factor the next tg_scan_host call will use, and the last measured scan / copy time ratio
+ * of one block (0 before any measurement). Either pointer may be NULL. */
+tg_status tg_host_ramp(const tg_ctx* ctx, double* factor, double* measured_ratio);
 
 /* Whether split-form scans decode the genotypes inside the contraction kernels (enable != 0)
  * or first write the decoded operand to device memory (enable == 0, the default). The fused

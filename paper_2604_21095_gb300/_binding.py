@@ -72,6 +72,8 @@ _SIGS = {
     "tg_tuning_load": (C.c_int, [_VP, C.c_char_p]),
     "tg_set_tuning_split": (C.c_int, [_VP, _I64, _I32]),
     "tg_tuning_split": (C.c_int, [_VP, _I64, C.POINTER(_I32)]),
+    "tg_set_host_ramp": (C.c_int, [_VP, C.c_double]),
+    "tg_host_ramp": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "tg_scan_graph_create": (C.c_int, [_VP, _VP, C.c_int, C.POINTER(_VP), C.POINTER(_I64),
                                        C.POINTER(_I64), C.POINTER(_VP), _I64, _I64, _I32, _I64,
                                        C.POINTER(tg_scan_opts), C.POINTER(tg_outputs),
@@ -345,6 +347,17 @@ def tg_tuning_split(ctx, M) -> int:
     v = _I32()
     _check(load().tg_tuning_split(ctx, M, C.byref(v)))
     return v.value
+
+
+def tg_set_host_ramp(ctx, factor: float = 0.0):
+    _check(load().tg_set_host_ramp(ctx, float(factor)))
+
+
+def tg_host_ramp(ctx):
+    """(factor the next tg_scan_host call uses, last measured scan / copy ratio)."""
+    f, r = C.c_double(), C.c_double()
+    _check(load().tg_host_ramp(ctx, C.byref(f), C.byref(r)))
+    return f.value, r.value
 
 
 def tg_tuning_save(ctx, path: str):

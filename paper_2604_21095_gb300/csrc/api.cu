@@ -559,7 +559,9 @@ tg_status tg_create(tg_ctx** out, int device) {
       (e = cudaEventCreateWithFlags(&c->ev_copied[0], cudaEventDisableTiming)) ||
       (e = cudaEventCreateWithFlags(&c->ev_copied[1], cudaEventDisableTiming)) ||
       (e = cudaEventCreateWithFlags(&c->ev_free[0], cudaEventDisableTiming)) ||
-      (e = cudaEventCreateWithFlags(&c->ev_free[1], cudaEventDisableTiming))) {
+      (e = cudaEventCreateWithFlags(&c->ev_free[1], cudaEventDisableTiming)) ||
+      (e = cudaEventCreate(&c->ev_rate[0])) || (e = cudaEventCreate(&c->ev_rate[1])) ||
+      (e = cudaEventCreate(&c->ev_rate[2])) || (e = cudaEventCreate(&c->ev_rate[3]))) {
     tg_destroy(c);
     return cuda_fail(e, "tg_create");
   }
@@ -584,6 +586,8 @@ tg_status tg_destroy(tg_ctx* c) {
     if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
     if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
   }
+  for (int i = 0; i < 4; ++i)
+    if (c->ev_rate[i]) cudaEventDestroy(c->ev_rate[i]);
   if (c->side) cudaStreamDestroy(c->side);
   delete c;
   return TG_OK;
@@ -913,6 +917,27 @@ tg_status tg_scan_block(tg_ctx* c, const tg_panel* p, const uint8_t* G, int64_t 
   return scan_impl(c, p, a, (cudaStream_t)stream);
 }
 
+// Growth factor of tg_scan_host's block sizes: fixed by the caller, else the last measured
+// scan / copy ratio within [1, 2], else 2.
+double host_ramp_factor(const tg_ctx* c) {
+  if (c->ramp_fixed > 0.0) return c->ramp_fixed;
+  return c->ramp_ratio > 0.0 ? std::min(2.0, std::max(1.0, c->ramp_ratio)) : 2.0;
+}
+
+tg_status tg_set_host_ramp(tg_ctx* c, double factor) {
+  TG_ARG(c, "null context");
+  TG_ARG(factor == 0.0 || (factor >= 1.0 && factor <= 8.0), "ramp factor must be 0 or in [1, 8]");
+  c->ramp_fixed = factor;
+  return TG_OK;
+}
+
+tg_status tg_host_ramp(const tg_ctx* c, double* factor, double* measured_ratio) {
+  TG_ARG(c, "null context");
+  if (factor) *factor = host_ramp_factor(c);
+  if (measured_ratio) *measured_ratio = c->ramp_ratio;
+  return TG_OK;
+}
+
 tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int64_t ldg,
                        int32_t encoding, int64_t N, int64_t M, int64_t block_markers,
                        int64_t marker_offset, const tg_scan_opts* opts, tg_hit* hits_host,
@@ -954,28 +979,41 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
   o.hit_capacity = hit_capacity;
   o.n_hits = c->dnhits;
   o.best = best_host ? c->dbest : nullptr;
-  // Block sizes ramp up from about block_markers / 8, doubling, so that only a short first
-  // copy runs before the first scan; every later copy hides behind the previous block's scan.
+  // Block sizes ramp up from about block_markers / 8 by a factor f per block, so that only a
+  // short first copy runs before the first scan, and each copy hides behind the previous
+  // block's scan as long as it is at most f times shorter. f = 2 until a call has measured one
+  // block's scan against its copy; then f is that ratio within [1, 2]: with a copy about as
+  // slow as the scan, larger blocks would only leave the scan waiting for their copies.
+  const double f = host_ramp_factor(c);
   int64_t next = block_markers;
   if (block_markers >= 8 * 256) next = round_up(block_markers / 8, 256);
+  bool timed = false;
   // the first waits on ev_free find no recorded work and pass
   for (int64_t m0 = 0, b = 0, rows = 0; m0 < M; m0 += rows, ++b) {
     const int buf = (int)(b & 1);
     rows = std::min<int64_t>(next, M - m0);
-    next = std::min<int64_t>(block_markers, 2 * next);
+    next = std::min<int64_t>(block_markers, round_up((int64_t)((double)next * f), 256));
+    const bool time_it = b == 1;  // the second block: its copy and scan, each on its own stream
     TG_CUDA(cudaStreamWaitEvent(c->side, c->ev_free[buf], 0));
+    if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[0], c->side));
     {
       StageScope s(c, STAGE_H2D, c->side, 0);
       TG_CUDA(cudaMemcpyAsync(c->stage_buf[buf], G_host + m0 * ldg, (size_t)(rows * ldg),
                               cudaMemcpyHostToDevice, c->side));
     }
+    if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[1], c->side));
     TG_CUDA(cudaEventRecord(c->ev_copied[buf], c->side));
     TG_CUDA(cudaStreamWaitEvent(st, c->ev_copied[buf], 0));
+    if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[2], st));
     ScanArgs a{c->stage_buf[buf], ldg, encoding, N, rows, marker_offset + m0, nullptr, 0, *opts, o};
     tg_status s = check_scan_args(c, p, a);
     if (s != TG_OK) return s;
     s = scan_impl(c, p, a, st);
     if (s != TG_OK) return s;
+    if (time_it) {
+      TG_CUDA(cudaEventRecord(c->ev_rate[3], st));
+      timed = true;
+    }
     TG_CUDA(cudaEventRecord(c->ev_free[buf], st));
   }
   unsigned long long nh = 0;
@@ -990,6 +1028,13 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
     TG_CUDA(cudaMemcpyAsync(best_host, c->dbest, sizeof(unsigned long long) * (size_t)p->P,
                             cudaMemcpyDeviceToHost, st));
   TG_CUDA(cudaStreamSynchronize(st));
+  if (timed) {  // both streams are past the timed block: the scan of every block has finished
+    float copy_ms = 0.0f, scan_ms = 0.0f;
+    if (cudaEventElapsedTime(&copy_ms, c->ev_rate[0], c->ev_rate[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&scan_ms, c->ev_rate[2], c->ev_rate[3]) == cudaSuccess &&
+        copy_ms > 0.0f)
+      c->ramp_ratio = (double)scan_ms / (double)copy_ms;
+  }
   if ((int64_t)nh > hit_capacity) return fail(TG_ERR_CAPACITY, "more hits than hit_capacity");
   return TG_OK;
 }

@@ -173,6 +173,11 @@ struct tg_ctx {
   int64_t dbest_cap = 0;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  // timing of one block's copy (0, 1) and scan (2, 3) in a host-streamed scan, and their ratio
+  // (scan time / copy time, 0 = not measured yet), which sets the next call's block ramp
+  cudaEvent_t ev_rate[4] = {nullptr, nullptr, nullptr, nullptr};
+  double ramp_ratio = 0.0;
+  double ramp_fixed = 0.0;  // > 0: a fixed growth factor set by the caller
   // profiling
   bool prof = false;
   std::vector<tg::Events> pending;

@@ -23,8 +23,11 @@
 // toward zero at each chained addition, which over 23,000 samples biases |r| low by about
 // 5e-5 relative; chunks of 1024 keep that bias near 2e-6. Two chunk accumulators (512 TMEM
 // columns) alternate, so draining one overlaps the products of the next.
-// Tiles are 128 x 256, or 128 x 64 for the covariate projection and panels of at most 64
-// phenotypes. With split-K (ep.ksplit > 1, for blocks with fewer tiles than SMs) a work item is
+// Tiles are 128 x 256, or 128 x 64 for panels of at most 64 phenotypes. In raw mode (the
+// covariate projection, alone or joint with a small panel whose phenotypes follow the q - 1
+// projection columns in one B operand) the tile is the narrowest of 64, 128 and 256 columns
+// that holds them, and the products are written unnormalised; k_raw_stats turns a joint pass's
+// panel columns into statistics once the marker norms exist. With split-K (ep.ksplit > 1, for blocks with fewer tiles than SMs) a work item is
 // a tile and a chunk-aligned range of the samples; the tile's first range adds the other
 // ranges' partial sums (handed over in global memory) in range order before its epilogue.
 // Every wait is bounded: past the limit the kernel latches ST_TIMEOUT, raises a shared abort
@@ -400,24 +403,36 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Statistics of a small panel from its raw products: each warp takes 32 consecutive marker
-// rows (a lane per row, as in the contraction epilogue) and runs the same per-element code on
-// the row's P <= 256 products, 128 at a time, whose shift add-back is already in (shift 0).
-__global__ void __launch_bounds__(128) k_raw_stats(const float* __restrict__ raw, long long ld,
+// Statistics of a small panel from its raw products: thread = phenotype column, block = 64
+// consecutive marker rows, so every row is read coalesced, each column keeps its best key over
+// the block's rows and offers it once. Per element the arithmetic of the contraction epilogue
+// (D already holds the shift's add-back): r = D / |a_res| clamped, the hit test on r^2, r in
+// FULL mode, and the key (|r| bits, ~marker) whose maximum is the column's best marker.
+constexpr int kRawRows = 64;
+__global__ void __launch_bounds__(256) k_raw_stats(const float* __restrict__ raw, long long ld,
                                                    EpiParams ep) {
-  const int lane = threadIdx.x & 31;
-  const long long row_base = ((long long)blockIdx.x * 4 + (threadIdx.x >> 5)) * 32;
-  if (row_base >= ep.M) return;  // warp-uniform
-  const long long row = row_base + lane;
-  const bool row_ok = row < ep.M;
-  const float rinv = row_ok ? ep.row_inv[row] : __int_as_float(0x7fc00000);
-  for (int col0 = 0; col0 < ep.P; col0 += 128) {
-    float tot[128];
-#pragma unroll
-    for (int e = 0; e < 128; ++e)
-      tot[e] = (row_ok && col0 + e < ep.P) ? raw[row * ld + col0 + e] : 0.0f;
-    epilogue_tile(ep, tot, row, row_base, row_ok, rinv, 0.0f, col0, lane);
+  const int col = threadIdx.x;
+  if (col >= ep.P) return;  // no block-wide synchronisation below
+  const long long r0 = (long long)blockIdx.x * kRawRows;
+  const long long r1 = r0 + kRawRows < (long long)ep.M ? r0 + kRawRows : (long long)ep.M;
+  const float rmul = ep.col_rmul[col];
+  unsigned long long best = 0;
+  bool any = false;
+#pragma unroll 4
+  for (long long row = r0; row < r1; ++row) {
+    const float D = raw[row * ld + col];
+    const float r = corr_nan(D, ep.row_inv[row], rmul);
+    if (ep.do_hits && r * r >= ep.r2_thr) emit_hit_raw(ep, D, row, col);
+    if (ep.do_full) ep.rstore[row * ep.ldo + col] = r;
+    if (r == r) {
+      const unsigned long long key =
+          ((unsigned long long)__float_as_uint(fabsf(r)) << 32) |
+          (unsigned long long)(0xFFFFFFFFu - (uint32_t)(ep.marker_offset + row));
+      best = key > best ? key : best;
+      any = true;
+    }
   }
+  if (ep.do_best && any) best_offer(ep.best + col, best);
 }
 
 __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, uint32_t* result) {
@@ -494,8 +509,8 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
 cudaError_t launch_raw_stats(const float* raw, int64_t ld, const EpiParams& ep, cudaStream_t st) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   if (ep.P > JCOLS) return cudaErrorInvalidValue;
-  const long long blocks = ((long long)ep.M + 127) / 128;
-  k_raw_stats<<<(unsigned)blocks, 128, 0, st>>>(raw, (long long)ld, ep);
+  const long long blocks = ((long long)ep.M + kRawRows - 1) / kRawRows;
+  k_raw_stats<<<(unsigned)blocks, 256, 0, st>>>(raw, (long long)ld, ep);
   return cudaGetLastError();
 }
 

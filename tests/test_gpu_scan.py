@@ -259,6 +259,38 @@ def test_host_streamed_scan_matches_oracle(tgctx, panels, encoding, block):
     want, got = compare_hits(res, ref, THR, marker_offset=11)
     assert want > 0 and got > 0
     compare_best(res, ref, marker_offset=11)
+    # on a fresh context (default kernel choice), later calls block by the measured copy and
+    # scan times: the same hits and best markers as the first call
+    ctx2 = tg.tg_create(0)
+    try:
+        assert tg.tg_host_ramp(ctx2) == (2.0, 0.0)  # nothing measured yet: doubling
+        with pytest.raises(tg.TgError):
+            tg.tg_set_host_ramp(ctx2, 0.5)
+        runs = []
+        for _ in range(3):
+            nh2 = tg.tg_scan_host(ctx2, panel, G_host, w.N, w.M, enc_id(encoding), block, opts,
+                                  hits_h, best_h, marker_offset=11)
+            assert nh2 == nh
+            hh = np.frombuffer(hits_h.numpy().tobytes(), dtype=HIT_DTYPE)[:nh2]
+            runs.append((np.sort(hh, order=["marker", "pheno"]), best_h.numpy().copy()))
+        assert np.array_equal(runs[0][0][["marker", "pheno"]],
+                              np.sort(res["hits"], order=["marker", "pheno"])[["marker", "pheno"]])
+        for hh, bb in runs[1:]:
+            assert np.array_equal(hh, runs[0][0])
+            assert np.array_equal(bb, runs[0][1])
+        f, ratio = tg.tg_host_ramp(ctx2)
+        if block < w.M:  # a second block was timed
+            assert ratio > 0.0 and f == min(2.0, max(1.0, ratio))
+        else:
+            assert (f, ratio) == (2.0, 0.0)
+        tg.tg_set_host_ramp(ctx2, 1.0)  # fixed: equal blocks of block / 8 markers
+        assert tg.tg_host_ramp(ctx2)[0] == 1.0
+        nh3 = tg.tg_scan_host(ctx2, panel, G_host, w.N, w.M, enc_id(encoding), block, opts,
+                              hits_h, best_h, marker_offset=11)
+        hh = np.frombuffer(hits_h.numpy().tobytes(), dtype=HIT_DTYPE)[:nh3]
+        assert np.array_equal(np.sort(hh, order=["marker", "pheno"]), runs[0][0])
+    finally:
+        tg.tg_destroy(ctx2)
 
 
 @pytest.mark.parametrize("encoding,masked", [("2bit", False), ("u8", True)])
