@@ -2,7 +2,8 @@
 2-bit blocks and unmasked dosage blocks) against the default path that first writes the
 decoded operand to device memory: every output must be bit-identical, for both kernels (CTA
 pairs and one CTA per tile), both encodings, sample counts that end inside a K block and blocks
-whose last m-tiles are partly or wholly past M. The decoded-operand path itself is checked
+whose last m-tiles are partly or wholly past M, and small panels whose products come from the
+projection's pass (64-, 128- and 256-column joint tiles). The decoded-operand path itself is checked
 against the oracle by the scan tests."""
 import numpy as np
 import pytest
@@ -24,7 +25,7 @@ def _outputs_equal(a, b):
 @pytest.mark.parametrize("encoding", ["2bit", "u8"])
 @pytest.mark.parametrize("kernel", ["pair", "single"])
 @pytest.mark.parametrize("N,M,P", [(2000, 1000, 300), (1999, 777, 513), (257, 300, 40),
-                                   (23000, 520, 600)])
+                                   (23000, 520, 600), (2000, 1000, 100), (1999, 777, 230)])
 def test_fused_decode_is_bit_identical(encoding, kernel, N, M, P):
     w = synth.Workload(f"fused_{encoding}_{N}_{M}_{P}", N=N, M=M, P=P, n_cov=4,
                        encoding=encoding, missing=0.03 if encoding == "2bit" else 0.0, seed=29,
