@@ -376,14 +376,16 @@ def _ours(args, dist, rank, ws):
     # end to end through the host-buffer entry point: pinned host blocks in, hits and best out
     e2e = None
     if args.e2e_steps > 0:
-        host = torch.empty((RESIDENT * M, blocks[0].shape[1]), dtype=torch.uint8, pin_memory=True)
-        for i, b in enumerate(blocks):
-            host[i * M:(i + 1) * M].copy_(b)
+        # one call streams all e2e steps' blocks (the resident blocks cycled), as a scan of a
+        # genome chunk would: 1.5 GB of pinned host memory per step
+        per_call = args.e2e_steps
+        calls = 1
+        host = torch.empty((per_call * M, blocks[0].shape[1]), dtype=torch.uint8, pin_memory=True)
+        for i in range(per_call):
+            host[i * M:(i + 1) * M].copy_(blocks[i % len(blocks)])
         hits_h = torch.zeros(cap * 24, dtype=torch.uint8, pin_memory=True)
         best_h = torch.zeros(w.P, dtype=torch.int64, pin_memory=True)
         opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, THR)
-        per_call = RESIDENT
-        calls = max(1, args.e2e_steps // per_call)
         tg.tg_scan_host(ctx, panel, host, w.N, per_call * M, enc, M, opts, hits_h,
                         best_h, stream=stream)
         torch.cuda.synchronize()
@@ -399,7 +401,9 @@ def _ours(args, dist, rank, ws):
         tg.tg_set_profiling(ctx, False)
         ste = tg.tg_stage_times(ctx, reset=True)
         steps_e2e = calls * per_call
+        growth, ratio = tg.tg_host_ramp(ctx)
         e2e = {"value": tests_step * steps_e2e * ws / dt, "unit": UNIT,
+               "block_growth": {"factor": growth, "scan_over_copy": ratio},
                "h2d_bytes_per_step": int(M * blocks[0].shape[1]),
                "d2h_bytes_per_step": int((8 + 24 * min(nh_e2e, cap) + 8 * w.P) / per_call),
                "ms_per_step": 1000 * dt / steps_e2e, "api": "tg_scan_host (C ABI, host buffers)",
