@@ -44,19 +44,23 @@ namespace {
 
 using namespace tcx;
 
-template <int OPA, int KS = 1, int BR = 64>
+template <int OPA, int KS = 1, int BR = 64, int MS = 1>
 struct Cfg {
-  // A, B_hi, B_lo and (when decoding here) the CTA's packed rows: 40 KB (+ 2 or 4 KB), 5 stages;
-  // two K blocks of up to 64 B rows use the same slot; two K blocks of 128 B rows take
-  // 2 x (8 + 2 x 8) = 48 KB, 4 stages
-  static constexpr bool kWide = KS == 2 && BR > 64;
-  static constexpr int kStageBytes =
-      kWide ? KS * (A_BYTES + 2 * BR * TBK * 2) : A_BYTES + 2 * B_BYTES + DecCfg<OPA>::kPackBytes;
-  static constexpr int kStages = kWide ? 4 : 5;
+  // A, B_hi, B_lo and (when decoding here) the CTA's packed rows: 40 KB (+ 2 or 4 KB), 5 stages.
+  // Two K blocks of MS A sub-tiles and BR B rows: the same slot for MS = 1 and BR = 64, else
+  // 2 x (MS x 8 + 2 x BR x 64 B): 48 KB in 4 stages or 64 KB in 3
+  static constexpr bool kWide = KS == 2 && (BR > 64 || MS > 1);
+  static constexpr int kStageBytes = kWide ? KS * (MS * A_BYTES + 2 * BR * TBK * 2)
+                                           : A_BYTES + 2 * B_BYTES + DecCfg<OPA>::kPackBytes;
+  static constexpr int kStages = !kWide ? 5 : kStageBytes <= 48 * 1024 ? 4 : 3;
   static constexpr int kBarBytes = 256;
   static constexpr int kSmem = kStages * kStageBytes + kBarBytes + 1024;  // + alignment slack
 };
 
+// MS = 128-marker sub-tiles per tile (KS = 2 only): with MS = 2 a CTA takes 256 markers, two
+// accumulators of 128 TMEM lanes at columns +0 and +128 sharing every B stage, which halves the
+// B operand's traffic from L2 into shared memory; each element's products and additions are
+// the same as with MS = 1, so the results are too.
 // KS = K blocks per stage, BR = B rows per K block when KS = 2. With 64- or 128-column tiles (the
 // covariate projection, alone or joint with a small panel, and panels of at most 64 phenotypes)
 // the kernel streams the 3 GB operand and is bound by HBM, where two consecutive 64-byte row
@@ -79,14 +83,15 @@ __device__ __forceinline__ int chunk_end_in(int kb0, int lo, int hi) {
   return e < hi ? e : hi;
 }
 
-template <int OPA, int KS, int BR>
+template <int OPA, int KS, int BR, int MS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_scan(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmBhi,
               const __grid_constant__ CUtensorMap tmBlo, int num_kb, int n_mt, int n_nt, int bn,
               int group_m, long long spin_ns, EpiParams ep,
               const __grid_constant__ DecodeArgs da) {
   // bn = B rows per tile: 256 for the phenotype panel, 64 or 128 (<= BR) with KS = 2
-  using C = Cfg<OPA, KS, BR>;
+  using C = Cfg<OPA, KS, BR, MS>;
+  static_assert(MS == 1 || (MS == 2 && KS == 2 && BR <= 128), "two sub-tiles: two K blocks, <= 128 B rows");
   constexpr bool kFused = OPA != OPA_TMA;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -108,15 +113,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto sBhi = [&](int s) { return base + s * C::kStageBytes + A_BYTES; };
   auto sBlo = [&](int s) { return base + s * C::kStageBytes + A_BYTES + B_BYTES; };
   auto sPk = [&](int s) { return base + s * C::kStageBytes + A_BYTES + 2 * B_BYTES; };
-  constexpr int kBk = BR * TBK * 2;  // one K block of B rows (KS = 2)
-  static_assert(KS == 1 || (KS == 2 && !kFused && 2 * A_BYTES + 4 * kBk <= C::kStageBytes),
+  constexpr int kBk = BR * TBK * 2;   // one K block of B rows (KS = 2)
+  constexpr int kAk = MS * A_BYTES;   // one K block of A rows (KS = 2)
+  static_assert(KS == 1 || (KS == 2 && !kFused && 2 * kAk + 4 * kBk <= C::kStageBytes),
                 "two K blocks per stage: decoded operand and at most BR B rows");
-  auto sAk = [&](int s, int h) { return KS == 1 ? sA(s) : sA(s) + (uint32_t)(h * A_BYTES); };
+  auto sAk = [&](int s, int h, int sub) {
+    return KS == 1 ? sA(s) : sA(s) + (uint32_t)(h * kAk + sub * A_BYTES);
+  };
   auto sBhik = [&](int s, int h) {
-    return KS == 1 ? sBhi(s) : sA(s) + (uint32_t)(2 * A_BYTES + h * kBk);
+    return KS == 1 ? sBhi(s) : sA(s) + (uint32_t)(2 * kAk + h * kBk);
   };
   auto sBlok = [&](int s, int h) {
-    return KS == 1 ? sBlo(s) : sA(s) + (uint32_t)(2 * A_BYTES + 2 * kBk + h * kBk);
+    return KS == 1 ? sBlo(s) : sA(s) + (uint32_t)(2 * kAk + 2 * kBk + h * kBk);
   };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -167,7 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tile_coord(tile, n_mt, n_nt, group_m, mt, nt);
       split_range(num_kb, ks, item - tile * ks, kb_lo, kb_hi);
       const uint32_t bytes =
-          (uint32_t)KS * ((kFused ? 0u : (uint32_t)A_BYTES) + 2u * (uint32_t)bn * (TBK * 2));
+          (uint32_t)KS * ((kFused ? 0u : (uint32_t)kAk) + 2u * (uint32_t)bn * (TBK * 2));
       for (int kb = kb_lo; kb < kb_hi; kb += KS) {
         if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, spin_ns, ep.status)) {
           ok = false;
@@ -182,7 +190,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int h = 0; h < KS; ++h) {
           if (!kFused)
-            tma_load_2d(&tmAhi, sAk(stage, h), full_bar(stage), (kb + h) * TBK, mt * TBM);
+#pragma unroll
+            for (int sub = 0; sub < MS; ++sub)
+              tma_load_2d(&tmAhi, sAk(stage, h, sub), full_bar(stage), (kb + h) * TBK,
+                          (mt * MS + sub) * TBM);
           tma_load_2d(&tmBhi, sBhik(stage, h), full_bar(stage), (kb + h) * TBK, nt * bn);
           tma_load_2d(&tmBlo, sBlok(stage, h), full_bar(stage), (kb + h) * TBK, nt * bn);
         }
@@ -231,11 +242,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int h = 0; h < KS; ++h)
 #pragma unroll
             for (int k = 0; k < TBK / 16; ++k) {
-              const uint64_t a = sdesc_sw64(sAk(stage, h) + 32u * k);
               const uint64_t bh = sdesc_sw64(sBhik(stage, h) + 32u * k);
               const uint64_t bl = sdesc_sw64(sBlok(stage, h) + 32u * k);
-              tc_mma(d, a, bh, idesc, (kb > kb0 || h > 0 || k > 0) ? 1u : 0u);
-              tc_mma(d, a, bl, idesc, 1u);
+#pragma unroll
+              for (int sub = 0; sub < MS; ++sub) {  // sub-tile accumulators at +0 and +128
+                const uint64_t a = sdesc_sw64(sAk(stage, h, sub) + 32u * k);
+                const uint32_t ds = d + (uint32_t)(sub * 128);
+                tc_mma(ds, a, bh, idesc, (kb > kb0 || h > 0 || k > 0) ? 1u : 0u);
+                tc_mma(ds, a, bl, idesc, 1u);
+              }
             }
           tc_commit(empty_bar(stage));
           if (++stage == S) {
@@ -370,7 +385,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
-      const long long row_base = (long long)mt * TBM + quarter * 32;
+      // MS = 1: warps of half h hold columns h*128.. of the tile's 128 rows; MS = 2: warps of
+      // half h hold the (at most 128) columns of sub-tile h's 128 rows
+      const long long row_base =
+          (long long)(MS == 2 ? (mt * MS + half) : mt) * TBM + quarter * 32;
+      const int col_half = MS == 2 ? 0 : half * 128;
       const long long row = row_base + lane;
       const bool row_ok = row < ep.M;
       const float rinv = (row_ok && ep.row_inv) ? ep.row_inv[row] : __int_as_float(0x7fc00000);
@@ -381,13 +400,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (row_ok) {
 #pragma unroll
           for (int e = 0; e < 128; ++e) {  // fully unrolled: tot stays in registers
-            const int col = half * 128 + e;
+            const int col = col_half + e;
             if (col < ep.raw_cols)
               ep.raw_out[row * ep.raw_ld + col] = fmaf(shift, ep.col_cs[col], tot[e]);
           }
         }
       } else {
-        epilogue_tile(ep, tot, row, row_base, row_ok, rinv, shift, nt * TBN + half * 128, lane);
+        epilogue_tile(ep, tot, row, row_base, row_ok, rinv, shift,
+                      (MS == 2 ? nt * bn : nt * TBN) + col_half, lane);
       }
       __syncwarp();
     }
@@ -450,19 +470,19 @@ __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, u
   }
 }
 
-template <int OPA, int KS, int BR = 64>
+template <int OPA, int KS, int BR = 64, int MS = 1>
 cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* bl, int64_t K,
                const EpiParams& ep, int sm_count, int group_m, long long spin_ns, cudaStream_t st,
                const DecodeArgs& da, int bn) {
   static bool attr_set = false;  // per process and instantiation; the attribute is per function
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_scan<OPA, KS, BR>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_scan<OPA, KS, BR, MS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg<OPA, KS, BR>::kSmem);
+                                         Cfg<OPA, KS, BR, MS>::kSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int n_mt = (ep.M + TBM - 1) / TBM;
+  const int n_mt = (ep.M + MS * TBM - 1) / (MS * TBM);
   const int n_nt = (ep.P + bn - 1) / bn;
   const int ks = ep.ksplit > 1 ? ep.ksplit : 1;
   if (ks > 1 && (!ep.sk_ws || !ep.sk_cnt || sm_count < ks))
@@ -471,7 +491,7 @@ cudaError_t go(const CUtensorMap* a, const CUtensorMap* bh, const CUtensorMap* b
   // a multiple of ks, so that the splits of a tile run in the same round
   const int grid = (items < sm_count ? items : sm_count) / ks * ks;
   if (KS == 2 && (bn > BR || (K / TBK) % 2)) return cudaErrorInvalidValue;
-  k_tc_scan<OPA, KS, BR><<<grid, kThreads, Cfg<OPA, KS, BR>::kSmem, st>>>(
+  k_tc_scan<OPA, KS, BR, MS><<<grid, kThreads, Cfg<OPA, KS, BR, MS>::kSmem, st>>>(
       *a, *bh, *bl, (int)(K / TBK), n_mt, n_nt, bn, group_m, spin_ns, ep, da);
   return cudaGetLastError();
 }
@@ -491,12 +511,19 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
   if (narrow && ep.P > 64) return cudaErrorInvalidValue;
   if (ep.raw_out && (ep.raw_cols > TBN || ep.P != ep.raw_cols)) return cudaErrorInvalidValue;
   if (!dec) {
+    // 256-marker tiles (two sub-tiles sharing B) once they fill every SM at least once, and
+    // not with split-K, whose workspace the host sized for 128-marker tiles
+    const bool two = ep.ksplit <= 1 && (ep.M + 2 * TBM - 1) / (2 * TBM) >= sm_count;
     if (bn == 64)  // the covariate projection, or a panel of at most 64 phenotypes
-      return go<OPA_TMA, 2, 64>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st,
-                                DecodeArgs{}, bn);
+      return two ? go<OPA_TMA, 2, 64, 2>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns,
+                                         st, DecodeArgs{}, bn)
+                 : go<OPA_TMA, 2, 64, 1>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns,
+                                         st, DecodeArgs{}, bn);
     if (bn == 128)  // the projection joint with a panel of at most 128 - (q - 1) phenotypes
-      return go<OPA_TMA, 2, 128>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st,
-                                 DecodeArgs{}, bn);
+      return two ? go<OPA_TMA, 2, 128, 2>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns,
+                                          st, DecodeArgs{}, bn)
+                 : go<OPA_TMA, 2, 128, 1>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns,
+                                          st, DecodeArgs{}, bn);
     return go<OPA_TMA, 1>(tmA, tmBhi, tmBlo, K, ep, sm_count, group_m, spin_ns, st, DecodeArgs{},
                           bn);
   }

@@ -568,3 +568,39 @@ def test_joint_pass_at_the_small_panel_boundaries(tgctx, encoding):
         for k in ("beta", "se", "t", "mlog10p"):
             assert np.array_equal(res[a][k], res[b][k][:, :a], equal_nan=True), (a, b, k)
         assert np.array_equal(res[a]["best_key"], res[b]["best_key"][:a]), (a, b)
+
+
+@pytest.mark.parametrize("P,mode", [(16, tg.TG_MODE_PROJECTED), (100, tg.TG_MODE_PROJECTED),
+                                    (40, tg.TG_MODE_PAPER)])
+def test_256_marker_tiles_equal_128_marker_tiles(tgctx, P, mode):
+    """Blocks whose 256-marker tiles fill every SM (M >= 152 x 256) run the 64- and 128-column
+    passes (the projection, a joint pass, a panel of at most 64 phenotypes) with two 128-marker
+    sub-tiles per CTA sharing each B stage. The same markers scanned in two halves (128-marker
+    tiles) give bit-identical statistics, and both match the oracle."""
+    N, M, n_cov = 1000, 40000, 19
+    w = synth.Workload(f"sub2_{P}", N=N, M=M, P=P, n_cov=n_cov, encoding="2bit", missing=0.01,
+                       seed=93, block=M, causal_per_pheno=1)
+    pan = synth.make_panel(w)
+    blk = synth.make_block(w, 0)
+    panel = tg.tg_prepare_panel(tgctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+    try:
+        G = blk["G"].cuda()
+        whole = run_scan(tgctx, panel, G, N, P, "2bit", "split", full=True, hit_mlog10p=THR,
+                         mode=mode)
+        h = M // 2
+        parts = [run_scan(tgctx, panel, G[o:o + h].contiguous(), N, P, "2bit", "split",
+                          full=True, hit_mlog10p=THR, marker_offset=o, mode=mode)
+                 for o in (0, h)]
+    finally:
+        tg.tg_panel_free(panel)
+    assert whole["status"] == tg.TG_OK
+    for k in ("beta", "se", "t", "mlog10p"):
+        assert np.array_equal(whole[k], np.concatenate([parts[0][k], parts[1][k]]),
+                              equal_nan=True), k
+    assert np.array_equal(whole["best_key"], np.maximum(parts[0]["best_key"],
+                                                        parts[1]["best_key"]))
+    ref = oracle.scan(blk["G"].numpy(), "2bit", oracle_panel(pan["Yt"], pan["cov_t"]),
+                      mode="projected" if mode == tg.TG_MODE_PROJECTED else "paper")
+    compare_full(whole, ref, label=f"256-marker tiles P={P}")
+    compare_hits(whole, ref, THR)
+    compare_best(whole, ref)
