@@ -126,7 +126,10 @@ tg_status tg_destroy(tg_ctx* ctx);
  * Builds X = [1, C], an orthonormal basis Q of span(X) by FP64 Householder QR (a column
  * whose remaining norm is <= 1e-9 of its own norm is dropped; q = rank), the residualised
  * panel Y_res = (I - Q Q^T)(Y - Ybar) in FP64, the column norms s_p = |y_res,p| and the
- * unit-norm panel in the forms the scan consumes.
+ * unit-norm panel in the forms the scan consumes. A panel with P + q - 1 <= 256 also keeps a
+ * joint copy of its split operand behind the q - 1 projection columns (64, 128 or 256 rows of
+ * round_up(N, 64) bf16 pairs), so that split-form scans in the projected mode take the
+ * projection and the panel's products from one pass over each block.
  *   Y: device, float [P][ldy] storage = column-major N x P (phenotype p at Y + p*ldy), ldy >= N.
  *   C: device, double column-major N x n_cov (covariate k at C + k*ldc), ldc >= N; NULL if n_cov = 0.
  *      The intercept is added by the library and must not be passed.
