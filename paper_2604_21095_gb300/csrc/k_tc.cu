@@ -23,13 +23,16 @@
 // toward zero at each chained addition, which over 23,000 samples biases |r| low by about
 // 5e-5 relative; chunks of 1024 keep that bias near 2e-6. Two chunk accumulators (512 TMEM
 // columns) alternate, so draining one overlaps the products of the next.
-// Tiles are 128 x 256, or 128 x 64 for panels of at most 64 phenotypes. In raw mode (the
-// covariate projection, alone or joint with a small panel whose phenotypes follow the q - 1
-// projection columns in one B operand) the tile is the narrowest of 64, 128 and 256 columns
-// that holds them, and the products are written unnormalised; k_raw_stats turns a joint pass's
-// panel columns into statistics once the marker norms exist. With split-K (ep.ksplit > 1, for blocks with fewer tiles than SMs) a work item is
-// a tile and a chunk-aligned range of the samples; the tile's first range adds the other
-// ranges' partial sums (handed over in global memory) in range order before its epilogue.
+// Tiles are 128 x 256, or 128 x 64 for panels of at most 64 phenotypes. 64- and 128-column
+// tiles of blocks with at least one 256-marker tile per SM take 256 markers, as two 128-row
+// sub-tiles with their own accumulators sharing each B stage (half the B traffic from L2).
+// In raw mode (the covariate projection, alone or joint with a small panel whose phenotypes
+// follow the q - 1 projection columns in one B operand) the tile is the narrowest of 64, 128
+// and 256 columns that holds them, and the products are written unnormalised; k_raw_stats
+// turns a joint pass's panel columns into statistics once the marker norms exist.
+// With split-K (ep.ksplit > 1, for blocks with fewer tiles than SMs) a work item is a tile and
+// a chunk-aligned range of the samples; the tile's first range adds the other ranges' partial
+// sums (handed over in global memory) in range order before its epilogue.
 // Every wait is bounded: past the limit the kernel latches ST_TIMEOUT, raises a shared abort
 // flag, lets in-flight copies and products finish (again bounded), frees its TMEM and returns.
 #include <cuda.h>
