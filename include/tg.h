@@ -276,6 +276,12 @@ tg_status tg_set_host_ramp(tg_ctx* ctx, double factor);
  * of one block (0 before any measurement). Either pointer may be NULL. */
 tg_status tg_host_ramp(const tg_ctx* ctx, double* factor, double* measured_ratio);
 
+/* The block sizes tg_scan_host uses for M markers, blocks of at most block_markers and growth
+ * factor `factor` in [1, 8] (host only, no device work): *n_blocks = their number, and the
+ * first min(capacity, *n_blocks) sizes are written to `sizes` (host int64 [capacity]). */
+tg_status tg_host_block_sizes(int64_t M, int64_t block_markers, double factor, int64_t* sizes,
+                              int64_t capacity, int64_t* n_blocks);
+
 /* Whether split-form scans decode the genotypes inside the contraction kernels (enable != 0)
  * or first write the decoded operand to device memory (enable == 0, the default). The fused
  * form applies to 2-bit blocks and to dosage blocks without a missing mask (others always use

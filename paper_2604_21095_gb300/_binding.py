@@ -74,6 +74,8 @@ _SIGS = {
     "tg_tuning_split": (C.c_int, [_VP, _I64, C.POINTER(_I32)]),
     "tg_set_host_ramp": (C.c_int, [_VP, C.c_double]),
     "tg_host_ramp": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "tg_host_block_sizes": (C.c_int, [_I64, _I64, C.c_double, C.POINTER(_I64), _I64,
+                                      C.POINTER(_I64)]),
     "tg_scan_graph_create": (C.c_int, [_VP, _VP, C.c_int, C.POINTER(_VP), C.POINTER(_I64),
                                        C.POINTER(_I64), C.POINTER(_VP), _I64, _I64, _I32, _I64,
                                        C.POINTER(tg_scan_opts), C.POINTER(tg_outputs),
@@ -358,6 +360,15 @@ def tg_host_ramp(ctx):
     f, r = C.c_double(), C.c_double()
     _check(load().tg_host_ramp(ctx, C.byref(f), C.byref(r)))
     return f.value, r.value
+
+
+def tg_host_block_sizes(M, block_markers, factor=2.0):
+    """The block sizes tg_scan_host streams M markers in (host only)."""
+    n = _I64()
+    _check(load().tg_host_block_sizes(M, block_markers, float(factor), None, 0, C.byref(n)))
+    buf = (_I64 * max(1, n.value))()
+    _check(load().tg_host_block_sizes(M, block_markers, float(factor), buf, n.value, C.byref(n)))
+    return list(buf[:n.value])
 
 
 def tg_tuning_save(ctx, path: str):

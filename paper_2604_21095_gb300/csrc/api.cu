@@ -917,6 +917,31 @@ tg_status tg_scan_block(tg_ctx* c, const tg_panel* p, const uint8_t* G, int64_t 
   return scan_impl(c, p, a, (cudaStream_t)stream);
 }
 
+// Block sizes of tg_scan_host for M markers: round_up(B / 8, 256) first when B >= 2048 (else
+// B), each next one f times the previous rounded up to 256, at most B; the last takes the rest.
+std::vector<int64_t> host_block_sizes(int64_t M, int64_t B, double f) {
+  std::vector<int64_t> v;
+  int64_t next = B >= 8 * 256 ? round_up(B / 8, 256) : B;
+  for (int64_t m0 = 0; m0 < M;) {
+    const int64_t rows = std::min<int64_t>(next, M - m0);
+    v.push_back(rows);
+    m0 += rows;
+    next = std::min<int64_t>(B, round_up((int64_t)((double)next * f), 256));
+  }
+  return v;
+}
+
+tg_status tg_host_block_sizes(int64_t M, int64_t block_markers, double factor, int64_t* sizes,
+                              int64_t capacity, int64_t* n_blocks) {
+  TG_ARG(M >= 0 && block_markers > 0 && n_blocks, "bad arguments");
+  TG_ARG(factor >= 1.0 && factor <= 8.0, "growth factor must be in [1, 8]");
+  TG_ARG(capacity >= 0 && (sizes || capacity == 0), "bad size buffer");
+  const std::vector<int64_t> v = host_block_sizes(M, block_markers, factor);
+  *n_blocks = (int64_t)v.size();
+  for (size_t i = 0; i < v.size() && (int64_t)i < capacity; ++i) sizes[i] = v[i];
+  return TG_OK;
+}
+
 // Growth factor of tg_scan_host's block sizes: fixed by the caller, else the last measured
 // scan / copy ratio within [1, 2], else 2.
 double host_ramp_factor(const tg_ctx* c) {
@@ -984,15 +1009,12 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
   // block's scan as long as it is at most f times shorter. f = 2 until a call has measured one
   // block's scan against its copy; then f is that ratio within [1, 2]: with a copy about as
   // slow as the scan, larger blocks would only leave the scan waiting for their copies.
-  const double f = host_ramp_factor(c);
-  int64_t next = block_markers;
-  if (block_markers >= 8 * 256) next = round_up(block_markers / 8, 256);
+  const std::vector<int64_t> sizes = host_block_sizes(M, block_markers, host_ramp_factor(c));
   bool timed = false;
   // the first waits on ev_free find no recorded work and pass
-  for (int64_t m0 = 0, b = 0, rows = 0; m0 < M; m0 += rows, ++b) {
+  for (int64_t m0 = 0, b = 0, rows = 0; b < (int64_t)sizes.size(); m0 += rows, ++b) {
     const int buf = (int)(b & 1);
-    rows = std::min<int64_t>(next, M - m0);
-    next = std::min<int64_t>(block_markers, round_up((int64_t)((double)next * f), 256));
+    rows = sizes[(size_t)b];
     const bool time_it = b == 1;  // the second block: its copy and scan, each on its own stream
     TG_CUDA(cudaStreamWaitEvent(c->side, c->ev_free[buf], 0));
     if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[0], c->side));
