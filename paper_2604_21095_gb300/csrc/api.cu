@@ -936,6 +936,9 @@ tg_status tg_host_block_sizes(int64_t M, int64_t block_markers, double factor, i
   TG_ARG(M >= 0 && block_markers > 0 && n_blocks, "bad arguments");
   TG_ARG(factor >= 1.0 && factor <= 8.0, "growth factor must be in [1, 8]");
   TG_ARG(capacity >= 0 && (sizes || capacity == 0), "bad size buffer");
+  // blocks never shrink below the first one, which bounds their number
+  const int64_t first = block_markers >= 8 * 256 ? round_up(block_markers / 8, 256) : block_markers;
+  if (M / first >= (1ll << 28)) return fail(TG_ERR_UNSUPPORTED, "more than 2^28 blocks");
   const std::vector<int64_t> v = host_block_sizes(M, block_markers, factor);
   *n_blocks = (int64_t)v.size();
   for (size_t i = 0; i < v.size() && (int64_t)i < capacity; ++i) sizes[i] = v[i];

@@ -40,3 +40,5 @@ def test_degenerate_sizes_and_bad_arguments():
         with pytest.raises(tg.TgError):
             tg.tg_host_block_sizes(*args)
     assert sum(tg.tg_host_block_sizes(10_007, 4096, 1.5)) == 10_007
+    with pytest.raises(tg.TgError):  # a list it will not build
+        tg.tg_host_block_sizes(1 << 40, 1, 1.0)
