@@ -278,7 +278,8 @@ tg_status tg_host_ramp(const tg_ctx* ctx, double* factor, double* measured_ratio
 
 /* The block sizes tg_scan_host uses for M markers, blocks of at most block_markers and growth
  * factor `factor` in [1, 8] (host only, no device work): *n_blocks = their number, and the
- * first min(capacity, *n_blocks) sizes are written to `sizes` (host int64 [capacity]). */
+ * first min(capacity, *n_blocks) sizes are written to `sizes` (host int64 [capacity]).
+ * TG_ERR_UNSUPPORTED when M would take 2^28 blocks or more. */
 tg_status tg_host_block_sizes(int64_t M, int64_t block_markers, double factor, int64_t* sizes,
                               int64_t capacity, int64_t* n_blocks);
 
