@@ -9,8 +9,10 @@ panel (1.9 GB of bf16 operands) are far larger than the 129 MB L2, so no flush i
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line. --impl reference times the FP64 CPU oracle on the host cores on a
-bounded sample of the same workload.
+Prints one JSON line. Its "e2e" entry streams --e2e-steps blocks from pinned host memory
+through one tg_scan_host call (hits and best markers read back), after one untimed call that
+measures the copy / scan ratio the block sizes grow by. --impl reference times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
