@@ -21,10 +21,21 @@ from __future__ import annotations
 
 import numpy as np
 
-# A marker is untestable when it has no observed call, is constant, or is (up to
-# this relative residual) inside the covariate span: |g_res|^2 <= 1e-5 |g_c|^2, i.e. the
-# covariates explain at least 99.999% of its variance (variance inflation >= 1e5).
-MARKER_TOL = 1e-5
+# Reading (the paper is silent on collinear markers): a marker is untestable when it has no
+# observed call, is constant, or its variance inflation factor on the covariates,
+#   VIF = |g_c|^2 / |g_res|^2 = 1 / (1 - R^2 of g on [1, C]),
+# exceeds MAX_VIF = 50, i.e. the covariates explain more than 98% of its variance. The sampling
+# variance of the marker's effect is inflated by exactly this factor; 50 is the limit that
+# PLINK's linear model applies by default to each of its predictors (PLINK is the tool the
+# paper checks its concordance against, Section 3.1). A marker exactly at the limit is tested.
+MAX_VIF = 50.0
+
+
+def testable(gc2, gres2):
+    """True where a marker with |g_c|^2 = gc2 and |g_res|^2 = gres2 is tested (NaN: not)."""
+    gc2 = np.asarray(gc2, dtype=np.float64)
+    gres2 = np.asarray(gres2, dtype=np.float64)
+    return (gc2 > 0.0) & (MAX_VIF * gres2 >= gc2)
 
 
 def ols_direct(X: np.ndarray, g: np.ndarray, Y: np.ndarray):
@@ -48,8 +59,8 @@ def ols_direct(X: np.ndarray, g: np.ndarray, Y: np.ndarray):
         W = np.column_stack([X, g[j]])
         Qw, Rw = np.linalg.qr(W)
         gc = g[j] - g[j].mean()
-        rgg = abs(Rw[-1, -1])
-        if not np.isfinite(rgg) or np.linalg.norm(gc) == 0.0 or rgg <= MARKER_TOL ** 0.5 * np.linalg.norm(gc):
+        rgg = abs(Rw[-1, -1])                 # |g_res|: what is left of g after [1, C]
+        if not np.isfinite(rgg) or not testable(gc @ gc, rgg * rgg):
             continue
         coef = np.linalg.solve(Rw, Qw.T @ Y)
         resid = Y - W @ coef
@@ -78,7 +89,7 @@ def ols_projected(Q: np.ndarray, g: np.ndarray, Yres: np.ndarray):
     gres = gc - (gc @ Q) @ Q.T
     gres2 = (gres * gres).sum(axis=1)
     gc2 = (gc * gc).sum(axis=1)
-    bad = ~(gres2 > MARKER_TOL * gc2)
+    bad = ~testable(gc2, gres2)
     ynorm = np.linalg.norm(Yres, axis=0)
     num = gres @ Yres
     with np.errstate(invalid="ignore", divide="ignore"):

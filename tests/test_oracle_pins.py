@@ -400,6 +400,63 @@ def test_untestable_markers_are_nan():
     assert np.isnan(b1[:2]).all() and np.isfinite(b1[2]).all()
 
 
+def _marker_with_vif(seed, N, vif, n_other=2):
+    """A 0/1/2 marker g and covariates C such that g's variance inflation factor on [1, C] is
+    `vif` by construction: C[:, 0] = g_c + lam e with e orthogonal to 1 and g_c, so that the
+    residual of g_c on [1, C[:, 0]] has |g_res|^2 / |g_c|^2 = lam^2 |e|^2 / (|g_c|^2 + lam^2 |e|^2)
+    = 1 / vif; the other covariates are orthogonal to 1, g_c and e, so they change nothing."""
+    r = _rng(seed)
+    g = r.integers(0, 3, N).astype(float)
+    gc = g - g.mean()
+    B = np.column_stack([np.ones(N), gc])
+    e = r.standard_normal(N)
+    e -= B @ np.linalg.lstsq(B, e, rcond=None)[0]
+    rho = 1.0 / vif
+    lam = math.sqrt((gc @ gc) * rho / (1.0 - rho) / (e @ e))
+    O = r.standard_normal((N, n_other))
+    B3 = np.column_stack([B, e])
+    O -= B3 @ np.linalg.lstsq(B3, O, rcond=None)[0]
+    C = np.column_stack([gc + lam * e, O])
+    return g, C
+
+
+@pytest.mark.parametrize("N", [60, 400])
+def test_marker_cut_either_side_of_the_variance_inflation_limit(N):
+    """Markers built at VIF = 50 (1 -/+ 1e-6), and far from the limit (VIF 10 and 1,000): the
+    direct OLS and the projected form test the ones at or below 50 and give NaN above it. The
+    VIF of each construction is checked independently (R^2 of g on [1, C] by lstsq)."""
+    cases = [(50.0 * (1 - 1e-6), True), (50.0 * (1 + 1e-6), False), (10.0, True), (1000.0, False)]
+    for k, (vif, tested) in enumerate(cases):
+        g, C = _marker_with_vif(100 + k, N, vif)
+        X = oracle.design_matrix(C, N)
+        coef, *_ = np.linalg.lstsq(X, g, rcond=None)
+        res = g - X @ coef
+        gc = g - g.mean()
+        assert abs((gc @ gc) / (res @ res) / vif - 1.0) < 1e-9
+        Y = X @ _rng(k).standard_normal((X.shape[1], 2)) + 0.5 * g[:, None] + _rng(200 + k).standard_normal((N, 2))
+        beta, se, t, df = oracle.ols_direct(X, g[None, :], Y)
+        Q, _ = oracle.householder_basis(X)
+        Yres, _, _ = oracle.residualise(Y, Q)
+        rr, b2, s2, t2, _, gres2 = oracle.ols_projected(Q, g[None, :], Yres)
+        assert bool(np.isfinite(beta).all()) == tested and bool(np.isnan(beta).all()) == (not tested), vif
+        assert bool(np.isfinite(rr).all()) == tested and bool(np.isnan(rr).all()) == (not tested), vif
+        if tested:  # the values next to the limit are the OLS ones (brute force)
+            W = np.column_stack([X, g])
+            cw, *_ = np.linalg.lstsq(W, Y, rcond=None)
+            assert np.allclose(beta[0], cw[-1], rtol=1e-8)
+            assert np.allclose(b2[0], cw[-1], rtol=1e-8)
+            assert abs(gres2[0] / (res @ res) - 1.0) < 1e-9
+
+
+def test_testable_rule_at_the_limit():
+    """The rule itself: tested iff |g_c|^2 > 0 and |g_c|^2 / |g_res|^2 <= 50."""
+    from oracle.ols import MAX_VIF, testable
+    assert MAX_VIF == 50.0
+    gc2 = np.array([50.0, 50.0, 50.0, 0.0, 1.0, np.nan])
+    gres2 = np.array([1.0, 1.0 - 1e-12, 1.0 + 1e-12, 0.0, 1.0, 1.0])
+    assert testable(gc2, gres2).tolist() == [True, False, True, False, True, False]
+
+
 # ---------------------------------------------------------------- p-values
 
 def _p_df1(t):
