@@ -46,6 +46,9 @@ def _args():
     a.add_argument("--e2e-steps", type=int, default=8)
     a.add_argument("--cpu-seconds", type=float, default=15.0)
     a.add_argument("--no-cpu-baseline", action="store_true")
+    a.add_argument("--no-extra", action="store_true",
+                   help="leave out the other workloads (2-bit P=2,048, N=2,000 P=16, batched, "
+                        "P sweep) that the default line carries under other_configs")
     # smaller cases of the same kernels (profiling captures); the default is the full size
     a.add_argument("--workload", default=WORKLOAD,
                    help="n23000_m8900000_p20480_c20_u8 (default, 8-bit dosages, P=20,480), "
@@ -280,6 +283,12 @@ def _config(w):
                   f"{2 * w.block * w.N / 1e9:.2f} GB per block"}
 
 
+def fp32_simt_peak_tflops(peaks) -> float:
+    """FP32 FFMA peak of the SIMT cores: 152 SMs x 128 lanes x 2 flop per cycle at the maximum
+    SM clock (80.5 TFLOP/s at 2,070 MHz)."""
+    return 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
 # ------------------------------------------------------------------------- ours
 
 def _ours(args, dist, rank, ws):
@@ -370,9 +379,16 @@ def _ours(args, dist, rank, ws):
         tg.tg_set_profiling(ctx, False)
         st32 = tg.tg_stage_times(ctx, reset=True)
         ms32 = _max_over_ranks(dist, e0.elapsed_time(e1))
+        k32 = st32["scan"][0] / max(1, st32["scan"][1])
+        a32 = 2.0 * w.N * M * w.P / (k32 / 1000.0) / 1e12
+        p32 = fp32_simt_peak_tflops(_peaks()[0])
         fp32 = {"value": tests_step * args.fp32_steps * ws / (ms32 / 1000.0), "unit": UNIT,
                 "ms_per_step": ms32 / args.fp32_steps,
-                "scan_kernel_ms": st32["scan"][0] / max(1, st32["scan"][1]),
+                "scan_kernel_ms": k32,
+                "roofline": {"bound": "alu", "achieved": a32, "peak": p32, "unit": "TFLOP/s",
+                             "frac": a32 / p32,
+                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FFMA) "
+                                            "x the maximum SM clock (not measured)"},
                 "stage_ms_per_step": {k: v[0] / args.fp32_steps for k, v in st32.items()}}
 
     # end to end through the host-buffer entry point: pinned host blocks in, hits and best out
@@ -437,26 +453,32 @@ def _ours(args, dist, rank, ws):
         if one:
             cpu["one_core"] = {"value": one[0], "unit": UNIT, "sample": one[1]}
 
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak",
-            "vs_baseline": (value / _paper_rate(w)) if _paper_rate(w) else None,
-            "dtype": "bf16", "data": "synthetic",
-            "config": _config(w), "clocks": clk.summary(), "gpu_launches": launches,
-            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "fp32": fp32,
-            "split_vs_fp32": (value / fp32["value"]) if fp32 else None,
-            "prepare_panel_ms": prepare_ms, "hits_in_timed_steps": nh,
-        }))
+    rec = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": (value / _paper_rate(w)) if _paper_rate(w) else None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": _config(w), "clocks": clk.summary(), "gpu_launches": launches,
+        "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "fp32": fp32,
+        "split_vs_fp32": (value / fp32["value"]) if fp32 else None,
+        "prepare_panel_ms": prepare_ms, "hits_in_timed_steps": nh,
+    }
     tg.tg_panel_free(panel)
     tg.tg_destroy(ctx)
+    return rec
 
 
-def _ours_batched(args, dist, rank, ws):
+def _ours_batched(args, dist, rank, ws, workload=None, steps=None, warmup=None, e2e_steps=None,
+                  cpu_seconds=None):
     """The batched form: 12 panels of uneven P (8,192 columns) concatenated into one panel,
     500,000 markers in ragged blocks (1k-64k), every block's scan captured in one CUDA graph
-    and replayed once per step, with the tensor-core kernel autotuned per block-size bucket."""
+    and replayed once per step, with the tensor-core kernel autotuned per block-size bucket.
+    Returns the bench record (rank 0) or None."""
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    e2e_steps = args.e2e_steps if e2e_steps is None else e2e_steps
+    cpu_seconds = (0.0 if args.no_cpu_baseline else args.cpu_seconds) if cpu_seconds is None else cpu_seconds
     import numpy as np
     import torch
 
@@ -467,7 +489,7 @@ def _ours_batched(args, dist, rank, ws):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     tg.build()
-    w = synth.WORKLOADS[args.workload]
+    w = synth.WORKLOADS[workload or args.workload]
     ctx = tg.tg_create(local)
     stream = torch.cuda.current_stream(dev)
     pan = synth.make_panel(w, device=dev, planted_blocks=1)
@@ -504,7 +526,7 @@ def _ours_batched(args, dist, rank, ws):
     graph = tg.tg_scan_graph_create(ctx, panel, blocks, w.N, enc, opts, out,
                                     [int(offs[i]) for i in mine])
     markers = sum(sizes[i] for i in mine)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         tg.tg_scan_graph_launch(graph, stream=stream)
     torch.cuda.synchronize()
     n_hits.zero_()
@@ -515,7 +537,7 @@ def _ours_batched(args, dist, rank, ws):
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             tg.tg_scan_graph_launch(graph, stream=stream)
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -526,7 +548,7 @@ def _ours_batched(args, dist, rank, ws):
         raise SystemExit(f"device status {status}: {tg.tg_last_error()}")
     launches = sum(n for _, n in tg.tg_stage_times(ctx, reset=True).values())
     total_markers = sum(sizes)
-    value = total_markers * w.P * args.steps / (ms / 1000.0)
+    value = total_markers * w.P * steps / (ms / 1000.0)
     nh = int(n_hits.item())
     tg.tg_scan_graph_free(graph)
 
@@ -534,7 +556,7 @@ def _ours_batched(args, dist, rank, ws):
     # replay copies them to the device on a forked stream while the previous block is scanned;
     # each step reads the hit count, the best keys and the hits back to the host
     e2e = None
-    if args.e2e_steps > 0 and ws == 1:
+    if e2e_steps > 0 and ws == 1:
         ldg = blocks[0].shape[1]
         host = [b.cpu().pin_memory() for b in blocks]
         hg = tg.tg_scan_graph_create_host(ctx, panel, host, w.N, enc, opts, out,
@@ -544,7 +566,7 @@ def _ours_batched(args, dist, rank, ws):
         hits_h = torch.zeros(cap * 24, dtype=torch.uint8, pin_memory=True)
         tg.tg_scan_graph_launch(hg, stream=stream)  # warm-up
         torch.cuda.synchronize()
-        reps = max(1, args.e2e_steps // 2)
+        reps = max(1, e2e_steps // 2)
         d2h = 0
         t0 = time.perf_counter()
         for _ in range(reps):
@@ -570,19 +592,20 @@ def _ours_batched(args, dist, rank, ws):
 
     peaks, peak_src = _peaks()
     flops = 2.0 * w.N * total_markers * w.P
-    achieved = flops / (ms / args.steps / 1000.0) / 1e12
+    achieved = flops / (ms / steps / 1000.0) / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and cpu_seconds > 0:
         done, secs, P = _oracle_sample(pan["Yt"].cpu(), pan["cov_t"].cpu(), blocks[0][:4096].cpu(),
-                                       args.cpu_seconds, w.encoding)
+                                       cpu_seconds, w.encoding)
         cpu = {"value": done * P / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{done} markers x {P} phenotypes, FP64 projected OLS with p-values, "
                          f"{secs:.1f} s (panel preparation excluded)"}
+    rec = None
     if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        rec = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"{w.name}: N={w.N} samples, 12 panels of P = "
                                    f"{list(synth.BATCHED_PANELS)} (8,192 columns) sharing the "
@@ -601,9 +624,10 @@ def _ours_batched(args, dist, rank, ws):
                          "peak_source": f"{peak_src} bf16 sustained"},
             "cpu_baseline": cpu, "fp32": None, "prepare_panel_ms": prepare_ms,
             "hits_in_timed_steps": nh,
-        }))
+        }
     tg.tg_panel_free(panel)
     tg.tg_destroy(ctx)
+    return rec
 
 
 def _kernel_profile():
@@ -629,56 +653,165 @@ def _kernel_profile():
         return {}
 
 
-def _sweep_p(args):
-    """Per-block time of the whole scan path against the panel size P, on one GPU."""
+def _hbm_bytes_per_block(N: int, M: int, encoding: str, P: int, q: int) -> float:
+    """Algorithmic DRAM bytes of one block's scan when the decoded operand goes through HBM:
+    read the packed rows, write the 2-byte operand, read it once more for each pass over it
+    (one joint pass when the panel and the q - 1 projection columns fit a 256-column tile,
+    else the projection and the contraction), and read the bf16 hi + lo panel once."""
+    npad = (N + 63) // 64 * 64
+    packed = M * (N if encoding == "u8" else (N + 3) // 4)
+    operand = 2 * M * npad
+    passes = 1 if P + q - 1 <= 256 else 2
+    return packed + operand + passes * operand + 2 * 2 * P * npad
+
+
+def _scan_points(w, Ps, dev, reps_for, flush_bytes=0):
+    """Per-block time of the whole scan path (one tg_scan_block of block 0 of workload w) for
+    panels of each size in Ps (the first P phenotypes of the workload's panel), with the stage
+    times and the binding roofline of each point. With flush_bytes > 0 a buffer that large is
+    written before every timed scan and each scan is timed alone (for inputs that fit L2)."""
     import torch
 
     import paper_2604_21095_gb300 as tg
     import synth
 
-    dev = torch.device("cuda", 0)
-    tg.build()
-    w = _workload(args)
     enc = tg.TG_ENC_U8_DOSAGE if w.encoding == "u8" else tg.TG_ENC_2BIT
-    ctx = tg.tg_create(0)
+    peaks, src = _peaks()
+    ctx = tg.tg_create(dev.index or 0)
     stream = torch.cuda.current_stream(dev)
     pan = synth.make_panel(w, device=dev, planted_blocks=1)
     G = synth.make_block(w, 0, device=dev)["G"]
     M = G.shape[0]
     hits = torch.zeros((1 << 20) * 24, dtype=torch.uint8, device=dev)
     n_hits = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(flush_bytes, dtype=torch.uint8, device=dev) if flush_bytes else None
     points = []
-    for P in (16, 40, 64, 100, 200, 256, 1024, 2048, 4096, 8192, 20480):
+    for P in Ps:
         if P > w.P:
             break
         Yt = pan["Yt"][:P].contiguous()
         panel = tg.tg_prepare_panel(ctx, Yt, w.N, P, pan["cov_t"], stream=stream)
+        q = tg.tg_panel_info(panel)[2]
         best = torch.zeros(P, dtype=torch.int64, device=dev)
         out = tg.make_outputs(hits=hits, n_hits=n_hits, best=best)
         opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, THR)
-        reps = max(3, min(50, int(20480 * 5 / P)))
-        for _ in range(2):
+        reps = reps_for(P)
+        for _ in range(3):
             tg.tg_scan_block(ctx, panel, G, w.N, M, enc, opts, out, stream=stream)
         torch.cuda.synchronize()
         tg.tg_stage_times(ctx, reset=True)
         tg.tg_set_profiling(ctx, True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            tg.tg_scan_block(ctx, panel, G, w.N, M, enc, opts, out, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
+        ms = 0.0
+        if flush is None:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                tg.tg_scan_block(ctx, panel, G, w.N, M, enc, opts, out, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        else:
+            evs = []
+            for _ in range(reps):
+                flush.fill_(1)  # evicts the block, the operand and the panel from L2
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tg.tg_scan_block(ctx, panel, G, w.N, M, enc, opts, out, stream=stream)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in evs) / reps
         tg.tg_set_profiling(ctx, False)
         st = tg.tg_stage_times(ctx, reset=True)
-        ms = e0.elapsed_time(e1) / reps
-        points.append({"P": P, "ms_per_block": ms, "tests_per_s": M * P / (ms / 1000.0),
-                       "stage_ms": {k: v[0] / reps for k, v in st.items() if v[1]}})
+        if tg.tg_status_poll(ctx, stream) != tg.TG_OK:
+            raise RuntimeError(tg.tg_last_error())
+        flops = 2.0 * w.N * M * P
+        byts = _hbm_bytes_per_block(w.N, M, w.encoding, P, q)
+        hbm_frac = byts / (ms / 1000.0) / 1e9 / float(peaks["hbm_gbs"])
+        tflops = flops / (ms / 1000.0) / 1e12
+        tens_frac = tflops / float(peaks["bf16_tflops"])
+        hbm_bound = hbm_frac >= tens_frac
+        points.append({
+            "P": P, "ms_per_block": ms, "tests_per_s": M * P / (ms / 1000.0),
+            "roofline": {"bound": "hbm" if hbm_bound else "tensor",
+                         "achieved": byts / (ms / 1000.0) / 1e9 if hbm_bound else tflops,
+                         "peak": float(peaks["hbm_gbs"]) if hbm_bound else float(peaks["bf16_tflops"]),
+                         "unit": "GB/s" if hbm_bound else "TFLOP/s",
+                         "frac": hbm_frac if hbm_bound else tens_frac,
+                         "basis": "whole step: algorithmic DRAM bytes (packed rows, operand written "
+                                  "and read per pass, panel) or Eq. 2 flops (2 N M P) per block, "
+                                  f"against the {src} HBM copy rate / burst bf16 rate"},
+            "stage_ms": {k: v[0] / reps for k, v in st.items() if v[1]}})
         n_hits.zero_()
         tg.tg_panel_free(panel)
     tg.tg_destroy(ctx)
+    return M, points
+
+
+def _sweep_p(args):
+    """Per-block time of the whole scan path against the panel size P, on one GPU."""
+    import torch
+
+    w = _workload(args)
+    M, points = _scan_points(w, (16, 40, 64, 100, 200, 256, 1024, 2048, 4096, 8192, 20480),
+                             torch.device("cuda", 0), lambda P: max(3, min(50, int(20480 * 5 / P))))
     print(json.dumps({"metric": "per-block scan time vs number of phenotypes", "unit": "ms",
                       "workload": f"{w.name}: one {M}-marker block, N={w.N}, C={w.n_cov + 1}",
                       "points": points}))
+
+
+def _other_configs(args):
+    """The benchmark set's other workloads on the same GPU after the headline, each with its
+    binding roofline: the 2-bit P = 2,048 workload (one 65,536-marker block), the N = 2,000,
+    P = 16 workload (its whole 10,000 markers per step; they fit L2, so L2 is flushed before
+    every timed scan), the batched form (12 panels, ragged blocks, one graph per step) and a
+    few points of the scaling in the number of phenotypes (Section 3.2) on the dosage workload."""
+    import dataclasses
+
+    import torch
+
+    import synth
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    out = {}
+
+    def run(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as e:  # a failed extra is reported on the line, not hidden
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+
+    def cfg_block(name, reps, flush):
+        w = synth.WORKLOADS[name]
+        M, pts = _scan_points(w, (w.P,), dev, lambda P: reps, flush)
+        pt = pts[0]
+        pt.update(workload=f"{name}: one {M}-marker block, N={w.N}, P={w.P}, C={w.n_cov + 1}, "
+                           f"{'8-bit dosages' if w.encoding == 'u8' else '2-bit calls'}"
+                           + (f", L2 flushed ({flush >> 20} MiB written) before each scan" if flush else ""))
+        return pt
+
+    run("n23000_m1000000_p2048_c10_2bit", lambda: cfg_block("n23000_m1000000_p2048_c10_2bit", 10, 0))
+    run("n2000_m10000_p16_c5_2bit", lambda: cfg_block("n2000_m10000_p16_c5_2bit", 20, 256 << 20))
+
+    def batched():
+        r = _ours_batched(args, None, 0, 1, workload="n23000_m500000_12panels_p8192_2bit",
+                          steps=5, warmup=2, e2e_steps=0, cpu_seconds=0.0)
+        keep = ("value", "unit", "ms_per_step", "steps", "clocks", "gpu_launches", "roofline")
+        d = {k: r[k] for k in keep}
+        d["workload"] = r["config"]["workload"]
+        d["tuning"] = r["config"]["tuning"]
+        return d
+
+    run("n23000_m500000_12panels_p8192_2bit", batched)
+
+    def sweep():
+        w = dataclasses.replace(synth.WORKLOADS[WORKLOAD], P=4096)
+        M, pts = _scan_points(w, (16, 100, 256, 1024, 4096), dev,
+                              lambda P: max(3, min(30, int(20480 * 3 / P))))
+        return {"workload": f"{WORKLOAD}: one {M}-marker block, N={w.N}, C={w.n_cov + 1}, "
+                            "panels of the first P phenotypes", "points": pts}
+
+    run("sweep_p_n23000_u8", sweep)
+    return out
 
 
 def main():
@@ -690,9 +823,18 @@ def main():
     if args.impl == "reference":
         _reference(args, dist, rank, ws)
     elif "panels" in args.workload:
-        _ours_batched(args, dist, rank, ws)
+        rec = _ours_batched(args, dist, rank, ws)
+        if rank == 0:
+            print(json.dumps(rec))
     else:
-        _ours(args, dist, rank, ws)
+        rec = _ours(args, dist, rank, ws)
+        if rank == 0:
+            if ws == 1 and not args.no_extra and args.workload == WORKLOAD and not (
+                    args.phenotypes or args.block_markers):
+                t0 = time.perf_counter()
+                rec["other_configs"] = _other_configs(args)
+                rec["other_configs"]["seconds"] = time.perf_counter() - t0
+            print(json.dumps(rec))
     if dist is not None:
         dist.destroy_process_group()
 

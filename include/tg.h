@@ -104,7 +104,9 @@ typedef struct {
   unsigned long long* best;   /* [P] running per-phenotype best marker; the caller zeroes it.
                                  key = (bits of float |r|) << 32 | (0xFFFFFFFF - marker):
                                  larger |r| wins, ties go to the smaller marker */
-  double* marker_norm2;   /* [M] |g_res|^2 in allele units (NaN: marker untestable) */
+  double* marker_norm2;   /* [M] |g_res|^2 in allele units (NaN: marker untestable: no observed
+                             call, constant, or in TG_MODE_PROJECTED a variance inflation
+                             factor |g_c|^2 / |g_res|^2 above 50 on the covariates) */
   int32_t* marker_nobs;   /* [M] observed calls */
   double* marker_mean;    /* [M] observed mean in decode units (counts, or bytes for dosages) */
 } tg_outputs;
@@ -210,6 +212,9 @@ tg_status tg_decode_block(tg_ctx* ctx, const uint8_t* G, int64_t ldg, int32_t en
  * project each marker on Q (|g_res|^2 = |g_c|^2 - |Q^T g_c|^2), contract the block with the
  * whole panel, and turn every correlation r into t = r sqrt(df / (1 - r^2)),
  * beta = r s_p / |g_res|, se = |beta / t| and -log10 p, p = I_{1-r^2}(df/2, 1/2) (two-sided).
+ * A marker with no observed call, a constant one, or (TG_MODE_PROJECTED) one whose variance
+ * inflation factor on the covariates, |g_c|^2 / |g_res|^2, exceeds 50 (the covariates explain
+ * more than 98% of its variance) is untestable: NaN outputs, no hit, never a best marker.
  *   G, ldg, encoding, missing, ldm: as tg_decode_block; N must equal the panel's N.
  *   marker_offset: global index of the block's first marker (used in hits and best).
  *   opts: precision, full output and hit threshold. out: see tg_outputs.
@@ -278,19 +283,28 @@ tg_status tg_host_ramp(const tg_ctx* ctx, double* factor, double* measured_ratio
 
 /* The block sizes tg_scan_host uses for M markers, blocks of at most block_markers and growth
  * factor `factor` in [1, 8] (host only, no device work): *n_blocks = their number, and the
- * first min(capacity, *n_blocks) sizes are written to `sizes` (host int64 [capacity]).
- * TG_ERR_UNSUPPORTED when M would take 2^28 blocks or more. */
+ * first min(capacity, *n_blocks) sizes are written to `sizes` (host int64 [capacity]; NULL
+ * with capacity 0 returns the count alone, with no list built). block_markers is at most 2^32
+ * (TG_ERR_INVALID_ARG above, here and in tg_scan_host). TG_ERR_UNSUPPORTED when M would take
+ * 2^28 blocks or more. */
 tg_status tg_host_block_sizes(int64_t M, int64_t block_markers, double factor, int64_t* sizes,
                               int64_t capacity, int64_t* n_blocks);
 
-/* Whether split-form scans decode the genotypes inside the contraction kernels (enable != 0)
- * or first write the decoded operand to device memory (enable == 0, the default). The fused
- * form applies to 2-bit blocks and to dosage blocks without a missing mask (others always use
- * the decoded operand); it needs no operand buffer (about 2 x round_up(N, 64) bytes per marker)
- * and reads the packed rows instead, but its two decoder warps per CTA take about 3,000 cycles
- * per 32-sample K block, against 512 for the products, so on GB300 it is slower at every panel
- * size. Both forms compute bit-identical results. Not allowed while a captured scan graph uses
- * the context (TG_ERR_INVALID_ARG). */
+/* Where split-form scans decode the genotypes inside the contraction kernels instead of first
+ * writing the decoded operand (about 2 x round_up(N, 64) bytes per marker) to device memory.
+ * The fused forms apply to 2-bit blocks and to dosage blocks without a missing mask (others always
+ * use the decoded operand) and compute bit-identical results.
+ *   enable = 2 (the default): only the joint projection pass of a small panel (projected mode,
+ *     P + q - 1 <= 128, blocks of at least one 128-marker tile per SM), where the scan is one pass
+ *     bound by the bytes it reads: the pass reads the packed rows (1 or 1/4 byte per sample)
+ *     and decodes them in shared memory with 8 decoder warps, removing the operand's write and
+ *     read (Section 2.4: the scan is bound by the reader's bandwidth).
+ *   enable = 1: also the contraction kernels of larger panels, whose two decoder warps per CTA
+ *     take about 3,000 cycles per 32-sample K block against 512 for the products, so on GB300
+ *     they are slower there.
+ *   enable = 0: never; every block goes through the decoded operand.
+ * Not allowed while a captured scan graph uses the context (TG_ERR_INVALID_ARG); other values
+ * give TG_ERR_INVALID_ARG. */
 tg_status tg_set_fused_decode(tg_ctx* ctx, int enable);
 
 /* ---- Batched form: many panels, ragged blocks, one captured graph, tuned tiles ----------- */

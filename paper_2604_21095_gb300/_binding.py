@@ -407,8 +407,15 @@ def tg_phenotype_masks(ctx, Yt, N, P, masks, stream=None):
                                      _stream(stream)))
 
 
-def tg_set_fused_decode(ctx, enable: bool):
-    _check(load().tg_set_fused_decode(ctx, 1 if enable else 0))
+TG_FUSED_OFF, TG_FUSED_ALL, TG_FUSED_SMALL_PANELS = 0, 1, 2
+
+
+def tg_set_fused_decode(ctx, enable):
+    """True / TG_FUSED_ALL: every kernel that can decode in its producer does; False /
+    TG_FUSED_OFF: none (the decoded operand always); TG_FUSED_SMALL_PANELS: the default, only the
+    joint projection pass of panels with P + q - 1 <= 128."""
+    setting = int(enable) if not isinstance(enable, bool) else (TG_FUSED_ALL if enable else TG_FUSED_OFF)
+    _check(load().tg_set_fused_decode(ctx, setting))
 
 
 def tg_set_profiling(ctx, enable: bool):

@@ -57,12 +57,13 @@ bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
-bool make_tmap_packed(CUtensorMap* m, const void* ptr, int64_t rows, int64_t ld, uint32_t box_bytes) {
+bool make_tmap_packed(CUtensorMap* m, const void* ptr, int64_t rows, int64_t ld, uint32_t box_bytes,
+                      uint32_t box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld};
-  cuuint32_t box[2] = {box_bytes, (cuuint32_t)MT};
+  cuuint32_t box[2] = {box_bytes, box_rows};
   cuuint32_t estr[2] = {1u, 1u};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(ptr), dims, strides, box,
                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -304,9 +305,14 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   if (a.M == 0) return TG_OK;
   const int prec = a.opts.precision;
   const bool split = prec == TG_PREC_SPLIT_BF16;
+  // a small panel's joint projection pass (projected form, joint operand of at most 128 rows,
+  // at least one 128-marker tile per SM) reads the packed rows and decodes them in shared memory
+  const bool fuse_joint = split && c->fuse_joint && a.missing == nullptr &&
+                          a.opts.mode == TG_MODE_PROJECTED && p->q > 1 && p->joint_cols > 0 &&
+                          p->joint_cols <= 128 && (a.M + MT - 1) / MT >= c->sm_count;
   // split-form 2-bit blocks and unmasked dosage blocks are decoded inside the contraction
-  // kernels; the rest go through a decoded operand in HBM
-  const bool fused = split && c->fuse_decode && a.missing == nullptr;
+  // kernels when the context asks for it; the rest go through a decoded operand in HBM
+  const bool fused = split && a.missing == nullptr && (c->fuse_decode || fuse_joint);
   if (c->graphs_alive > 0) {
     const bool grow = a.M > c->cap_m || (!fused && (round_up(a.M, MT) > c->cap_rows ||
                                                     p->Npad > c->cap_npad ||
@@ -331,13 +337,17 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
                           split ? c->shift : nullptr, split ? c->mh : nullptr, p->Npad, c->nobs,
                           nullptr, nullptr, c->mean, c->gc2, st));
   }
-  DecodeArgs da{};
+  DecodeArgs da{}, dj{};
   if (fused) {
     da.N = (int)a.N;
     da.M = (int)a.M;
     da.shift = c->shift;
     da.mh = c->mh;
-    if (!make_tmap_packed(&da.tmG, a.G, a.M, a.ldg, a.encoding == TG_ENC_U8_DOSAGE ? 32u : 16u))
+    dj = da;
+    const bool u8 = a.encoding == TG_ENC_U8_DOSAGE;
+    if (!make_tmap_packed(&da.tmG, a.G, a.M, a.ldg, u8 ? 32u : 16u) ||
+        (fuse_joint && !make_tmap_packed(&dj.tmG, a.G, a.M, a.ldg, u8 ? 64u : 16u,
+                                         (uint32_t)joint_fused_rows(a.M, c->sm_count))))
       return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the packed genotypes");
   }
   const DecodeArgs* dec = fused ? &da : nullptr;
@@ -363,16 +373,22 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       pp.raw_out = c->qg;
       pp.raw_cols = pp.P;
       pp.raw_ld = (int)ldq;
-      const SplitChoice sc = pick_split(c, p, a.M, true, true);
-      if (sc.ks > 1) {  // a small block: split K so that more SMs stream the operand
-        TG_CUDA(ensure_split(c, sc));
-        pp.ksplit = sc.ks;
-        pp.sk_ws = c->sk_ws;
-        pp.sk_cnt = c->sk_cnt;
-        TG_CUDA(cudaMemsetAsync(pp.sk_cnt, 0, sizeof(unsigned) * (size_t)sc.tiles, st));
+      if (fuse_joint) {
+        TG_CUDA(launch_joint_fused(&p->tmQYhi, &p->tmQYlo, p->Npad, pp, c->sm_count, kSpinNs, st,
+                                   dj, a.encoding));
+      } else {
+        const SplitChoice sc = pick_split(c, p, a.M, true, true);
+        if (sc.ks > 1) {  // a small block: split K so that more SMs stream the operand
+          TG_CUDA(ensure_split(c, sc));
+          pp.ksplit = sc.ks;
+          pp.sk_ws = c->sk_ws;
+          pp.sk_cnt = c->sk_cnt;
+          TG_CUDA(cudaMemsetAsync(pp.sk_cnt, 0, sizeof(unsigned) * (size_t)sc.tiles, st));
+        }
+        TG_CUDA(launch_tc_scan(&tA, joint ? &p->tmQYhi : &p->tmQhi, joint ? &p->tmQYlo : &p->tmQlo,
+                               p->Npad, pp, c->sm_count, kSpinNs, st, kGroupDefault,
+                               c->fuse_decode ? dec : nullptr, a.encoding));
       }
-      TG_CUDA(launch_tc_scan(&tA, joint ? &p->tmQYhi : &p->tmQhi, joint ? &p->tmQYlo : &p->tmQlo,
-                             p->Npad, pp, c->sm_count, kSpinNs, st, kGroupDefault, dec, a.encoding));
     }
   }
   if (p->samples) {  // a subset panel: |g_c|^2 over its samples
@@ -407,6 +423,7 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   ep.do_best = a.out.best != nullptr;
   ep.row_inv = c->rinv;
   ep.row_inv64 = c->rinv64;
+  ep.exact = ExactArgs{a.G, a.ldg, a.encoding, (int)a.N, a.missing, a.ldm, c->mean, p->Yres, p->N};
   ep.col_s = p->col_s;
   ep.col_s64 = p->s;
   ep.col_rmul = p->col_rmul;
@@ -917,31 +934,47 @@ tg_status tg_scan_block(tg_ctx* c, const tg_panel* p, const uint8_t* G, int64_t 
   return scan_impl(c, p, a, (cudaStream_t)stream);
 }
 
-// Block sizes of tg_scan_host for M markers: round_up(B / 8, 256) first when B >= 2048 (else
-// B), each next one f times the previous rounded up to 256, at most B; the last takes the rest.
-std::vector<int64_t> host_block_sizes(int64_t M, int64_t B, double f) {
-  std::vector<int64_t> v;
+// Largest block_markers of the host-streamed scan: keeps f * block sizes and block bytes far
+// inside int64.
+constexpr int64_t kMaxBlockMarkers = 1ll << 32;
+
+// Block sizes of tg_scan_host for M markers (B <= kMaxBlockMarkers, f in [1, 8]):
+// round_up(B / 8, 256) first when B >= 2048 (else B), each next one f times the previous
+// rounded up to 256, at most B; the last takes the rest. Calls emit(rows) per block in order.
+extern "C++" {
+template <class Emit>
+void for_each_host_block(int64_t M, int64_t B, double f, Emit emit) {
   int64_t next = B >= 8 * 256 ? round_up(B / 8, 256) : B;
   for (int64_t m0 = 0; m0 < M;) {
     const int64_t rows = std::min<int64_t>(next, M - m0);
-    v.push_back(rows);
+    emit(rows);
     m0 += rows;
     next = std::min<int64_t>(B, round_up((int64_t)((double)next * f), 256));
   }
+}
+}
+
+std::vector<int64_t> host_block_sizes(int64_t M, int64_t B, double f) {
+  std::vector<int64_t> v;
+  for_each_host_block(M, B, f, [&](int64_t rows) { v.push_back(rows); });
   return v;
 }
 
 tg_status tg_host_block_sizes(int64_t M, int64_t block_markers, double factor, int64_t* sizes,
                               int64_t capacity, int64_t* n_blocks) {
   TG_ARG(M >= 0 && block_markers > 0 && n_blocks, "bad arguments");
+  TG_ARG(block_markers <= kMaxBlockMarkers, "block_markers above 2^32");
   TG_ARG(factor >= 1.0 && factor <= 8.0, "growth factor must be in [1, 8]");
   TG_ARG(capacity >= 0 && (sizes || capacity == 0), "bad size buffer");
   // blocks never shrink below the first one, which bounds their number
   const int64_t first = block_markers >= 8 * 256 ? round_up(block_markers / 8, 256) : block_markers;
   if (M / first >= (1ll << 28)) return fail(TG_ERR_UNSUPPORTED, "more than 2^28 blocks");
-  const std::vector<int64_t> v = host_block_sizes(M, block_markers, factor);
-  *n_blocks = (int64_t)v.size();
-  for (size_t i = 0; i < v.size() && (int64_t)i < capacity; ++i) sizes[i] = v[i];
+  int64_t n = 0;  // counted as they come: nothing is stored beyond the caller's capacity
+  for_each_host_block(M, block_markers, factor, [&](int64_t rows) {
+    if (n < capacity) sizes[n] = rows;
+    ++n;
+  });
+  *n_blocks = n;
   return TG_OK;
 }
 
@@ -974,6 +1007,8 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
   TG_ARG(c && p && opts && n_hits, "null argument");
   TG_ARG(!opts->full_output, "tg_scan_host collects hits only");
   TG_ARG(block_markers > 0 && M >= 0, "bad block size");
+  TG_ARG(block_markers <= kMaxBlockMarkers, "block_markers above 2^32");
+  TG_ARG(ldg > 0 && ldg <= (1ll << 31), "bad ldg");
   TG_ARG(hit_capacity >= 0 && (hits_host || hit_capacity == 0), "bad hit buffer");
   TG_ARG(G_host || M == 0, "null G_host");
   TG_CUDA(cudaSetDevice(c->device));
@@ -1079,8 +1114,10 @@ tg_status tg_status_poll(tg_ctx* c, void* stream) {
 
 tg_status tg_set_fused_decode(tg_ctx* c, int enable) {
   TG_ARG(c, "null context");
+  TG_ARG(enable >= 0 && enable <= 2, "fused decode setting must be 0, 1 or 2");
   TG_ARG(c->graphs_alive == 0, "a captured scan graph uses this context");
-  c->fuse_decode = enable != 0;
+  c->fuse_decode = enable == 1;
+  c->fuse_joint = enable != 0;
   return TG_OK;
 }
 

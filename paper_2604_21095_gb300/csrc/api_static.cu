@@ -240,6 +240,7 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   ep.do_best = out->best != nullptr;
   ep.row_inv = rinv;
   ep.row_inv64 = rinv64;
+  ep.exact = ExactArgs{G, ldg, encoding, (int)N, missing, ldm, mean, p->Yres, p->N};
   ep.col_s = p->col_s;
   ep.col_s64 = p->s;
   ep.col_rmul = p->col_rmul;

@@ -29,6 +29,27 @@ enum Stage { STAGE_DECODE = 0, STAGE_PROJECT = 1, STAGE_NORM = 2, STAGE_GEMM = 3
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// What the FP64 recomputation of a product g_j . y_res,p needs (hits, and FULL elements near
+// |r| = 1): the packed genotype block, its FP64 observed means (decode units; a missing call is
+// imputed with it) and the panel's FP64 residualised phenotypes [P][ldy]. G = NULL: off.
+struct ExactArgs {
+  const uint8_t* G;
+  long long ldg;
+  int encoding;
+  int N;
+  const uint32_t* missing;  // dosage mask [M][ldm] or NULL
+  long long ldm;
+  const double* mean;       // [M]
+  const double* Yres;       // [P][ldy], zero outside a subset panel's samples
+  long long ldy;
+};
+
+// FULL elements whose FP32 1 - r^2 is below this are recomputed in FP64 (hits always are):
+// r from the FP32 product carries an absolute error of up to ~5e-7, and d(-log10 p)/dr =
+// df |r| / ((1 - r^2) ln 10) makes that exceed the 1e-5 relative tolerance on -log10 p once
+// (1 - r^2) ln(1 / (1 - r^2)) < ~0.1, i.e. 1 - r^2 < ~0.03, at every df.
+constexpr float kExactOmr2 = 0.05f;
+
 // Per-element statistics inputs shared by both contraction kernels' epilogues.
 struct EpiParams {
   int M, P;                    // block rows (markers) and panel phenotypes
@@ -64,6 +85,7 @@ struct EpiParams {
   int ksplit;
   float* sk_ws;
   unsigned* sk_cnt;
+  ExactArgs exact;             // FP64 recomputation of hits and of FULL elements near |r| = 1
 };
 
 // Packed genotypes for a contraction kernel that decodes its A operand in the producer
@@ -189,6 +211,9 @@ struct tg_ctx {
   // split-form scans decode 2-bit / unmasked dosage blocks in the contraction producer
   // (off by default: slower than the decoded operand on GB300, see tg_set_fused_decode)
   bool fuse_decode = false;
+  // small panels' joint projection pass reads the packed rows and decodes them in shared memory
+  // (on by default: it removes the decoded operand's round trip through HBM)
+  bool fuse_joint = true;
   // autotuned kernel per block-size bucket
   int tune_kernel[tg::kTuneBuckets] = {};
   int tune_group[tg::kTuneBuckets] = {};
@@ -210,8 +235,9 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* p, const ScanArgs& a, cudaStream_
 void mode_df(const tg_panel* p, int mode, double* df, double* lnB);
 bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t ld,
                uint32_t box_rows);
-// uint8 map over packed genotype rows [rows][ld], boxes of box_bytes x 128 rows, zero fill.
-bool make_tmap_packed(CUtensorMap* m, const void* ptr, int64_t rows, int64_t ld, uint32_t box_bytes);
+// uint8 map over packed genotype rows [rows][ld], boxes of box_bytes x box_rows, zero fill.
+bool make_tmap_packed(CUtensorMap* m, const void* ptr, int64_t rows, int64_t ld, uint32_t box_bytes,
+                      uint32_t box_rows = 128);
 
 // panel kernels (k_panel.cu)
 cudaError_t launch_build_design(double* X, const double* C, int64_t ldc, int64_t N, int64_t n_cov,
@@ -286,6 +312,15 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
                            const CUtensorMap* tmBlo, int64_t K, const EpiParams& ep, int sm_count,
                            long long spin_ns, cudaStream_t st, int group_m = 16,
                            const DecodeArgs* dec = nullptr, int encoding = 0, bool narrow = false);
+
+// The joint projection pass of a small panel (joint operand of 64 or 128 rows) with the decode
+// fused in (k_fused.cu): reads the packed rows through da.tmG, whose boxes must be
+// joint_fused_rows(M, sm_count) rows of 64 bytes (dosage) or 16 bytes (2-bit calls); raw mode
+// only, no split-K, K a multiple of 64. Writes the same raw products as launch_tc_scan.
+int joint_fused_rows(int64_t M, int sm_count);
+cudaError_t launch_joint_fused(const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
+                               const EpiParams& ep, int sm_count, long long spin_ns, cudaStream_t st,
+                               const DecodeArgs& da, int encoding);
 
 // The statistics of a small panel (P <= 256) from the joint pass's raw products (k_tc.cu): D of
 // marker row m and phenotype p at raw[m * ld + p] (the shift's add-back included), the same

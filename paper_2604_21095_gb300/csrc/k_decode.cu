@@ -245,9 +245,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_decode(
 template <int ENC, int GPT, int THREADS>
 __global__ void __launch_bounds__(THREADS, GPT * THREADS <= 1536 ? 4 : 2) k_decode_rows(
     const uint8_t* __restrict__ G, long long ldg, int N, const uint32_t* __restrict__ miss,
-    long long ldm, __nv_bfloat16* __restrict__ A, float* __restrict__ shift_out, long long lda,
-    int32_t* __restrict__ nobs_out, long long* __restrict__ S_out, long long* __restrict__ S2_out,
-    double* __restrict__ mean_out, double* __restrict__ gc2_out) {
+    long long ldm, __nv_bfloat16* __restrict__ A, float* __restrict__ shift_out,
+    uint32_t* __restrict__ mh_out, long long lda, int32_t* __restrict__ nobs_out,
+    long long* __restrict__ S_out, long long* __restrict__ S2_out, double* __restrict__ mean_out,
+    double* __restrict__ gc2_out) {
   __shared__ unsigned long long red[3][THREADS / 32];
   __shared__ float s_c;
   __shared__ uint32_t s_mh;
@@ -345,7 +346,11 @@ __global__ void __launch_bounds__(THREADS, GPT * THREADS <= 1536 ? 4 : 2) k_deco
     if (shift_out) shift_out[j] = (float)c;
     s_c = (float)c;
     s_mh = (uint32_t)__bfloat16_as_ushort(__double2bfloat16((tn ? mean : 0.0) - c));
+    if (mh_out) mh_out[j] = s_mh;
   }
+  // without an operand (the contraction decodes in its producer): the statistics, the shift
+  // and the missing value only
+  if (!A) return;
   __syncthreads();
   // pass 2: the operand row from registers, zeros past N
   const float cf = s_c;
@@ -459,23 +464,23 @@ cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32
                int64_t* S, int64_t* S2, double* mean, double* gc2, cudaStream_t st) {
   // Split form: one block per marker row with the row in registers (read from HBM once):
   // 256 threads x 6 groups of 16 samples for dosage rows, 128 x 12 for 2-bit rows; 12 and 24
-  // groups up to twice those N. The statistics-only form (Ahi NULL) and longer rows read each
-  // row twice in the warp-per-row kernel.
+  // groups up to twice those N, with or without the operand (Ahi NULL: statistics, shift and
+  // missing value only). Longer rows read each row twice in the warp-per-row kernel.
   if constexpr (PREC == TG_PREC_SPLIT_BF16) {
     constexpr int T = ENC == TG_ENC_2BIT ? 128 : 256;
     constexpr int G1 = ENC == TG_ENC_2BIT ? 12 : 6;
     __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(Ahi);
     long long* S64 = reinterpret_cast<long long*>(S);
     long long* S264 = reinterpret_cast<long long*>(S2);
-    if (A && N <= T * G1 * 16) {
+    if (N <= T * G1 * 16) {
       k_decode_rows<ENC, G1, T><<<(unsigned)M, T, 0, st>>>(G, ldg, (int)N, missing, ldm, A, shift,
-                                                          lda, nobs, S64, S264, mean, gc2);
+                                                          mh, lda, nobs, S64, S264, mean, gc2);
       return cudaGetLastError();
     }
-    if (A && N <= T * 2 * G1 * 16) {
+    if (N <= T * 2 * G1 * 16) {
       k_decode_rows<ENC, 2 * G1, T><<<(unsigned)M, T, 0, st>>>(G, ldg, (int)N, missing, ldm, A,
-                                                              shift, lda, nobs, S64, S264, mean,
-                                                              gc2);
+                                                              shift, mh, lda, nobs, S64, S264,
+                                                              mean, gc2);
       return cudaGetLastError();
     }
   }

@@ -92,6 +92,17 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ A, lo
 // rounding of the projections by |g_c|^2 / |g_res|^2 (>= 2 here).
 constexpr double kRefineShare = 0.5;
 
+// A marker is tested when it has an observed call, is not constant and its variance inflation
+// factor on the covariates, |g_c|^2 / |g_res|^2 = 1 / (1 - R^2 of g on [1, C]), is at most
+// kMaxVif: beyond it the covariates explain more than 98% of its variance (the collinearity
+// limit PLINK's linear model applies to its predictors by default). Every marker near the
+// limit has a ratio far above 1 / (1 - kRefineShare), so its norm is decided in FP64.
+constexpr double kMaxVif = 50.0;
+
+__device__ __forceinline__ bool marker_testable(int n_obs, double c2, double r2) {
+  return n_obs > 0 && c2 > 0.0 && kMaxVif * r2 >= c2;
+}
+
 __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
                               const double* __restrict__ gc2, const float* __restrict__ qg,
                               long long ldq, int nq,
@@ -108,7 +119,7 @@ __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
     s += v * v;
   }
   const double r2 = c2 - s;
-  const bool ok = nobs[j] > 0 && c2 > 0.0 && r2 > 1e-5 * c2;  // untestable: R^2 on covariates >= 0.99999
+  const bool ok = marker_testable(nobs[j], c2, r2);
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   const double inv = ok ? 1.0 / sqrt(r2) : nan;
   gres2u[j] = ok ? r2 : nan;
@@ -165,7 +176,7 @@ __global__ void __launch_bounds__(256) k_marker_refine(MarkerRefine rf, const in
     if (threadIdx.x == 0) {
       const double c2 = gc2[j];
       const double r2 = c2 - s;
-      const bool ok = nobs[j] > 0 && c2 > 0.0 && r2 > 1e-5 * c2;
+      const bool ok = marker_testable(nobs[j], c2, r2);
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
       const double inv = ok ? 1.0 / sqrt(r2) : nan;
       gres2u[j] = ok ? r2 : nan;

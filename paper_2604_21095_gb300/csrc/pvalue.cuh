@@ -67,8 +67,37 @@ TG_HD double mlog10p_r(double r, double df, double lnB) {
   return -log1p(-fmin(comp, 1.0)) / kLn10;
 }
 
-// FP32 forms, used on the GPU for every statistic and hit (GB300 has little FP64 throughput:
-// the FP64 form costs ~8 ns per element there).
+// -log10 p from Hill's (1970, Comm. ACM 13(10), Algorithm 395) normal deviate for Student's t,
+// in FP64 (the formula is written out with the FP32 form below). Within 0.05 of the tolerance
+// max(1e-3, 1e-5 -log10 p) for df >= 1500 and 1 - r^2 >= 0.05.
+__device__ __forceinline__ double mlog10p_r_hill(double r, double df) {
+  const double ar = fabs(r);
+  if (ar != ar) return ar;
+  if (ar >= 1.0) return INFINITY;
+  const double y = ar * ar;
+  const double a = df - 0.5;
+  const double Y = -a * ((y < 0.5) ? log1p(-y) : log((1.0 - ar) * (1.0 + ar)));
+  const double B = 48.0 * a * a;
+  const double z =
+      ((((((-0.4 * Y - 3.3) * Y - 24.0) * Y - 85.5) / (0.8 * Y * Y + 100.0 + B) + Y + 3.0) / B) + 1.0) *
+      sqrt(Y);
+  const double x = z * 0.70710678118654752440;
+  return (x * x - log(erfcx(x))) * 0.43429448190325182765;
+}
+
+// -log10 p of a hit, or of an element recomputed in FP64, on the GPU: the continued fraction,
+// except for df >= 1500 and 1 - r^2 >= 0.05, where x = 1 - r^2 lies close to the fraction's
+// branch point (a + 1) / (a + b + 2) and it needs up to ~300 iterations of FP64 divisions (a
+// fraction of a millisecond per thread on GB300), while Hill's deviate is closed-form and
+// within 0.05 of the tolerance there.
+__device__ __forceinline__ double mlog10p_r_dev(double r, double df, double lnB) {
+  if (df >= 1500.0 && (1.0 - fabs(r)) * (1.0 + fabs(r)) >= 0.05) return mlog10p_r_hill(r, df);
+  return mlog10p_r(r, df, lnB);
+}
+
+// FP32 forms, used on the GPU for the FULL statistics with 1 - r^2 >= 0.05 (GB300 has little
+// FP64 throughput: the FP64 form costs ~8 ns per element there; hits and the elements closer to
+// |r| = 1 take the FP64 form above, from an FP64 product).
 //
 // For df < 1500 the same continued fraction in FP32: near the branch point x ~ (a+1)/(a+b+2)
 // its terms cancel by a factor of about a, which FP32 still carries to ~1e-5 for a < 750.
@@ -77,8 +106,9 @@ TG_HD double mlog10p_r(double r, double df, double lnB) {
 // a = df - 1/2, Y = a ln(1 + t^2/df) = -a ln(1 - r^2) and B = 48 a^2,
 //   z = sqrt(Y) (1 + (Y + 3 + ((((-0.4 Y - 3.3) Y - 24) Y - 85.5) / (0.8 Y^2 + 100 + B)) / B),
 // p = erfc(z / sqrt 2), and -log10 p = (x^2 - ln erfcx(x)) / ln 10 with x = z / sqrt 2.
-// Against the FP64 continued fraction this is within 1e-4 of the tolerance for df >= 5000 and
-// within 0.1 of it (max(1e-3, 1e-5 -log10 p)) for df >= 1000; every term is well conditioned.
+// Against the FP64 continued fraction this is within 0.05 of the tolerance
+// (max(1e-3, 1e-5 -log10 p)) for df >= 1500 over the t it is used on, t <= max(400, sqrt(19 df))
+// (1 - r^2 >= 0.05), and within 0.004 of it for df >= 5000; every term is well conditioned.
 __device__ __forceinline__ float incbeta_cf_f(float a, float b, float x, float y) {
   const float kTiny = 1e-30f;
   const float kEps = 1.2e-7f;
@@ -119,7 +149,8 @@ __device__ __forceinline__ float mlog10p_r_f(float r, float df, float lnB) {
   const float y = ar * ar;
   if (df >= 1500.0f) {
     const float a = df - 0.5f;
-    const float Y = -a * log1pf(-y);
+    // ln(1 - r^2) without cancellation: log1p(-r^2) for small r, ln((1 - |r|)(1 + |r|)) above
+    const float Y = -a * ((y < 0.5f) ? log1pf(-y) : logf((1.0f - ar) * (1.0f + ar)));
     const float B = 48.0f * a * a;
     const float z =
         ((((((-0.4f * Y - 3.3f) * Y - 24.0f) * Y - 85.5f) / (0.8f * Y * Y + 100.0f + B) + Y + 3.0f) / B) +

@@ -1,7 +1,7 @@
 """Helpers shared by the GPU parity tests: run the library through its C ABI, run the
 oracle on the same inputs, and compare within the stated tolerances.
 
-Tolerances (split BF16 and FP32 forms), derived in the design doc from the arithmetic:
+Tolerances (split BF16 and FP32 forms), derived from the arithmetic of the two forms:
   |d r|           <= r_tol(df) = 5e-7 + 4e-5 / sqrt(df)
                      (accumulation bias plus the random error of the bf16 hi+lo panel,
                       sigma = 2^-17/sqrt(3) * |a|/|a_res| / sqrt(N), taken at 5 sigma)
@@ -141,10 +141,15 @@ def compare_hits(res, ref, thr, marker_offset=0, tol_band=None):
     return len(want), len(got)
 
 
-def compare_best(res, ref, rtol=None, marker_offset=0):
-    """Per phenotype the GPU's best marker is a valid argmax of |r| within the r tolerance."""
+def compare_best(res, ref, rtol=None, marker_offset=0, rel=0.0):
+    """Per phenotype the GPU's best marker is a valid argmax of |r| within the r tolerance.
+
+    The best key holds |r| from the FP32 product; `rel` adds a tolerance proportional to |r| for
+    cases with |r| close to 1, where the tensor-core accumulation's rounding of a sum of terms of
+    one sign is relative to |r| rather than to the terms (returned: the largest deviation)."""
     rtol = r_tol(ref["df"]) if rtol is None else rtol
     absr = np.abs(np.nan_to_num(ref["r"], nan=-1.0))
+    worst = 0.0
     for p in range(absr.shape[1]):
         col = absr[:, p]
         if col.max() < 0:
@@ -152,5 +157,9 @@ def compare_best(res, ref, rtol=None, marker_offset=0):
             continue
         j = res["best_marker"][p] - marker_offset
         assert 0 <= j < col.size
-        assert col[j] >= col.max() - 2 * rtol, (p, j, col[j], col.max())
-        assert abs(res["best_absr"][p] - col[j]) <= rtol * 2 + 1e-7
+        tol = rtol * 2 + 1e-7 + rel * col.max()
+        assert col[j] >= col.max() - tol, (p, j, col[j], col.max())
+        dev = abs(float(res["best_absr"][p]) - col[j])
+        worst = max(worst, dev)
+        assert dev <= tol, (p, j, float(res["best_absr"][p]), col[j], dev)
+    return worst

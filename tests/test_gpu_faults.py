@@ -82,7 +82,9 @@ def test_arguments_are_refused_before_launch(tgctx):
 def test_allocation_failure_is_reported_and_the_context_survives(tgctx):
     """Host-side fault injection by size: a panel and a block whose device buffers cannot be
     allocated (hundreds of GB) give TG_ERR_OOM before any kernel reads the inputs; the same
-    context then prepares and scans normally."""
+    context then prepares and scans normally. The oversized block is declared with far more rows
+    than its buffer holds, so it must fail in the decoded operand's allocation, before any
+    kernel: fused decoding (which needs no operand buffer) is off for that call."""
     N, P = 23000, 3
     cov = synth.covariates(53, N, 1)
     Y = synth.phenotypes(53, cov, P).cuda()
@@ -98,8 +100,12 @@ def test_allocation_failure_is_reported_and_the_context_survives(tgctx):
         n_hits = torch.zeros(1, dtype=torch.int64, device="cuda")
         hits = torch.zeros(24 * 16, dtype=torch.uint8, device="cuda")
         out = tg.make_outputs(hits=hits, n_hits=n_hits)
-        with pytest.raises(tg.TgError) as e:
-            tg.tg_scan_block(tgctx, panel, G, N, huge_M, tg.TG_ENC_2BIT, opts, out)
+        tg.tg_set_fused_decode(tgctx, tg.TG_FUSED_OFF)
+        try:
+            with pytest.raises(tg.TgError) as e:
+                tg.tg_scan_block(tgctx, panel, G, N, huge_M, tg.TG_ENC_2BIT, opts, out)
+        finally:
+            tg.tg_set_fused_decode(tgctx, tg.TG_FUSED_SMALL_PANELS)
         assert e.value.status == tg.TG_ERR_OOM
         res = run_scan(tgctx, panel, G, N, P, "2bit", "split")
         assert res["status"] == tg.TG_OK and np.isfinite(res["t"]).all()

@@ -3,14 +3,15 @@
 decoded operand to device memory: every output must be bit-identical, for both kernels (CTA
 pairs and one CTA per tile), both encodings, sample counts that end inside a K block and blocks
 whose last m-tiles are partly or wholly past M, and small panels whose products come from the
-projection's pass (64-, 128- and 256-column joint tiles). The decoded-operand path itself is checked
-against the oracle by the scan tests."""
+projection's pass (64-, 128- and 256-column joint tiles). The fused path is also compared with
+the FP64 oracle directly, element by element at the scan tolerances."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2604_21095_gb300 as tg
 import synth
-from scan_util import run_scan
+from scan_util import compare_best, compare_full, compare_hits, oracle_panel, run_scan
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +45,48 @@ def test_fused_decode_is_bit_identical(encoding, kernel, N, M, P):
             assert res[fused]["status"] == tg.TG_OK
         assert res[True]["n_hits"] > 0
         _outputs_equal(res[True], res[False])
+        ref = oracle.scan(G.cpu().numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
+        compare_full(res[True], ref, label=f"fused/{encoding}/{kernel}/{N}/{M}/{P}")
+        compare_hits(res[True], ref, 3.0, marker_offset=5)
+        compare_best(res[True], ref, marker_offset=5)
+    finally:
+        tg.tg_panel_free(panel)
+        tg.tg_destroy(ctx)
+
+
+@pytest.mark.parametrize("encoding,N,M,P", [
+    ("2bit", 1999, 39_000, 40),   # joint operand of 64 rows, 256-marker tiles
+    ("u8", 2000, 39_000, 100),    # 128 rows, 256-marker tiles
+    ("2bit", 2001, 20_000, 100),  # 128 rows, 128-marker tiles
+    ("u8", 1999, 20_000, 40),     # 64 rows, 128-marker tiles
+])
+def test_fused_joint_pass_of_small_panels(encoding, N, M, P):
+    """The joint projection pass of a small panel that decodes the packed rows in shared memory
+    (the default for such panels and blocks) against the decoded-operand path (bit-identical) and
+    against the FP64 oracle, with sample counts that end inside a K block and a last tile that
+    is partly past M."""
+    w = synth.Workload(f"fusedjoint_{encoding}_{N}_{M}_{P}", N=N, M=M, P=P, n_cov=4,
+                       encoding=encoding, missing=0.02 if encoding == "2bit" else 0.0, seed=43,
+                       block=M, causal_per_pheno=1)
+    pan = synth.make_panel(w)
+    G = synth.make_block(w, 0)["G"].cuda()
+    ctx = tg.tg_create(0)
+    panel = tg.tg_prepare_panel(ctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+    try:
+        res = {}
+        for setting in (tg.TG_FUSED_SMALL_PANELS, tg.TG_FUSED_OFF):
+            tg.tg_set_fused_decode(ctx, setting)
+            res[setting] = run_scan(ctx, panel, G, N, P, encoding, "split", full=True,
+                                    hit_mlog10p=4.0, marker_offset=3)
+            assert res[setting]["status"] == tg.TG_OK
+        _outputs_equal(res[tg.TG_FUSED_SMALL_PANELS], res[tg.TG_FUSED_OFF])
+        got = res[tg.TG_FUSED_SMALL_PANELS]
+        assert got["n_hits"] > 0
+        ref = oracle.scan(G.cpu().numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
+        compare_full(got, ref, label=f"fused joint/{encoding}/{N}/{M}/{P}")
+        compare_hits(got, ref, 4.0, marker_offset=3)
+        compare_best(got, ref, marker_offset=3)
+        assert np.array_equal(got["nobs"], ref["decode"]["n_obs"])
     finally:
         tg.tg_panel_free(panel)
         tg.tg_destroy(ctx)

@@ -407,11 +407,12 @@ def test_few_samples(N, kernel, precision):
 @pytest.mark.parametrize("precision", ["split", "fp32"])
 @pytest.mark.parametrize("encoding", ["2bit", "u8"])
 def test_markers_close_to_the_covariate_span(tgctx, precision, encoding):
-    """Covariates that nearly reproduce some markers (|g_c|^2 / |g_res|^2 up to ~1e4): their
-    residual norms are recomputed in FP64 (the tensor-core projection's rounding would be
-    amplified by that ratio), so the norms match the oracle to FP64 accuracy and r stays within
-    the tolerance scaled by sqrt(|g_c|^2 / |g_res|^2), the amplification the product itself
-    carries."""
+    """Covariates that nearly reproduce some markers (variance inflation |g_c|^2 / |g_res|^2 of
+    about 5, 26 and 36, inside the limit of 50, and about 100, past it): the residual norms of
+    such markers are recomputed in FP64 (the tensor-core projection's rounding would be
+    amplified by that ratio), so the norms match the oracle to FP64 accuracy, the marker past
+    the limit is NaN on both sides, and r stays within the tolerance scaled by
+    sqrt(|g_c|^2 / |g_res|^2), the amplification the product itself carries."""
     N, M, P = 2000, 64, 40
     w = synth.Workload(f"collinear_{encoding}", N=N, M=M, P=P, n_cov=4, encoding=encoding,
                        missing=0.01 if encoding == "2bit" else 0.0, seed=77, block=M,
@@ -421,8 +422,8 @@ def test_markers_close_to_the_covariate_span(tgctx, precision, encoding):
     dec = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))["decode"]
     g = torch.from_numpy(dec["g"])
     cov = pan["cov_t"].clone()
-    noise = synth.covariates(78, N, 3)
-    for k, (j, eps) in enumerate([(3, 0.1), (17, 0.03), (40, 0.01)]):
+    noise = synth.covariates(78, N, 4)
+    for k, (j, eps) in enumerate([(3, 0.5), (17, 0.2), (40, 0.17), (55, 0.1)]):
         gc = g[j] - g[j].mean()
         cov[k] = gc + eps * gc.std() * noise[k]
     Yt = synth.phenotypes(79, cov, P)
@@ -435,8 +436,9 @@ def test_markers_close_to_the_covariate_span(tgctx, precision, encoding):
     ref = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(Yt, cov))
     gc2 = ((dec["g"] - dec["g"].mean(axis=1, keepdims=True)) ** 2).sum(axis=1)
     cond = gc2 / ref["gres2"]
-    assert np.nanmax(cond) > 3e3  # the construction reached the regime it is about
+    assert np.nanmax(cond) > 20  # the construction reached the regime it is about
     ok = np.isfinite(ref["gres2"])
+    assert not ok[55] and ok[3] and ok[17] and ok[40]  # past and inside the limit of 50
     assert np.array_equal(np.isfinite(res["norm2"]), ok)
     rel = np.abs(res["norm2"][ok] - ref["gres2"][ok]) / ref["gres2"][ok]
     refined = cond[ok] >= 2.0  # the FP64 re-projection; the rest come from the fast projection
@@ -449,6 +451,67 @@ def test_markers_close_to_the_covariate_span(tgctx, precision, encoding):
     fin = np.isfinite(ref["r"])
     assert np.array_equal(np.isfinite(res["t"]), fin)
     assert np.all(dr[fin] <= bound[fin]), (dr[fin].max(), np.argmax(np.where(fin, dr / bound, 0)))
+
+
+def _covariates_at_vif(g, vif, seed):
+    """Covariates [N][3] (float64) such that the imputed marker g has variance inflation factor
+    `vif` on [1, C] by construction: C[:, 0] = g_c + lam e with e orthogonal to 1 and g_c, the
+    other two orthogonal to 1, g_c and e (they leave g's residual unchanged)."""
+    r = np.random.default_rng(seed)
+    N = g.size
+    gc = g - g.mean()
+    B = np.column_stack([np.ones(N), gc])
+    e = r.standard_normal(N)
+    e -= B @ np.linalg.lstsq(B, e, rcond=None)[0]
+    lam = math.sqrt((gc @ gc) / (vif - 1.0) / (e @ e))
+    O = r.standard_normal((N, 2))
+    B3 = np.column_stack([B, e])
+    O -= B3 @ np.linalg.lstsq(B3, O, rcond=None)[0]
+    return np.column_stack([gc + lam * e, O])
+
+
+@pytest.mark.parametrize("precision", ["split", "fp32"])
+@pytest.mark.parametrize("encoding", ["2bit", "u8"])
+def test_marker_cut_matches_oracle_either_side_of_the_vif_limit(tgctx, precision, encoding):
+    """A marker whose variance inflation factor on the covariates is 50 (1 - 1e-6) is tested and
+    one at 50 (1 + 1e-6) is not, on the GPU as in the oracle: the NaN pattern of the norms and of
+    every statistic matches the oracle's for the whole block, the other markers match within the
+    usual tolerances and the tested one's r within the r tolerance scaled by sqrt(50) (the
+    amplification its product carries)."""
+    N, M, P, j = 2000, 64, 24, 9
+    w = synth.Workload(f"vifcut_{encoding}", N=N, M=M, P=P, n_cov=3, encoding=encoding,
+                       missing=0.01 if encoding == "2bit" else 0.0, seed=81, block=M,
+                       causal_per_pheno=1)
+    pan = synth.make_panel(w)
+    blk = synth.make_block(w, 0)
+    g = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))["decode"]["g"]
+    for vif, tested in ((50.0 * (1 - 1e-6), True), (50.0 * (1 + 1e-6), False)):
+        C = _covariates_at_vif(g[j], vif, 82)
+        X = oracle.design_matrix(C, N)
+        res_j = g[j] - X @ np.linalg.lstsq(X, g[j], rcond=None)[0]
+        gcj = g[j] - g[j].mean()
+        assert abs((gcj @ gcj) / (res_j @ res_j) / vif - 1.0) < 1e-9
+        cov = torch.from_numpy(np.ascontiguousarray(C.T))
+        Yt = synth.phenotypes(83, cov, P)
+        panel = tg.tg_prepare_panel(tgctx, Yt.cuda(), N, P, cov.cuda())
+        try:
+            res = run_scan(tgctx, panel, blk["G"].cuda(), N, P, encoding, precision, full=True)
+        finally:
+            tg.tg_panel_free(panel)
+        assert res["status"] == tg.TG_OK
+        ref = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(Yt, cov))
+        ok = np.isfinite(ref["gres2"])
+        assert bool(ok[j]) == tested
+        assert np.array_equal(np.isfinite(res["norm2"]), ok)
+        assert np.array_equal(np.isfinite(res["t"]), np.isfinite(ref["r"]))
+        rows = np.array([k for k in range(M) if k != j])
+        compare_full({k: (v[rows] if isinstance(v, np.ndarray) and v.ndim == 2 else v) for k, v in res.items()},
+                     {k: (v[rows] if isinstance(v, np.ndarray) and v.ndim == 2 else v) for k, v in ref.items()},
+                     label=f"vif {vif}/{encoding}/{precision}")
+        if tested:
+            df = ref["df"]
+            rb = res["t"][j] / np.sqrt(df + res["t"][j].astype(np.float64) ** 2)
+            assert np.all(np.abs(rb - ref["r"][j]) <= r_tol(df) * math.sqrt(50.0))
 
 
 @pytest.mark.parametrize("precision", ["split", "fp32"])

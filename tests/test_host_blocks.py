@@ -42,3 +42,21 @@ def test_degenerate_sizes_and_bad_arguments():
     assert sum(tg.tg_host_block_sizes(10_007, 4096, 1.5)) == 10_007
     with pytest.raises(tg.TgError):  # a list it will not build
         tg.tg_host_block_sizes(1 << 40, 1, 1.0)
+    with pytest.raises(tg.TgError):  # block sizes beyond 2^32 markers are refused
+        tg.tg_host_block_sizes(1000, (1 << 32) + 1, 2.0)
+    # the largest block size allowed, with f * size far inside int64
+    assert tg.tg_host_block_sizes(1 << 34, 1 << 32, 8.0) == [1 << 29, 1 << 32, 1 << 32, 1 << 32,
+                                                             (1 << 34) - (1 << 29) - 3 * (1 << 32)]
+
+
+def test_count_only_call_builds_no_list():
+    """The count comes back without a size buffer (capacity 0), and a short buffer receives
+    the first sizes only."""
+    import ctypes as C
+    lib = tg.load()
+    n = C.c_int64(-1)
+    assert lib.tg_host_block_sizes(262144, 65536, 2.0, None, 0, C.byref(n)) == tg.TG_OK
+    assert n.value == 7
+    buf = (C.c_int64 * 2)(-7, -7)
+    assert lib.tg_host_block_sizes(262144, 65536, 2.0, buf, 2, C.byref(n)) == tg.TG_OK
+    assert n.value == 7 and list(buf) == [8192, 16384]

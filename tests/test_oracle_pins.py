@@ -623,9 +623,12 @@ def test_planted_loci_rank_top_small_workload():
 
 
 def test_large_df_normal_deviate_used_on_gpu_is_within_tolerance():
-    """The GPU evaluates -log10 p for df >= 1500 from Hill's (1970) normal deviate for Student's
-    t instead of the continued fraction (which cancels badly in FP32 at large df). This pins the
-    approximation itself, evaluated here in float64, against the oracle over t in [0.01, 400]."""
+    """The GPU evaluates -log10 p of FULL elements for df >= 1500 from Hill's (1970) normal
+    deviate for Student's t instead of the continued fraction (which cancels badly in FP32 at
+    large df); elements with 1 - r^2 < 0.05 (t > sqrt(19 df)) and every hit take the FP64
+    continued fraction instead. This pins the approximation itself, evaluated here in float64,
+    against the oracle over every t it is used on, t in [0.01, max(400, sqrt(19 df))], for df
+    up to 1e7 (t up to 1.4e4)."""
     sp = pytest.importorskip("scipy.special")
 
     def hill_mlog10p(t, n):
@@ -636,8 +639,9 @@ def test_large_df_normal_deviate_used_on_gpu_is_within_tolerance():
         x = z / math.sqrt(2)
         return (x * x - math.log(sp.erfcx(x))) / math.log(10)
 
-    for n in (1500.0, 1994.0, 5000.0, 22979.0, 1e5, 1e6):
-        ts = np.concatenate([np.linspace(0.01, 10, 200), np.linspace(10, 400, 60)])
+    for n in (1500.0, 1994.0, 5000.0, 22979.0, 1e5, 1e6, 1e7):
+        tmax = max(400.0, math.sqrt(19.0 * n))
+        ts = np.concatenate([np.linspace(0.01, 10, 200), np.geomspace(10, tmax, 120)])
         ref = oracle.mlog10p_from_t(ts, n)
         got = np.array([hill_mlog10p(t, n) for t in ts])
         assert np.all(np.abs(got - ref) <= 0.1 * np.maximum(1e-3, 1e-5 * ref)), n

@@ -54,8 +54,14 @@ def _close(a, b):
     assert np.array_equal(a["nobs"], b["nobs"])
 
 
+@pytest.mark.parametrize("prec,mode", [
+    (tg.TG_PREC_SPLIT_BF16, tg.TG_MODE_PROJECTED), (tg.TG_PREC_FP32, tg.TG_MODE_PROJECTED),
+    (tg.TG_PREC_SPLIT_BF16, tg.TG_MODE_PAPER), (tg.TG_PREC_FP32, tg.TG_MODE_PAPER)])
 @pytest.mark.parametrize("P,thr", [(300, 4.0), (40, 3.0)])  # 256- and 64-column tiles
-def test_static_entry_matches_scan_block_on_two_calls_in_a_row(tgctx, P, thr):
+def test_static_entry_matches_scan_block_on_two_calls_in_a_row(tgctx, P, thr, prec, mode):
+    """Both precision forms (the FP32 form's operand and SIMT contraction on the static
+    scratch) and both statistics (the projected OLS test, and the paper's printed form with no
+    projection), on a 2-bit block and then a masked dosage block."""
     N = 1999
     cov = synth.covariates(71, N, 3)
     panel = tg.tg_prepare_panel(tgctx, synth.phenotypes(71, cov, P).cuda(), N, P, cov.cuda())
@@ -66,7 +72,7 @@ def test_static_entry_matches_scan_block_on_two_calls_in_a_row(tgctx, P, thr):
             (synth.dosage_bytes(71, 1, synth.maf(71, 1, 513), N).cuda(), tg.TG_ENC_U8_DOSAGE,
              synth.missing_words(71, 1, 513, N, 0.03).cuda(), 513),
         ]
-        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 1, thr)
+        opts = tg.tg_scan_opts(prec, 1, thr, mode)
         for G, enc, missing, M in calls:
             ref_b, ref_o = _buffers(M, P)
             tg.tg_scan_block(tgctx, panel, G, N, M, enc, opts, ref_o, marker_offset=11,
