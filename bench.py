@@ -631,11 +631,12 @@ def _ours_batched(args, dist, rank, ws, workload=None, steps=None, warmup=None, 
 
 
 def _kernel_profile():
-    """DRAM bytes per launch and the tensor pipe's active fraction of the elapsed cycles of the
-    contraction kernel, from the committed full-size ncu summary, if it was taken on the current
-    kernel sources (else an empty dict)."""
+    """DRAM bytes per launch (a small case of the same wave shape, scaled to one bench launch by
+    the tests it processes) and the tensor pipe's active fraction of the elapsed cycles of the
+    contraction kernel, from the committed ncu summary, if it was taken on the current kernel
+    sources (else an empty dict)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "tc2_scan_traffic_n23000_p20480_u8.md")
+    path = os.path.join(ROOT, "profiles", "tc2_scan_traffic_n23000_p4864_m19456_u8.md")
     csrc = os.path.join(ROOT, "paper_2604_21095_gb300", "csrc")
     try:
         h = hashlib.sha256(b"".join(open(os.path.join(csrc, f), "rb").read()
@@ -653,13 +654,25 @@ def _kernel_profile():
         return {}
 
 
-def _hbm_bytes_per_block(N: int, M: int, encoding: str, P: int, q: int) -> float:
-    """Algorithmic DRAM bytes of one block's scan when the decoded operand goes through HBM:
-    read the packed rows, write the 2-byte operand, read it once more for each pass over it
-    (one joint pass when the panel and the q - 1 projection columns fit a 256-column tile,
-    else the projection and the contraction), and read the bf16 hi + lo panel once."""
+def fused_joint(M: int, P: int, q: int, sm_count: int) -> bool:
+    """Whether the library scans a block with the decode fused into the small panel's joint
+    projection pass (its documented default: projected form, no mask, P + q - 1 <= 128 and at
+    least one 128-marker tile per SM)."""
+    return q > 1 and P + q - 1 <= 128 and (M + 127) // 128 >= sm_count
+
+
+def _hbm_bytes_per_block(N: int, M: int, encoding: str, P: int, q: int, fused: bool = False) -> float:
+    """Algorithmic DRAM bytes of one block's scan. With the decoded operand in HBM: read the
+    packed rows, write the 2-byte operand, read it once more for each pass over it (one joint
+    pass when the panel and the q - 1 projection columns fit a 256-column tile, else the
+    projection and the contraction), and read the bf16 hi + lo panel once. With the decode fused
+    into the joint pass: read the packed rows twice (the counting pass, then the joint pass)
+    and the joint operand (64 or 128 rows of hi + lo) once."""
     npad = (N + 63) // 64 * 64
     packed = M * (N if encoding == "u8" else (N + 3) // 4)
+    if fused:
+        jc = 64 if P + q - 1 <= 64 else 128
+        return 2 * packed + 2 * 2 * jc * npad
     operand = 2 * M * npad
     passes = 1 if P + q - 1 <= 256 else 2
     return packed + operand + passes * operand + 2 * 2 * P * npad
@@ -726,21 +739,24 @@ def _scan_points(w, Ps, dev, reps_for, flush_bytes=0):
         if tg.tg_status_poll(ctx, stream) != tg.TG_OK:
             raise RuntimeError(tg.tg_last_error())
         flops = 2.0 * w.N * M * P
-        byts = _hbm_bytes_per_block(w.N, M, w.encoding, P, q)
+        fz = fused_joint(M, P, q, torch.cuda.get_device_properties(dev).multi_processor_count)
+        byts = _hbm_bytes_per_block(w.N, M, w.encoding, P, q, fz)
         hbm_frac = byts / (ms / 1000.0) / 1e9 / float(peaks["hbm_gbs"])
         tflops = flops / (ms / 1000.0) / 1e12
         tens_frac = tflops / float(peaks["bf16_tflops"])
         hbm_bound = hbm_frac >= tens_frac
         points.append({
             "P": P, "ms_per_block": ms, "tests_per_s": M * P / (ms / 1000.0),
+            "decode": "fused into the joint pass" if fz else "decoded operand in HBM",
             "roofline": {"bound": "hbm" if hbm_bound else "tensor",
                          "achieved": byts / (ms / 1000.0) / 1e9 if hbm_bound else tflops,
                          "peak": float(peaks["hbm_gbs"]) if hbm_bound else float(peaks["bf16_tflops"]),
                          "unit": "GB/s" if hbm_bound else "TFLOP/s",
                          "frac": hbm_frac if hbm_bound else tens_frac,
-                         "basis": "whole step: algorithmic DRAM bytes (packed rows, operand written "
-                                  "and read per pass, panel) or Eq. 2 flops (2 N M P) per block, "
-                                  f"against the {src} HBM copy rate / burst bf16 rate"},
+                         "basis": "whole step: algorithmic DRAM bytes (packed rows read twice with "
+                                  "the fused decode; else packed rows, operand written and read per "
+                                  "pass; panel) or Eq. 2 flops (2 N M P) per block, against the "
+                                  f"{src} HBM copy rate / burst bf16 rate"},
             "stage_ms": {k: v[0] / reps for k, v in st.items() if v[1]}})
         n_hits.zero_()
         tg.tg_panel_free(panel)

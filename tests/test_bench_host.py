@@ -69,3 +69,21 @@ def test_replicas_partition_the_blocks():
     for ws in (1, 2, 3, 8):
         got = sorted(b for r in range(ws) for b in bench.rank_blocks(r, ws, 5))
         assert got == list(range(5 * ws))
+
+
+def test_fused_joint_rule_and_bytes():
+    """The bench counts the bytes of the path the library takes: the fused joint pass (the
+    packed rows read twice) for small panels on blocks of at least one 128-marker tile per SM,
+    else the decoded operand written and read per pass."""
+    import bench
+    assert bench.fused_joint(65536, 16, 20, 152) and bench.fused_joint(65536, 109, 20, 152)
+    assert not bench.fused_joint(65536, 110, 20, 152)   # P + q - 1 = 129 > 128
+    assert not bench.fused_joint(10000, 16, 5, 152)     # fewer 128-marker tiles than SMs
+    assert not bench.fused_joint(65536, 16, 1, 152)     # no covariate projection
+    N, M = 23000, 65536
+    fused = bench._hbm_bytes_per_block(N, M, "u8", 16, 20, True)
+    assert fused == 2 * M * N + 2 * 2 * 64 * 23040
+    plain = bench._hbm_bytes_per_block(N, M, "u8", 16, 20, False)
+    assert plain == M * N + 2 * (2 * M * 23040) + 2 * 2 * 16 * 23040
+    two_pass = bench._hbm_bytes_per_block(N, M, "2bit", 300, 20, False)
+    assert two_pass == M * 5750 + 3 * (2 * M * 23040) + 2 * 2 * 300 * 23040
