@@ -34,6 +34,8 @@ UNIT = "SNP-phenotype tests/s"
 WORKLOAD = "n23000_m8900000_p20480_c20_u8"
 THR = 7.30103  # -log10(5e-8)
 RESIDENT = 4   # distinct genotype blocks kept in HBM and cycled
+# ncu summary of the contraction kernel's DRAM traffic and tensor-pipe activity (profiles/)
+PROFILE_TRAFFIC = "tc2_scan_traffic_n23000_p4864_m19456_u8.md"
 
 
 def _args():
@@ -60,6 +62,11 @@ def _args():
                    help="instead of the bench line: time one block of the workload against panels "
                         "of growing P (the paper's Section 3.2 scaling in the number of phenotypes) "
                         "and print one JSON line with every point")
+    a.add_argument("--points", default=None,
+                   help="with --sweep-p: comma-separated panel sizes (default 16,40,64,100,200,256,"
+                        "1024,2048,4096,8192,20480)")
+    a.add_argument("--reps", type=int, default=None,
+                   help="with --sweep-p: timed scans per point (default from P)")
     return a.parse_args()
 
 
@@ -283,6 +290,33 @@ def _config(w):
                   f"{2 * w.block * w.N / 1e9:.2f} GB per block"}
 
 
+def sgemm_rate_tflops(dev, K: int) -> float:
+    """The FP32 rate of cuBLAS SGEMM on this GPU (TF32 off): 8,192 x 8,192 outputs over K, the
+    best of 3 timed calls after 2 warm-up calls (CUDA events). A library GEMM used only as the
+    FP32 scan's yardstick."""
+    import torch
+    prev = torch.get_float32_matmul_precision()
+    torch.set_float32_matmul_precision("highest")
+    try:
+        g = torch.Generator(device=dev).manual_seed(7)
+        a = torch.randn(8192, K, device=dev, generator=g)
+        b = torch.randn(K, 8192, device=dev, generator=g)
+        for _ in range(2):
+            torch.matmul(a, b)
+        best = float("inf")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b
+        return 2.0 * 8192 * 8192 * K / (best / 1000.0) / 1e12
+    finally:
+        torch.set_float32_matmul_precision(prev)
+
+
 def fp32_simt_peak_tflops(peaks) -> float:
     """FP32 FFMA peak of the SIMT cores: 152 SMs x 128 lanes x 2 flop per cycle at the maximum
     SM clock (80.5 TFLOP/s at 2,070 MHz)."""
@@ -381,14 +415,18 @@ def _ours(args, dist, rank, ws):
         ms32 = _max_over_ranks(dist, e0.elapsed_time(e1))
         k32 = st32["scan"][0] / max(1, st32["scan"][1])
         a32 = 2.0 * w.N * M * w.P / (k32 / 1000.0) / 1e12
-        p32 = fp32_simt_peak_tflops(_peaks()[0])
+        nominal32 = fp32_simt_peak_tflops(_peaks()[0])
+        sgemm = sgemm_rate_tflops(dev, (w.N + 63) // 64 * 64)
         fp32 = {"value": tests_step * args.fp32_steps * ws / (ms32 / 1000.0), "unit": UNIT,
                 "ms_per_step": ms32 / args.fp32_steps,
                 "scan_kernel_ms": k32,
-                "roofline": {"bound": "alu", "achieved": a32, "peak": p32, "unit": "TFLOP/s",
-                             "frac": a32 / p32,
-                             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FFMA) "
-                                            "x the maximum SM clock (not measured)"},
+                "roofline": {"bound": "alu", "achieved": a32, "peak": sgemm, "unit": "TFLOP/s",
+                             "frac": a32 / sgemm,
+                             "peak_source": "measured: cuBLAS SGEMM (TF32 off), 8192 x 8192 x "
+                                            "Npad on this GPU, best of 3",
+                             "nominal_peak": nominal32, "nominal_frac": a32 / nominal32,
+                             "nominal_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FFMA) "
+                                               "x the maximum SM clock"},
                 "stage_ms_per_step": {k: v[0] / args.fp32_steps for k, v in st32.items()}}
 
     # end to end through the host-buffer entry point: pinned host blocks in, hits and best out
@@ -636,7 +674,7 @@ def _kernel_profile():
     contraction kernel, from the committed ncu summary, if it was taken on the current kernel
     sources (else an empty dict)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "tc2_scan_traffic_n23000_p4864_m19456_u8.md")
+    path = os.path.join(ROOT, "profiles", PROFILE_TRAFFIC)
     csrc = os.path.join(ROOT, "paper_2604_21095_gb300", "csrc")
     try:
         h = hashlib.sha256(b"".join(open(os.path.join(csrc, f), "rb").read()
@@ -769,8 +807,11 @@ def _sweep_p(args):
     import torch
 
     w = _workload(args)
-    M, points = _scan_points(w, (16, 40, 64, 100, 200, 256, 1024, 2048, 4096, 8192, 20480),
-                             torch.device("cuda", 0), lambda P: max(3, min(50, int(20480 * 5 / P))))
+    Ps = tuple(int(x) for x in args.points.split(",")) if args.points else (
+        16, 40, 64, 100, 200, 256, 1024, 2048, 4096, 8192, 20480)
+    M, points = _scan_points(w, Ps, torch.device("cuda", 0),
+                             (lambda P: args.reps) if args.reps else
+                             (lambda P: max(3, min(50, int(20480 * 5 / P)))))
     print(json.dumps({"metric": "per-block scan time vs number of phenotypes", "unit": "ms",
                       "workload": f"{w.name}: one {M}-marker block, N={w.N}, C={w.n_cov + 1}",
                       "points": points}))

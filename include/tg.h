@@ -293,7 +293,10 @@ tg_status tg_host_block_sizes(int64_t M, int64_t block_markers, double factor, i
 /* Where split-form scans decode the genotypes inside the contraction kernels instead of first
  * writing the decoded operand (about 2 x round_up(N, 64) bytes per marker) to device memory.
  * The fused forms apply to 2-bit blocks and to dosage blocks without a missing mask (others always
- * use the decoded operand) and compute bit-identical results.
+ * use the decoded operand). They compute bit-identical results, except the small-panel pass on
+ * dosage blocks (enable = 2 or 1), which expands the bytes into f16 (b - c exactly) against an
+ * f16 hi + lo copy of the joint operand (about 22 significant bits against bf16's 16): its
+ * results differ from the decoded operand's within the float tolerance.
  *   enable = 2 (the default): only the joint projection pass of a small panel (projected mode,
  *     P + q - 1 <= 128, blocks of at least one 128-marker tile per SM), where the scan is one pass
  *     bound by the bytes it reads: the pass reads the packed rows (1 or 1/4 byte per sample)

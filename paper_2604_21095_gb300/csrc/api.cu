@@ -58,7 +58,8 @@ bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t
   return r == CUDA_SUCCESS;
 }
 bool make_tmap_packed(CUtensorMap* m, const void* ptr, int64_t rows, int64_t ld, uint32_t box_bytes,
-                      uint32_t box_rows) {
+                      uint32_t box_rows, bool swizzle64) {
+  if (swizzle64 && box_bytes != 64) return false;
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
@@ -66,7 +67,8 @@ bool make_tmap_packed(CUtensorMap* m, const void* ptr, int64_t rows, int64_t ld,
   cuuint32_t box[2] = {box_bytes, box_rows};
   cuuint32_t estr[2] = {1u, 1u};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(ptr), dims, strides, box,
-                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -309,7 +311,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   // at least one 128-marker tile per SM) reads the packed rows and decodes them in shared memory
   const bool fuse_joint = split && c->fuse_joint && a.missing == nullptr &&
                           a.opts.mode == TG_MODE_PROJECTED && p->q > 1 && p->joint_cols > 0 &&
-                          p->joint_cols <= 128 && (a.M + MT - 1) / MT >= c->sm_count;
+                          p->joint_cols <= 128 && p->QYhi16 != nullptr &&
+                          (a.M + MT - 1) / MT >= c->sm_count;
   // split-form 2-bit blocks and unmasked dosage blocks are decoded inside the contraction
   // kernels when the context asks for it; the rest go through a decoded operand in HBM
   const bool fused = split && a.missing == nullptr && (c->fuse_decode || fuse_joint);
@@ -347,7 +350,8 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     const bool u8 = a.encoding == TG_ENC_U8_DOSAGE;
     if (!make_tmap_packed(&da.tmG, a.G, a.M, a.ldg, u8 ? 32u : 16u) ||
         (fuse_joint && !make_tmap_packed(&dj.tmG, a.G, a.M, a.ldg, u8 ? 64u : 16u,
-                                         (uint32_t)joint_fused_rows(a.M, c->sm_count))))
+                                         (uint32_t)joint_fused_rows(a.M, c->sm_count, p->joint_cols),
+                                         u8)))
       return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the packed genotypes");
   }
   const DecodeArgs* dec = fused ? &da : nullptr;
@@ -374,8 +378,10 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       pp.raw_cols = pp.P;
       pp.raw_ld = (int)ldq;
       if (fuse_joint) {
-        TG_CUDA(launch_joint_fused(&p->tmQYhi, &p->tmQYlo, p->Npad, pp, c->sm_count, kSpinNs, st,
-                                   dj, a.encoding));
+        const bool u8 = a.encoding == TG_ENC_U8_DOSAGE;  // dosage rows: the f16 joint operand
+        if (u8) pp.col_cs = p->qycs16;
+        TG_CUDA(launch_joint_fused(u8 ? &p->tmQYhi16 : &p->tmQYhi, u8 ? &p->tmQYlo16 : &p->tmQYlo,
+                                   p->Npad, pp, c->sm_count, kSpinNs, st, dj, a.encoding));
       } else {
         const SplitChoice sc = pick_split(c, p, a.M, true, true);
         if (sc.ks > 1) {  // a small block: split K so that more SMs stream the operand
@@ -637,6 +643,18 @@ tg_status build_joint(tg_panel* p, cudaStream_t st) {
   if (!make_tmap(&p->tmQYhi, p->QYhi, jc, Np, Np, (uint32_t)jc) ||
       !make_tmap(&p->tmQYlo, p->QYlo, jc, Np, Np, (uint32_t)jc))
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the joint operand");
+  if (jc <= 128) {  // the f16 copy for the joint pass that decodes dosage rows in shared memory
+    if ((e = dalloc(&p->QYhi16, (size_t)(jc * Np))) || (e = dalloc(&p->QYlo16, (size_t)(jc * Np))) ||
+        (e = dalloc(&p->qycs16, (size_t)jc)) ||
+        (e = launch_joint_f16(p->Q, p->N, nq, p->Yres, p->s, p->col_rmul, P, jc, Np, p->QYhi16,
+                              p->QYlo16, p->qycs16, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return cuda_fail(e, "f16 joint projection and panel operand");
+    // 2-byte elements: the bf16 map layout serves (TMA copies bytes, it converts nothing)
+    if (!make_tmap(&p->tmQYhi16, p->QYhi16, jc, Np, Np, (uint32_t)jc) ||
+        !make_tmap(&p->tmQYlo16, p->QYlo16, jc, Np, Np, (uint32_t)jc))
+      return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the f16 joint operand");
+  }
   p->joint_cols = (int)jc;
   return TG_OK;
 }
@@ -893,6 +911,7 @@ tg_status tg_panel_free(tg_panel* p) {
   dfree(p->col_cs); dfree(p->qcs); dfree(p->samples);
   dfree(p->Bhi); dfree(p->Blo); dfree(p->B32); dfree(p->QB); dfree(p->QBhi); dfree(p->QBlo);
   dfree(p->QYhi); dfree(p->QYlo); dfree(p->qycs);
+  dfree(p->QYhi16); dfree(p->QYlo16); dfree(p->qycs16);
   delete p;
   return TG_OK;
 }

@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -23,6 +24,9 @@ constexpr int QMAX = 64;     // intercept + at most 63 covariates
 constexpr int QCOLS = 64;    // projection columns (Q columns 1..q-1), zero padded
 constexpr int JCOLS = 256;   // widest joint operand: projection columns + panel in one tile
 constexpr int MT = 128;      // marker rows per tensor-core tile
+// Scale of the f16 joint operand (k_joint_f16): values of at most 1 in magnitude become at most
+// 2^14, inside f16's range, with the low piece a normal number for |v| >= ~2^-25.
+constexpr double kJointF16Scale = 16384.0;
 
 enum Stage { STAGE_DECODE = 0, STAGE_PROJECT = 1, STAGE_NORM = 2, STAGE_GEMM = 3, STAGE_H2D = 4,
              STAGE_STATS = 5 };
@@ -161,6 +165,12 @@ struct tg_panel {
   __nv_bfloat16* QYlo = nullptr;
   float* qycs = nullptr;          // [joint_cols] qcs then col_cs
   CUtensorMap tmQYhi, tmQYlo;     // boxes of joint_cols rows
+  // The same joint operand as f16 hi + lo of 2^14 v (joint_cols <= 128 only), for the joint pass
+  // that decodes dosage rows in shared memory into f16 (k_fused.cu); scaled column sums.
+  __half* QYhi16 = nullptr;       // [joint_cols][Npad]
+  __half* QYlo16 = nullptr;
+  float* qycs16 = nullptr;        // [joint_cols]
+  CUtensorMap tmQYhi16, tmQYlo16;
 };
 
 struct tg_ctx {
@@ -235,9 +245,10 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* p, const ScanArgs& a, cudaStream_
 void mode_df(const tg_panel* p, int mode, double* df, double* lnB);
 bool make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t ld,
                uint32_t box_rows);
-// uint8 map over packed genotype rows [rows][ld], boxes of box_bytes x box_rows, zero fill.
+// uint8 map over packed genotype rows [rows][ld], boxes of box_bytes x box_rows, zero fill;
+// swizzle64: the 64-byte swizzle (box_bytes must be 64).
 bool make_tmap_packed(CUtensorMap* m, const void* ptr, int64_t rows, int64_t ld, uint32_t box_bytes,
-                      uint32_t box_rows = 128);
+                      uint32_t box_rows = 128, bool swizzle64 = false);
 
 // panel kernels (k_panel.cu)
 cudaError_t launch_build_design(double* X, const double* C, int64_t ldc, int64_t N, int64_t n_cov,
@@ -248,6 +259,11 @@ cudaError_t launch_residualise(const float* Y, int64_t ldy, const double* Q, int
                                int64_t q, int64_t Npad, double* Yres, double* s, float* col_s,
                                float* col_rmul, __nv_bfloat16* Bhi, __nv_bfloat16* Blo, float* B32,
                                float* col_cs, uint32_t* flags, cudaStream_t st);
+// The joint operand of a small panel as scaled f16 hi + lo (rows of the q - 1 projection columns,
+// then the P phenotypes, zero to `rows`), with its scaled column sums.
+cudaError_t launch_joint_f16(const double* Q, int64_t N, int64_t nq, const double* Yres,
+                             const double* s, const float* rmul, int64_t P, int64_t rows,
+                             int64_t Npad, __half* hi, __half* lo, float* cs, cudaStream_t st);
 cudaError_t launch_qcols(const double* Q, int64_t N, int64_t q, int64_t Npad, float* QB,
                          __nv_bfloat16* QBhi, __nv_bfloat16* QBlo, float* qcs, cudaStream_t st);
 // subset panels: rows gathered to a compact copy and scattered back (elements of 2, 4 or 8
@@ -315,9 +331,13 @@ cudaError_t launch_tc_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,
 
 // The joint projection pass of a small panel (joint operand of 64 or 128 rows) with the decode
 // fused in (k_fused.cu): reads the packed rows through da.tmG, whose boxes must be
-// joint_fused_rows(M, sm_count) rows of 64 bytes (dosage) or 16 bytes (2-bit calls); raw mode
-// only, no split-K, K a multiple of 64. Writes the same raw products as launch_tc_scan.
-int joint_fused_rows(int64_t M, int sm_count);
+// joint_fused_rows(M, sm_count, joint_cols) rows of 64 bytes with the 64-byte swizzle (dosage)
+// or 16 bytes (2-bit calls); raw mode only, no split-K, K a multiple of 64. Writes the raw
+// products launch_tc_scan writes.
+int joint_fused_rows(int64_t M, int sm_count, int joint_cols);
+// Dosage rows are expanded into f16 (b - c exact) against the f16 joint operand (tmBhi / tmBlo
+// then map QYhi16 / QYlo16 and ep.col_cs is qycs16; the raw products are scaled back by 2^-14);
+// 2-bit calls into bf16 against the bf16 joint operand.
 cudaError_t launch_joint_fused(const CUtensorMap* tmBhi, const CUtensorMap* tmBlo, int64_t K,
                                const EpiParams& ep, int sm_count, long long spin_ns, cudaStream_t st,
                                const DecodeArgs& da, int encoding);

@@ -14,6 +14,7 @@
 // full sample axis with zeros elsewhere (k_gather, k_scatter); k_pheno_masks gives each
 // phenotype's finite-value mask, from which such subsets are formed.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "device.cuh"
 #include "internal.h"
@@ -216,6 +217,45 @@ __global__ void k_qcols(const double* __restrict__ Q, long long N, int q, long l
   QBlo[o] = __double2bfloat16(v - (double)__bfloat162float(h));
 }
 
+// The joint operand of a small panel in f16, for the joint pass that decodes dosage rows in
+// shared memory (k_fused.cu): rows [0, nq) = Q columns 1..nq, rows [nq, nq + P) = the unit-norm
+// residualised phenotypes (0 for an untestable one), the rest 0; each value v (|v| <= 1) scaled
+// by 2^14 and split into hi = f16(2^14 v), lo = f16(2^14 v - hi), about 22 significant bits
+// (|2^14 v| <= 16,384, inside f16's range, and lo stays a normal number down to |v| ~ 2^-25).
+// cs[r] = sum_i (hi + lo) in FP64, rounded to FP32, the scaled column sum of the shift add-back.
+__global__ void __launch_bounds__(256) k_joint_f16(const double* __restrict__ Q, long long N, int nq,
+                                                   const double* __restrict__ Yres,
+                                                   const double* __restrict__ s,
+                                                   const float* __restrict__ rmul, int P,
+                                                   long long Npad, __half* __restrict__ hi,
+                                                   __half* __restrict__ lo, float* __restrict__ cs) {
+  __shared__ double red[33];
+  const int r = blockIdx.x;
+  const double* src = nullptr;
+  double mul = 0.0;
+  if (r < nq) {
+    src = Q + (long long)(r + 1) * N;
+    mul = kJointF16Scale;
+  } else if (r < nq + P) {
+    const int p = r - nq;
+    if (rmul[p] == rmul[p]) {  // a testable phenotype: y_res / s, as the bf16 panel
+      src = Yres + (long long)p * N;
+      mul = (1.0 / s[p]) * kJointF16Scale;
+    }
+  }
+  double sum = 0.0;
+  for (long long i = threadIdx.x; i < Npad; i += blockDim.x) {
+    const double u = (src && i < N) ? src[i] * mul : 0.0;
+    const __half h = __double2half(u);
+    const __half l = __double2half(u - (double)__half2float(h));
+    hi[(long long)r * Npad + i] = h;
+    lo[(long long)r * Npad + i] = l;
+    sum += (double)__half2float(h) + (double)__half2float(l);
+  }
+  sum = block_sum(sum, red);
+  if (threadIdx.x == 0) cs[r] = (float)sum;
+}
+
 // dst[r][i] = src[r * lds + idx[i]] for r < R, i < ns (rows of a compact copy).
 template <class T>
 __global__ void k_gather(const T* __restrict__ src, long long lds, T* __restrict__ dst, long long ldd,
@@ -321,6 +361,14 @@ cudaError_t launch_residualise(const float* Y, int64_t ldy, const double* Q, int
   if (P == 0) return cudaSuccess;
   k_residualise<<<(unsigned)P, 256, 0, st>>>(Y, ldy, Q, N, (int)q, Npad, Yres, s, col_s, col_rmul,
                                              Bhi, Blo, B32, col_cs, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_joint_f16(const double* Q, int64_t N, int64_t nq, const double* Yres,
+                             const double* s, const float* rmul, int64_t P, int64_t rows,
+                             int64_t Npad, __half* hi, __half* lo, float* cs, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  k_joint_f16<<<(unsigned)rows, 256, 0, st>>>(Q, N, (int)nq, Yres, s, rmul, (int)P, Npad, hi, lo, cs);
   return cudaGetLastError();
 }
 

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(256) k_marker_refine(MarkerRefine rf, const in
 // ---------------------------------------------------------------- FP32 scan
 constexpr int BM = 128, BN = 128, BK = 16;
 
-__global__ void __launch_bounds__(256, 1) k_sgemm_scan(const float* __restrict__ A, long long lda,
+__global__ void __launch_bounds__(256, 2) k_sgemm_scan(const float* __restrict__ A, long long lda,
                                                     const float* __restrict__ B, long long ldb,
                                                     int K, EpiParams ep) {
   __shared__ __align__(16) float As[2][BK][BM + 4];

@@ -52,6 +52,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16_m(int m, int n) {
          ((uint32_t)(m >> 4) << 24);
 }
 __host__ __device__ constexpr uint32_t idesc_bf16(int n) { return idesc_bf16_m(TBM, n); }
+// The same with A = B = F16 (type code 0 in bits 7-9 and 10-12), M = 128.
+__host__ __device__ constexpr uint32_t idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -198,7 +202,7 @@ __device__ __forceinline__ void dec_expand_store(uint32_t packed, uint2 k, bool 
   const uint32_t src = packed + (uint32_t)(r * BOX) + (OPA == OPA_2BIT ? 8u * (uint32_t)(kb & 1) : 0u);
   const uint32_t row_base = a_tile + (uint32_t)r * 64u;
   const uint32_t sw = (uint32_t)((r >> 1) & 3);
-#pragma unroll
+#pragma unroll 1  // rolled: unrolled, the dosage form spilled in the CTA-pair kernel
   for (int h = 0; h < 2; ++h) {
     uint32_t o[8];
     if (OPA == OPA_2BIT) {

@@ -24,7 +24,7 @@ def _fake_repo(tmp_path, sha):
     (csrc / "tc_common.cuh").write_bytes(b"header b")
     prof = tmp_path / "profiles"
     prof.mkdir()
-    (prof / "tc2_scan_traffic_n23000_p20480_u8.md").write_text(
+    (prof / bench.PROFILE_TRAFFIC).write_text(
         "# title: with a colon\n\n| metric | value |\n|---|---|\n| a: b | c |\n\n"
         "Workload: something\n"
         "dram_bytes_per_launch: 123456\n"
@@ -46,8 +46,7 @@ def test_kernel_profile_needs_the_sources_it_was_taken_on(tmp_path, monkeypatch)
 
 def test_committed_profile_parses():
     rec = {}
-    path = os.path.join(os.path.dirname(bench.__file__), "profiles",
-                        "tc2_scan_traffic_n23000_p20480_u8.md")
+    path = os.path.join(os.path.dirname(bench.__file__), "profiles", bench.PROFILE_TRAFFIC)
     for line in open(path):
         if ":" in line and not line.startswith(("|", "#", " ")):
             k, v = line.split(":", 1)

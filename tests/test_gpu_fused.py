@@ -62,9 +62,11 @@ def test_fused_decode_is_bit_identical(encoding, kernel, N, M, P):
 ])
 def test_fused_joint_pass_of_small_panels(encoding, N, M, P):
     """The joint projection pass of a small panel that decodes the packed rows in shared memory
-    (the default for such panels and blocks) against the decoded-operand path (bit-identical) and
-    against the FP64 oracle, with sample counts that end inside a K block and a last tile that
-    is partly past M."""
+    (the default for such panels and blocks) against the FP64 oracle and the decoded-operand
+    path, with sample counts that end inside a K block and a last tile that is partly past M.
+    2-bit calls take the same bf16 values as the decoded operand, so their results are
+    bit-identical to it; dosage bytes are expanded into f16 against an f16 hi + lo joint operand
+    (a different split of the panel), so both paths are held to the oracle's tolerances."""
     w = synth.Workload(f"fusedjoint_{encoding}_{N}_{M}_{P}", N=N, M=M, P=P, n_cov=4,
                        encoding=encoding, missing=0.02 if encoding == "2bit" else 0.0, seed=43,
                        block=M, causal_per_pheno=1)
@@ -79,14 +81,16 @@ def test_fused_joint_pass_of_small_panels(encoding, N, M, P):
             res[setting] = run_scan(ctx, panel, G, N, P, encoding, "split", full=True,
                                     hit_mlog10p=4.0, marker_offset=3)
             assert res[setting]["status"] == tg.TG_OK
-        _outputs_equal(res[tg.TG_FUSED_SMALL_PANELS], res[tg.TG_FUSED_OFF])
         got = res[tg.TG_FUSED_SMALL_PANELS]
+        if encoding == "2bit":
+            _outputs_equal(got, res[tg.TG_FUSED_OFF])
         assert got["n_hits"] > 0
         ref = oracle.scan(G.cpu().numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
-        compare_full(got, ref, label=f"fused joint/{encoding}/{N}/{M}/{P}")
-        compare_hits(got, ref, 4.0, marker_offset=3)
-        compare_best(got, ref, marker_offset=3)
-        assert np.array_equal(got["nobs"], ref["decode"]["n_obs"])
+        for setting, r in res.items():
+            compare_full(r, ref, label=f"fused joint {setting}/{encoding}/{N}/{M}/{P}")
+            compare_hits(r, ref, 4.0, marker_offset=3)
+            compare_best(r, ref, marker_offset=3)
+            assert np.array_equal(r["nobs"], ref["decode"]["n_obs"])
     finally:
         tg.tg_panel_free(panel)
         tg.tg_destroy(ctx)
