@@ -49,9 +49,18 @@ typedef enum {
 } tg_status;
 
 typedef enum {
-  TG_PREC_FP32 = 0,      /* FP32 operands, FP32 SIMT contraction */
-  TG_PREC_SPLIT_BF16 = 1 /* exact BF16 genotype codes, panel split into BF16 hi + lo,
-                            two tcgen05 tensor-core products accumulated in FP32 */
+  TG_PREC_FP32 = 0,       /* FP32 operands, FP32 SIMT contraction */
+  TG_PREC_SPLIT_BF16 = 1, /* exact BF16 genotype codes, panel split into BF16 hi + lo,
+                             two tcgen05 tensor-core products accumulated in FP32 */
+  TG_PREC_FP4_PIECES = 2  /* experimental, 2-bit calls only: exact E2M1 genotype counts, each
+                             panel column scaled by a power of two and split into 6 E2M1 pieces
+                             (piece k at scale 8^-k), block-scaled tcgen05 kind::mxf4 products
+                             accumulated in FP32. A marker with a missing call has no test in this
+                             form (NaN outputs, no hit): the E2M1 operand cannot hold its imputed
+                             mean. The pieces of a panel (6 x round_up(P, 256) x round_up(N, 64) / 2
+                             bytes) are built on its first FP4 scan, synchronously. Dosage blocks,
+                             subset panels, tg_scan_block_static and captured graphs give
+                             TG_ERR_UNSUPPORTED. */
 } tg_precision;
 
 typedef enum {

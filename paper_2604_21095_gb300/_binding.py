@@ -15,7 +15,7 @@ from . import build as _build
 
 TG_OK, TG_ERR_INVALID_ARG, TG_ERR_CUDA, TG_ERR_OOM, TG_ERR_NONFINITE, TG_ERR_RANK, \
     TG_ERR_CAPACITY, TG_ERR_TIMEOUT, TG_ERR_UNSUPPORTED = range(9)
-TG_PREC_FP32, TG_PREC_SPLIT_BF16 = 0, 1
+TG_PREC_FP32, TG_PREC_SPLIT_BF16, TG_PREC_FP4_PIECES = 0, 1, 2
 TG_ENC_2BIT, TG_ENC_U8_DOSAGE = 0, 1
 TG_MODE_PROJECTED, TG_MODE_PAPER = 0, 1
 TG_N_STAGES = 6

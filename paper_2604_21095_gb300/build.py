@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtg.so")
 SOURCES = ["api.cu", "api_static.cu", "k_panel.cu", "k_decode.cu", "k_simt.cu", "k_tc.cu",
-           "k_tc2.cu", "k_stats.cu", "k_fused.cu"]
+           "k_tc2.cu", "k_stats.cu", "k_fused.cu", "k_fp4.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

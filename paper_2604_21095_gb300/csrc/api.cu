@@ -263,8 +263,14 @@ namespace tg {
 tg_status check_scan_args(const tg_ctx* c, const tg_panel* p, const ScanArgs& a) {
   TG_ARG(c && p, "null context or panel");
   TG_ARG(a.encoding == TG_ENC_2BIT || a.encoding == TG_ENC_U8_DOSAGE, "unknown encoding");
-  TG_ARG(a.opts.precision == TG_PREC_FP32 || a.opts.precision == TG_PREC_SPLIT_BF16,
+  TG_ARG(a.opts.precision == TG_PREC_FP32 || a.opts.precision == TG_PREC_SPLIT_BF16 ||
+             a.opts.precision == TG_PREC_FP4_PIECES,
          "unknown precision");
+  if (a.opts.precision == TG_PREC_FP4_PIECES) {
+    if (a.encoding != TG_ENC_2BIT)
+      return fail(TG_ERR_UNSUPPORTED, "the FP4 form scans 2-bit calls only (dosage bytes are not E2M1 values)");
+    if (p->samples) return fail(TG_ERR_UNSUPPORTED, "the FP4 form does not scan subset panels");
+  }
   TG_ARG(a.opts.mode == TG_MODE_PROJECTED || a.opts.mode == TG_MODE_PAPER, "unknown mode");
   TG_ARG(a.opts.reserved == 0, "tg_scan_opts.reserved must be 0");
   TG_ARG(a.opts.mode == TG_MODE_PROJECTED || a.N > 2, "the paper's form needs N > 2");
@@ -302,9 +308,146 @@ float r2_threshold(double mlog10p, double df, double lnB) {
 
 namespace tg {
 
+// The E2M1 pieces of a panel for the FP4 form, built on its first FP4 scan (synchronous).
+tg_status ensure_fp4_panel(tg_ctx* c, tg_panel* p, cudaStream_t st) {
+  if (p->fp4B) return TG_OK;
+  if (c->graphs_alive > 0)
+    return fail(TG_ERR_INVALID_ARG, "the FP4 pieces of a panel are built outside captured graphs");
+  const int64_t Np = p->Npad, Pp = p->Ppad, nb = p->Npad / 2;
+  cudaError_t e;
+  auto undo = [&]() {
+    dfree(p->fp4B); dfree(p->fp4B_scale); dfree(p->fp4B_cs);
+    dfree(p->fp4Q); dfree(p->fp4Q_scale); dfree(p->fp4Q_cs);
+    p->fp4B = nullptr; p->fp4Q = nullptr;
+  };
+  if ((e = dalloc(&p->fp4B, (size_t)(kFp4Pieces * Pp * nb))) || (e = dalloc(&p->fp4B_scale, (size_t)Pp)) ||
+      (e = dalloc(&p->fp4B_cs, (size_t)Pp)) || (e = dalloc(&p->fp4Q, (size_t)(kFp4Pieces * QCOLS * nb))) ||
+      (e = dalloc(&p->fp4Q_scale, (size_t)QCOLS)) || (e = dalloc(&p->fp4Q_cs, (size_t)QCOLS))) {
+    undo();
+    return cuda_fail(e, "FP4 panel pieces allocation");
+  }
+  if ((e = launch_fp4_pieces(p->Yres, p->N, p->s, p->col_rmul, p->P, Pp, p->N, Np, p->fp4B,
+                             p->fp4B_scale, p->fp4B_cs, st)) ||
+      (e = launch_fp4_pieces(p->Q + p->N, p->N, nullptr, nullptr, p->q - 1, QCOLS, p->N, Np, p->fp4Q,
+                             p->fp4Q_scale, p->fp4Q_cs, st)) ||
+      (e = cudaStreamSynchronize(st))) {
+    undo();
+    return cuda_fail(e, "FP4 panel pieces");
+  }
+  if (!make_tmap_packed(&p->tmFB, p->fp4B, kFp4Pieces * Pp, nb, 64u, 128u, true) ||
+      !make_tmap_packed(&p->tmFQ, p->fp4Q, kFp4Pieces * QCOLS, nb, 64u, 64u, true)) {
+    undo();
+    return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the FP4 pieces");
+  }
+  return TG_OK;
+}
+
+// The FP4 form of a block scan (2-bit calls): counting decode, E2M1 operand, projection and
+// contraction on kind::mxf4 tensor cores, norms (markers with a missing call untestable), then
+// the same statistics as the split form.
+tg_status scan_fp4(tg_ctx* c, tg_panel* p, const ScanArgs& a, cudaStream_t st) {
+  const tg_status ps = ensure_fp4_panel(c, p, st);
+  if (ps != TG_OK) return ps;
+  TG_CUDA(ensure_markers(c, a.M));
+  const int64_t lda = p->Npad / 2;
+  const int64_t need = round_up(a.M, MT) * lda;
+  if (need > c->cap_fp4) {
+    if (c->graphs_alive > 0)
+      return fail(TG_ERR_INVALID_ARG, "the context's workspace is held by a captured scan graph");
+    dfree(c->Afp4);
+    c->Afp4 = nullptr;
+    c->cap_fp4 = 0;
+    TG_CUDA(dalloc(&c->Afp4, (size_t)need));
+    c->cap_fp4 = need;
+  }
+  {
+    StageScope s(c, STAGE_DECODE, st, 2);
+    TG_CUDA(launch_decode(a.G, a.ldg, a.encoding, a.N, a.M, nullptr, 0, TG_PREC_SPLIT_BF16, nullptr,
+                          c->shift, c->mh, p->Npad, c->nobs, nullptr, nullptr, c->mean, c->gc2, st));
+    TG_CUDA(launch_fp4_codes(a.G, a.ldg, a.N, a.M, c->Afp4, lda, c->mean, c->shift, st));
+  }
+  CUtensorMap tA;
+  if (!make_tmap_packed(&tA, c->Afp4, a.M, lda, 64u, (uint32_t)MT, true))
+    return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the E2M1 operand");
+  const int64_t nq = a.opts.mode == TG_MODE_PAPER ? 0 : p->q - 1;
+  if (nq > 0) {
+    StageScope s(c, STAGE_PROJECT, st, 1);
+    EpiParams pp{};
+    pp.M = (int)a.M;
+    pp.P = (int)nq;
+    pp.status = c->status;
+    pp.row_shift = c->shift;
+    pp.col_cs = p->fp4Q_cs;
+    pp.col_rmul = p->fp4Q_scale;
+    pp.raw_out = c->qg;
+    pp.raw_cols = (int)nq;
+    pp.raw_ld = QCOLS;
+    TG_CUDA(launch_fp4_scan(&tA, &p->tmFQ, QCOLS, p->Npad, pp, c->sm_count, kSpinNs, st));
+  }
+  {
+    StageScope s(c, STAGE_NORM, st, nq > 0 ? 2 : 1);
+    const MarkerRefine rf{a.G, a.ldg, a.encoding, a.N, nullptr, 0, c->mean, p->Q, (int)p->q,
+                          c->refine_list, c->scratch + 40};
+    TG_CUDA(launch_marker_norm(a.M, c->nobs, c->gc2, c->qg, QCOLS, nq, 1.0, c->gres2,
+                               a.out.marker_norm2, c->rinv, c->rinv64, &rf, st, a.N));
+    if (a.out.marker_nobs)
+      TG_CUDA(cudaMemcpyAsync(a.out.marker_nobs, c->nobs, sizeof(int32_t) * a.M,
+                              cudaMemcpyDeviceToDevice, st));
+    if (a.out.marker_mean)
+      TG_CUDA(cudaMemcpyAsync(a.out.marker_mean, c->mean, sizeof(double) * a.M,
+                              cudaMemcpyDeviceToDevice, st));
+  }
+  EpiParams ep{};
+  ep.M = (int)a.M;
+  ep.P = (int)p->P;
+  ep.marker_offset = a.marker_offset;
+  mode_df(p, a.opts.mode, &ep.df, &ep.lnB);
+  ep.df_f = (float)ep.df;
+  ep.kappa = 1.0f;
+  ep.kappa64 = 1.0;
+  ep.do_hits = a.opts.hit_mlog10p > 0.0 && a.out.n_hits != nullptr;
+  ep.r2_thr = ep.do_hits ? (float)host_r2_threshold(a.opts.hit_mlog10p, ep.df, ep.lnB) : 2.0f;
+  ep.do_full = a.opts.full_output ? 1 : 0;
+  ep.do_best = a.out.best != nullptr;
+  ep.row_inv = c->rinv;
+  ep.row_inv64 = c->rinv64;
+  ep.exact = ExactArgs{a.G, a.ldg, a.encoding, (int)a.N, nullptr, 0, c->mean, p->Yres, p->N};
+  ep.col_s = p->col_s;
+  ep.col_s64 = p->s;
+  ep.col_rmul = p->fp4B_scale;  // 2^-e of each column's pieces, NaN for an untestable phenotype
+  ep.row_shift = c->shift;      // -mean: the centring add-back
+  ep.col_cs = p->fp4B_cs;
+  ep.beta = a.out.beta;
+  ep.se = a.out.se;
+  ep.t = a.out.t;
+  ep.mlp = a.out.mlog10p;
+  ep.rstore = a.out.t ? a.out.t : a.out.mlog10p ? a.out.mlog10p : a.out.beta ? a.out.beta : a.out.se;
+  ep.ldo = a.out.ldo;
+  ep.hits = a.out.hits;
+  ep.hit_cap = a.out.hit_capacity;
+  ep.n_hits = a.out.n_hits;
+  ep.best = a.out.best;
+  ep.status = c->status;
+  unsigned long long* hit_start = reinterpret_cast<unsigned long long*>(c->scratch + 16);
+  if (ep.do_hits)
+    TG_CUDA(cudaMemcpyAsync(hit_start, ep.n_hits, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, st));
+  {
+    StageScope s(c, STAGE_GEMM, st, 1);
+    TG_CUDA(launch_fp4_scan(&tA, &p->tmFB, (int)p->Ppad, p->Npad, ep, c->sm_count, kSpinNs, st));
+  }
+  if (ep.do_hits || ep.do_full) {
+    StageScope s(c, STAGE_STATS, st, (ep.do_hits ? 1 : 0) + (ep.do_full ? 1 : 0));
+    if (ep.do_hits) TG_CUDA(launch_hit_stats(ep, hit_start, st));
+    if (ep.do_full) TG_CUDA(launch_full_stats(ep, st));
+  }
+  return TG_OK;
+}
+
 tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream_t st) {
   tg_panel* p = const_cast<tg_panel*>(pc);
   if (a.M == 0) return TG_OK;
+  if (a.opts.precision == TG_PREC_FP4_PIECES) return scan_fp4(c, p, a, st);
   const int prec = a.opts.precision;
   const bool split = prec == TG_PREC_SPLIT_BF16;
   // a small panel's joint projection pass (projected form, joint operand of at most 128 rows,
@@ -597,7 +740,7 @@ tg_status tg_destroy(tg_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   dfree(c->status); dfree(c->scratch);
-  dfree(c->Ahi); dfree(c->A32); dfree(c->shift); dfree(c->mh); dfree(c->gc2s);
+  dfree(c->Ahi); dfree(c->A32); dfree(c->Afp4); dfree(c->shift); dfree(c->mh); dfree(c->gc2s);
   dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
   dfree(c->rinv); dfree(c->rinv64); dfree(c->refine_list);
   dfree(c->sk_ws); dfree(c->sk_cnt);
@@ -912,6 +1055,8 @@ tg_status tg_panel_free(tg_panel* p) {
   dfree(p->Bhi); dfree(p->Blo); dfree(p->B32); dfree(p->QB); dfree(p->QBhi); dfree(p->QBlo);
   dfree(p->QYhi); dfree(p->QYlo); dfree(p->qycs);
   dfree(p->QYhi16); dfree(p->QYlo16); dfree(p->qycs16);
+  dfree(p->fp4B); dfree(p->fp4B_scale); dfree(p->fp4B_cs);
+  dfree(p->fp4Q); dfree(p->fp4Q_scale); dfree(p->fp4Q_cs);
   delete p;
   return TG_OK;
 }
@@ -1315,6 +1460,8 @@ tg_status tg_scan_graph_create(tg_ctx* c, const tg_panel* p, int n_blocks,
                                const tg_scan_opts* opts, const tg_outputs* out, tg_graph** graph) {
   TG_ARG(c && p && G && M && marker_offset && opts && out && graph && n_blocks >= 1, "bad arguments");
   *graph = nullptr;
+  if (opts->precision == TG_PREC_FP4_PIECES)
+    return fail(TG_ERR_UNSUPPORTED, "the FP4 form is not captured in scan graphs");
   TG_ARG(!opts->full_output, "captured scan graphs collect hits and best markers only");
   TG_ARG(!out->marker_norm2 && !out->marker_nobs && !out->marker_mean,
          "per-marker outputs are not supported in captured scan graphs");
@@ -1379,6 +1526,8 @@ tg_status tg_scan_graph_create_host(tg_ctx* c, const tg_panel* p, int n_blocks,
   TG_ARG(c && p && G_host && M && marker_offset && opts && out && graph && n_blocks >= 1,
          "bad arguments");
   *graph = nullptr;
+  if (opts->precision == TG_PREC_FP4_PIECES)
+    return fail(TG_ERR_UNSUPPORTED, "the FP4 form is not captured in scan graphs");
   TG_ARG(!opts->full_output, "captured scan graphs collect hits and best markers only");
   TG_ARG(!out->marker_norm2 && !out->marker_nobs && !out->marker_mean,
          "per-marker outputs are not supported in captured scan graphs");

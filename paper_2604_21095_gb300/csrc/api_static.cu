@@ -114,6 +114,8 @@ extern "C" tg_status tg_scan_block_static(const tg_panel* p, const uint8_t* G, i
   if (encoding != TG_ENC_2BIT && encoding != TG_ENC_U8_DOSAGE)
     return fail(TG_ERR_INVALID_ARG, "unknown encoding");
   const int prec = opts->precision;
+  if (prec == TG_PREC_FP4_PIECES)
+    return fail(TG_ERR_UNSUPPORTED, "the FP4 form is scanned with tg_scan_block, not the static form");
   if (prec != TG_PREC_FP32 && prec != TG_PREC_SPLIT_BF16) return fail(TG_ERR_INVALID_ARG, "unknown precision");
   if ((opts->mode != TG_MODE_PROJECTED && opts->mode != TG_MODE_PAPER) || opts->reserved != 0)
     return fail(TG_ERR_INVALID_ARG, "unknown mode (or tg_scan_opts.reserved != 0)");

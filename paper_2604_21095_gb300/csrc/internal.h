@@ -24,6 +24,7 @@ constexpr int QMAX = 64;     // intercept + at most 63 covariates
 constexpr int QCOLS = 64;    // projection columns (Q columns 1..q-1), zero padded
 constexpr int JCOLS = 256;   // widest joint operand: projection columns + panel in one tile
 constexpr int MT = 128;      // marker rows per tensor-core tile
+constexpr int kFp4Pieces = 6;  // E2M1 pieces of the panel in the FP4 form (k_fp4.cu)
 // Scale of the f16 joint operand (k_joint_f16): values of at most 1 in magnitude become at most
 // 2^14, inside f16's range, with the low piece a normal number for |v| >= ~2^-25.
 constexpr double kJointF16Scale = 16384.0;
@@ -171,6 +172,16 @@ struct tg_panel {
   __half* QYlo16 = nullptr;
   float* qycs16 = nullptr;        // [joint_cols]
   CUtensorMap tmQYhi16, tmQYlo16;
+  // The FP4 form's E2M1 pieces (built on the panel's first FP4 scan): the panel's columns
+  // [kFp4Pieces][Ppad][Npad/2] and the projection columns [kFp4Pieces][QCOLS][Npad/2], each with
+  // its column scale 2^-e (NaN: no test) and scaled column sum.
+  uint8_t* fp4B = nullptr;
+  float* fp4B_scale = nullptr;
+  float* fp4B_cs = nullptr;
+  uint8_t* fp4Q = nullptr;
+  float* fp4Q_scale = nullptr;
+  float* fp4Q_cs = nullptr;
+  CUtensorMap tmFB, tmFQ;
 };
 
 struct tg_ctx {
@@ -182,6 +193,8 @@ struct tg_ctx {
   // decode / projection workspace
   int64_t cap_rows = 0, cap_npad = 0;          // A buffers: rows x npad
   __nv_bfloat16* Ahi = nullptr;                 // centred split operand
+  uint8_t* Afp4 = nullptr;                      // E2M1 operand of the FP4 form
+  int64_t cap_fp4 = 0;                          // its bytes
   float* A32 = nullptr;
   int64_t cap_m = 0;                            // per-marker arrays
   int32_t* nobs = nullptr;
@@ -307,10 +320,11 @@ struct MarkerRefine {
   int* list;
   unsigned* count;
 };
+// complete_n > 0: markers with fewer than complete_n observed calls are untestable too.
 cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
                                int64_t ldq, int64_t nq, double kappa, double* gres2_units_out,
                                double* norm2_allele_out, float* rinv, double* rinv64,
-                               const MarkerRefine* refine, cudaStream_t st);
+                               const MarkerRefine* refine, cudaStream_t st, int64_t complete_n = 0);
 cudaError_t launch_sgemm_scan(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t K,
                               const EpiParams& ep, cudaStream_t st);
 
@@ -346,6 +360,22 @@ cudaError_t launch_joint_fused(const CUtensorMap* tmBhi, const CUtensorMap* tmBl
 // marker row m and phenotype p at raw[m * ld + p] (the shift's add-back included), the same
 // per-element epilogue as the contraction kernels.
 cudaError_t launch_raw_stats(const float* raw, int64_t ld, const EpiParams& ep, cudaStream_t st);
+
+// The FP4 form (k_fp4.cu). Pieces: rows r < nrows of src (stride lds; divided by div[r] when
+// div is not NULL; skipped where valid[r] is NaN) as kFp4Pieces E2M1 pieces, out[k][rows_pad][Npad/2]
+// bytes, with scale[r] = 2^-e (NaN for a skipped row) and cs[r] = the scaled column sum.
+cudaError_t launch_fp4_pieces(const double* src, int64_t lds, const double* div, const float* valid,
+                              int64_t nrows, int64_t rows_pad, int64_t N, int64_t Npad, uint8_t* out,
+                              float* scale, float* cs, cudaStream_t st);
+// 2-bit calls to the E2M1 operand [M][lda] bytes (lda = Npad / 2), and shift[j] = -mean[j].
+cudaError_t launch_fp4_codes(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, uint8_t* A,
+                             int64_t lda, const double* mean, float* shift, cudaStream_t st);
+// The contraction: tmA over the E2M1 operand (boxes of 64 bytes x 128 rows, 64-byte swizzle),
+// tmB over kFp4Pieces x b_rows_pad piece rows (boxes of 64 bytes x 128 rows, or 64 rows in raw
+// mode: the covariate projection, at most 64 columns).
+cudaError_t launch_fp4_scan(const CUtensorMap* tmA, const CUtensorMap* tmB, int b_rows_pad,
+                            int64_t Npad, const EpiParams& ep, int sm_count, long long spin_ns,
+                            cudaStream_t st);
 
 // tensor-core kernel on CTA pairs, 256 x 256 tiles (k_tc2.cu)
 cudaError_t launch_tc2_scan(const CUtensorMap* tmA, const CUtensorMap* tmBhi,

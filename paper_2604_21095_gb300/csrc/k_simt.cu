@@ -102,6 +102,11 @@ constexpr double kMaxVif = 50.0;
 __device__ __forceinline__ bool marker_testable(int n_obs, double c2, double r2) {
   return n_obs > 0 && c2 > 0.0 && kMaxVif * r2 >= c2;
 }
+// complete_n > 0: a marker must also have all complete_n calls observed (the FP4 form, whose
+// operand cannot hold a missing call's imputed mean).
+__device__ __forceinline__ bool marker_testable(int n_obs, double c2, double r2, int complete_n) {
+  return marker_testable(n_obs, c2, r2) && (complete_n <= 0 || n_obs == complete_n);
+}
 
 __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
                               const double* __restrict__ gc2, const float* __restrict__ qg,
@@ -109,7 +114,7 @@ __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
                               double kappa, double* __restrict__ gres2u,
                               double* __restrict__ norm2_allele, float* __restrict__ rinv,
                               double* __restrict__ rinv64, int* __restrict__ refine_list,
-                              unsigned* __restrict__ refine_count) {
+                              unsigned* __restrict__ refine_count, int complete_n) {
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (j >= M) return;
   const double c2 = gc2[j];
@@ -119,7 +124,7 @@ __global__ void k_marker_norm(long long M, const int32_t* __restrict__ nobs,
     s += v * v;
   }
   const double r2 = c2 - s;
-  const bool ok = marker_testable(nobs[j], c2, r2);
+  const bool ok = marker_testable(nobs[j], c2, r2, complete_n);
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   const double inv = ok ? 1.0 / sqrt(r2) : nan;
   gres2u[j] = ok ? r2 : nan;
@@ -140,7 +145,8 @@ __global__ void __launch_bounds__(256) k_marker_refine(MarkerRefine rf, const in
                                                        double* __restrict__ gres2u,
                                                        double* __restrict__ norm2_allele,
                                                        float* __restrict__ rinv,
-                                                       double* __restrict__ rinv64) {
+                                                       double* __restrict__ rinv64,
+                                                       int complete_n) {
   __shared__ double red[8];
   const unsigned n = *rf.count;
   for (unsigned li = blockIdx.x; li < n; li += gridDim.x) {
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(256) k_marker_refine(MarkerRefine rf, const in
     if (threadIdx.x == 0) {
       const double c2 = gc2[j];
       const double r2 = c2 - s;
-      const bool ok = marker_testable(nobs[j], c2, r2);
+      const bool ok = marker_testable(nobs[j], c2, r2, complete_n);
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
       const double inv = ok ? 1.0 / sqrt(r2) : nan;
       gres2u[j] = ok ? r2 : nan;
@@ -310,7 +316,7 @@ cudaError_t launch_project(const float* A, int64_t lda, int64_t M, int64_t K, co
 cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2, const float* qg,
                                int64_t ldq, int64_t nq, double kappa, double* gres2_units_out,
                                double* norm2_allele_out, float* rinv, double* rinv64,
-                               const MarkerRefine* refine, cudaStream_t st) {
+                               const MarkerRefine* refine, cudaStream_t st, int64_t complete_n) {
   if (M == 0) return cudaSuccess;
   const bool rf = refine != nullptr && nq > 0;
   if (rf) {
@@ -319,11 +325,11 @@ cudaError_t launch_marker_norm(int64_t M, const int32_t* nobs, const double* gc2
   }
   k_marker_norm<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(
       M, nobs, gc2, qg, (long long)ldq, (int)nq, kappa, gres2_units_out, norm2_allele_out, rinv, rinv64,
-      rf ? refine->list : nullptr, rf ? refine->count : nullptr);
+      rf ? refine->list : nullptr, rf ? refine->count : nullptr, (int)complete_n);
   if (!rf) return cudaGetLastError();
   // a fixed grid, so that the launch does not depend on the count (graph capture)
   k_marker_refine<<<304, 256, 0, st>>>(*refine, nobs, gc2, kappa, gres2_units_out,
-                                       norm2_allele_out, rinv, rinv64);
+                                       norm2_allele_out, rinv, rinv64, (int)complete_n);
   return cudaGetLastError();
 }
 

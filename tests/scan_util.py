@@ -34,7 +34,8 @@ def enc_id(encoding: str) -> int:
 
 
 def prec_id(precision: str) -> int:
-    return tg.TG_PREC_SPLIT_BF16 if precision == "split" else tg.TG_PREC_FP32
+    return {"split": tg.TG_PREC_SPLIT_BF16, "fp32": tg.TG_PREC_FP32,
+            "fp4": tg.TG_PREC_FP4_PIECES}[precision]
 
 
 def run_scan(ctx, panel, G, N, P, encoding, precision, full=True, hit_mlog10p=0.0,
@@ -148,7 +149,7 @@ def compare_best(res, ref, rtol=None, marker_offset=0, rel=0.0):
     cases with |r| close to 1, where the tensor-core accumulation's rounding of a sum of terms of
     one sign is relative to |r| rather than to the terms (returned: the largest deviation)."""
     rtol = r_tol(ref["df"]) if rtol is None else rtol
-    absr = np.abs(np.nan_to_num(ref["r"], nan=-1.0))
+    absr = np.nan_to_num(np.abs(ref["r"]), nan=-1.0)  # untestable markers rank below all
     worst = 0.0
     for p in range(absr.shape[1]):
         col = absr[:, p]
