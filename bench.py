@@ -67,6 +67,9 @@ def _args():
                         "1024,2048,4096,8192,20480)")
     a.add_argument("--reps", type=int, default=None,
                    help="with --sweep-p: timed scans per point (default from P)")
+    a.add_argument("--precision", default="split", choices=["split", "fp4"],
+                   help="with --sweep-p: split BF16 (default) or FP4 pieces (2-bit workloads; "
+                        "the block is drawn without missing calls, which the FP4 form does not test)")
     return a.parse_args()
 
 
@@ -716,11 +719,15 @@ def _hbm_bytes_per_block(N: int, M: int, encoding: str, P: int, q: int, fused: b
     return packed + operand + passes * operand + 2 * 2 * P * npad
 
 
-def _scan_points(w, Ps, dev, reps_for, flush_bytes=0):
+FP4_PIECES = 6  # E2M1 pieces of the panel in the FP4 form (one kind::mxf4 product each)
+
+
+def _scan_points(w, Ps, dev, reps_for, flush_bytes=0, prec="split"):
     """Per-block time of the whole scan path (one tg_scan_block of block 0 of workload w) for
     panels of each size in Ps (the first P phenotypes of the workload's panel), with the stage
     times and the binding roofline of each point. With flush_bytes > 0 a buffer that large is
-    written before every timed scan and each scan is timed alone (for inputs that fit L2)."""
+    written before every timed scan and each scan is timed alone (for inputs that fit L2).
+    prec is "split" (split BF16) or "fp4" (block-scaled FP4 pieces, complete 2-bit blocks)."""
     import torch
 
     import paper_2604_21095_gb300 as tg
@@ -745,7 +752,8 @@ def _scan_points(w, Ps, dev, reps_for, flush_bytes=0):
         q = tg.tg_panel_info(panel)[2]
         best = torch.zeros(P, dtype=torch.int64, device=dev)
         out = tg.make_outputs(hits=hits, n_hits=n_hits, best=best)
-        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, THR)
+        opts = tg.tg_scan_opts(tg.TG_PREC_FP4_PIECES if prec == "fp4" else tg.TG_PREC_SPLIT_BF16,
+                               0, THR)
         reps = reps_for(P)
         for _ in range(3):
             tg.tg_scan_block(ctx, panel, G, w.N, M, enc, opts, out, stream=stream)
@@ -777,6 +785,23 @@ def _scan_points(w, Ps, dev, reps_for, flush_bytes=0):
         if tg.tg_status_poll(ctx, stream) != tg.TG_OK:
             raise RuntimeError(tg.tg_last_error())
         flops = 2.0 * w.N * M * P
+        if prec == "fp4":
+            # one kind::mxf4 product per piece; FP4 peak = measured bf16 burst x the nominal
+            # dense FP4 / BF16 ratio (13.5 / 2.25 PFLOP/s)
+            issued = FP4_PIECES * flops / (ms / 1000.0) / 1e12
+            peak4 = float(peaks["bf16_tflops"]) * 13.5 / 2.25
+            points.append({
+                "P": P, "ms_per_block": ms, "tests_per_s": M * P / (ms / 1000.0),
+                "precision": f"FP4 pieces ({FP4_PIECES} block-scaled E2M1 pieces, kind::mxf4)",
+                "roofline": {"bound": "tensor", "achieved": issued, "peak": peak4,
+                             "unit": "TFLOP/s", "frac": issued / peak4,
+                             "basis": f"{FP4_PIECES} x Eq. 2 flops (2 N M P) per block, issued in "
+                                      f"FP4, against the {src} burst bf16 rate x 6 (nominal "
+                                      "FP4/BF16 ratio)"},
+                "stage_ms": {k: v[0] / reps for k, v in st.items() if v[1]}})
+            n_hits.zero_()
+            tg.tg_panel_free(panel)
+            continue
         fz = fused_joint(M, P, q, torch.cuda.get_device_properties(dev).multi_processor_count)
         byts = _hbm_bytes_per_block(w.N, M, w.encoding, P, q, fz)
         hbm_frac = byts / (ms / 1000.0) / 1e9 / float(peaks["hbm_gbs"])
@@ -806,21 +831,28 @@ def _sweep_p(args):
     """Per-block time of the whole scan path against the panel size P, on one GPU."""
     import torch
 
+    import dataclasses
+
     w = _workload(args)
+    if args.precision == "fp4":
+        w = dataclasses.replace(w, missing=0.0)
     Ps = tuple(int(x) for x in args.points.split(",")) if args.points else (
         16, 40, 64, 100, 200, 256, 1024, 2048, 4096, 8192, 20480)
     M, points = _scan_points(w, Ps, torch.device("cuda", 0),
                              (lambda P: args.reps) if args.reps else
-                             (lambda P: max(3, min(50, int(20480 * 5 / P)))))
+                             (lambda P: max(3, min(50, int(20480 * 5 / P)))),
+                             prec=args.precision)
     print(json.dumps({"metric": "per-block scan time vs number of phenotypes", "unit": "ms",
-                      "workload": f"{w.name}: one {M}-marker block, N={w.N}, C={w.n_cov + 1}",
+                      "precision": args.precision,
+                      "workload": f"{w.name}: one {M}-marker block, N={w.N}, C={w.n_cov + 1}"
+                                  + (", no missing calls" if args.precision == "fp4" else ""),
                       "points": points}))
 
 
 def _other_configs(args):
     """The benchmark set's other workloads on the same GPU after the headline, each with its
-    binding roofline: the 2-bit P = 2,048 workload (one 65,536-marker block), the N = 2,000,
-    P = 16 workload (its whole 10,000 markers per step; they fit L2, so L2 is flushed before
+    binding roofline: the 2-bit P = 2,048 workload (one 65,536-marker block), the same block
+    without missing calls in split BF16 and in FP4 pieces, the N = 2,000, P = 16 workload (its whole 10,000 markers per step; they fit L2, so L2 is flushed before
     every timed scan), the batched form (12 panels, ragged blocks, one graph per step) and a
     few points of the scaling in the number of phenotypes (Section 3.2) on the dosage workload."""
     import dataclasses
@@ -848,6 +880,20 @@ def _other_configs(args):
 
     run("n23000_m1000000_p2048_c10_2bit", lambda: cfg_block("n23000_m1000000_p2048_c10_2bit", 10, 0))
     run("n2000_m10000_p16_c5_2bit", lambda: cfg_block("n2000_m10000_p16_c5_2bit", 20, 256 << 20))
+
+    def fp4_vs_split():
+        # the FP4 form tests complete markers only: the same workload without missing calls
+        w = dataclasses.replace(synth.WORKLOADS["n23000_m1000000_p2048_c10_2bit"], missing=0.0)
+        res = {}
+        for prec in ("split", "fp4"):
+            M, pts = _scan_points(w, (w.P,), dev, lambda P: 10, 0, prec=prec)
+            res[prec] = pts[0]
+        res["workload"] = (f"{w.name} without missing calls: one {M}-marker block, N={w.N}, "
+                           f"P={w.P}, C={w.n_cov + 1}, 2-bit calls, both forms on the same block")
+        res["split_ms_over_fp4_ms"] = res["split"]["ms_per_block"] / res["fp4"]["ms_per_block"]
+        return res
+
+    run("fp4_vs_split_2bit_p2048", fp4_vs_split)
 
     def batched():
         r = _ours_batched(args, None, 0, 1, workload="n23000_m500000_12panels_p8192_2bit",
