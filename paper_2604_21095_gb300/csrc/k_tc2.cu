@@ -153,6 +153,14 @@ __device__ __forceinline__ int next_tile(unsigned long long* ctr, int i, int cid
   return (int)t;
 }
 
+// K direction of a tile: the tiles of odd waves stream K from the end. A wave reads about
+// 300 MB of A rows and panel columns at the bench's sizes, more than L2 holds, so a wave that
+// starts where the previous one ended finds the last-streamed slabs (chiefly the A rows of the
+// raster group's m-tile pairs, which consecutive waves share) still in L2 instead of fetching
+// them from DRAM again. Only the order of the FP32 chunk sums changes; every tile still adds
+// the same K blocks in chunks of the same sizes.
+__device__ __forceinline__ bool k_reversed(int tile, int ncl) { return ((tile / ncl) & 1) != 0; }
+
 // mbarrier wait with acquire at cluster scope (the phase may be completed by the other CTA),
 // bounded like mbar_wait.
 __device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
@@ -331,11 +339,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         if (tile >= num_tiles) break;
         int mp, nt;
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
+        const bool rev = k_reversed(tile, ncl);
         const int mt0 = 2 * mp;
         const uint32_t pair_bytes = 2u * KS * ((kFused ? 0u : (uint32_t)A_BYTES) + 2 * HB_BYTES);
         const int arow = (mt0 + (int)rank) * TBM;
         const int brow = nt * TBN + (int)rank * 128;
         for (int kb = 0; kb < num_kb; kb += KS) {
+          const int kx = rev ? num_kb - KS - kb : kb;  // first K block of this stage
           if (!wait(empty_bar(stage), phase ^ 1u)) {
             ok = false;
             break;
@@ -349,13 +359,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           const uint32_t fb = map_to_rank(full_bar(stage), 0u);
           if (kFused) {  // this CTA's packed rows, completing on its own barrier
             mbar_expect_tx(pfull_bar(stage), (uint32_t)DecCfg<OPA>::kPackBytes);
-            tma_load_2d(&da.tmG, sPk(stage), pfull_bar(stage), dec_box_x<OPA>(kb), arow);
+            tma_load_2d(&da.tmG, sPk(stage), pfull_bar(stage), dec_box_x<OPA>(kx), arow);
           }
 #pragma unroll
           for (int h = 0; h < KS; ++h) {
-            if (!kFused) tma_load_2d_pair(&tmAhi, sA(stage, h), fb, (kb + h) * TBK, arow);
-            tma_load_2d_pair(&tmBhi, sBhi(stage, h), fb, (kb + h) * TBK, brow);
-            tma_load_2d_pair(&tmBlo, sBlo(stage, h), fb, (kb + h) * TBK, brow);
+            if (!kFused) tma_load_2d_pair(&tmAhi, sA(stage, h), fb, (kx + h) * TBK, arow);
+            tma_load_2d_pair(&tmBhi, sBhi(stage, h), fb, (kx + h) * TBK, brow);
+            tma_load_2d_pair(&tmBlo, sBlo(stage, h), fb, (kx + h) * TBK, brow);
           }
           if (++stage == S) {
             stage = 0;
@@ -429,13 +439,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         tile_coord2(tile, n_mp, n_nt, group_p, mp, nt);
         const long long r0 = (long long)(2 * mp + (int)rank) * TBM + t;
         const uint2 k0 = dec_row_consts<OPA>(da, r0), k1 = dec_row_consts<OPA>(da, r0 + 64);
+        const bool rev = k_reversed(tile, ncl);
         for (int kb = 0; kb < num_kb; ++kb) {
+          const int kx = rev ? num_kb - 1 - kb : kb;  // the K block the producer loaded
           if (!wait(pfull_bar(stage), phase)) {
             ok = false;
             break;
           }
-          dec_expand_store<OPA>(sPk(stage), k0, r0 < da.M, t, kb, da.N, sA(stage, 0));
-          dec_expand_store<OPA>(sPk(stage), k1, r0 + 64 < da.M, t + 64, kb, da.N, sA(stage, 0));
+          dec_expand_store<OPA>(sPk(stage), k0, r0 < da.M, t, kx, da.N, sA(stage, 0));
+          dec_expand_store<OPA>(sPk(stage), k1, r0 + 64 < da.M, t + 64, kx, da.N, sA(stage, 0));
           // the leader's tensor core reads this CTA's tile: make the stores visible to the
           // async proxy at cluster scope before signalling
           asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
