@@ -179,7 +179,7 @@ cudaError_t launch_full_stats(const EpiParams& ep, cudaStream_t st) {
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   const long long total = (long long)ep.M * ep.P;
   long long grid = (total + 255) / 256;
-  if (grid > 148 * 32) grid = 148 * 32;
+  if (grid > 152 * 32) grid = 152 * 32;  // a grid-stride loop: 32 blocks per SM at most
   k_full_stats<<<(unsigned)grid, 256, 0, st>>>(ep);
   return cudaGetLastError();
 }
