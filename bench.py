@@ -702,18 +702,27 @@ def fused_joint(M: int, P: int, q: int, sm_count: int) -> bool:
     return q > 1 and P + q - 1 <= 128 and (M + 127) // 128 >= sm_count
 
 
-def _hbm_bytes_per_block(N: int, M: int, encoding: str, P: int, q: int, fused: bool = False) -> float:
+def one_pass_joint(N: int, M: int, encoding: str, sm_count: int) -> bool:
+    """Whether the fused joint pass also writes the marker statistics, so that no counting pass
+    reads the block first: dosage rows (no mask) on 256-marker tiles (at least one per SM), and
+    N <= 66,051 (the rows' sums of squared bytes fit 32 bits)."""
+    return encoding == "u8" and N <= 66051 and (M + 255) // 256 >= sm_count
+
+
+def _hbm_bytes_per_block(N: int, M: int, encoding: str, P: int, q: int, fused: bool = False,
+                         one_pass: bool = False) -> float:
     """Algorithmic DRAM bytes of one block's scan. With the decoded operand in HBM: read the
     packed rows, write the 2-byte operand, read it once more for each pass over it (one joint
     pass when the panel and the q - 1 projection columns fit a 256-column tile, else the
     projection and the contraction), and read the bf16 hi + lo panel once. With the decode fused
-    into the joint pass: read the packed rows twice (the counting pass, then the joint pass)
-    and the joint operand (64 or 128 rows of hi + lo) once."""
+    into the joint pass: read the packed rows twice (the counting pass, then the joint pass), or
+    once where the joint pass writes the statistics itself (one_pass), and the joint operand (64
+    or 128 rows of hi + lo) once."""
     npad = (N + 63) // 64 * 64
     packed = M * (N if encoding == "u8" else (N + 3) // 4)
     if fused:
         jc = 64 if P + q - 1 <= 64 else 128
-        return 2 * packed + 2 * 2 * jc * npad
+        return (1 if one_pass else 2) * packed + 2 * 2 * jc * npad
     operand = 2 * M * npad
     passes = 1 if P + q - 1 <= 256 else 2
     return packed + operand + passes * operand + 2 * 2 * P * npad
@@ -802,22 +811,26 @@ def _scan_points(w, Ps, dev, reps_for, flush_bytes=0, prec="split"):
             n_hits.zero_()
             tg.tg_panel_free(panel)
             continue
-        fz = fused_joint(M, P, q, torch.cuda.get_device_properties(dev).multi_processor_count)
-        byts = _hbm_bytes_per_block(w.N, M, w.encoding, P, q, fz)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        fz = fused_joint(M, P, q, sms)
+        op = fz and one_pass_joint(w.N, M, w.encoding, sms)
+        byts = _hbm_bytes_per_block(w.N, M, w.encoding, P, q, fz, op)
         hbm_frac = byts / (ms / 1000.0) / 1e9 / float(peaks["hbm_gbs"])
         tflops = flops / (ms / 1000.0) / 1e12
         tens_frac = tflops / float(peaks["bf16_tflops"])
         hbm_bound = hbm_frac >= tens_frac
         points.append({
             "P": P, "ms_per_block": ms, "tests_per_s": M * P / (ms / 1000.0),
-            "decode": "fused into the joint pass" if fz else "decoded operand in HBM",
+            "decode": ("fused into the joint pass, which also writes the marker statistics"
+                       if op else "fused into the joint pass, after a counting pass" if fz
+                       else "decoded operand in HBM"),
             "roofline": {"bound": "hbm" if hbm_bound else "tensor",
                          "achieved": byts / (ms / 1000.0) / 1e9 if hbm_bound else tflops,
                          "peak": float(peaks["hbm_gbs"]) if hbm_bound else float(peaks["bf16_tflops"]),
                          "unit": "GB/s" if hbm_bound else "TFLOP/s",
                          "frac": hbm_frac if hbm_bound else tens_frac,
-                         "basis": "whole step: algorithmic DRAM bytes (packed rows read twice with "
-                                  "the fused decode; else packed rows, operand written and read per "
+                         "basis": "whole step: algorithmic DRAM bytes (packed rows read once or "
+                                  "twice with the fused decode; else packed rows, operand written and read per "
                                   "pass; panel) or Eq. 2 flops (2 N M P) per block, against the "
                                   f"{src} HBM copy rate / burst bf16 rate"},
             "stage_ms": {k: v[0] / reps for k, v in st.items() if v[1]}})

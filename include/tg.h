@@ -309,8 +309,13 @@ tg_status tg_host_block_sizes(int64_t M, int64_t block_markers, double factor, i
  *   enable = 2 (the default): only the joint projection pass of a small panel (projected mode,
  *     P + q - 1 <= 128, blocks of at least one 128-marker tile per SM), where the scan is one pass
  *     bound by the bytes it reads: the pass reads the packed rows (1 or 1/4 byte per sample)
- *     and decodes them in shared memory with 8 decoder warps, removing the operand's write and
- *     read (Section 2.4: the scan is bound by the reader's bandwidth).
+ *     and decodes them on chip with 8 decoder warps, removing the operand's write and read
+ *     (Section 2.4: the scan is bound by the reader's bandwidth). A counting pass over the rows
+ *     (n_obs, sums, the mean each row is centred on) comes first, except for dosage rows on
+ *     256-marker tiles (blocks of at least 256 markers per SM, N <= 66,051): there the pass
+ *     centres each row on the rounded mean of its first 64 bytes and takes the row's exact
+ *     sums as it expands it, so the block is read once. The statistics are the same integers
+ *     and the same FP64 mean either way.
  *   enable = 1: also the contraction kernels of larger panels, whose two decoder warps per CTA
  *     take about 3,000 cycles per 32-sample K block against 512 for the products, so on GB300
  *     they are slower there.

@@ -477,7 +477,11 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   const double kappa64 = a.encoding == TG_ENC_U8_DOSAGE ? 2.0 / 255.0 : 1.0;
   const float kappa = (float)kappa64;
   void* Ahi = fused ? nullptr : prec == TG_PREC_FP32 ? (void*)c->A32 : (void*)c->Ahi;
-  {
+  // dosage rows in the joint pass on 256-row tiles: that pass writes the row statistics itself
+  // (a thread holds a whole row), so no counting pass reads the block first
+  const bool one_pass = fuse_joint && a.encoding == TG_ENC_U8_DOSAGE && a.N <= kOnePassMaxN &&
+                        joint_fused_rows(a.M, c->sm_count, p->joint_cols) == 2 * MT;
+  if (!one_pass) {
     StageScope s(c, STAGE_DECODE, st, 1);
     TG_CUDA(launch_decode(a.G, a.ldg, a.encoding, a.N, a.M, a.missing, a.ldm, prec, Ahi,
                           split ? c->shift : nullptr, split ? c->mh : nullptr, p->Npad, c->nobs,
@@ -490,6 +494,12 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     da.shift = c->shift;
     da.mh = c->mh;
     dj = da;
+    if (one_pass) {
+      dj.shift_out = c->shift;
+      dj.nobs_out = c->nobs;
+      dj.mean_out = c->mean;
+      dj.gc2_out = c->gc2;
+    }
     const bool u8 = a.encoding == TG_ENC_U8_DOSAGE;
     if (!make_tmap_packed(&da.tmG, a.G, a.M, a.ldg, u8 ? 32u : 16u) ||
         (fuse_joint && !make_tmap_packed(&dj.tmG, a.G, a.M, a.ldg, u8 ? 64u : 16u,

@@ -96,12 +96,21 @@ struct EpiParams {
 // Packed genotypes for a contraction kernel that decodes its A operand in the producer
 // (2-bit calls, or dosage bytes without a missing mask; split form only). The kernel loads the
 // packed rows through `tmG` (uint8, {ldg, M}, boxes of 32 or 16 bytes x 128 rows).
+constexpr int kOnePassMaxN = 66051;  // 255^2 * N < 2^32
 struct DecodeArgs {
   CUtensorMap tmG;
   int N;                  // samples; K columns >= N are zero
   int M;                  // rows of the block; rows >= M are zero
   const float* shift;     // [M] row shift c
   const uint32_t* mh;     // [M] bf16 bits of (mean - c), the missing-call value
+  // Dosage rows without a mask in the joint pass on 256-row tiles: when shift_out is set, the
+  // pass takes each row's shift from the row's first 64 samples instead of reading `shift`, sums
+  // the row's bytes and their squares as it expands them, and writes the row's statistics (the
+  // counting pass's outputs: n_obs = N, mean, |g_c|^2 and the shift), so no counting pass runs.
+  float* shift_out;  // (N <= kOnePassMaxN: the sum of squared bytes fits 32 bits)
+  int32_t* nobs_out;
+  double* mean_out;
+  double* gc2_out;
 };
 
 struct Events {

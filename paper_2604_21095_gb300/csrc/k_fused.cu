@@ -49,6 +49,12 @@ namespace {
 
 using namespace tcx;
 
+// Register split of the joint passes: warpgroup 0 holds only the producer and the MMA issuer
+// (warps 2-3 idle; the epilogue warps decode), so it gives back down to 56 registers and the two
+// epilogue warpgroups take 224: 128 x 56 + 256 x 224 = 64,512, the launch total (384 x 168).
+constexpr int kJointLow = 56, kJointHigh = 224;
+static_assert(128 * kJointLow + 256 * kJointHigh <= kThreads * 168, "register split exceeds launch");
+
 template <int OPA, int BR, int MS>
 struct FCfg {
   static constexpr int kRows = MS * TBM;                          // tile rows
@@ -124,14 +130,74 @@ __device__ __forceinline__ void tc_mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint
       : "memory");
 }
 
+// Sum and sum of squares of 16 dosage bytes whose first sample is i0, the samples >= N left out
+// (past N the packed row holds the caller's padding).
+__device__ __forceinline__ void sums16_u8(uint4 v, int i0, int N, uint32_t& s, uint32_t& s2) {
+  const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+  if (i0 + 16 <= N) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      s = __dp4a(w4[q], 0x01010101u, s);
+      s2 = __dp4a(w4[q], w4[q], s2);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const uint32_t u = (w4[q] >> (8 * b)) & 0xFFu;
+        if (i0 + 4 * q + b < N) {
+          s += u;
+          s2 += u * u;
+        }
+      }
+  }
+}
+
+// A dosage row's shift taken from its first packed slot (samples 0..63, 64-byte swizzle): the
+// rounded mean of its first min(N, 64) bytes. Any integer shift leaves b - c exact in f16; one
+// near the row's mean keeps the partial sums of the products small, as the full mean does.
+__device__ __forceinline__ uint32_t first_slot_shift_u8(uint32_t src, int r, int N) {
+  const uint32_t sw = (uint32_t)((r >> 1) & 3);
+  uint32_t s = 0, s2 = 0;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    if (16 * g >= N) break;
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(src + ((((uint32_t)g) ^ sw) << 4)));
+    sums16_u8(v, 16 * g, N, s, s2);
+  }
+  const int n = N < 64 ? N : 64;
+  const int c = (int)rintf((float)s / (float)n);
+  return (uint32_t)(c < 0 ? 0 : c > 255 ? 255 : c);
+}
+
+// A dosage row's statistics from its exact byte sums, as the counting pass writes them: n_obs =
+// N (no mask), mean = S / N, |g_c|^2 = (N S2 - S^2) / N (the numerator exact in 64-bit
+// integers), and the shift the row was expanded with. S2 <= 255^2 N fits 32 bits for
+// N <= 66,051, the limit of this form.
+__device__ __forceinline__ void write_row_stats(const DecodeArgs& da, long long row, uint32_t c,
+                                                uint32_t S, uint32_t S2) {
+  const double dn = (double)da.N;
+  da.nobs_out[row] = da.N;
+  da.mean_out[row] = (double)S / dn;
+  const long long num = (long long)S2 * (long long)da.N - (long long)S * (long long)S;
+  da.gc2_out[row] = (double)num / dn;
+  da.shift_out[row] = (float)c;
+}
+
 // Expand `n16` groups of 16 samples of one row, starting at sample i0, from the packed slot
 // (row base `src`, shared) into o (8 words per group): 2-bit calls as bf16 (k = the row's lookup
 // pair), dosage bytes as f16 (k.x = the f16 pair of 1024 + c). Dosage slots carry the TMA's
 // 64-byte swizzle (16-byte chunk j of row r at r * 64 + 16 * (j ^ ((r >> 1) & 3))), so the 8
-// threads of a quarter warp, 8 consecutive rows, read 8 distinct bank groups.
+// threads of a quarter warp, 8 consecutive rows, read 8 distinct bank groups. Dosage bytes are
+// also added into s and s2 (their sum and sum of squares, samples < N only).
 template <int OPA>
 __device__ __forceinline__ void expand_groups(uint32_t src, int r, int g0, int n16, uint2 k,
-                                              bool row_ok, int i0, int N, uint32_t* o) {
+                                              bool row_ok, int i0, int N, uint32_t* o,
+                                              uint32_t& s, uint32_t& s2) {
   if (OPA == OPA_2BIT) {
     uint32_t w[4];
     if (n16 == 4) {
@@ -154,6 +220,7 @@ __device__ __forceinline__ void expand_groups(uint32_t src, int r, int g0, int n
                    : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                    : "r"(src + ((((uint32_t)(g0 + g)) ^ sw) << 4)));
       split16_u8_f16(v, k.x, o + 8 * g);
+      sums16_u8(v, i0 + 16 * g, N, s, s2);
     }
   }
 #pragma unroll
@@ -234,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int total = my_tiles * stages_per_tile;  // this CTA's stages, tile after tile
 
   if (warp < 4) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kLow));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kJointLow));
     if (warp == 0 && lane == 0) {
       // ---------------------------------------------------------- TMA producer
       // stage j of this CTA: tile blockIdx.x + (j / stages_per_tile) * gridDim.x, K blocks
@@ -326,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(drain_bar, 0u, abort_flag, spin_ns, ep.status);
     }
   } else {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kHigh));
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kJointHigh));
     // ------------------------------------------------------------ decoders, then epilogue
     const int quarter = warp & 3;
     const int half = (warp - 4) >> 2;
@@ -345,13 +412,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int mt = (int)blockIdx.x + t * (int)gridDim.x;
       const long long row = (long long)mt * C::kRows + trow;
       const bool row_ok = row < ep.M;
-      uint2 kc;
+      // one pass (dosage rows on 256-row tiles, statistics written here): the row's shift comes
+      // from the tile's first packed slot, in the first stage
+      const bool one_pass = OPA == OPA_U8 && MS == 2 && da.shift_out != nullptr;
+      uint32_t c_row = 0;
+      uint2 kc = make_uint2(0u, 0u);
       if (OPA == OPA_2BIT) {
         kc = dec_row_consts<OPA>(da, row);
-      } else {  // the f16 pair of 1024 + c (c = the row's integer shift)
-        const uint32_t c16 = 0x6400u + (row_ok ? (uint32_t)da.shift[row] : 0u);
+      } else if (!one_pass) {  // the f16 pair of 1024 + c (c = the row's integer shift)
+        c_row = row_ok ? (uint32_t)da.shift[row] : 0u;
+        const uint32_t c16 = 0x6400u + c_row;
         kc = make_uint2(c16 | (c16 << 16), 0u);
       }
+      uint32_t sum1 = 0, sum2 = 0;  // the row's bytes and their squares (dosage; N <= 66,051)
       float tot[BR];
 #pragma unroll
       for (int e = 0; e < BR; ++e) tot[e] = 0.0f;
@@ -387,15 +460,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();  // the products that read this A stage have completed
           const uint32_t src = sPk(p) + (uint32_t)(trow * C::kBoxP);
+          if (one_pass && kb == 0) {
+            c_row = row_ok ? first_slot_shift_u8(src, trow, da.N) : 0u;
+            const uint32_t c16 = 0x6400u + c_row;
+            kc = make_uint2(c16 | (c16 << 16), 0u);
+          }
           uint32_t o[32];
+          uint32_t s1 = 0, s2 = 0;
           const uint32_t a_row = tmem_base + lane_addr + (uint32_t)(C::kACol + s * C::kAStageCols);
           if (MS == 2) {  // the row's 64 samples: 32 columns of sub-tile `half`
-            expand_groups<OPA>(src, trow, 0, 4, kc, row_ok, kb * TBK, da.N, o);
+            expand_groups<OPA>(src, trow, 0, 4, kc, row_ok, kb * TBK, da.N, o, s1, s2);
+            sum1 += s1;
+            sum2 += s2;
             __syncwarp();
             if (lane == 0) mbar_arrive(pempty_bar(p));  // the packed slot is read
             tc_st32(a_row + (uint32_t)(sub * 32), o);
           } else {  // K block `half`: 32 samples, 16 columns
-            expand_groups<OPA>(src, trow, 2 * half, 2, kc, row_ok, (kb + half) * TBK, da.N, o);
+            expand_groups<OPA>(src, trow, 2 * half, 2, kc, row_ok, (kb + half) * TBK, da.N, o, s1,
+                               s2);
             __syncwarp();
             if (lane == 0) mbar_arrive(pempty_bar(p));
             tc_st16(a_row + (uint32_t)(half * 16), o);
@@ -416,10 +498,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = false;
         break;
       }
+      if (one_pass && row_ok) write_row_stats(da, row, c_row, sum1, sum2);
       // the tile's raw products: the first raw_cols columns, unnormalised, with the shift's
       // add-back
       if (drains && row_ok) {
-        const float shift = ep.row_shift ? ep.row_shift[row] : 0.0f;
+        const float shift = one_pass ? (float)c_row : ep.row_shift ? ep.row_shift[row] : 0.0f;
         // the f16 joint operand holds 2^14 v (an exact power of two to take back)
         constexpr float kUnscale = OPA == OPA_U8 ? (float)(1.0 / kJointF16Scale) : 1.0f;
 #pragma unroll
@@ -533,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int total = my_tiles * stages_per_tile;
 
   if (warp < 4) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kLow));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kJointLow));
     if (warp == 0 && lane == 0) {
       // ---------------------------------------------------------- TMA producer
       auto load_packed = [&](int j) -> bool {
@@ -616,7 +699,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(drain_bar, 0u, abort_flag, spin_ns, ep.status);
     }
   } else {
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(RegSplit<OPA>::kHigh));
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kJointHigh));
     // ------------------------------------------------------------ decoders, then epilogue
     const int quarter = warp & 3;
     const int half = (warp - 4) >> 2;  // sub-tile
@@ -630,13 +713,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int mt = (int)blockIdx.x + t * (int)gridDim.x;
       const long long row = (long long)mt * C::kRows + trow;
       const bool row_ok = row < ep.M;
-      uint2 kc;
+      // one pass (dosage rows, statistics written here): the shift from the first packed slot
+      const bool one_pass = OPA == OPA_U8 && da.shift_out != nullptr;
+      uint32_t c_row = 0;
+      uint2 kc = make_uint2(0u, 0u);
       if (OPA == OPA_2BIT) {
         kc = dec_row_consts<OPA>(da, row);
-      } else {
-        const uint32_t c16 = 0x6400u + (row_ok ? (uint32_t)da.shift[row] : 0u);
+      } else if (!one_pass) {
+        c_row = row_ok ? (uint32_t)da.shift[row] : 0u;
+        const uint32_t c16 = 0x6400u + c_row;
         kc = make_uint2(c16 | (c16 << 16), 0u);
       }
+      uint32_t sum1 = 0, sum2 = 0;  // the row's bytes and their squares (dosage; N <= 66,051)
       float tot[BR];
 #pragma unroll
       for (int e = 0; e < BR; ++e) tot[e] = 0.0f;
@@ -669,11 +757,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
+          const uint32_t src = sPk(p) + (uint32_t)(trow * C::kBoxP);
+          if (one_pass && kb == 0) {
+            c_row = row_ok ? first_slot_shift_u8(src, trow, da.N) : 0u;
+            const uint32_t c16 = 0x6400u + c_row;
+            kc = make_uint2(c16 | (c16 << 16), 0u);
+          }
+          uint32_t s1 = 0, s2 = 0;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {  // one K block (32 samples, 64 bytes of the row) at a time
             uint32_t o[16];
-            expand_groups<OPA>(sPk(p) + (uint32_t)(trow * C::kBoxP), trow, 2 * h, 2, kc, row_ok,
-                               (kb + h) * TBK, da.N, o);
+            expand_groups<OPA>(src, trow, 2 * h, 2, kc, row_ok, (kb + h) * TBK, da.N, o, s1, s2);
             const uint32_t row_base = sA(s, h, half) + (uint32_t)rr * 64u;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
@@ -682,6 +776,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                            "r"(o[4 * c]), "r"(o[4 * c + 1]), "r"(o[4 * c + 2]), "r"(o[4 * c + 3])
                            : "memory");
           }
+          sum1 += s1;
+          sum2 += s2;
           __syncwarp();
           if (lane == 0) mbar_arrive(pempty_bar(p));  // the packed slot is read
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the MMA
@@ -698,8 +794,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = false;
         break;
       }
+      if (one_pass && row_ok) write_row_stats(da, row, c_row, sum1, sum2);
       if (row_ok) {
-        const float shift = ep.row_shift ? ep.row_shift[row] : 0.0f;
+        const float shift = one_pass ? (float)c_row : ep.row_shift ? ep.row_shift[row] : 0.0f;
         constexpr float kUnscale = OPA == OPA_U8 ? (float)(1.0 / kJointF16Scale) : 1.0f;
 #pragma unroll
         for (int e = 0; e < BR; ++e)
@@ -775,6 +872,10 @@ cudaError_t launch_joint_fused(const CUtensorMap* tmBhi, const CUtensorMap* tmBl
   const int jc = ep.raw_cols <= 64 ? 64 : 128;
   const bool two = joint_fused_rows(ep.M, sm_count, jc) == 2 * TBM;
   const bool u8 = encoding == TG_ENC_U8_DOSAGE;
+  // the one-pass statistics need a thread per row: dosage rows on 256-row tiles
+  if (da.shift_out && (!u8 || !two || da.N > kOnePassMaxN || !da.nobs_out || !da.mean_out ||
+                       !da.gc2_out))
+    return cudaErrorInvalidValue;
   if (jc == 64) {  // A in tensor memory
     if (u8) return two ? go_fused<OPA_U8, 64, 2>(tmBhi, tmBlo, K, ep, sm_count, spin_ns, st, da)
                        : go_fused<OPA_U8, 64, 1>(tmBhi, tmBlo, K, ep, sm_count, spin_ns, st, da);

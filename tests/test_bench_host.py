@@ -86,3 +86,9 @@ def test_fused_joint_rule_and_bytes():
     assert plain == M * N + 2 * (2 * M * 23040) + 2 * 2 * 16 * 23040
     two_pass = bench._hbm_bytes_per_block(N, M, "2bit", 300, 20, False)
     assert two_pass == M * 5750 + 3 * (2 * M * 23040) + 2 * 2 * 300 * 23040
+    # dosage rows on 256-marker tiles: the joint pass writes the statistics, one read of the rows
+    assert bench.one_pass_joint(N, M, "u8", 152) and not bench.one_pass_joint(N, M, "2bit", 152)
+    assert not bench.one_pass_joint(N, 38_000, "u8", 152)   # fewer 256-marker tiles than SMs
+    assert not bench.one_pass_joint(70_000, M, "u8", 152)   # sums of squares past 32 bits
+    one = bench._hbm_bytes_per_block(N, M, "u8", 16, 20, True, True)
+    assert one == M * N + 2 * 2 * 64 * 23040

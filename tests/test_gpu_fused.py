@@ -56,7 +56,9 @@ def test_fused_decode_is_bit_identical(encoding, kernel, N, M, P):
 
 @pytest.mark.parametrize("encoding,N,M,P", [
     ("2bit", 1999, 39_000, 40),   # joint operand of 64 rows, 256-marker tiles
-    ("u8", 2000, 39_000, 100),    # 128 rows, 256-marker tiles
+    ("u8", 2000, 39_000, 100),    # 128 rows, 256-marker tiles (one pass: no counting pass)
+    ("u8", 1999, 39_000, 40),     # 64 rows, 256-marker tiles (one pass)
+    ("u8", 45, 39_000, 16),       # one pass with N < 64: the shift from fewer samples
     ("2bit", 2001, 20_000, 100),  # 128 rows, 128-marker tiles
     ("u8", 1999, 20_000, 40),     # 64 rows, 128-marker tiles
 ])
@@ -66,12 +68,17 @@ def test_fused_joint_pass_of_small_panels(encoding, N, M, P):
     path, with sample counts that end inside a K block and a last tile that is partly past M.
     2-bit calls take the same bf16 values as the decoded operand, so their results are
     bit-identical to it; dosage bytes are expanded into f16 against an f16 hi + lo joint operand
-    (a different split of the panel), so both paths are held to the oracle's tolerances."""
+    (a different split of the panel), so both paths are held to the oracle's tolerances. On
+    256-marker tiles the dosage pass also writes the marker statistics itself (no counting pass
+    runs first): n_obs and the mean must equal the counting pass's bit for bit, with the bytes
+    past N in each row set to nonzero padding that neither path may count."""
     w = synth.Workload(f"fusedjoint_{encoding}_{N}_{M}_{P}", N=N, M=M, P=P, n_cov=4,
                        encoding=encoding, missing=0.02 if encoding == "2bit" else 0.0, seed=43,
                        block=M, causal_per_pheno=1)
     pan = synth.make_panel(w)
     G = synth.make_block(w, 0)["G"].cuda()
+    if encoding == "u8" and G.shape[1] > N:
+        G[:, N:] = 0xAB  # row padding: not samples
     ctx = tg.tg_create(0)
     panel = tg.tg_prepare_panel(ctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
     try:
@@ -84,6 +91,9 @@ def test_fused_joint_pass_of_small_panels(encoding, N, M, P):
         got = res[tg.TG_FUSED_SMALL_PANELS]
         if encoding == "2bit":
             _outputs_equal(got, res[tg.TG_FUSED_OFF])
+        else:
+            for k in ("nobs", "mean"):
+                assert np.array_equal(got[k], res[tg.TG_FUSED_OFF][k]), k
         assert got["n_hits"] > 0
         ref = oracle.scan(G.cpu().numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
         for setting, r in res.items():
