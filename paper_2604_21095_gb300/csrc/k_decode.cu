@@ -32,6 +32,7 @@ namespace tg {
 namespace {
 
 constexpr int kWarps = 8;
+constexpr int kWarpRowN = 4096;  // split-form rows up to this many samples: one warp per row
 
 template <int ENC>
 __device__ __forceinline__ void row_stats(const uint8_t* __restrict__ row, int N,
@@ -465,8 +466,17 @@ cudaError_t go(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, const uint32
   // Split form: one block per marker row with the row in registers (read from HBM once):
   // 256 threads x 6 groups of 16 samples for dosage rows, 128 x 12 for 2-bit rows; 12 and 24
   // groups up to twice those N, with or without the operand (Ahi NULL: statistics, shift and
-  // missing value only). Longer rows read each row twice in the warp-per-row kernel.
+  // missing value only). Short rows (N <= kWarpRowN: at most 8 groups per lane) and long ones
+  // go to the warp-per-row kernel: a block per short row would leave most of its threads idle
+  // and take several waves of blocks for a block of short rows.
   if constexpr (PREC == TG_PREC_SPLIT_BF16) {
+    if (N <= kWarpRowN) {
+      const unsigned grid = (unsigned)((M + kWarps - 1) / kWarps);
+      k_decode<ENC, PREC><<<grid, kWarps * 32, 0, st>>>(
+          G, ldg, (int)N, M, missing, ldm, Ahi, shift, mh, lda, nobs,
+          reinterpret_cast<long long*>(S), reinterpret_cast<long long*>(S2), mean, gc2);
+      return cudaGetLastError();
+    }
     constexpr int T = ENC == TG_ENC_2BIT ? 128 : 256;
     constexpr int G1 = ENC == TG_ENC_2BIT ? 12 : 6;
     __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(Ahi);

@@ -426,36 +426,57 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Statistics of a small panel from its raw products: thread = phenotype column, block = 64
-// consecutive marker rows, so every row is read coalesced, each column keeps its best key over
-// the block's rows and offers it once. Per element the arithmetic of the contraction epilogue
-// (D already holds the shift's add-back): r = D / |a_res| clamped, the hit test on r^2, r in
-// FULL mode, and the key (|r| bits, ~marker) whose maximum is the column's best marker.
+// Statistics of a small panel from its raw products: a block takes 64 consecutive marker rows,
+// its threads split into 256 / P groups of P (thread = phenotype column) that take every
+// (256 / P)-th row, so each row is read coalesced and a small panel still keeps the block busy.
+// Per element the arithmetic of the contraction epilogue (D already holds the shift's add-back):
+// r = D / |a_res| clamped, the hit test on r^2, r in FULL mode, and the key (|r| bits, ~marker)
+// whose maximum is the column's best marker; the groups' keys meet in shared memory and each
+// column offers one per block.
 constexpr int kRawRows = 64;
-__global__ void __launch_bounds__(256) k_raw_stats(const float* __restrict__ raw, long long ld,
-                                                   EpiParams ep) {
-  const int col = threadIdx.x;
-  if (col >= ep.P) return;  // no block-wide synchronisation below
+constexpr int kRawThreads = 256;
+static_assert(JCOLS <= kRawThreads, "a group of P threads per block");
+__global__ void __launch_bounds__(kRawThreads) k_raw_stats(const float* __restrict__ raw,
+                                                           long long ld, EpiParams ep) {
+  __shared__ unsigned long long keys[kRawThreads];
+  __shared__ int has[kRawThreads];
+  const int groups = kRawThreads / ep.P;  // P <= JCOLS <= kRawThreads
+  const int col = (int)threadIdx.x % ep.P, sub = (int)threadIdx.x / ep.P;
+  const bool active = sub < groups;
   const long long r0 = (long long)blockIdx.x * kRawRows;
   const long long r1 = r0 + kRawRows < (long long)ep.M ? r0 + kRawRows : (long long)ep.M;
-  const float rmul = ep.col_rmul[col];
   unsigned long long best = 0;
   bool any = false;
-#pragma unroll 4
-  for (long long row = r0; row < r1; ++row) {
-    const float D = raw[row * ld + col];
-    const float r = corr_nan(D, ep.row_inv[row], rmul);
-    if (ep.do_hits && r * r >= ep.r2_thr) emit_hit_raw(ep, D, row, col);
-    if (ep.do_full) ep.rstore[row * ep.ldo + col] = r;
-    if (r == r) {
-      const unsigned long long key =
-          ((unsigned long long)__float_as_uint(fabsf(r)) << 32) |
-          (unsigned long long)(0xFFFFFFFFu - (uint32_t)(ep.marker_offset + row));
-      best = key > best ? key : best;
-      any = true;
+  if (active) {
+    const float rmul = ep.col_rmul[col];
+    for (long long row = r0 + sub; row < r1; row += groups) {
+      const float D = raw[row * ld + col];
+      const float r = corr_nan(D, ep.row_inv[row], rmul);
+      if (ep.do_hits && r * r >= ep.r2_thr) emit_hit_raw(ep, D, row, col);
+      if (ep.do_full) ep.rstore[row * ep.ldo + col] = r;
+      if (r == r) {
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(fabsf(r)) << 32) |
+            (unsigned long long)(0xFFFFFFFFu - (uint32_t)(ep.marker_offset + row));
+        best = key > best ? key : best;
+        any = true;
+      }
     }
   }
-  if (ep.do_best && any) best_offer(ep.best + col, best);
+  if (!ep.do_best) return;  // the same for every thread of the launch
+  keys[threadIdx.x] = best;
+  has[threadIdx.x] = any ? 1 : 0;
+  __syncthreads();
+  if (active && sub == 0) {
+    for (int g = 1; g < groups; ++g) {
+      const int t = g * ep.P + col;
+      if (has[t]) {
+        best = keys[t] > best ? keys[t] : best;
+        any = true;
+      }
+    }
+    if (any) best_offer(ep.best + col, best);
+  }
 }
 
 __global__ void k_wait_test(const volatile uint32_t* flag, long long limit_ns, uint32_t* result) {
@@ -540,7 +561,7 @@ cudaError_t launch_raw_stats(const float* raw, int64_t ld, const EpiParams& ep, 
   if (ep.M == 0 || ep.P == 0) return cudaSuccess;
   if (ep.P > JCOLS) return cudaErrorInvalidValue;
   const long long blocks = ((long long)ep.M + kRawRows - 1) / kRawRows;
-  k_raw_stats<<<(unsigned)blocks, 256, 0, st>>>(raw, (long long)ld, ep);
+  k_raw_stats<<<(unsigned)blocks, kRawThreads, 0, st>>>(raw, (long long)ld, ep);
   return cudaGetLastError();
 }
 
