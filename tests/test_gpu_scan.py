@@ -667,3 +667,28 @@ def test_256_marker_tiles_equal_128_marker_tiles(tgctx, P, mode):
     compare_full(whole, ref, label=f"256-marker tiles P={P}")
     compare_hits(whole, ref, THR)
     compare_best(whole, ref)
+
+
+@pytest.mark.parametrize("encoding", ["2bit", "u8"])
+def test_second_wave_of_tiles_streams_k_backwards(tgctx, encoding):
+    """The CTA-pair contraction streams K from the end on the tiles of every odd wave (a wave =
+    one tile per CTA pair). A block of 12,288 markers against 300 phenotypes makes 48 x 2 = 96
+    tiles of 256 x 256, more than one wave on 152 SMs, so some tiles run reversed: every
+    statistic is compared with the oracle, and hits and per-phenotype best keys."""
+    N, M, P = 2000, 12_288, 300
+    pairs = torch.cuda.get_device_properties(0).multi_processor_count // 2
+    tiles = ((M + 255) // 256) * ((P + 255) // 256)
+    assert pairs < tiles < 2 * pairs, (pairs, tiles)  # a second, partly reversed wave
+    w, pan, blk, _ = _case(encoding, N=N, M=M, P=P, seed=17)
+    panel = tg.tg_prepare_panel(tgctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+    try:
+        res = run_scan(tgctx, panel, blk["G"].cuda(), N, P, encoding, "split", full=True,
+                       hit_mlog10p=THR)
+    finally:
+        tg.tg_panel_free(panel)
+    assert res["status"] == tg.TG_OK
+    ref = oracle.scan(blk["G"].numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
+    err = compare_full(res, ref, label=f"second wave/{encoding}")
+    compare_hits(res, ref, THR)
+    compare_best(res, ref)
+    print(f"\nsecond wave of tiles ({tiles} tiles on {pairs} pairs), {encoding}: max errors {err}")
