@@ -1,4 +1,4 @@
-"""The FP4 form (TG_PREC_FP4_PIECES, SURVEY's low-precision multi-piece variant): 2-bit calls
+"""The FP4 form (TG_PREC_FP4_PIECES, the low-precision multi-piece variant of the split form): 2-bit calls
 exact in E2M1, the panel in six block-scaled E2M1 pieces, tcgen05 kind::mxf4 products. Compared
 element by element with the FP64 oracle at the split form's tolerances; markers with a missing call
 have no test in this form (NaN outputs, no hits); dosage blocks, subset panels and the static entry
