@@ -116,3 +116,40 @@ def test_fp4_refuses_dosage_blocks_subset_panels_and_the_static_entry(tgctx):
         assert e.value.status == tg.TG_ERR_UNSUPPORTED
     finally:
         tg.tg_panel_free(sp)
+
+
+def test_fp4_host_streamed_scan(tgctx):
+    """tg_scan_host in the FP4 form: a complete 2-bit block streamed from pinned host memory in
+    blocks that ramp up from 128 markers; the hits and per-phenotype best markers are the
+    oracle's, and the same as one tg_scan_block call over the whole block."""
+    from scan_util import HIT_DTYPE
+    N, M, P = 2001, 3000, 300
+    cov = synth.covariates(64, N, 4)
+    G = _complete_block(64, N, M)
+    Yt = synth.phenotypes(64, cov, P)
+    panel = tg.tg_prepare_panel(tgctx, Yt.cuda(), N, P, cov.cuda())
+    try:
+        cap = 1 << 14
+        hits_h = torch.zeros(cap * HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        best_h = torch.zeros(P, dtype=torch.int64).pin_memory()
+        opts = tg.tg_scan_opts(tg.TG_PREC_FP4_PIECES, 0, 3.0)
+        nh = tg.tg_scan_host(tgctx, panel, G.pin_memory(), N, M, tg.TG_ENC_2BIT, 1024, opts,
+                             hits_h, best_h, marker_offset=5)
+        assert 0 < nh <= cap
+        whole = run_scan(tgctx, panel, G.cuda(), N, P, "2bit", "fp4", full=False,
+                         hit_mlog10p=3.0, marker_offset=5)
+    finally:
+        tg.tg_panel_free(panel)
+    b = best_h.numpy().view(np.uint64)
+    res = {"n_hits": nh,
+           "hits": np.frombuffer(hits_h.numpy().tobytes(), dtype=HIT_DTYPE)[:nh],
+           "best_key": b,
+           "best_marker": np.where(b == 0, -1, (0xFFFFFFFF - (b & 0xFFFFFFFF)).astype(np.int64)),
+           "best_absr": np.frombuffer(((b >> 32).astype(np.uint32)).tobytes(), dtype=np.float32)}
+    ref = oracle.scan(G.numpy(), "2bit", oracle_panel(Yt, cov))
+    want, got = compare_hits(res, ref, 3.0, marker_offset=5)
+    assert want > 0 and got > 0
+    compare_best(res, ref, marker_offset=5)
+    key = lambda h: sorted((int(x["marker"]), int(x["pheno"])) for x in h)
+    assert key(res["hits"]) == key(whole["hits"])
+    assert np.array_equal(b, whole["best_key"].astype(np.uint64))
