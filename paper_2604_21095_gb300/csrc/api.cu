@@ -342,9 +342,9 @@ tg_status ensure_fp4_panel(tg_ctx* c, tg_panel* p, cudaStream_t st) {
   return TG_OK;
 }
 
-// The FP4 form of a block scan (2-bit calls): counting decode, E2M1 operand, projection and
-// contraction on kind::mxf4 tensor cores, norms (markers with a missing call untestable), then
-// the same statistics as the split form.
+// The FP4 form of a block scan (2-bit calls): a one-pass decode (the E2M1 operand and the row
+// statistics), projection and contraction on kind::mxf4 tensor cores, norms (markers with a
+// missing call untestable), then the same statistics as the split form.
 tg_status scan_fp4(tg_ctx* c, tg_panel* p, const ScanArgs& a, cudaStream_t st) {
   const tg_status ps = ensure_fp4_panel(c, p, st);
   if (ps != TG_OK) return ps;
@@ -361,10 +361,9 @@ tg_status scan_fp4(tg_ctx* c, tg_panel* p, const ScanArgs& a, cudaStream_t st) {
     c->cap_fp4 = need;
   }
   {
-    StageScope s(c, STAGE_DECODE, st, 2);
-    TG_CUDA(launch_decode(a.G, a.ldg, a.encoding, a.N, a.M, nullptr, 0, TG_PREC_SPLIT_BF16, nullptr,
-                          c->shift, c->mh, p->Npad, c->nobs, nullptr, nullptr, c->mean, c->gc2, st));
-    TG_CUDA(launch_fp4_codes(a.G, a.ldg, a.N, a.M, c->Afp4, lda, c->mean, c->shift, st));
+    StageScope s(c, STAGE_DECODE, st, 1);
+    TG_CUDA(launch_fp4_decode(a.G, a.ldg, a.N, a.M, c->Afp4, lda, c->nobs, c->mean, c->gc2,
+                              c->shift, st));
   }
   CUtensorMap tA;
   if (!make_tmap_packed(&tA, c->Afp4, a.M, lda, 64u, (uint32_t)MT, true))

@@ -57,4 +57,22 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 
+// Exact counts of one 32-bit word of 2-bit fields (16 samples, the first of which is `left`
+// samples before N; fields at or past N are ignored): n observed calls, S the sum of their
+// allele-1 counts and S2 the sum of squares (field 00 -> 2, 10 -> 1, 11 -> 0, 01 missing).
+__device__ __forceinline__ void count16_2bit(uint32_t w, int left, unsigned long long& n,
+                                             unsigned long long& S, unsigned long long& S2) {
+  if (left <= 0) return;
+  const uint32_t valid = (left >= 16) ? 0x55555555u : (0x55555555u & ((1u << (2 * left)) - 1u));
+  const uint32_t lo = w & 0x55555555u;
+  const uint32_t hi = (w >> 1) & 0x55555555u;
+  const uint32_t two = ~lo & ~hi & valid;
+  const uint32_t one = hi & ~lo & valid;
+  const uint32_t zero = lo & hi & valid;
+  const int c2 = __popc(two), c1 = __popc(one);
+  n += (unsigned)(c2 + c1 + __popc(zero));
+  S += (unsigned)(2 * c2 + c1);
+  S2 += (unsigned)(4 * c2 + c1);
+}
+
 }  // namespace tg

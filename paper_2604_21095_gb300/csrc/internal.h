@@ -376,9 +376,11 @@ cudaError_t launch_raw_stats(const float* raw, int64_t ld, const EpiParams& ep, 
 cudaError_t launch_fp4_pieces(const double* src, int64_t lds, const double* div, const float* valid,
                               int64_t nrows, int64_t rows_pad, int64_t N, int64_t Npad, uint8_t* out,
                               float* scale, float* cs, cudaStream_t st);
-// 2-bit calls to the E2M1 operand [M][lda] bytes (lda = Npad / 2), and shift[j] = -mean[j].
-cudaError_t launch_fp4_codes(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, uint8_t* A,
-                             int64_t lda, const double* mean, float* shift, cudaStream_t st);
+// The FP4 form's decode of 2-bit rows in one pass: the E2M1 operand [M][lda] bytes (lda =
+// Npad / 2, a multiple of 32) and each row's n_obs, FP64 mean, |g_c|^2 and shift = -mean.
+cudaError_t launch_fp4_decode(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, uint8_t* A,
+                              int64_t lda, int32_t* nobs, double* mean, double* gc2, float* shift,
+                              cudaStream_t st);
 // The contraction: tmA over the E2M1 operand (boxes of 64 bytes x 128 rows, 64-byte swizzle),
 // tmB over kFp4Pieces x b_rows_pad piece rows (boxes of 64 bytes x 128 rows, or 64 rows in raw
 // mode: the covariate projection, at most 64 columns).

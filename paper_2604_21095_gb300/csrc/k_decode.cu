@@ -48,23 +48,8 @@ __device__ __forceinline__ void row_stats(const uint8_t* __restrict__ row, int N
       const uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + c);
       const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int base = c * 64 + q * 16;  // first sample of this word
-        const int left = N - base;
-        if (left <= 0) break;
-        const uint32_t valid =
-            (left >= 16) ? 0x55555555u : (0x55555555u & ((1u << (2 * left)) - 1u));
-        const uint32_t w = w4[q];
-        const uint32_t lo = w & 0x55555555u;
-        const uint32_t hi = (w >> 1) & 0x55555555u;
-        const uint32_t two = ~lo & ~hi & valid;
-        const uint32_t one = hi & ~lo & valid;
-        const uint32_t zero = lo & hi & valid;
-        const int c2 = __popc(two), c1 = __popc(one);
-        n += (unsigned)(c2 + c1 + __popc(zero));
-        S += (unsigned)(2 * c2 + c1);
-        S2 += (unsigned)(4 * c2 + c1);
-      }
+      for (int q = 0; q < 4; ++q)  // word q: samples from c * 64 + q * 16
+        count16_2bit(w4[q], N - (c * 64 + q * 16), n, S, S2);
     }
   } else {
     const int nchunk = (N + 15) >> 4;

@@ -118,34 +118,90 @@ __global__ void __launch_bounds__(256) k_fp4_pieces(const double* __restrict__ s
   }
 }
 
-// 2-bit calls to the E2M1 operand: field 00 (2 copies) -> 2.0 (code 4), 10 -> 1.0 (2), 11 -> 0,
-// 01 (missing) -> 0; samples past N -> 0. One thread per 4 input bytes (16 samples, 8 output
-// bytes). Also shift[j] = -mean[j], the centring add-back of the epilogue.
-__global__ void __launch_bounds__(256) k_fp4_codes(const uint8_t* __restrict__ G, long long ldg,
-                                                   int N, long long M, uint8_t* __restrict__ A,
-                                                   long long lda, const double* __restrict__ mean,
-                                                   float* __restrict__ shift) {
-  const long long groups = lda / 8;  // 16 samples per group
-  const long long total = M * groups;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long j = t / groups, g = t - j * groups;
-    const int i0 = (int)(g * 16);
-    uint32_t w = 0;
-    for (int b = 0; b < 4; ++b) {
-      const int ib = i0 + 4 * b;
-      if (ib < N) w |= (uint32_t)G[j * ldg + (ib >> 2)] << (8 * b);
-    }
-    uint32_t lo = 0, hi = 0;
+// Bit b of a 16-bit value to bit 2b.
+__device__ __forceinline__ uint32_t spread2(uint32_t m) {
+  m = (m | (m << 8)) & 0x00FF00FFu;
+  m = (m | (m << 4)) & 0x0F0F0F0Fu;
+  m = (m | (m << 2)) & 0x33333333u;
+  m = (m | (m << 1)) & 0x55555555u;
+  return m;
+}
+// Bits at the even positions 2b of a 32-bit value to bit b.
+__device__ __forceinline__ uint32_t compact2(uint32_t m) {
+  m &= 0x55555555u;
+  m = (m | (m >> 1)) & 0x33333333u;
+  m = (m | (m >> 2)) & 0x0F0F0F0Fu;
+  m = (m | (m >> 4)) & 0x00FF00FFu;
+  m = (m | (m >> 8)) & 0x0000FFFFu;
+  return m;
+}
+
+// E2M1 codes of 16 2-bit fields (field 00, 2 copies -> 2.0 = code 4; 10 -> 1.0 = code 2; 11 and
+// 01, missing -> 0), samples from `left` before N on (codes past N are 0): sample s's nibble at
+// bits 4s of lo (s < 8) or of hi. Per field, code bit 2 is set for 00 and code bit 1 for 10;
+// both flags move from bit 2s of the word to bit 4s of the output.
+__device__ __forceinline__ uint2 e2m1_codes16(uint32_t w, int left) {
+  if (left <= 0) return make_uint2(0u, 0u);
+  const uint32_t a = w & 0x55555555u, b = (w >> 1) & 0x55555555u;
+  const uint32_t two = compact2(~a & ~b);  // bit s: field s is 00
+  const uint32_t one = compact2(~a & b);   // bit s: field s is 10
+  uint32_t lo = (spread2(spread2(two & 0xFFu)) << 2) | (spread2(spread2(one & 0xFFu)) << 1);
+  uint32_t hi = (spread2(spread2(two >> 8)) << 2) | (spread2(spread2(one >> 8)) << 1);
+  if (left < 16) {
+    const unsigned long long keep = (1ull << (4 * left)) - 1ull;
+    lo &= (uint32_t)keep;
+    hi &= (uint32_t)(keep >> 32);
+  }
+  return make_uint2(lo, hi);
+}
+
+// The FP4 form's decode of 2-bit rows in one pass, one warp per row: each lane takes 64-sample
+// chunks (a 16-byte load of the packed row; G is 16-byte aligned, ldg a multiple of 16, and the
+// chunk of a sample below N lies inside the row) and writes their E2M1 codes (32 bytes), and
+// the warp sums the exact counts of the row (n_obs, S, S2, as the counting pass does) and writes
+// n_obs, the FP64 mean S / n, |g_c|^2 = (n S2 - S^2) / n and shift = -mean (the epilogue's
+// centring add-back; NaN mean and shift for a row without an observed call).
+constexpr int kF4DecWarps = 8;
+__global__ void __launch_bounds__(kF4DecWarps * 32) k_fp4_decode(
+    const uint8_t* __restrict__ G, long long ldg, int N, long long M, uint8_t* __restrict__ A,
+    long long lda, int32_t* __restrict__ nobs, double* __restrict__ mean_out,
+    double* __restrict__ gc2_out, float* __restrict__ shift) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long j = (long long)blockIdx.x * kF4DecWarps + warp;
+  if (j >= M) return;
+  const uint4* row = reinterpret_cast<const uint4*>(G + j * ldg);
+  uint4* out = reinterpret_cast<uint4*>(A + j * lda);
+  const int chunks = (int)(lda / 32);  // 64 samples each: 32 bytes of codes
+  unsigned long long n = 0, S = 0, S2 = 0;
+  for (int c = lane; c < chunks; c += 32) {
+    const int i0 = c * 64;
+    uint2 q[4] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u)};
+    if (i0 < N) {
+      const uint4 v = __ldg(row + c);
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
-      const uint32_t f = (w >> (2 * s)) & 3u;
-      const uint32_t c = (i0 + s < N) ? (f == 0u ? 4u : f == 2u ? 2u : 0u) : 0u;
-      if (s < 8) lo |= c << (4 * s);
-      else hi |= c << (4 * (s - 8));
+      for (int k = 0; k < 4; ++k) {
+        q[k] = e2m1_codes16(w4[k], N - (i0 + 16 * k));
+        count16_2bit(w4[k], N - (i0 + 16 * k), n, S, S2);
+      }
     }
-    *reinterpret_cast<uint2*>(A + j * lda + g * 8) = make_uint2(lo, hi);
-    if (g == 0) shift[j] = -(float)mean[j];
+    out[2 * c] = make_uint4(q[0].x, q[0].y, q[1].x, q[1].y);
+    out[2 * c + 1] = make_uint4(q[2].x, q[2].y, q[3].x, q[3].y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+    S += __shfl_xor_sync(0xffffffffu, S, o);
+    S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+  }
+  if (lane == 0) {
+    const double dn = (double)n;
+    const double mean = n ? (double)S / dn : __longlong_as_double(0x7ff8000000000000ll);
+    const long long num = (long long)S2 * (long long)n - (long long)S * (long long)S;
+    nobs[j] = (int32_t)n;
+    mean_out[j] = mean;
+    gc2_out[j] = n ? (double)num / dn : __longlong_as_double(0x7ff8000000000000ll);
+    shift[j] = -(float)mean;
   }
 }
 
@@ -414,14 +470,14 @@ cudaError_t launch_fp4_pieces(const double* src, int64_t lds, const double* div,
   return cudaGetLastError();
 }
 
-cudaError_t launch_fp4_codes(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, uint8_t* A,
-                             int64_t lda, const double* mean, float* shift, cudaStream_t st) {
+cudaError_t launch_fp4_decode(const uint8_t* G, int64_t ldg, int64_t N, int64_t M, uint8_t* A,
+                              int64_t lda, int32_t* nobs, double* mean, double* gc2, float* shift,
+                              cudaStream_t st) {
   if (M == 0) return cudaSuccess;
-  if (lda % 16) return cudaErrorInvalidValue;
-  const long long total = M * (lda / 8);
-  long long grid = (total + 255) / 256;
-  if (grid > 152 * 16) grid = 152 * 16;
-  k_fp4_codes<<<(unsigned)grid, 256, 0, st>>>(G, ldg, (int)N, M, A, lda, mean, shift);
+  if (lda % 32 || ldg % 16 || lda * 2 < N) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((M + kF4DecWarps - 1) / kF4DecWarps);
+  k_fp4_decode<<<grid, kF4DecWarps * 32, 0, st>>>(G, ldg, (int)N, M, A, lda, nobs, mean, gc2,
+                                                   shift);
   return cudaGetLastError();
 }
 
