@@ -291,3 +291,45 @@ def test_second_graph_cannot_move_the_first_graphs_workspace(tgctx):
     finally:
         tg.tg_destroy(ctx2)
         tg.tg_panel_free(panel)
+
+
+@pytest.mark.parametrize("encoding", ["u8", "2bit"])
+def test_graph_of_small_panel_blocks_takes_the_fused_pass(tgctx, encoding):
+    """A small panel (P = 16) over ragged blocks large enough for the fused joint pass: 40,000
+    markers (256-marker tiles; for dosage rows the pass also writes the marker statistics),
+    20,000 (128-marker tiles after a counting pass) and 1,000 (the decoded operand). Captured
+    into one graph, the replay gives the eager scans' hits and best markers exactly."""
+    Nf, P = 300, 16
+    cov = synth.covariates(89, Nf, 3)
+    panel = tg.tg_prepare_panel(tgctx, synth.phenotypes(89, cov, P).cuda(), Nf, P, cov.cuda())
+    ctx2 = tg.tg_create(0)
+    try:
+        w = synth.Workload("fused_graph", N=Nf, M=61_000, P=P, n_cov=3, encoding=encoding,
+                           missing=0.01 if encoding == "2bit" else 0.0, seed=89, block=40_000)
+        sizes = [40_000, 20_000, 1_000]
+        blocks = [synth.make_ragged_block(w, i, m, device="cuda") for i, m in enumerate(sizes)]
+        offs = [int(o) for o in np.cumsum([0] + sizes[:-1])]
+        enc = tg.TG_ENC_U8_DOSAGE if encoding == "u8" else tg.TG_ENC_2BIT
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, 3.0)
+        hits, n, best, out = _accum_outputs(P)
+        for b, o in zip(blocks, offs):
+            tg.tg_scan_block(tgctx, panel, b, Nf, b.shape[0], enc, opts, out, marker_offset=o)
+        assert tg.tg_status_poll(tgctx) == tg.TG_OK
+        eager = (_hitset(hits, n), best.cpu().numpy().copy())
+        assert len(eager[0]) > 0
+        hits2, n2, best2, out2 = _accum_outputs(P)
+        g = tg.tg_scan_graph_create(ctx2, panel, blocks, Nf, enc, opts, out2, offs)
+        try:
+            for _ in range(2):
+                n2.zero_()
+                best2.zero_()
+                tg.tg_scan_graph_launch(g)
+                assert tg.tg_status_poll(ctx2) == tg.TG_OK
+                got = _hitset(hits2, n2)
+                assert got == eager[0]
+                assert np.array_equal(best2.cpu().numpy(), eager[1])
+        finally:
+            tg.tg_scan_graph_free(g)
+    finally:
+        tg.tg_destroy(ctx2)
+        tg.tg_panel_free(panel)
