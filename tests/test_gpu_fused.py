@@ -7,6 +7,7 @@ projection's pass (64-, 128- and 256-column joint tiles). The fused path is also
 the FP64 oracle directly, element by element at the scan tolerances."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import paper_2604_21095_gb300 as tg
@@ -126,3 +127,44 @@ def test_masked_dosage_blocks_use_the_decoded_operand():
     finally:
         tg.tg_panel_free(panel)
         tg.tg_destroy(ctx)
+
+
+@pytest.mark.parametrize("encoding", ["u8", "2bit"])
+def test_host_streamed_small_panel_mixes_the_paths(encoding):
+    """tg_scan_host with a small panel (P = 16): its blocks ramp up from 8,192 markers, so the
+    first go through the decoded operand and the later ones through the fused joint pass (on
+    128- and then 256-marker tiles; for dosage rows the latter writes the marker statistics
+    itself). The hits and best markers of the whole stream are the oracle's."""
+    from scan_util import HIT_DTYPE
+    N, M, P = 300, 100_000, 16
+    w = synth.Workload(f"fused_host_{encoding}", N=N, M=M, P=P, n_cov=3, encoding=encoding,
+                       missing=0.01 if encoding == "2bit" else 0.0, seed=47, block=M,
+                       causal_per_pheno=2)
+    pan = synth.make_panel(w)
+    G = synth.make_block(w, 0)["G"]
+    ctx = tg.tg_create(0)
+    panel = tg.tg_prepare_panel(ctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+    try:
+        sizes = tg.tg_host_block_sizes(M, 65_536, tg.tg_host_ramp(ctx)[0])
+        assert sizes[0] < 128 * 152 and max(sizes) >= 256 * 152  # both routes are taken
+        cap = 1 << 16
+        hits_h = torch.zeros(cap * HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        best_h = torch.zeros(P, dtype=torch.int64).pin_memory()
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, 4.0)
+        nh = tg.tg_scan_host(ctx, panel, G.pin_memory(), N, M,
+                             tg.TG_ENC_U8_DOSAGE if encoding == "u8" else tg.TG_ENC_2BIT,
+                             65_536, opts, hits_h, best_h)
+        assert 0 < nh <= cap
+    finally:
+        tg.tg_panel_free(panel)
+        tg.tg_destroy(ctx)
+    b = best_h.numpy().view(np.uint64)
+    res = {"n_hits": nh,
+           "hits": np.frombuffer(hits_h.numpy().tobytes(), dtype=HIT_DTYPE)[:nh],
+           "best_key": b,
+           "best_marker": np.where(b == 0, -1, (0xFFFFFFFF - (b & 0xFFFFFFFF)).astype(np.int64)),
+           "best_absr": np.frombuffer(((b >> 32).astype(np.uint32)).tobytes(), dtype=np.float32)}
+    ref = oracle.scan(G.numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
+    want, got = compare_hits(res, ref, 4.0)
+    assert want > 0 and got > 0
+    compare_best(res, ref)
