@@ -702,6 +702,13 @@ def fused_joint(M: int, P: int, q: int, sm_count: int) -> bool:
     return q > 1 and P + q - 1 <= 128 and (M + 127) // 128 >= sm_count
 
 
+def fused_projection(M: int, P: int, q: int, sm_count: int) -> bool:
+    """Whether the library runs a larger panel's projection as the pass over the packed rows
+    that also writes the block's operand (its default for P + q - 1 > 128 in the projected form,
+    no mask, at least one 128-marker tile per SM)."""
+    return q > 1 and P + q - 1 > 128 and (M + 127) // 128 >= sm_count
+
+
 def one_pass_joint(N: int, M: int, encoding: str, sm_count: int) -> bool:
     """Whether the fused joint pass also writes the marker statistics, so that no counting pass
     reads the block first: dosage rows (no mask) on 256-marker tiles (at least one per SM), and
@@ -710,20 +717,25 @@ def one_pass_joint(N: int, M: int, encoding: str, sm_count: int) -> bool:
 
 
 def _hbm_bytes_per_block(N: int, M: int, encoding: str, P: int, q: int, fused: bool = False,
-                         one_pass: bool = False) -> float:
+                         one_pass: bool = False, fused_proj: bool = False) -> float:
     """Algorithmic DRAM bytes of one block's scan. With the decoded operand in HBM: read the
     packed rows, write the 2-byte operand, read it once more for each pass over it (one joint
     pass when the panel and the q - 1 projection columns fit a 256-column tile, else the
     projection and the contraction), and read the bf16 hi + lo panel once. With the decode fused
     into the joint pass: read the packed rows twice (the counting pass, then the joint pass), or
     once where the joint pass writes the statistics itself (one_pass), and the joint operand (64
-    or 128 rows of hi + lo) once."""
+    or 128 rows of hi + lo) once. With the projection pass that writes the operand (fused_proj):
+    the packed rows once or twice as before, the projection columns (64 rows of hi + lo) once,
+    the operand written once and read once (the contraction), and the panel once."""
     npad = (N + 63) // 64 * 64
     packed = M * (N if encoding == "u8" else (N + 3) // 4)
     if fused:
         jc = 64 if P + q - 1 <= 64 else 128
         return (1 if one_pass else 2) * packed + 2 * 2 * jc * npad
     operand = 2 * M * npad
+    if fused_proj:
+        return ((1 if one_pass else 2) * packed + 2 * 2 * 64 * npad + 2 * operand
+                + 2 * 2 * P * npad)
     passes = 1 if P + q - 1 <= 256 else 2
     return packed + operand + passes * operand + 2 * 2 * P * npad
 
@@ -813,8 +825,9 @@ def _scan_points(w, Ps, dev, reps_for, flush_bytes=0, prec="split"):
             continue
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         fz = fused_joint(M, P, q, sms)
-        op = fz and one_pass_joint(w.N, M, w.encoding, sms)
-        byts = _hbm_bytes_per_block(w.N, M, w.encoding, P, q, fz, op)
+        fp = fused_projection(M, P, q, sms)
+        op = (fz or fp) and one_pass_joint(w.N, M, w.encoding, sms)
+        byts = _hbm_bytes_per_block(w.N, M, w.encoding, P, q, fz, op, fp)
         hbm_frac = byts / (ms / 1000.0) / 1e9 / float(peaks["hbm_gbs"])
         tflops = flops / (ms / 1000.0) / 1e12
         tens_frac = tflops / float(peaks["bf16_tflops"])
@@ -822,8 +835,10 @@ def _scan_points(w, Ps, dev, reps_for, flush_bytes=0, prec="split"):
         points.append({
             "P": P, "ms_per_block": ms, "tests_per_s": M * P / (ms / 1000.0),
             "decode": ("fused into the joint pass, which also writes the marker statistics"
-                       if op else "fused into the joint pass, after a counting pass" if fz
-                       else "decoded operand in HBM"),
+                       if op and fz else "fused into the joint pass, after a counting pass" if fz
+                       else "in the projection pass, which writes the operand and the marker "
+                       "statistics" if op else "in the projection pass, which writes the "
+                       "operand, after a counting pass" if fp else "decoded operand in HBM"),
             "roofline": {"bound": "hbm" if hbm_bound else "tensor",
                          "achieved": byts / (ms / 1000.0) / 1e9 if hbm_bound else tflops,
                          "peak": float(peaks["hbm_gbs"]) if hbm_bound else float(peaks["bf16_tflops"]),

@@ -316,6 +316,13 @@ tg_status tg_host_block_sizes(int64_t M, int64_t block_markers, double factor, i
  *     centres each row on the rounded mean of its first 64 bytes and takes the row's exact
  *     sums as it expands it, so the block is read once. The statistics are the same integers
  *     and the same FP64 mean either way.
+ *   The same setting runs a larger panel's projection (P + q - 1 > 128; same conditions
+ *     otherwise) as that pass with the q - 1 projection columns alone, which also writes the
+ *     block's decoded operand as it expands the rows (the contraction of the panel then reads
+ *     it): the operand is written once and read once instead of read a second time for the
+ *     projection. Dosage rows take f16 projection columns there and, on 256-marker tiles, the
+ *     one-pass statistics above; 2-bit calls give results bit-identical to enable = 0 for
+ *     panels with P + q - 1 > 256.
  *   enable = 1: also the contraction kernels of larger panels, whose two decoder warps per CTA
  *     take about 3,000 cycles per 32-sample K block against 512 for the products, so on GB300
  *     they are slower there.

@@ -455,6 +455,13 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
                           a.opts.mode == TG_MODE_PROJECTED && p->q > 1 && p->joint_cols > 0 &&
                           p->joint_cols <= 128 && p->QYhi16 != nullptr &&
                           (a.M + MT - 1) / MT >= c->sm_count;
+  // a larger panel's projection (P + q - 1 > 128, same conditions otherwise): the same pass with
+  // the 64 projection columns alone reads the packed rows and also writes the block's operand
+  // as it expands them, so the operand is written once and read once (by the panel's
+  // contraction) instead of being read a second time for the projection
+  const bool fuse_proj = split && c->fuse_joint && !c->fuse_decode && !fuse_joint &&
+                         a.missing == nullptr && a.opts.mode == TG_MODE_PROJECTED && p->q > 1 &&
+                         p->QBhi16 != nullptr && (a.M + MT - 1) / MT >= c->sm_count;
   // split-form 2-bit blocks and unmasked dosage blocks are decoded inside the contraction
   // kernels when the context asks for it; the rest go through a decoded operand in HBM
   const bool fused = split && a.missing == nullptr && (c->fuse_decode || fuse_joint);
@@ -476,18 +483,22 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   const double kappa64 = a.encoding == TG_ENC_U8_DOSAGE ? 2.0 / 255.0 : 1.0;
   const float kappa = (float)kappa64;
   void* Ahi = fused ? nullptr : prec == TG_PREC_FP32 ? (void*)c->A32 : (void*)c->Ahi;
-  // dosage rows in the joint pass on 256-row tiles: that pass writes the row statistics itself
-  // (a thread holds a whole row), so no counting pass reads the block first
-  const bool one_pass = fuse_joint && a.encoding == TG_ENC_U8_DOSAGE && a.N <= kOnePassMaxN &&
-                        joint_fused_rows(a.M, c->sm_count, p->joint_cols) == 2 * MT;
-  if (!one_pass) {
+  // dosage rows in the joint pass (or the projection pass that writes the operand) on 256-row
+  // tiles: that pass writes the row statistics itself (a thread holds a whole row), so no
+  // counting pass reads the block first
+  const int pass_cols = fuse_proj ? QCOLS : p->joint_cols;
+  const bool one_pass = (fuse_joint || fuse_proj) && a.encoding == TG_ENC_U8_DOSAGE &&
+                        a.N <= kOnePassMaxN &&
+                        joint_fused_rows(a.M, c->sm_count, pass_cols) == 2 * MT;
+  if (!one_pass) {  // (a counting pass alone before the projection pass that writes the operand)
     StageScope s(c, STAGE_DECODE, st, 1);
-    TG_CUDA(launch_decode(a.G, a.ldg, a.encoding, a.N, a.M, a.missing, a.ldm, prec, Ahi,
-                          split ? c->shift : nullptr, split ? c->mh : nullptr, p->Npad, c->nobs,
-                          nullptr, nullptr, c->mean, c->gc2, st));
+    TG_CUDA(launch_decode(a.G, a.ldg, a.encoding, a.N, a.M, a.missing, a.ldm, prec,
+                          fuse_proj ? nullptr : Ahi, split ? c->shift : nullptr,
+                          split ? c->mh : nullptr, p->Npad, c->nobs, nullptr, nullptr, c->mean,
+                          c->gc2, st));
   }
   DecodeArgs da{}, dj{};
-  if (fused) {
+  if (fused || fuse_proj) {
     da.N = (int)a.N;
     da.M = (int)a.M;
     da.shift = c->shift;
@@ -499,11 +510,15 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
       dj.mean_out = c->mean;
       dj.gc2_out = c->gc2;
     }
+    if (fuse_proj) {
+      dj.a_out = c->Ahi;
+      dj.lda_out = p->Npad;
+    }
     const bool u8 = a.encoding == TG_ENC_U8_DOSAGE;
-    if (!make_tmap_packed(&da.tmG, a.G, a.M, a.ldg, u8 ? 32u : 16u) ||
-        (fuse_joint && !make_tmap_packed(&dj.tmG, a.G, a.M, a.ldg, u8 ? 64u : 16u,
-                                         (uint32_t)joint_fused_rows(a.M, c->sm_count, p->joint_cols),
-                                         u8)))
+    if ((fused && !make_tmap_packed(&da.tmG, a.G, a.M, a.ldg, u8 ? 32u : 16u)) ||
+        ((fuse_joint || fuse_proj) &&
+         !make_tmap_packed(&dj.tmG, a.G, a.M, a.ldg, u8 ? 64u : 16u,
+                           (uint32_t)joint_fused_rows(a.M, c->sm_count, pass_cols), u8)))
       return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the packed genotypes");
   }
   const DecodeArgs* dec = fused ? &da : nullptr;
@@ -513,7 +528,7 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
     return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
   // a small panel in the projected form: one pass over the operand gives the projection and the
   // panel's products (raw, into qg after the projection columns); the statistics follow the norms
-  const bool joint = split && nq > 0 && p->joint_cols > 0;
+  const bool joint = split && nq > 0 && p->joint_cols > 0 && !fuse_proj;
   const int64_t ldq = joint ? p->joint_cols : QCOLS;  // qg row stride
   if (nq > 0) {
     StageScope s(c, STAGE_PROJECT, st, 1);
@@ -533,6 +548,11 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
         const bool u8 = a.encoding == TG_ENC_U8_DOSAGE;  // dosage rows: the f16 joint operand
         if (u8) pp.col_cs = p->qycs16;
         TG_CUDA(launch_joint_fused(u8 ? &p->tmQYhi16 : &p->tmQYhi, u8 ? &p->tmQYlo16 : &p->tmQYlo,
+                                   p->Npad, pp, c->sm_count, kSpinNs, st, dj, a.encoding));
+      } else if (fuse_proj) {  // the projection alone, writing the operand as it goes
+        const bool u8 = a.encoding == TG_ENC_U8_DOSAGE;
+        if (u8) pp.col_cs = p->qcs16;
+        TG_CUDA(launch_joint_fused(u8 ? &p->tmQhi16 : &p->tmQhi, u8 ? &p->tmQlo16 : &p->tmQlo,
                                    p->Npad, pp, c->sm_count, kSpinNs, st, dj, a.encoding));
       } else {
         const SplitChoice sc = pick_split(c, p, a.M, true, true);
@@ -771,14 +791,27 @@ tg_status tg_destroy(tg_ctx* c) {
 // The joint operand of a small panel (tg_panel::QYhi): the q - 1 projection rows, then the P
 // phenotype rows, copied from the panel's own split operands, in the fewest of 64, 128 or 256
 // rows that hold them. Nothing for a panel without covariate columns or with P + q - 1 > 256.
-// Synchronous on st.
+// A panel with P + q - 1 > 128 gets the f16 copy of its projection columns alone instead of the
+// joint f16 operand (tg_panel::QBhi16). Synchronous on st.
 tg_status build_joint(tg_panel* p, cudaStream_t st) {
   const int64_t nq = p->q - 1, P = p->P, Np = p->Npad;
-  if (nq <= 0 || P <= 0 || P + nq > JCOLS) return TG_OK;
+  if (nq <= 0 || P <= 0) return TG_OK;
+  cudaError_t e;
+  if (P + nq > 128) {  // the projection pass that also writes the operand reads these
+    if ((e = dalloc(&p->QBhi16, (size_t)(QCOLS * Np))) ||
+        (e = dalloc(&p->QBlo16, (size_t)(QCOLS * Np))) || (e = dalloc(&p->qcs16, (size_t)QCOLS)) ||
+        (e = launch_joint_f16(p->Q, p->N, nq, p->Yres, p->s, p->col_rmul, 0, QCOLS, Np, p->QBhi16,
+                              p->QBlo16, p->qcs16, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return cuda_fail(e, "f16 projection operand");
+    if (!make_tmap(&p->tmQhi16, p->QBhi16, QCOLS, Np, Np, QCOLS) ||
+        !make_tmap(&p->tmQlo16, p->QBlo16, QCOLS, Np, Np, QCOLS))
+      return fail(TG_ERR_CUDA, "cuTensorMapEncodeTiled failed for the f16 projection operand");
+  }
+  if (P + nq > JCOLS) return TG_OK;
   const int64_t jc = P + nq <= 64 ? 64 : P + nq <= 128 ? 128 : 256;
   const size_t row = sizeof(__nv_bfloat16) * (size_t)Np;
   const auto d2d = cudaMemcpyDeviceToDevice;
-  cudaError_t e;
   if ((e = dalloc(&p->QYhi, (size_t)(jc * Np))) || (e = dalloc(&p->QYlo, (size_t)(jc * Np))) ||
       (e = dalloc(&p->qycs, (size_t)jc)) ||
       (e = cudaMemsetAsync(p->QYhi, 0, row * jc, st)) ||
@@ -1064,6 +1097,7 @@ tg_status tg_panel_free(tg_panel* p) {
   dfree(p->Bhi); dfree(p->Blo); dfree(p->B32); dfree(p->QB); dfree(p->QBhi); dfree(p->QBlo);
   dfree(p->QYhi); dfree(p->QYlo); dfree(p->qycs);
   dfree(p->QYhi16); dfree(p->QYlo16); dfree(p->qycs16);
+  dfree(p->QBhi16); dfree(p->QBlo16); dfree(p->qcs16);
   dfree(p->fp4B); dfree(p->fp4B_scale); dfree(p->fp4B_cs);
   dfree(p->fp4Q); dfree(p->fp4Q_scale); dfree(p->fp4Q_cs);
   delete p;

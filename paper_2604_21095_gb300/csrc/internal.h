@@ -111,6 +111,12 @@ struct DecodeArgs {
   int32_t* nobs_out;
   double* mean_out;
   double* gc2_out;
+  // The projection pass of a larger panel (the 64 projection columns alone): when a_out is set,
+  // the pass also stores each expanded row as the block's bf16 operand (row-major, lda_out
+  // elements per row, every column of rows < M), which the panel's contraction then reads as it
+  // would the decoded operand.
+  __nv_bfloat16* a_out;
+  long long lda_out;
 };
 
 struct Events {
@@ -181,6 +187,12 @@ struct tg_panel {
   __half* QYlo16 = nullptr;
   float* qycs16 = nullptr;        // [joint_cols]
   CUtensorMap tmQYhi16, tmQYlo16;
+  // The projection columns alone in the same f16 form (64 rows; panels with P + q - 1 > 128),
+  // for the projection pass over dosage rows that also writes the block's operand (k_fused.cu).
+  __half* QBhi16 = nullptr;       // [QCOLS][Npad]
+  __half* QBlo16 = nullptr;
+  float* qcs16 = nullptr;         // [QCOLS]
+  CUtensorMap tmQhi16, tmQlo16;
   // The FP4 form's E2M1 pieces (built on the panel's first FP4 scan): the panel's columns
   // [kFp4Pieces][Ppad][Npad/2] and the projection columns [kFp4Pieces][QCOLS][Npad/2], each with
   // its column scale 2^-e (NaN: no test) and scaled column sum.

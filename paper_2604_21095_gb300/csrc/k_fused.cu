@@ -31,6 +31,11 @@
 //                  stage of each chunk they drain the chunk before it (tcgen05.ld) into FP32
 //                  totals in registers; at the end of a tile they drain its last chunk and write
 //                  their row's raw products D + c * sum_i B (as k_tc_scan's raw mode).
+// The projection of a larger panel (P + q - 1 > 128) runs as the same pass with the 64
+// projection columns alone; there the decoders also write the block's bf16 operand for the
+// panel's contraction as they expand each stage (staged per warp in shared memory so that each
+// store instruction writes whole 128-byte row segments). The operand is then written once and
+// read once, by the contraction, and the projection reads the packed rows instead of it.
 // TMEM: the two chunk accumulators (MS x bn columns each) from column 0, four A stages of
 // MS x 32 columns (two 16-bit values per column) from column 256. The 128-column pass on
 // 256-marker tiles cannot fit its A stages there and keeps A in shared memory
@@ -71,7 +76,12 @@ struct FCfg {
   static constexpr int kAStageCols = MS * 32;
   static_assert(2 * kAccCols <= kACol && kACol + kStages * kAStageCols <= kTmemCols, "TMEM");
   static constexpr int kBarBytes = 256;
-  static constexpr int kSmem = kStages * kStageBytes + kPS * kPackBytes + kBarBytes + 1024;
+  // the operand write (64-column pass): each decoder warp stages its 32 rows of a stage (MS x 64
+  // bytes each) so that its global stores cover whole rows' segments
+  static constexpr int kStgRow = MS * 64;
+  static constexpr int kStgBytes = BR == 64 ? kEpiWarps * 32 * kStgRow : 0;
+  static constexpr int kSmem =
+      kStages * kStageBytes + kPS * kPackBytes + kBarBytes + kStgBytes + 1024;
   static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 
@@ -235,6 +245,56 @@ __device__ __forceinline__ void expand_groups(uint32_t src, int r, int g0, int n
   }
 }
 
+// Write a stage of the block's bf16 operand from the expanded rows of one decoder warp: lane l
+// holds row l of the warp's 32 (NW words, two 16-bit values each, NW = 32: 64 samples, or 16:
+// 32 samples). The rows go through the warp's staging area in shared memory (`stg`, 32 rows of
+// 4 NW bytes; 16-byte chunk c of row l at chunk c ^ swz(l), which keeps each quarter warp on
+// distinct banks both ways), then each store instruction writes 4 rows of 128 bytes (NW = 32) or
+// 8 rows of 64 bytes (NW = 16), whole segments, instead of 32 scattered 16-byte pieces. Row l
+// goes to dst0 + l * ld (16-byte aligned); rows at or past `rows` are skipped.
+// 2-bit values are bf16 already. Dosage values are f16 of b - c, integers of magnitude at most
+// 255 (or 0 past N), which bf16 holds exactly, so the conversion through f32 is exact and gives
+// the decoded operand's bits.
+template <int OPA, int NW>
+__device__ __forceinline__ void store_operand_warp(uint32_t stg, const uint32_t* o, int lane,
+                                                   __nv_bfloat16* dst0, long long ld, int rows) {
+  constexpr int kChunks = NW / 4;          // 16-byte chunks per row
+  constexpr int kRowB = NW * 4;            // bytes per row
+  constexpr int kRowsPer = 32 / kChunks;   // rows per store instruction
+  auto swz = [](int r) { return kChunks == 8 ? (r & 7) : ((r >> 1) & 3); };
+  __syncwarp();  // the previous stage's staged rows have been read
+#pragma unroll
+  for (int c = 0; c < kChunks; ++c) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint32_t x = o[4 * c + i];
+      if (OPA == OPA_U8) {
+        __half2 h;
+        memcpy(&h, &x, 4);
+        const __nv_bfloat162 b = __float22bfloat162_rn(__half22float2(h));
+        memcpy(&x, &b, 4);
+      }
+      w[i] = x;
+    }
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
+                     stg + (uint32_t)(lane * kRowB + ((c ^ swz(lane)) << 4))),
+                 "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+                 : "memory");
+  }
+  __syncwarp();
+  const int cc = lane % kChunks;
+#pragma unroll
+  for (int i = 0; i < 32 / kRowsPer; ++i) {
+    const int r = i * kRowsPer + lane / kChunks;
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(stg + (uint32_t)(r * kRowB + ((cc ^ swz(r)) << 4))));
+    if (r < rows) *reinterpret_cast<uint4*>(dst0 + r * ld + cc * 8) = v;
+  }
+}
+
 template <int OPA, int BR, int MS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_joint_fused(const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
@@ -259,6 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       reinterpret_cast<uint32_t*>(gbase + (bars - base) + 8 * (2 * S + 2 * PS + 5));
   static_assert(8 * (2 * S + 2 * PS + 5) + 8 <= C::kBarBytes, "barrier area");
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const uint32_t stg_base = bars + C::kBarBytes;  // the operand write's staging rows
 
   auto sBhi = [&](int s, int h) { return base + (uint32_t)(s * C::kStageBytes + h * C::kBk); };
   auto sBlo = [&](int s, int h) {
@@ -486,6 +547,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(full_bar(s));
+          // the projection pass of a larger panel: the expanded rows are also the block's operand
+          if (da.a_out != nullptr) {
+            const long long row0 = row - lane;  // the warp's first row
+            const int rows = ep.M - row0 < 32 ? (int)(ep.M - row0) : 32;
+            __nv_bfloat16* dst0 =
+                da.a_out + row0 * da.lda_out + (long long)(MS == 2 ? kb : kb + half) * TBK;
+            const uint32_t stg = stg_base + (uint32_t)((warp - 4) * 32 * C::kStgRow);
+            if (MS == 2) store_operand_warp<OPA, 32>(stg, o, lane, dst0, da.lda_out, rows);
+            else store_operand_warp<OPA, 16>(stg, o, lane, dst0, da.lda_out, rows);
+          }
         }
         if (!ok) break;
         // the chunk before this one is complete: drain it while the products of this one run
@@ -875,6 +946,11 @@ cudaError_t launch_joint_fused(const CUtensorMap* tmBhi, const CUtensorMap* tmBl
   // the one-pass statistics need a thread per row: dosage rows on 256-row tiles
   if (da.shift_out && (!u8 || !two || da.N > kOnePassMaxN || !da.nobs_out || !da.mean_out ||
                        !da.gc2_out))
+    return cudaErrorInvalidValue;
+  // the operand write: the 64-column pass (A in tensor memory), every column of a row in
+  // 16-byte stores
+  if (da.a_out && (jc != 64 || da.lda_out < K || da.lda_out % 8 ||
+                   reinterpret_cast<uintptr_t>(da.a_out) % 16))
     return cudaErrorInvalidValue;
   if (jc == 64) {  // A in tensor memory
     if (u8) return two ? go_fused<OPA_U8, 64, 2>(tmBhi, tmBlo, K, ep, sm_count, spin_ns, st, da)

@@ -92,3 +92,24 @@ def test_fused_joint_rule_and_bytes():
     assert not bench.one_pass_joint(70_000, M, "u8", 152)   # sums of squares past 32 bits
     one = bench._hbm_bytes_per_block(N, M, "u8", 16, 20, True, True)
     assert one == M * N + 2 * 2 * 64 * 23040
+
+
+def test_fused_projection_rule_and_bytes():
+    """A panel too large for the joint pass (P + q - 1 > 128) takes the projection pass that
+    writes the operand on blocks of at least one 128-marker tile per SM: the bench counts the
+    packed rows (once with the one-pass statistics, else twice), the 64 projection rows of hi +
+    lo, the operand written once and read once, and the panel."""
+    import bench
+    N, M = 23000, 65536
+    assert bench.fused_projection(M, 110, 20, 152) and bench.fused_projection(M, 20480, 20, 152)
+    assert not bench.fused_projection(M, 109, 20, 152)      # the joint pass takes it
+    assert not bench.fused_projection(10000, 300, 5, 152)   # fewer 128-marker tiles than SMs
+    assert not bench.fused_projection(M, 300, 1, 152)       # no covariate projection
+    op = bench._hbm_bytes_per_block(N, M, "u8", 300, 20, False, True, True)
+    assert op == M * N + 2 * 2 * 64 * 23040 + 2 * (2 * M * 23040) + 2 * 2 * 300 * 23040
+    tp = bench._hbm_bytes_per_block(N, M, "2bit", 300, 20, False, False, True)
+    assert tp == 2 * M * 5750 + 2 * 2 * 64 * 23040 + 2 * (2 * M * 23040) + 2 * 2 * 300 * 23040
+    # one read of the operand fewer than the decoded-operand path's, for an extra read of the
+    # packed rows at most
+    plain = bench._hbm_bytes_per_block(N, M, "2bit", 300, 20, False)
+    assert plain - tp == 2 * M * 23040 - M * 5750 - 2 * 2 * 64 * 23040

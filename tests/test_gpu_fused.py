@@ -107,6 +107,59 @@ def test_fused_joint_pass_of_small_panels(encoding, N, M, P):
         tg.tg_destroy(ctx)
 
 
+@pytest.mark.parametrize("encoding,N,M,P", [
+    ("2bit", 1999, 39_000, 300),  # 256-marker tiles after a counting pass
+    ("u8", 2000, 39_000, 300),    # 256-marker tiles, one pass (no counting pass)
+    ("u8", 45, 39_000, 200),      # one pass with N < 64; a panel that had a 256-row joint operand
+    ("2bit", 2001, 20_000, 300),  # 128-marker tiles
+    ("2bit", 2001, 20_000, 150),  # 128-marker tiles; a 256-row joint operand's panel
+    ("u8", 1999, 20_000, 513),    # 128-marker tiles after a counting pass
+])
+def test_fused_projection_pass_writes_the_operand(encoding, N, M, P):
+    """A panel too large for the joint pass (P + q - 1 > 128): its projection runs as the same
+    pass over the packed rows with the projection columns alone, which also writes the block's
+    operand for the panel's contraction. Against the FP64 oracle and the decoded-operand path.
+    2-bit calls expand to the decoded operand's bf16 values and the projection reads the same
+    bf16 projection columns, so the two paths agree bit for bit where the panel's products come
+    from the same contraction (P + q - 1 > 256; a smaller panel's decoded-operand path takes them
+    from its 256-row joint pass instead, a different summation). Dosage rows take the f16
+    projection columns (and, on 256-marker tiles, each row's shift from its first 64 bytes, the
+    statistics written by the pass), so they are held to the oracle's tolerances, with n_obs and
+    the mean equal to the counting pass's and nonzero padding past N in every row."""
+    w = synth.Workload(f"fusedproj_{encoding}_{N}_{M}_{P}", N=N, M=M, P=P, n_cov=4,
+                       encoding=encoding, missing=0.02 if encoding == "2bit" else 0.0, seed=53,
+                       block=M, causal_per_pheno=1)
+    pan = synth.make_panel(w)
+    G = synth.make_block(w, 0)["G"].cuda()
+    if encoding == "u8" and G.shape[1] > N:
+        G[:, N:] = 0xAB  # row padding: not samples
+    ctx = tg.tg_create(0)
+    panel = tg.tg_prepare_panel(ctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+    try:
+        res = {}
+        for setting in (tg.TG_FUSED_SMALL_PANELS, tg.TG_FUSED_OFF):
+            tg.tg_set_fused_decode(ctx, setting)
+            res[setting] = run_scan(ctx, panel, G, N, P, encoding, "split", full=True,
+                                    hit_mlog10p=4.0, marker_offset=7)
+            assert res[setting]["status"] == tg.TG_OK
+        got = res[tg.TG_FUSED_SMALL_PANELS]
+        if encoding == "2bit" and P + 4 > 256:
+            _outputs_equal(got, res[tg.TG_FUSED_OFF])
+        else:
+            for k in ("nobs", "mean"):
+                assert np.array_equal(got[k], res[tg.TG_FUSED_OFF][k]), k
+        assert got["n_hits"] > 0
+        ref = oracle.scan(G.cpu().numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
+        for setting, r in res.items():
+            compare_full(r, ref, label=f"fused projection {setting}/{encoding}/{N}/{M}/{P}")
+            compare_hits(r, ref, 4.0, marker_offset=7)
+            compare_best(r, ref, marker_offset=7)
+            assert np.array_equal(r["nobs"], ref["decode"]["n_obs"])
+    finally:
+        tg.tg_panel_free(panel)
+        tg.tg_destroy(ctx)
+
+
 def test_masked_dosage_blocks_use_the_decoded_operand():
     """A dosage block with a missing mask is scanned through the decoded operand whatever the
     setting; the result does not depend on it."""
