@@ -702,11 +702,13 @@ def fused_joint(M: int, P: int, q: int, sm_count: int) -> bool:
     return q > 1 and P + q - 1 <= 128 and (M + 127) // 128 >= sm_count
 
 
-def fused_projection(M: int, P: int, q: int, sm_count: int) -> bool:
+def fused_projection(N: int, M: int, encoding: str, P: int, q: int, sm_count: int) -> bool:
     """Whether the library runs a larger panel's projection as the pass over the packed rows
     that also writes the block's operand (its default for P + q - 1 > 128 in the projected form,
-    no mask, at least one 128-marker tile per SM)."""
-    return q > 1 and P + q - 1 > 128 and (M + 127) // 128 >= sm_count
+    no mask, at least one 128-marker tile per SM; a panel with a 256-row joint operand,
+    P + q - 1 <= 256, only where that pass also writes the marker statistics)."""
+    return (q > 1 and P + q - 1 > 128 and (M + 127) // 128 >= sm_count and
+            (P + q - 1 > 256 or one_pass_joint(N, M, encoding, sm_count)))
 
 
 def one_pass_joint(N: int, M: int, encoding: str, sm_count: int) -> bool:
@@ -825,7 +827,7 @@ def _scan_points(w, Ps, dev, reps_for, flush_bytes=0, prec="split"):
             continue
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         fz = fused_joint(M, P, q, sms)
-        fp = fused_projection(M, P, q, sms)
+        fp = fused_projection(w.N, M, w.encoding, P, q, sms)
         op = (fz or fp) and one_pass_joint(w.N, M, w.encoding, sms)
         byts = _hbm_bytes_per_block(w.N, M, w.encoding, P, q, fz, op, fp)
         hbm_frac = byts / (ms / 1000.0) / 1e9 / float(peaks["hbm_gbs"])

@@ -73,6 +73,7 @@ _SIGS = {
     "tg_set_tuning_split": (C.c_int, [_VP, _I64, _I32]),
     "tg_tuning_split": (C.c_int, [_VP, _I64, C.POINTER(_I32)]),
     "tg_set_host_ramp": (C.c_int, [_VP, C.c_double]),
+    "tg_set_host_buffers": (C.c_int, [_VP, C.c_int]),
     "tg_host_ramp": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "tg_host_block_sizes": (C.c_int, [_I64, _I64, C.c_double, C.POINTER(_I64), _I64,
                                       C.POINTER(_I64)]),
@@ -353,6 +354,10 @@ def tg_tuning_split(ctx, M) -> int:
 
 def tg_set_host_ramp(ctx, factor: float = 0.0):
     _check(load().tg_set_host_ramp(ctx, float(factor)))
+
+
+def tg_set_host_buffers(ctx, n_buffers: int = 3):
+    _check(load().tg_set_host_buffers(ctx, int(n_buffers)))
 
 
 def tg_host_ramp(ctx):

@@ -458,10 +458,16 @@ tg_status scan_impl(tg_ctx* c, const tg_panel* pc, const ScanArgs& a, cudaStream
   // a larger panel's projection (P + q - 1 > 128, same conditions otherwise): the same pass with
   // the 64 projection columns alone reads the packed rows and also writes the block's operand
   // as it expands them, so the operand is written once and read once (by the panel's
-  // contraction) instead of being read a second time for the projection
+  // contraction) instead of being read a second time for the projection. A panel with a
+  // 256-row joint operand keeps its one joint pass over the decoded operand unless this pass
+  // also takes the statistics (dosage rows on 256-marker tiles): with a counting pass first the
+  // projection and the contraction as two passes take longer than the decode and one pass.
+  const bool one_pass_rows = a.encoding == TG_ENC_U8_DOSAGE && a.N <= kOnePassMaxN &&
+                             joint_fused_rows(a.M, c->sm_count, QCOLS) == 2 * MT;
   const bool fuse_proj = split && c->fuse_joint && !c->fuse_decode && !fuse_joint &&
                          a.missing == nullptr && a.opts.mode == TG_MODE_PROJECTED && p->q > 1 &&
-                         p->QBhi16 != nullptr && (a.M + MT - 1) / MT >= c->sm_count;
+                         p->QBhi16 != nullptr && (a.M + MT - 1) / MT >= c->sm_count &&
+                         (p->joint_cols == 0 || one_pass_rows);
   // split-form 2-bit blocks and unmasked dosage blocks are decoded inside the contraction
   // kernels when the context asks for it; the rest go through a decoded operand in HBM
   const bool fused = split && a.missing == nullptr && (c->fuse_decode || fuse_joint);
@@ -751,15 +757,17 @@ tg_status tg_create(tg_ctx** out, int device) {
   if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) ||
       (e = dalloc(&c->status, 4)) || (e = dalloc(&c->scratch, 256)) ||
       (e = cudaMemset(c->status, 0, 16)) ||
-      (e = cudaEventCreateWithFlags(&c->ev_copied[0], cudaEventDisableTiming)) ||
-      (e = cudaEventCreateWithFlags(&c->ev_copied[1], cudaEventDisableTiming)) ||
-      (e = cudaEventCreateWithFlags(&c->ev_free[0], cudaEventDisableTiming)) ||
-      (e = cudaEventCreateWithFlags(&c->ev_free[1], cudaEventDisableTiming)) ||
       (e = cudaEventCreate(&c->ev_rate[0])) || (e = cudaEventCreate(&c->ev_rate[1])) ||
       (e = cudaEventCreate(&c->ev_rate[2])) || (e = cudaEventCreate(&c->ev_rate[3]))) {
     tg_destroy(c);
     return cuda_fail(e, "tg_create");
   }
+  for (int i = 0; i < kMaxHostBufs; ++i)
+    if ((e = cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming))) {
+      tg_destroy(c);
+      return cuda_fail(e, "tg_create");
+    }
   *out = c;
   return TG_OK;
 }
@@ -773,11 +781,11 @@ tg_status tg_destroy(tg_ctx* c) {
   dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
   dfree(c->rinv); dfree(c->rinv64); dfree(c->refine_list);
   dfree(c->sk_ws); dfree(c->sk_cnt);
-  dfree(c->stage_buf[0]); dfree(c->stage_buf[1]);
+  for (int i = 0; i < kMaxHostBufs; ++i) dfree(c->stage_buf[i]);
   dfree(c->dhits); dfree(c->dnhits); dfree(c->dbest);
   for (auto& ev : c->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
   for (auto ev : c->event_pool) cudaEventDestroy(ev);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kMaxHostBufs; ++i) {
     if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
     if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
   }
@@ -1199,6 +1207,17 @@ tg_status tg_set_host_ramp(tg_ctx* c, double factor) {
   return TG_OK;
 }
 
+tg_status tg_set_host_buffers(tg_ctx* c, int n_buffers) {
+  TG_ARG(c, "null context");
+  TG_ARG(n_buffers >= 2 && n_buffers <= kMaxHostBufs, "host buffers must be 2, 3 or 4");
+  TG_CUDA(cudaSetDevice(c->device));
+  // tg_scan_host is synchronous: between calls no copy or scan uses the ring
+  for (int i = n_buffers; i < c->stage_n; ++i) dfree(c->stage_buf[i]);
+  c->stage_n = std::min(c->stage_n, n_buffers);
+  c->host_bufs = n_buffers;
+  return TG_OK;
+}
+
 tg_status tg_host_ramp(const tg_ctx* c, double* factor, double* measured_ratio) {
   TG_ARG(c, "null context");
   if (factor) *factor = host_ramp_factor(c);
@@ -1221,14 +1240,14 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
   TG_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t blk_bytes = (size_t)(block_markers * ldg);
-  if (c->stage_bytes < blk_bytes) {
-    dfree(c->stage_buf[0]);
-    dfree(c->stage_buf[1]);
-    c->stage_bytes = 0;
-    TG_CUDA(dalloc(&c->stage_buf[0], blk_bytes));
-    TG_CUDA(dalloc(&c->stage_buf[1], blk_bytes));
+  const int nbuf = c->host_bufs;
+  if (c->stage_bytes < blk_bytes) {  // larger blocks: a new ring
+    for (int i = 0; i < kMaxHostBufs; ++i) dfree(c->stage_buf[i]);
+    c->stage_n = 0;
     c->stage_bytes = blk_bytes;
   }
+  for (; c->stage_n < nbuf; ++c->stage_n)
+    TG_CUDA(dalloc(&c->stage_buf[c->stage_n], c->stage_bytes));
   if (c->dhits_cap < std::max<int64_t>(hit_capacity, 1)) {
     dfree(c->dhits);
     c->dhits_cap = 0;
@@ -1258,7 +1277,7 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
   bool timed = false;
   // the first waits on ev_free find no recorded work and pass
   for (int64_t m0 = 0, b = 0, rows = 0; b < (int64_t)sizes.size(); m0 += rows, ++b) {
-    const int buf = (int)(b & 1);
+    const int buf = (int)(b % nbuf);
     rows = sizes[(size_t)b];
     const bool time_it = b == 1;  // the second block: its copy and scan, each on its own stream
     TG_CUDA(cudaStreamWaitEvent(c->side, c->ev_free[buf], 0));

@@ -96,15 +96,20 @@ def test_fused_joint_rule_and_bytes():
 
 def test_fused_projection_rule_and_bytes():
     """A panel too large for the joint pass (P + q - 1 > 128) takes the projection pass that
-    writes the operand on blocks of at least one 128-marker tile per SM: the bench counts the
+    writes the operand on blocks of at least one 128-marker tile per SM (with a 256-row joint
+    operand, only where that pass writes the statistics): the bench counts the
     packed rows (once with the one-pass statistics, else twice), the 64 projection rows of hi +
     lo, the operand written once and read once, and the panel."""
     import bench
     N, M = 23000, 65536
-    assert bench.fused_projection(M, 110, 20, 152) and bench.fused_projection(M, 20480, 20, 152)
-    assert not bench.fused_projection(M, 109, 20, 152)      # the joint pass takes it
-    assert not bench.fused_projection(10000, 300, 5, 152)   # fewer 128-marker tiles than SMs
-    assert not bench.fused_projection(M, 300, 1, 152)       # no covariate projection
+    fp = bench.fused_projection
+    assert fp(N, M, "u8", 110, 20, 152) and fp(N, M, "u8", 20480, 20, 152)
+    assert fp(N, M, "2bit", 238, 20, 152)                  # P + q - 1 = 257: no joint operand
+    assert not fp(N, M, "2bit", 237, 20, 152)              # the 256-row joint pass, counted rows
+    assert not fp(N, 38_000, "u8", 200, 20, 152)           # the same on 128-marker tiles
+    assert not fp(N, M, "u8", 109, 20, 152)                # the joint pass takes it
+    assert not fp(N, 10000, "u8", 300, 5, 152)             # fewer 128-marker tiles than SMs
+    assert not fp(N, M, "u8", 300, 1, 152)                 # no covariate projection
     op = bench._hbm_bytes_per_block(N, M, "u8", 300, 20, False, True, True)
     assert op == M * N + 2 * 2 * 64 * 23040 + 2 * (2 * M * 23040) + 2 * 2 * 300 * 23040
     tp = bench._hbm_bytes_per_block(N, M, "2bit", 300, 20, False, False, True)

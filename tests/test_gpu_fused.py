@@ -112,17 +112,18 @@ def test_fused_joint_pass_of_small_panels(encoding, N, M, P):
     ("u8", 2000, 39_000, 300),    # 256-marker tiles, one pass (no counting pass)
     ("u8", 45, 39_000, 200),      # one pass with N < 64; a panel that had a 256-row joint operand
     ("2bit", 2001, 20_000, 300),  # 128-marker tiles
-    ("2bit", 2001, 20_000, 150),  # 128-marker tiles; a 256-row joint operand's panel
+    ("u8", 1999, 39_000, 150),    # one pass; a 256-row joint operand's panel
     ("u8", 1999, 20_000, 513),    # 128-marker tiles after a counting pass
+    ("2bit", 2001, 39_000, 150),  # a 256-row joint operand with a counting pass: the joint pass
 ])
 def test_fused_projection_pass_writes_the_operand(encoding, N, M, P):
     """A panel too large for the joint pass (P + q - 1 > 128): its projection runs as the same
     pass over the packed rows with the projection columns alone, which also writes the block's
     operand for the panel's contraction. Against the FP64 oracle and the decoded-operand path.
     2-bit calls expand to the decoded operand's bf16 values and the projection reads the same
-    bf16 projection columns, so the two paths agree bit for bit where the panel's products come
-    from the same contraction (P + q - 1 > 256; a smaller panel's decoded-operand path takes them
-    from its 256-row joint pass instead, a different summation). Dosage rows take the f16
+    bf16 projection columns, so the two paths agree bit for bit. (A panel with a 256-row joint
+    operand, P + q - 1 <= 256, takes this pass only where the pass writes the statistics, dosage
+    rows on 256-marker tiles; 2-bit blocks keep its one joint pass.) Dosage rows take the f16
     projection columns (and, on 256-marker tiles, each row's shift from its first 64 bytes, the
     statistics written by the pass), so they are held to the oracle's tolerances, with n_obs and
     the mean equal to the counting pass's and nonzero padding past N in every row."""
@@ -143,7 +144,7 @@ def test_fused_projection_pass_writes_the_operand(encoding, N, M, P):
                                     hit_mlog10p=4.0, marker_offset=7)
             assert res[setting]["status"] == tg.TG_OK
         got = res[tg.TG_FUSED_SMALL_PANELS]
-        if encoding == "2bit" and P + 4 > 256:
+        if encoding == "2bit":
             _outputs_equal(got, res[tg.TG_FUSED_OFF])
         else:
             for k in ("nobs", "mean"):

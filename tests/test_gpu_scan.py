@@ -237,7 +237,8 @@ def test_blocks_accumulate_hits_and_best(tgctx, panels):
 @pytest.mark.parametrize("encoding,block", [("2bit", 2048), ("u8", 1000), ("2bit", 100_000)])
 def test_host_streamed_scan_matches_oracle(tgctx, panels, encoding, block):
     """tg_scan_host from pinned host memory: blocks ramp up from block/8 (256, 512, 1024, 2048
-    ... for block = 2048) and the hits and best markers equal the oracle's."""
+    ... for block = 2048) and the hits and best markers equal the oracle's, whatever the growth
+    factor and the number of block buffers in the ring."""
     w, pan, blk, _ = _case(encoding, M=3000, P=300)
     panel = _panel(tgctx, panels, ("host", encoding), pan, w.N, w.P)
     G_host = blk["G"].pin_memory()
@@ -289,6 +290,17 @@ def test_host_streamed_scan_matches_oracle(tgctx, panels, encoding, block):
                               hits_h, best_h, marker_offset=11)
         hh = np.frombuffer(hits_h.numpy().tobytes(), dtype=HIT_DTYPE)[:nh3]
         assert np.array_equal(np.sort(hh, order=["marker", "pheno"]), runs[0][0])
+        # rings of 2, 4 and again 3 block buffers (shrinking frees the extra ones): the same
+        for nbuf in (2, 4, 3):
+            tg.tg_set_host_buffers(ctx2, nbuf)
+            nh4 = tg.tg_scan_host(ctx2, panel, G_host, w.N, w.M, enc_id(encoding), block, opts,
+                                  hits_h, best_h, marker_offset=11)
+            hh = np.frombuffer(hits_h.numpy().tobytes(), dtype=HIT_DTYPE)[:nh4]
+            assert np.array_equal(np.sort(hh, order=["marker", "pheno"]), runs[0][0])
+            assert np.array_equal(best_h.numpy(), runs[0][1])
+        for bad in (1, 5):
+            with pytest.raises(tg.TgError):
+                tg.tg_set_host_buffers(ctx2, bad)
     finally:
         tg.tg_destroy(ctx2)
 
