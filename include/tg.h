@@ -263,9 +263,12 @@ tg_status tg_scan_block_static(const tg_panel* panel, const uint8_t* G, int64_t 
 
 /* The scan of a whole genotype matrix held in HOST memory (pinned for overlap): blocks of
  * at most block_markers rows are copied to the device on the context's side stream, into a
- * ring of block buffers (3 by default, tg_set_host_buffers), while earlier blocks are scanned
- * on `stream`; hits, their count and the per-phenotype best keys are copied back to host
- * memory at the end. Synchronous.
+ * device ring the size of a few full blocks (3 by default, tg_set_host_buffers), while earlier
+ * blocks are scanned on `stream`; hits, their count and the per-phenotype best keys are copied
+ * back to host memory at the end. Synchronous.
+ *   The ring: blocks are placed back to back (each on a 256-byte boundary) and wrap to its
+ *   start; a copy waits only for the scans of the blocks whose bytes it overwrites, so the
+ *   smaller ramped blocks let the copies run up to 8 x n_buffers blocks ahead.
  *   Blocking: when block_markers >= 2048 the first block has round_up(block_markers / 8, 256)
  *   rows and each next block f times as many (rounded up to 256), up to block_markers, so that
  *   only a short first copy is not hidden behind a scan. f = 2 on a context's first host scan;
@@ -287,12 +290,13 @@ tg_status tg_scan_host(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G_host
  * TG_ERR_INVALID_ARG for other values. */
 tg_status tg_set_host_ramp(tg_ctx* ctx, double factor);
 
-/* The number of block buffers of tg_scan_host (2, 3 or 4; 3 on a new context), each of
- * block_markers x ldg bytes of device memory, allocated by the next call. With two, a block's
- * copy waits for the scan of the block two before it, so any copy slower than the scan it runs
- * beside stalls the scan; each further buffer lets the copies run one more block ahead, which
- * absorbs a host link whose rate varies from copy to copy as long as its average keeps up.
- * TG_ERR_INVALID_ARG for other values. */
+/* The size of tg_scan_host's device ring in full blocks (2, 3 or 4; 3 on a new context):
+ * n_buffers x block_markers x ldg bytes (each block rounded up to 256 bytes) of device memory,
+ * allocated by the next call. With two and full-size blocks, a block's copy waits for the scan
+ * of the block two before it, so any copy slower than the scan it runs beside stalls the scan;
+ * each further full block of ring lets the copies run one more block ahead, which absorbs a host
+ * link whose rate varies from copy to copy as long as its average keeps up. Ramped blocks are
+ * smaller, so more of them fit. TG_ERR_INVALID_ARG for other values. */
 tg_status tg_set_host_buffers(tg_ctx* ctx, int n_buffers);
 
 /* The factor the next tg_scan_host call will use, and the last measured scan / copy time ratio

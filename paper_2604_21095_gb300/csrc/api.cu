@@ -762,9 +762,12 @@ tg_status tg_create(tg_ctx** out, int device) {
     tg_destroy(c);
     return cuda_fail(e, "tg_create");
   }
-  for (int i = 0; i < kMaxHostBufs; ++i)
-    if ((e = cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming)) ||
-        (e = cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming))) {
+  if ((e = cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming))) {
+    tg_destroy(c);
+    return cuda_fail(e, "tg_create");
+  }
+  for (int i = 0; i < kRingEvents; ++i)
+    if ((e = cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming))) {
       tg_destroy(c);
       return cuda_fail(e, "tg_create");
     }
@@ -781,14 +784,13 @@ tg_status tg_destroy(tg_ctx* c) {
   dfree(c->nobs); dfree(c->mean); dfree(c->gc2); dfree(c->qg); dfree(c->gres2);
   dfree(c->rinv); dfree(c->rinv64); dfree(c->refine_list);
   dfree(c->sk_ws); dfree(c->sk_cnt);
-  for (int i = 0; i < kMaxHostBufs; ++i) dfree(c->stage_buf[i]);
+  dfree(c->stage);
   dfree(c->dhits); dfree(c->dnhits); dfree(c->dbest);
   for (auto& ev : c->pending) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
   for (auto ev : c->event_pool) cudaEventDestroy(ev);
-  for (int i = 0; i < kMaxHostBufs; ++i) {
-    if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+  if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+  for (int i = 0; i < kRingEvents; ++i)
     if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
-  }
   for (int i = 0; i < 4; ++i)
     if (c->ev_rate[i]) cudaEventDestroy(c->ev_rate[i]);
   if (c->side) cudaStreamDestroy(c->side);
@@ -1152,6 +1154,8 @@ tg_status tg_scan_block(tg_ctx* c, const tg_panel* p, const uint8_t* G, int64_t 
 // Largest block_markers of the host-streamed scan: keeps f * block sizes and block bytes far
 // inside int64.
 constexpr int64_t kMaxBlockMarkers = 1ll << 32;
+// Alignment of each block's bytes in the host-streamed scan's device ring (that of cudaMalloc).
+constexpr int64_t kRingAlign = 256;
 
 // Block sizes of tg_scan_host for M markers (B <= kMaxBlockMarkers, f in [1, 8]):
 // round_up(B / 8, 256) first when B >= 2048 (else B), each next one f times the previous
@@ -1211,9 +1215,12 @@ tg_status tg_set_host_buffers(tg_ctx* c, int n_buffers) {
   TG_ARG(c, "null context");
   TG_ARG(n_buffers >= 2 && n_buffers <= kMaxHostBufs, "host buffers must be 2, 3 or 4");
   TG_CUDA(cudaSetDevice(c->device));
-  // tg_scan_host is synchronous: between calls no copy or scan uses the ring
-  for (int i = n_buffers; i < c->stage_n; ++i) dfree(c->stage_buf[i]);
-  c->stage_n = std::min(c->stage_n, n_buffers);
+  // tg_scan_host is synchronous: between calls no copy or scan uses the ring, which the next
+  // call allocates again at the new size
+  if (n_buffers != c->host_bufs) {
+    dfree(c->stage);
+    c->stage_cap = 0;
+  }
   c->host_bufs = n_buffers;
   return TG_OK;
 }
@@ -1239,15 +1246,15 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
   TG_ARG(G_host || M == 0, "null G_host");
   TG_CUDA(cudaSetDevice(c->device));
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t blk_bytes = (size_t)(block_markers * ldg);
-  const int nbuf = c->host_bufs;
-  if (c->stage_bytes < blk_bytes) {  // larger blocks: a new ring
-    for (int i = 0; i < kMaxHostBufs; ++i) dfree(c->stage_buf[i]);
-    c->stage_n = 0;
-    c->stage_bytes = blk_bytes;
+  // the ring: host_bufs whole blocks, each starting on a 256-byte boundary
+  const size_t blk_bytes = (size_t)round_up(block_markers * ldg, kRingAlign);
+  const size_t ring_bytes = blk_bytes * (size_t)c->host_bufs;
+  if (c->stage_cap < ring_bytes) {  // larger blocks: a new ring
+    dfree(c->stage);
+    c->stage_cap = 0;
+    TG_CUDA(dalloc(&c->stage, ring_bytes));
+    c->stage_cap = ring_bytes;
   }
-  for (; c->stage_n < nbuf; ++c->stage_n)
-    TG_CUDA(dalloc(&c->stage_buf[c->stage_n], c->stage_bytes));
   if (c->dhits_cap < std::max<int64_t>(hit_capacity, 1)) {
     dfree(c->dhits);
     c->dhits_cap = 0;
@@ -1275,23 +1282,48 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
   // slow as the scan, larger blocks would only leave the scan waiting for their copies.
   const std::vector<int64_t> sizes = host_block_sizes(M, block_markers, host_ramp_factor(c));
   bool timed = false;
-  // the first waits on ev_free find no recorded work and pass
+  // Blocks fill the ring front to back, each at the next 256-byte boundary, and wrap to its
+  // start when the next one does not fit before the end. A block's copy waits (on the side
+  // stream) for the scans of the earlier blocks whose bytes it overwrites; the scans finish in
+  // order on `stream`, so waiting for the newest of them is enough. The ramped first blocks are
+  // smaller than block_markers, so up to 8 x host_bufs of them are in flight at once: the copies
+  // run as far ahead of the scans as the ring's bytes allow, which absorbs a host link whose
+  // rate varies from copy to copy.
+  struct InFlight {
+    size_t off, end;
+    int ev;
+  };
+  std::vector<InFlight> q;  // blocks whose scan may still read their bytes, oldest first
+  size_t head = 0, q0 = 0;  // q0: first live entry of q
   for (int64_t m0 = 0, b = 0, rows = 0; b < (int64_t)sizes.size(); m0 += rows, ++b) {
-    const int buf = (int)(b % nbuf);
     rows = sizes[(size_t)b];
+    const size_t len = (size_t)(rows * ldg);
+    size_t off = (size_t)round_up((int64_t)head, kRingAlign);
+    if (off + len > c->stage_cap) off = 0;
+    // the newest live block that overlaps [off, off + len); at least enough of the oldest to
+    // keep fewer than kRingEvents live, so that this block's event is not still awaited
+    int64_t last = -1;
+    for (size_t j = q0; j < q.size(); ++j)
+      if (q[j].off < off + len && off < q[j].end) last = (int64_t)j;
+    const int64_t live = (int64_t)(q.size() - q0);
+    if (live >= kRingEvents) last = std::max<int64_t>(last, (int64_t)q0 + live - kRingEvents);
+    if (last >= 0) {
+      TG_CUDA(cudaStreamWaitEvent(c->side, c->ev_free[q[(size_t)last].ev], 0));
+      q0 = (size_t)last + 1;
+    }
+    uint8_t* dst = c->stage + off;
     const bool time_it = b == 1;  // the second block: its copy and scan, each on its own stream
-    TG_CUDA(cudaStreamWaitEvent(c->side, c->ev_free[buf], 0));
     if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[0], c->side));
     {
       StageScope s(c, STAGE_H2D, c->side, 0);
-      TG_CUDA(cudaMemcpyAsync(c->stage_buf[buf], G_host + m0 * ldg, (size_t)(rows * ldg),
-                              cudaMemcpyHostToDevice, c->side));
+      TG_CUDA(cudaMemcpyAsync(dst, G_host + m0 * ldg, len, cudaMemcpyHostToDevice, c->side));
     }
     if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[1], c->side));
-    TG_CUDA(cudaEventRecord(c->ev_copied[buf], c->side));
-    TG_CUDA(cudaStreamWaitEvent(st, c->ev_copied[buf], 0));
+    // a wait takes the event's latest record at the time of the call: one event serves all
+    TG_CUDA(cudaEventRecord(c->ev_copied, c->side));
+    TG_CUDA(cudaStreamWaitEvent(st, c->ev_copied, 0));
     if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[2], st));
-    ScanArgs a{c->stage_buf[buf], ldg, encoding, N, rows, marker_offset + m0, nullptr, 0, *opts, o};
+    ScanArgs a{dst, ldg, encoding, N, rows, marker_offset + m0, nullptr, 0, *opts, o};
     tg_status s = check_scan_args(c, p, a);
     if (s != TG_OK) return s;
     s = scan_impl(c, p, a, st);
@@ -1300,7 +1332,10 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
       TG_CUDA(cudaEventRecord(c->ev_rate[3], st));
       timed = true;
     }
-    TG_CUDA(cudaEventRecord(c->ev_free[buf], st));
+    const int ev = (int)(b % kRingEvents);
+    TG_CUDA(cudaEventRecord(c->ev_free[ev], st));
+    q.push_back({off, off + len, ev});
+    head = off + len;
   }
   unsigned long long nh = 0;
   TG_CUDA(cudaMemcpyAsync(&nh, c->dnhits, sizeof(nh), cudaMemcpyDeviceToHost, st));

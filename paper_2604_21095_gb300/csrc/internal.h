@@ -22,6 +22,8 @@ constexpr int kAccumChunkKB = 32;  // tensor-core accumulation chunk: 32 K block
 constexpr int PPAD = 256;    // phenotype rows padding of the panel operands (tensor-core N tile)
 constexpr int QMAX = 64;     // intercept + at most 63 covariates
 constexpr int kMaxHostBufs = 4;  // block buffers of the host-streamed scan, at most
+// blocks of the host-streamed scan in flight at once (their scan-done events), at most
+constexpr int kRingEvents = 8 * kMaxHostBufs + 8;
 constexpr int QCOLS = 64;    // projection columns (Q columns 1..q-1), zero padded
 constexpr int JCOLS = 256;   // widest joint operand: projection columns + panel in one tile
 constexpr int MT = 128;      // marker rows per tensor-core tile
@@ -230,18 +232,17 @@ struct tg_ctx {
   float* rinv = nullptr;
   double* rinv64 = nullptr;
   int* refine_list = nullptr;                   // [cap_m] markers re-projected in FP64
-  // host-streamed scan: a ring of host_bufs block buffers (stage_n of stage_bytes allocated)
-  uint8_t* stage_buf[tg::kMaxHostBufs] = {};
-  size_t stage_bytes = 0;
-  int stage_n = 0;
+  // host-streamed scan: a device ring of host_bufs block buffers' bytes (stage_cap allocated)
+  uint8_t* stage = nullptr;
+  size_t stage_cap = 0;
   int host_bufs = 3;
   tg_hit* dhits = nullptr;
   int64_t dhits_cap = 0;
   unsigned long long* dnhits = nullptr;
   unsigned long long* dbest = nullptr;
   int64_t dbest_cap = 0;
-  cudaEvent_t ev_copied[tg::kMaxHostBufs] = {};
-  cudaEvent_t ev_free[tg::kMaxHostBufs] = {};
+  cudaEvent_t ev_copied = nullptr;
+  cudaEvent_t ev_free[tg::kRingEvents] = {};
   // timing of one block's copy (0, 1) and scan (2, 3) in a host-streamed scan, and their ratio
   // (scan time / copy time, 0 = not measured yet), which sets the next call's block ramp
   cudaEvent_t ev_rate[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -305,6 +305,46 @@ def test_host_streamed_scan_matches_oracle(tgctx, panels, encoding, block):
         tg.tg_destroy(ctx2)
 
 
+@pytest.mark.parametrize("encoding", ["2bit", "u8"])
+def test_host_ring_wraps_with_many_small_blocks(tgctx, panels, encoding):
+    """tg_scan_host's device ring holds host_bufs full blocks' bytes and places the blocks back
+    to back, wrapping to its start. With the growth factor fixed at 1, every block of a
+    block_markers = 2,048 scan has 256 markers, so 8 x host_bufs of them are in flight at once:
+    5,000 markers in 20 blocks wrap a ring of two buffers (16 blocks per lap) and never reach
+    the end of a ring of four. The copies run far ahead of the scans, so a block that
+    overwrote bytes still being scanned would change the results: both rings give the same
+    hits and best markers, bit for bit, and the same hit set as one resident scan."""
+    w, pan, blk, _ = _case(encoding, M=5000, P=300)
+    panel = _panel(tgctx, panels, ("ring", encoding), pan, w.N, w.P)
+    G_host = blk["G"].pin_memory()
+    cap = 1 << 15
+    opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, THR)
+    ctx2 = tg.tg_create(0)
+    runs = []
+    try:
+        tg.tg_set_host_ramp(ctx2, 1.0)
+        for nbuf in (2, 4, 2):
+            tg.tg_set_host_buffers(ctx2, nbuf)
+            hits_h = torch.zeros(cap * HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+            best_h = torch.zeros(w.P, dtype=torch.int64).pin_memory()
+            nh = tg.tg_scan_host(ctx2, panel, G_host, w.N, w.M, enc_id(encoding), 2048, opts,
+                                 hits_h, best_h, marker_offset=3)
+            assert 0 < nh <= cap
+            hh = np.frombuffer(hits_h.numpy().tobytes(), dtype=HIT_DTYPE)[:nh]
+            runs.append((np.sort(hh, order=["marker", "pheno"]), best_h.numpy().copy()))
+    finally:
+        tg.tg_destroy(ctx2)
+    for hh, bb in runs[1:]:
+        assert np.array_equal(hh, runs[0][0])
+        assert np.array_equal(bb, runs[0][1])
+    res = run_scan(tgctx, panel, blk["G"].cuda(), w.N, w.P, encoding, "split", full=False,
+                   hit_mlog10p=THR, hit_capacity=cap, marker_offset=3)
+    assert res["n_hits"] == len(runs[0][0])
+    ref = np.sort(res["hits"], order=["marker", "pheno"])
+    assert np.array_equal(ref[["marker", "pheno"]], runs[0][0][["marker", "pheno"]])
+    assert np.allclose(ref["mlog10p"], runs[0][0]["mlog10p"], rtol=1e-5, atol=1e-4)
+
+
 @pytest.mark.parametrize("encoding,masked", [("2bit", False), ("u8", True)])
 @pytest.mark.parametrize("precision", ["fp32", "split"])
 def test_paper_mode_matches_oracle(tgctx, panels, encoding, masked, precision):
