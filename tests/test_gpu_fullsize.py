@@ -3,7 +3,8 @@ columns, 8-bit dosages, 65,536-marker blocks, split-BF16 tensor-core scan with h
 (the configuration the benchmark times). The oracle recomputes sampled outputs one by one:
 every hit, every planted pair, the best marker of sampled phenotypes and sampled marker norms.
 A second case writes every statistic for a 256-marker block at the same N and P and compares
-a sample of elements."""
+a sample of elements; others take the same block against small panels (the fused pass of the
+scaling in P) and a 2-bit block against 2,048 phenotypes."""
 import numpy as np
 import pytest
 import torch
@@ -172,3 +173,58 @@ def test_2bit_panel2048_block_hits_and_sampled_statistics(tgctx):
               f"sampled max |d -log10 p| {dm.max():.2e}")
     finally:
         tg.tg_panel_free(panel)
+
+
+@pytest.mark.parametrize("P", [16, 100])
+def test_fullsize_small_panel_fused_pass(tgctx, full, P):
+    """The small panels of the scaling in P at full size: the bench block (N = 23,000, 65,536
+    8-bit dosage markers, 20 covariate columns) against P phenotypes of the full panel that
+    include planted ones, so that the projection and the panel's products come from one pass
+    over the packed rows with the decode fused in (P + 19 <= 64: A in tensor memory; <= 128: A
+    in shared memory), which on these 256-marker tiles also writes the marker statistics. Every
+    hit, the planted pairs, the best marker of the planted phenotypes, every statistic of
+    sampled markers and the sampled markers' n_obs, mean and norm against the oracle."""
+    pan, _, blk = full
+    planted = sorted({p for _, p in pan["pairs"]})
+    phenos = (planted[:P // 2] + [p for p in range(W.P) if p not in set(planted)])[:P]
+    phenos = sorted(phenos)
+    Yt = pan["Yt"][phenos].contiguous()
+    panel = tg.tg_prepare_panel(tgctx, Yt, W.N, P, pan["cov_t"])
+    try:
+        res = run_scan(tgctx, panel, blk["G"], W.N, P, "u8", "split", full=True,
+                       hit_mlog10p=THR, hit_capacity=1 << 20)
+    finally:
+        tg.tg_panel_free(panel)
+    assert res["status"] == tg.TG_OK and 0 < res["n_hits"] == len(res["hits"])
+    col = {p: i for i, p in enumerate(phenos)}
+    got = {(int(h["marker"]), int(h["pheno"])) for h in res["hits"]}
+    pairs = [(m, col[p]) for m, p in pan["pairs"] if p in col]
+    assert pairs
+    planted_of = {}
+    for m, c in pairs:
+        assert (m, c) in got, (m, c)
+        planted_of.setdefault(c, set()).add(m)
+    for c, ms in planted_of.items():  # a phenotype's best marker is one of its planted ones
+        assert int(res["best_marker"][c]) in ms, (c, res["best_marker"][c], ms)
+    markers = sorted({int(h["marker"]) for h in res["hits"]})
+    rng = np.random.default_rng(3)
+    sm = sorted(set(markers) | set(rng.choice(blk["M"], 64, replace=False).tolist()))
+    ref = _sub_oracle(pan, blk, sm, phenos)
+    mi = {m: i for i, m in enumerate(sm)}
+    for h in res["hits"]:
+        j, c = mi[int(h["marker"])], int(h["pheno"])
+        mo = ref["mlog10p"][j, c]
+        assert abs(h["mlog10p"] - mo) <= max(1e-3, 1e-5 * mo), (h, mo)
+        assert abs(h["beta"] - ref["beta"][j, c]) <= 1e-4 * max(abs(ref["beta"][j, c]),
+                                                                ref["se"][j, c])
+    for k in ("mlog10p", "beta", "se", "t"):
+        assert np.isfinite(res[k][sm]).all(), k
+    dm = np.abs(res["mlog10p"][sm] - ref["mlog10p"])
+    assert np.all(dm <= np.maximum(1e-3, 1e-5 * ref["mlog10p"]))
+    db = np.abs(res["beta"][sm] - ref["beta"])
+    assert np.all(db <= 1e-4 * np.maximum(np.abs(ref["beta"]), ref["se"]))
+    assert np.all(np.abs(res["se"][sm] - ref["se"]) <= 1e-4 * ref["se"])
+    assert np.array_equal(res["nobs"][sm], ref["decode"]["n_obs"])
+    assert np.array_equal(res["mean"][sm], ref["decode"]["mean_units"])
+    assert np.allclose(res["norm2"][sm], ref["gres2"], rtol=1e-6)
+    print(f"\nfull size P={P}: {len(res['hits'])} hits, sampled max |d -log10 p| {dm.max():.2e}")
