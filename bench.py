@@ -461,8 +461,26 @@ def _ours(args, dist, rank, ws):
         ste = tg.tg_stage_times(ctx, reset=True)
         steps_e2e = calls * per_call
         growth, ratio = tg.tg_host_ramp(ctx)
+        # the host link's rate: one block's pinned copy with the GPU otherwise idle (after the
+        # timed region), against the copies' average while the scans ran
+        blk_bytes = int(M * blocks[0].shape[1])
+        dst = torch.empty(blk_bytes, dtype=torch.uint8, device=dev)
+        side = torch.cuda.Stream(dev)
+        idle_ms = []
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(side)
+                dst.copy_(host[:M].reshape(-1), non_blocking=True)
+                e1.record(side)
+                e1.synchronize()
+                idle_ms.append(e0.elapsed_time(e1))
+        del dst
+        h2d_ms = ste["h2d"][0] / steps_e2e if "h2d" in ste else 0.0
         e2e = {"value": tests_step * steps_e2e * ws / dt, "unit": UNIT,
                "block_growth": {"factor": growth, "scan_over_copy": ratio},
+               "copy_rate_gbs": {"idle": blk_bytes / min(idle_ms) / 1e6,
+                                 "during_scans": blk_bytes / h2d_ms / 1e6 if h2d_ms else None},
                "h2d_bytes_per_step": int(M * blocks[0].shape[1]),
                "d2h_bytes_per_step": int((8 + 24 * min(nh_e2e, cap) + 8 * w.P) / per_call),
                "ms_per_step": 1000 * dt / steps_e2e, "api": "tg_scan_host (C ABI, host buffers)",
