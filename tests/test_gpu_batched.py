@@ -333,3 +333,64 @@ def test_graph_of_small_panel_blocks_takes_the_fused_pass(tgctx, encoding):
     finally:
         tg.tg_destroy(ctx2)
         tg.tg_panel_free(panel)
+
+
+def test_batched_form_at_full_size(tgctx):
+    """The batched form at the benchmark's sizes: the 12 panels of uneven P (8,192 phenotypes in
+    all) over N = 23,000 samples with 2-bit calls (0.5% missing) and intercept + 9 covariates,
+    concatenated into one panel, and the planted 65,536-marker block cut into three ragged
+    blocks captured in one graph. Every planted pair is a hit, the best marker of each planted
+    phenotype is one of its planted markers, and every hit matches the oracle, recomputed for the
+    hits' markers and phenotypes at the scan tolerances."""
+    w = synth.WORKLOADS["n23000_m500000_12panels_p8192_2bit"]
+    pan = synth.make_panel(w, device="cuda", planted_blocks=1)
+    ctx2 = tg.tg_create(0)  # the graph holds its context's workspace
+    parts, o = [], 0
+    for k in synth.BATCHED_PANELS:
+        parts.append(tg.tg_prepare_panel(ctx2, pan["Yt"][o:o + k].contiguous(), w.N, k,
+                                         pan["cov_t"]))
+        o += k
+    try:
+        panel = tg.tg_panel_concat(ctx2, parts)
+    finally:
+        for p in parts:
+            tg.tg_panel_free(p)
+    try:
+        G = synth.make_block(w, 0, device="cuda")["G"]
+        cuts = [0, 1_537, 30_001, G.shape[0]]
+        blocks = [G[a:b].contiguous() for a, b in zip(cuts, cuts[1:])]
+        opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, 7.30103)
+        hits, n, best, out = _accum_outputs(w.P, cap=1 << 16)
+        g = tg.tg_scan_graph_create(ctx2, panel, blocks, w.N, tg.TG_ENC_2BIT, opts, out, cuts[:-1])
+        try:
+            tg.tg_scan_graph_launch(g)
+            assert tg.tg_status_poll(ctx2) == tg.TG_OK
+        finally:
+            tg.tg_scan_graph_free(g)
+        got = np.frombuffer(hits.cpu().numpy().tobytes(), dtype=HIT_DTYPE)[: int(n.item())]
+        assert len(got) > 0
+        pairs = {(int(h["marker"]), int(h["pheno"])) for h in got}
+        planted_of = {}
+        for m, p in pan["pairs"]:
+            assert (m, p) in pairs, (m, p)
+            planted_of.setdefault(p, set()).add(m)
+        bk = best.cpu().numpy().view(np.uint64)
+        for p, ms in planted_of.items():
+            assert int(0xFFFFFFFF - (int(bk[p]) & 0xFFFFFFFF)) in ms, p
+        markers = sorted({int(h["marker"]) for h in got})
+        phenos = sorted({int(h["pheno"]) for h in got})
+        Y = pan["Yt"][phenos].cpu().numpy().T.astype(np.float64)
+        ref = oracle.scan(G[markers].cpu().numpy(), "2bit",
+                          oracle.prepare_panel(Y, pan["cov_t"].cpu().numpy().T))
+        mi = {m: i for i, m in enumerate(markers)}
+        pi = {p: i for i, p in enumerate(phenos)}
+        for h in got:
+            j, c = mi[int(h["marker"])], pi[int(h["pheno"])]
+            mo = ref["mlog10p"][j, c]
+            assert abs(h["mlog10p"] - mo) <= max(1e-3, 1e-5 * mo), (h, mo)
+            assert abs(h["beta"] - ref["beta"][j, c]) <= 1e-4 * max(abs(ref["beta"][j, c]),
+                                                                    ref["se"][j, c])
+            assert abs(h["se"] - ref["se"][j, c]) <= 1e-4 * ref["se"][j, c]
+    finally:
+        tg.tg_panel_free(panel)
+        tg.tg_destroy(ctx2)
