@@ -345,6 +345,42 @@ def test_host_ring_wraps_with_many_small_blocks(tgctx, panels, encoding):
     assert np.allclose(ref["mlog10p"], runs[0][0]["mlog10p"], rtol=1e-5, atol=1e-4)
 
 
+def test_host_streamed_edge_cases(tgctx, panels):
+    """tg_scan_host at its edges, against one full call on the same context: no markers (no
+    hits, best keys untouched at zero), a hit buffer smaller than the hits (the true count comes
+    back, and the hits written are hits of the full call), no best-key buffer, and one block
+    larger than the whole matrix."""
+    w, pan, blk, _ = _case("2bit", M=3000, P=300)
+    panel = _panel(tgctx, panels, ("host", "2bit"), pan, w.N, w.P)
+    G_host = blk["G"].pin_memory()
+    opts = tg.tg_scan_opts(tg.TG_PREC_SPLIT_BF16, 0, THR)
+    cap = 1 << 14
+
+    def run(M, block, cap_, best=True):
+        hits_h = torch.zeros(cap_ * HIT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        best_h = torch.zeros(w.P, dtype=torch.int64).pin_memory() if best else None
+        nh = tg.tg_scan_host(tgctx, panel, G_host[:M], w.N, M, tg.TG_ENC_2BIT, block, opts,
+                             hits_h, best_h)
+        hh = np.frombuffer(hits_h.numpy().tobytes(), dtype=HIT_DTYPE)[:min(nh, cap_)]
+        return nh, hh, None if best_h is None else best_h.numpy().copy()
+
+    nh, hh, bb = run(w.M, 1024, cap)
+    assert 8 < nh <= cap
+    full = {(int(h["marker"]), int(h["pheno"])): h for h in hh}
+    n0, h0, b0 = run(0, 1024, cap)
+    assert n0 == 0 and len(h0) == 0 and not b0.any()
+    n3, h3, _ = run(w.M, 1024, 3)
+    assert n3 == nh and len(h3) == 3
+    for h in h3:
+        assert full[(int(h["marker"]), int(h["pheno"]))].tobytes() == h.tobytes()
+    n4, h4, b4 = run(w.M, 1024, cap, best=False)
+    assert n4 == nh and b4 is None
+    assert np.array_equal(np.sort(h4, order=["marker", "pheno"]), np.sort(hh, order=["marker", "pheno"]))
+    n5, h5, b5 = run(w.M, 10 * w.M, cap)
+    assert n5 == nh and np.array_equal(b5, bb)
+    assert set(full) == {(int(h["marker"]), int(h["pheno"])) for h in h5}
+
+
 @pytest.mark.parametrize("encoding,masked", [("2bit", False), ("u8", True)])
 @pytest.mark.parametrize("precision", ["fp32", "split"])
 def test_paper_mode_matches_oracle(tgctx, panels, encoding, masked, precision):
