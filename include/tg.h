@@ -278,6 +278,8 @@ tg_status tg_scan_block_static(const tg_panel* panel, const uint8_t* G, int64_t 
  *   blocking.
  *   G_host: host uint8 [M][ldg]; hits_host: host [hit_capacity]; n_hits: host, total hit
  *   count (may exceed hit_capacity, then TG_ERR_CAPACITY); best_host: host [P] or NULL.
+ *   Like tg_status_poll, the call reads and clears the context's device status word at the
+ *   end: TG_ERR_TIMEOUT if a bounded device wait ran out, TG_ERR_CAPACITY on overflow.
  * Only hit collection is supported here (opts->full_output must be 0). */
 tg_status tg_scan_host(tg_ctx* ctx, const tg_panel* panel, const uint8_t* G_host, int64_t ldg,
                        int32_t encoding, int64_t N, int64_t M, int64_t block_markers,

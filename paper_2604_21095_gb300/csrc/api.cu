@@ -1356,7 +1356,13 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
         copy_ms > 0.0f)
       c->ramp_ratio = (double)scan_ms / (double)copy_ms;
   }
-  if ((int64_t)nh > hit_capacity) return fail(TG_ERR_CAPACITY, "more hits than hit_capacity");
+  // synchronous, so the call reports what its kernels latched, and leaves the word clear
+  uint32_t word = 0;
+  TG_CUDA(cudaMemcpy(&word, c->status, sizeof(word), cudaMemcpyDeviceToHost));
+  TG_CUDA(cudaMemset(c->status, 0, sizeof(word)));
+  if (word & ST_TIMEOUT) return fail(TG_ERR_TIMEOUT, "a bounded device wait ran out");
+  if ((int64_t)nh > hit_capacity || (word & ST_CAPACITY))
+    return fail(TG_ERR_CAPACITY, "more hits than hit_capacity");
   return TG_OK;
 }
 

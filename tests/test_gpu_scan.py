@@ -348,8 +348,9 @@ def test_host_ring_wraps_with_many_small_blocks(tgctx, panels, encoding):
 def test_host_streamed_edge_cases(tgctx, panels):
     """tg_scan_host at its edges, against one full call on the same context: no markers (no
     hits, best keys untouched at zero), a hit buffer smaller than the hits (the true count comes
-    back, and the hits written are hits of the full call), no best-key buffer, and one block
-    larger than the whole matrix."""
+    back, the hits written are hits of the full call, and the overflow is reported by the call
+    itself, not left latched for a later status poll), no best-key buffer, and one block larger
+    than the whole matrix."""
     w, pan, blk, _ = _case("2bit", M=3000, P=300)
     panel = _panel(tgctx, panels, ("host", "2bit"), pan, w.N, w.P)
     G_host = blk["G"].pin_memory()
@@ -371,6 +372,7 @@ def test_host_streamed_edge_cases(tgctx, panels):
     assert n0 == 0 and len(h0) == 0 and not b0.any()
     n3, h3, _ = run(w.M, 1024, 3)
     assert n3 == nh and len(h3) == 3
+    assert tg.tg_status_poll(tgctx) == tg.TG_OK  # the call reported its overflow and cleared it
     for h in h3:
         assert full[(int(h["marker"]), int(h["pheno"]))].tobytes() == h.tobytes()
     n4, h4, b4 = run(w.M, 1024, cap, best=False)
