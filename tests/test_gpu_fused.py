@@ -222,3 +222,38 @@ def test_host_streamed_small_panel_mixes_the_paths(encoding):
     want, got = compare_hits(res, ref, 4.0)
     assert want > 0 and got > 0
     compare_best(res, ref)
+
+
+@pytest.mark.parametrize("encoding,N", [("u8", 70_000), ("2bit", 100_000)])
+def test_fused_joint_pass_at_a_long_sample_axis(encoding, N):
+    """The fused joint pass of a small panel (P = 40, 256-marker tiles) at biobank-like sample
+    counts: dosage rows beyond the one-pass limit (N > 66,051, where the sum of squared bytes
+    would overflow 32 bits) take a counting pass first, as 2-bit rows always do, and both run
+    hundreds of 64-sample stages per tile. Every hit and every statistic of sampled markers
+    against the oracle, recomputed for those markers; n_obs and the mean exact."""
+    M, P = 39_000, 40
+    w = synth.Workload(f"fusedlong_{encoding}_{N}", N=N, M=M, P=P, n_cov=4, encoding=encoding,
+                       missing=0.01 if encoding == "2bit" else 0.0, seed=61, block=M,
+                       causal_per_pheno=1)
+    pan = synth.make_panel(w)
+    G = synth.make_block(w, 0, device="cuda")["G"]
+    ctx = tg.tg_create(0)
+    panel = tg.tg_prepare_panel(ctx, pan["Yt"].cuda(), N, P, pan["cov_t"].cuda())
+    try:
+        res = run_scan(ctx, panel, G, N, P, encoding, "split", full=True, hit_mlog10p=5.0,
+                       hit_capacity=1 << 16)
+    finally:
+        tg.tg_panel_free(panel)
+        tg.tg_destroy(ctx)
+    assert res["status"] == tg.TG_OK and res["n_hits"] > 0
+    rng = np.random.default_rng(5)
+    sm = sorted({int(h["marker"]) for h in res["hits"]} | set(rng.choice(M, 48, replace=False).tolist()))
+    ref = oracle.scan(G[sm].cpu().numpy(), encoding, oracle_panel(pan["Yt"], pan["cov_t"]))
+    sub = {k: res[k][sm] for k in ("beta", "se", "t", "mlog10p", "nobs", "mean", "norm2")}
+    compare_full(sub, ref, label=f"fused joint N={N}/{encoding}")
+    mi = {m: i for i, m in enumerate(sm)}
+    for h in res["hits"]:
+        mo = ref["mlog10p"][mi[int(h["marker"])], int(h["pheno"])]
+        assert abs(h["mlog10p"] - mo) <= max(1e-3, 1e-5 * mo), (h, mo)
+    assert np.array_equal(sub["nobs"], ref["decode"]["n_obs"])
+    assert np.array_equal(sub["mean"], ref["decode"]["mean_units"])
