@@ -19,8 +19,9 @@
 //   warps 2, 3 (both CTAs)      with packed genotypes (OPA_2BIT / OPA_U8): decoders of the
 //                               local 128 A rows (tc_common.cuh); each warp arrives once on the
 //                               leader's full barrier after its stores
-// Accumulation is chunked exactly as in k_tc.cu (fresh accumulator every 1024 samples, FP32
-// totals in registers). Every wait is bounded; a timeout raises the abort flag in both CTAs.
+// Accumulation is chunked as in k_tc.cu (a fresh accumulator every 1024 samples, FP32 totals in
+// registers) when every statistic is written, every 2048 samples when only hits and best markers
+// are kept (chunk_kb). Every wait is bounded; a timeout raises the abort flag in both CTAs.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -151,6 +152,20 @@ __device__ __forceinline__ int next_tile(unsigned long long* ctr, int i, int cid
     __nanosleep(64);
   }
   return (int)t;
+}
+
+// Accumulation chunks (K blocks per fresh accumulator): kChunkKB (1,024 samples) when every
+// statistic is written (FULL), twice that when the launch keeps only hits and per-phenotype
+// best markers. There the products only decide which pairs pass the threshold and which marker
+// ranks first, and every reported statistic of a hit is recomputed in FP64 from the genotypes
+// (k_hit_stats); half the chunk drains take 3% off the launch, and the FP32 error of the
+// totals stays within the r tolerance (the best keys) and far inside the threshold band.
+__device__ __forceinline__ int chunk_kb(const EpiParams& ep) {
+  return ep.do_full ? kChunkKB : 2 * kChunkKB;
+}
+__device__ __forceinline__ int chunk_end_c(int kb0, int num_kb, int ckb) {
+  const int e = kb0 == 0 ? kFirstChunks * ckb : kb0 + ckb;
+  return e < num_kb ? e : num_kb;
 }
 
 // K direction of a tile: the tiles of odd waves stream K from the end. A wave reads about
@@ -285,6 +300,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
   const int n_mp = (n_mt + 1) / 2;
   const int num_tiles = n_mp * n_nt;
+  const int ckb = chunk_kb(ep);
   const int cid = (int)cluster_id(), ncl = (int)num_clusters();
   // a timeout in either CTA stops both
   auto wait = [&](uint32_t bar, uint32_t parity) {
@@ -389,7 +405,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       for (int i = 0; ok; ++i) {
         const int tile = take_tile(i, false);
         if (tile < 0 || tile >= num_tiles) break;
-        for (int kb0 = 0; kb0 < num_kb && ok; kb0 = chunk_end(kb0, num_kb), ++g) {
+        for (int kb0 = 0; kb0 < num_kb && ok; kb0 = chunk_end_c(kb0, num_kb, ckb), ++g) {
           const int acc = (int)(g & 1u);
           const uint32_t ph = (g >> 1) & 1u;
           if (!wait(cempty_bar(acc), ph ^ 1u)) {
@@ -398,7 +414,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem_base + (uint32_t)(acc * TBN);
-          const int kb1 = chunk_end(kb0, num_kb);
+          const int kb1 = chunk_end_c(kb0, num_kb, ckb);
           for (int kb = kb0; kb < kb1; kb += KS) {
             if (!wait(full_bar(stage), phase)) {
               ok = false;
@@ -477,7 +493,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
       float tot[128];
 #pragma unroll
       for (int e = 0; e < 128; ++e) tot[e] = 0.0f;
-      for (int kb0 = 0; kb0 < num_kb; kb0 = chunk_end(kb0, num_kb), ++g) {
+      for (int kb0 = 0; kb0 < num_kb; kb0 = chunk_end_c(kb0, num_kb, ckb), ++g) {
         const int acc = (int)(g & 1u);
         const uint32_t ph = (g >> 1) & 1u;
         if (!wait(cfull_bar(acc), ph)) {
