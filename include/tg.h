@@ -272,10 +272,10 @@ tg_status tg_scan_block_static(const tg_panel* panel, const uint8_t* G, int64_t 
  *   Blocking: when block_markers >= 2048 the first block has round_up(block_markers / 8, 256)
  *   rows and each next block f times as many (rounded up to 256), up to block_markers, so that
  *   only a short first copy is not hidden behind a scan. f = 2 on a context's first host scan;
- *   each call times its second block's copy and scan, and later calls use their ratio
- *   (scan / copy) clamped to [1, 2], so that a slow host link keeps the blocks small instead
- *   of leaving the scan waiting on a copy twice its own length. Results do not depend on the
- *   blocking.
+ *   each call times the copies and scans of its second to ninth blocks, and later calls use
+ *   the ratio of their sums (scan / copy) clamped to [1, 2], so that a slow host link keeps the
+ *   blocks small instead of leaving the scan waiting on a copy twice its own length. Results do
+ *   not depend on the blocking.
  *   G_host: host uint8 [M][ldg]; hits_host: host [hit_capacity]; n_hits: host, total hit
  *   count (may exceed hit_capacity, then TG_ERR_CAPACITY); best_host: host [P] or NULL.
  *   Like tg_status_poll, the call reads and clears the context's device status word at the

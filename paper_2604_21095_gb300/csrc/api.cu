@@ -756,12 +756,15 @@ tg_status tg_create(tg_ctx** out, int device) {
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking)) ||
       (e = dalloc(&c->status, 4)) || (e = dalloc(&c->scratch, 256)) ||
-      (e = cudaMemset(c->status, 0, 16)) ||
-      (e = cudaEventCreate(&c->ev_rate[0])) || (e = cudaEventCreate(&c->ev_rate[1])) ||
-      (e = cudaEventCreate(&c->ev_rate[2])) || (e = cudaEventCreate(&c->ev_rate[3]))) {
+      (e = cudaMemset(c->status, 0, 16))) {
     tg_destroy(c);
     return cuda_fail(e, "tg_create");
   }
+  for (int i = 0; i < 4 * kRateBlocks; ++i)
+    if ((e = cudaEventCreate(&c->ev_rate[i]))) {
+      tg_destroy(c);
+      return cuda_fail(e, "tg_create");
+    }
   if ((e = cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming))) {
     tg_destroy(c);
     return cuda_fail(e, "tg_create");
@@ -791,7 +794,7 @@ tg_status tg_destroy(tg_ctx* c) {
   if (c->ev_copied) cudaEventDestroy(c->ev_copied);
   for (int i = 0; i < kRingEvents; ++i)
     if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 4 * kRateBlocks; ++i)
     if (c->ev_rate[i]) cudaEventDestroy(c->ev_rate[i]);
   if (c->side) cudaStreamDestroy(c->side);
   delete c;
@@ -1277,11 +1280,12 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
   o.best = best_host ? c->dbest : nullptr;
   // Block sizes ramp up from about block_markers / 8 by a factor f per block, so that only a
   // short first copy runs before the first scan, and each copy hides behind the previous
-  // block's scan as long as it is at most f times shorter. f = 2 until a call has measured one
-  // block's scan against its copy; then f is that ratio within [1, 2]: with a copy about as
-  // slow as the scan, larger blocks would only leave the scan waiting for their copies.
+  // block's scan as long as it is at most f times shorter. f = 2 until a call has timed the
+  // scans of its second to ninth blocks against their copies; then f is the ratio of the sums
+  // within [1, 2]: with copies about as slow as the scans, larger blocks would only leave the
+  // scan waiting for their copies. (Several blocks, because one copy's rate varies.)
   const std::vector<int64_t> sizes = host_block_sizes(M, block_markers, host_ramp_factor(c));
-  bool timed = false;
+  int64_t timed = 0;  // blocks timed (1 .. kRateBlocks)
   // Blocks fill the ring front to back, each at the next 256-byte boundary, and wrap to its
   // start when the next one does not fit before the end. A block's copy waits (on the side
   // stream) for the scans of the earlier blocks whose bytes it overwrites; the scans finish in
@@ -1312,25 +1316,27 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
       q0 = (size_t)last + 1;
     }
     uint8_t* dst = c->stage + off;
-    const bool time_it = b == 1;  // the second block: its copy and scan, each on its own stream
-    if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[0], c->side));
+    // blocks 1 .. kRateBlocks: their copies and scans, each timed on its own stream
+    const bool time_it = b >= 1 && b <= kRateBlocks;
+    cudaEvent_t* er = c->ev_rate + 4 * (b - 1);
+    if (time_it) TG_CUDA(cudaEventRecord(er[0], c->side));
     {
       StageScope s(c, STAGE_H2D, c->side, 0);
       TG_CUDA(cudaMemcpyAsync(dst, G_host + m0 * ldg, len, cudaMemcpyHostToDevice, c->side));
     }
-    if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[1], c->side));
+    if (time_it) TG_CUDA(cudaEventRecord(er[1], c->side));
     // a wait takes the event's latest record at the time of the call: one event serves all
     TG_CUDA(cudaEventRecord(c->ev_copied, c->side));
     TG_CUDA(cudaStreamWaitEvent(st, c->ev_copied, 0));
-    if (time_it) TG_CUDA(cudaEventRecord(c->ev_rate[2], st));
+    if (time_it) TG_CUDA(cudaEventRecord(er[2], st));
     ScanArgs a{dst, ldg, encoding, N, rows, marker_offset + m0, nullptr, 0, *opts, o};
     tg_status s = check_scan_args(c, p, a);
     if (s != TG_OK) return s;
     s = scan_impl(c, p, a, st);
     if (s != TG_OK) return s;
     if (time_it) {
-      TG_CUDA(cudaEventRecord(c->ev_rate[3], st));
-      timed = true;
+      TG_CUDA(cudaEventRecord(er[3], st));
+      timed = b;
     }
     const int ev = (int)(b % kRingEvents);
     TG_CUDA(cudaEventRecord(c->ev_free[ev], st));
@@ -1349,12 +1355,17 @@ tg_status tg_scan_host(tg_ctx* c, const tg_panel* p, const uint8_t* G_host, int6
     TG_CUDA(cudaMemcpyAsync(best_host, c->dbest, sizeof(unsigned long long) * (size_t)p->P,
                             cudaMemcpyDeviceToHost, st));
   TG_CUDA(cudaStreamSynchronize(st));
-  if (timed) {  // both streams are past the timed block: the scan of every block has finished
-    float copy_ms = 0.0f, scan_ms = 0.0f;
-    if (cudaEventElapsedTime(&copy_ms, c->ev_rate[0], c->ev_rate[1]) == cudaSuccess &&
-        cudaEventElapsedTime(&scan_ms, c->ev_rate[2], c->ev_rate[3]) == cudaSuccess &&
-        copy_ms > 0.0f)
-      c->ramp_ratio = (double)scan_ms / (double)copy_ms;
+  if (timed > 0) {  // both streams are past the timed blocks: every scan has finished
+    double copy_ms = 0.0, scan_ms = 0.0;
+    bool ok = true;
+    for (int64_t i = 0; i < timed && ok; ++i) {
+      float cm = 0.0f, sm = 0.0f;
+      ok = cudaEventElapsedTime(&cm, c->ev_rate[4 * i], c->ev_rate[4 * i + 1]) == cudaSuccess &&
+           cudaEventElapsedTime(&sm, c->ev_rate[4 * i + 2], c->ev_rate[4 * i + 3]) == cudaSuccess;
+      copy_ms += cm;
+      scan_ms += sm;
+    }
+    if (ok && copy_ms > 0.0) c->ramp_ratio = scan_ms / copy_ms;
   }
   // synchronous, so the call reports what its kernels latched, and leaves the word clear
   uint32_t word = 0;

@@ -24,6 +24,9 @@ constexpr int QMAX = 64;     // intercept + at most 63 covariates
 constexpr int kMaxHostBufs = 4;  // block buffers of the host-streamed scan, at most
 // blocks of the host-streamed scan in flight at once (their scan-done events), at most
 constexpr int kRingEvents = 8 * kMaxHostBufs + 8;
+// blocks of a host-streamed scan (the second to the ninth) whose copies and scans are timed for
+// the next call's block growth
+constexpr int kRateBlocks = 8;
 constexpr int QCOLS = 64;    // projection columns (Q columns 1..q-1), zero padded
 constexpr int JCOLS = 256;   // widest joint operand: projection columns + panel in one tile
 constexpr int MT = 128;      // marker rows per tensor-core tile
@@ -245,7 +248,7 @@ struct tg_ctx {
   cudaEvent_t ev_free[tg::kRingEvents] = {};
   // timing of one block's copy (0, 1) and scan (2, 3) in a host-streamed scan, and their ratio
   // (scan time / copy time, 0 = not measured yet), which sets the next call's block ramp
-  cudaEvent_t ev_rate[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_rate[4 * tg::kRateBlocks] = {};
   double ramp_ratio = 0.0;
   double ramp_fixed = 0.0;  // > 0: a fixed growth factor set by the caller
   // profiling
